@@ -1,0 +1,145 @@
+/*
+ * gf_oracle.h -- plain FP64 CPU oracle for the Gabor-field rendering path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, the smoke check in
+ * __graft_entry__.py and the CPU-baseline leg of bench.py load this code.
+ * It shares no code, header, table or constant generator with the CUDA
+ * library: everything here is written from the paper's definitions
+ * (arXiv 2602.05081, "Gabor Fields") and is slow on purpose.
+ *
+ * Conventions (identical meaning to the CUDA library, independent code):
+ *   primitive i: mean mu, rotation R (unit quaternion w,x,y,z), scales
+ *   s = exp(log_scale), Sigma = R S S^T R^T (Sec. 4.2), carrier omega
+ *   (world rad/unit, or the whitened-frame vector k_W with
+ *   omega = R S^-1 k_W when omega_frame == 1, the tied form of Sec. 4.2 being
+ *   k_W = (w,w,w)), phase phi, amplitude A = weight (peak mode) or
+ *   weight / sqrt(8 pi^3 |Sigma|) (normalised mode, Eq. 6).
+ *   kernel: A exp(-q/2) cos(omega.(x-mu) + phi) 1[q <= k^2],
+ *   q = (x-mu)^T Sigma^-1 (x-mu)  (Eq. 6 with the k-sigma support of Sec. 3).
+ */
+#ifndef GF_ORACLE_H
+#define GF_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Philox stream tags: the fourth counter word is (sample<<12)|(bounce<<8)|tag. */
+#define OR_TAG_CAMERA 1u
+#define OR_TAG_MASK 2u
+#define OR_TAG_TRACK 3u
+#define OR_TAG_NEE 4u
+#define OR_TAG_NEE_MASK 5u
+#define OR_TAG_SCATTER 6u
+
+typedef struct {
+  int64_t n;
+  const float *mu, *quat, *log_scale, *omega, *phase, *weight; /* host arrays */
+  const uint8_t *band; /* nullable: derived from |omega| when NULL */
+  int weight_mode;     /* 0 peak amplitude, 1 normalised (Eq. 6) */
+  int omega_frame;     /* 0 world, 1 whitened frame (k_W) */
+  double k_sigma;      /* support radius in sigma units (3 in the paper) */
+} or_field_desc;
+
+typedef struct {
+  int freq_policy; /* 0 all, 1 cutoff, 2 uniform + control variate, 3 uniform */
+  int max_band;    /* bands above this are never used (cutoff / sampled modes) */
+  int cone_policy; /* 0 all, 1 importance w(a)=exp(-kbar^2 a^2/2), 2 uniform */
+} or_lod;
+
+typedef struct {
+  float eye[3], look_at[3], up[3];
+  float vfov_deg;
+  int width, height;
+} or_camera;
+
+typedef struct {
+  int integrator;   /* 0 tomography (mean over samples of exp(-tau)), 1 scattering */
+  int spp;
+  int max_bounces;  /* collisions per path; 1 = single scattering */
+  float albedo;
+  float light_dir[3]; /* direction towards the light */
+  float light_irradiance;
+} or_render_opts;
+
+typedef struct or_field or_field;
+
+or_field* or_field_create(const or_field_desc* desc);
+void or_field_free(or_field* f);
+int64_t or_field_size(const or_field* f);
+/* per-primitive labels (band, cone, cell) and per-cell mean |k_W| */
+void or_field_labels(const or_field* f, uint8_t* band, uint8_t* cone, uint8_t* cell);
+void or_field_cells(const or_field* f, uint64_t* occupied, double* kbar64);
+/* derived per-primitive quantities: Sigma^-1 (9, row major), omega (3), A */
+void or_field_prim(const or_field* f, int64_t i, double* sinv9, double* omega3, double* amp);
+
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* one LoD mask draw (Sec. 4.5, App. B tables): mask bits and per-cell weights */
+void or_sample_mask(const or_field* f, const or_lod* lod, const double v[3], uint64_t seed,
+                    uint32_t ray, uint32_t sample, uint32_t bounce, uint32_t tag,
+                    uint64_t* mask, double* w64);
+
+/* density kappa(x) (Eq. 1) under a mask (w64 == NULL: all cells weight 1) */
+double or_density(const or_field* f, const double x[3], uint64_t mask, const double* w64);
+
+/* chord of primitive i on ray o + t v (v normalised here), clipped to [tmin,tmax]:
+   returns 1 and lo/hi if non-empty */
+int or_chord(const or_field* f, int64_t i, const double o[3], const double v[3], double tmin,
+             double tmax, double* lo, double* hi);
+
+/* integral of primitive i over its chord on the ray (Eq. 2 with alpha folded in A) */
+double or_chord_integral(const or_field* f, int64_t i, const double o[3], const double v[3],
+                         double tmin, double tmax);
+
+/* tentative points of primitive i's chord (superposition sampler); returns the count
+   (may exceed cap: only the first cap are written) */
+int or_chord_points(const or_field* f, int64_t i, const double o[3], const double v[3], double tmin,
+                    double tmax, double weight, uint64_t seed, uint32_t ray, uint32_t word,
+                    double* t_out, double* uacc_out, int cap);
+
+/* majorant kappa_bar(t) on a ray under mask (per-segment majorant, see the .c file) */
+double or_majorant(const or_field* f, const double o[3], const double v[3], double tmin,
+                   double tmax, double t, uint64_t mask, const double* w64);
+
+/* transmittance of n rays (float inputs as the CUDA library receives them).
+   mode 0: deterministic quadrature of tau (averaged over spp mask draws), T = exp(-tau)
+   mode 1: ratio tracking, T = mean over spp of prod(1 - kappa/kappa_bar)      */
+void or_transmittance(const or_field* f, const or_lod* lod, const float* o, const float* d,
+                      const float* trange, int64_t n_rays, int mode, int spp, uint64_t seed,
+                      double* T, double* tau, int n_threads);
+
+/* delta tracking along one ray: returns 1 and the collision t, or 0 if the ray escapes */
+int or_delta_track(const or_field* f, const double o[3], const double v[3], double tmin,
+                   double tmax, uint64_t mask, const double* w64, uint64_t seed, uint32_t ray,
+                   uint32_t word, double* t_hit);
+
+/* render a crop [x0,x0+w) x [y0,y0+h) of the image (row-major, w*h doubles) */
+void or_render(const or_field* f, const or_lod* lod, const or_lod* lod_nee,
+               const or_camera* cam, const or_render_opts* ro, uint64_t seed, int x0, int y0,
+               int w, int h, double* out, int n_threads);
+
+/* per-pixel sample values of a crop: out has w*h*spp doubles (pixel-major) */
+void or_render_samples(const or_field* f, const or_lod* lod, const or_lod* lod_nee,
+                       const or_camera* cam, const or_render_opts* ro, uint64_t seed, int x0,
+                       int y0, int w, int h, double* out, int n_threads);
+
+/* camera ray of pixel (px,py), sample s */
+void or_camera_ray(const or_camera* cam, uint64_t seed, int px, int py, int s, double o[3],
+                   double v[3]);
+
+/* tomography loss and its gradient w.r.t. the 15 parameters of every primitive:
+   image I = mean_s exp(-tau_s) over jittered pinhole rays, L = sum (I - target)^2;
+   grad layout (SoA, like the inputs): mu[3N], quat[4N], log_scale[3N], omega[3N],
+   phase[N], weight[N].  Returns L. */
+double or_tomo_loss_grad(const or_field_desc* desc, const or_camera* cam, int spp, uint64_t seed,
+                         const float* target, double* grad, int n_threads);
+/* tomography image only (same estimator, deterministic quadrature, all cells) */
+void or_tomo_image(const or_field_desc* desc, const or_camera* cam, int spp, uint64_t seed,
+                   double* image, int n_threads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,525 @@
+"""Pins for the FP64 oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: closed forms
+(App. A.3, A.4, Sec. 4.4), library routines (scipy erf / Rotation / quad),
+brute force, invariants, Philox known-answer vectors, estimator expectations
+and finite differences.  CPU only.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import special, stats
+from scipy.spatial.transform import Rotation
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _single(mu, quat, s, omega, phase, weight, frame="world", mode="peak", k=3.0):
+    p = {"mu": np.array([mu], np.float32), "quat": np.array([quat], np.float32),
+         "log_scale": np.log(np.array([s], np.float64)).astype(np.float32),
+         "omega": np.array([omega], np.float32), "phase": np.array([phase], np.float32),
+         "weight": np.array([weight], np.float32)}
+    return oracle.Field(p, weight_mode=mode, omega_frame=frame, k_sigma=k), p
+
+
+def _geom(p, i=0):
+    """Sigma^-1, R, s from the float32 inputs, via scipy's Rotation (independent)."""
+    q = p["quat"][i].astype(np.float64)
+    R = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+    s = np.exp(p["log_scale"][i].astype(np.float64))
+    return R @ np.diag(1.0 / s ** 2) @ R.T, R, s
+
+
+def _rand_prim(rng, omega_scale=20.0):
+    mu = rng.random(3)
+    q = rng.standard_normal(4)
+    s = np.exp(rng.uniform(np.log(0.02), np.log(0.1), 3))
+    om = rng.standard_normal(3) * omega_scale
+    return mu, q, s, om, rng.uniform(0, 2 * np.pi), rng.uniform(0.5, 2.0)
+
+
+def _ray_near(rng, mu, spread):
+    v = rng.standard_normal(3)
+    v /= np.linalg.norm(v)
+    o = np.asarray(mu, np.float64) + spread * rng.standard_normal(3) - 1.0 * v
+    return o, v
+
+
+# --------------------------------------------------------------------------- Philox
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        vals = [int(x, 16) for x in r]
+        out = oracle.philox4x32_10(vals[0:4], vals[4:6])
+        assert [int(x) for x in out] == vals[6:10]
+
+
+# --------------------------------------------------------------------------- closed forms
+@pytest.mark.parametrize("mode", ["peak", "normalized"])
+def test_full_line_closed_form_appendix_a4(mode):
+    """Oracle quadrature over the whole line equals the boxed infinite-domain
+    integral of App. A.4 (a, beta, gamma, B, delta of App. A.1), phase added."""
+    rng = np.random.default_rng(1)
+    for trial in range(16):
+        mu, q, s, om, ph, w = _rand_prim(rng)
+        f, p = _single(mu, q, s, om, ph, w, mode=mode, k=40.0)
+        Sinv, R, s64 = _geom(p)
+        o, v = _ray_near(rng, p["mu"][0], 0.05)
+        d = o - p["mu"][0].astype(np.float64)
+        omw = p["omega"][0].astype(np.float64)
+        a = v @ Sinv @ v; beta = v @ Sinv @ d; gamma = d @ Sinv @ d
+        B = omw @ v; delta = omw @ d + float(p["phase"][0])
+        amp = float(p["weight"][0])
+        if mode == "normalized":
+            amp /= math.sqrt(8 * math.pi ** 3 * np.linalg.det(np.linalg.inv(Sinv)))
+        exact = amp * math.sqrt(2 * math.pi / a) * math.exp(-0.5 * (gamma - beta ** 2 / a)) \
+            * math.exp(-B ** 2 / (2 * a)) * math.cos(delta - beta * B / a)
+        got = f.chord_integral(0, o, v, -np.inf, np.inf)
+        scale = amp * math.sqrt(2 * math.pi / a) * math.exp(-0.5 * (gamma - beta ** 2 / a))
+        assert abs(got - exact) <= 1e-10 * scale + 1e-300, (trial, got, exact)
+
+
+def test_whitened_form_sec44_matches_unwhitened():
+    """Sec. 4.4 whitened form with W = S^-1 R^T and k_W = S R^T omega equals the
+    oracle; the literal W = R^T S^-1, k_W = W omega does not (reading of Eq. 11)."""
+    rng = np.random.default_rng(2)
+    literal_bad = 0
+    for trial in range(12):
+        mu, q, s, om, ph, w = _rand_prim(rng, omega_scale=10.0)
+        f, p = _single(mu, q, s, om, ph, w, mode="normalized", k=40.0)
+        Sinv, R, s64 = _geom(p)
+        o, v = _ray_near(rng, p["mu"][0], 0.03)
+        m = p["mu"][0].astype(np.float64)
+        omw = p["omega"][0].astype(np.float64)
+        phase = float(p["phase"][0])
+        alpha = float(p["weight"][0])
+        det_sigma = np.prod(s64) ** 2
+
+        def whitened(W, kW):
+            pW = W @ (o - m); Wv = W @ v; nWv = np.linalg.norm(Wv); vW = Wv / nWv
+            b = pW @ vW; c = pW @ pW; Om = kW @ vW; dd = kW @ pW + phase
+            K = 1.0 / (2 * math.pi * math.sqrt(det_sigma) * nWv)
+            return alpha * K * math.exp(-0.5 * (c - b * b + Om * Om)) * math.cos(dd - Om * b)
+
+        W = np.diag(1 / s64) @ R.T
+        got = f.chord_integral(0, o, v, -np.inf, np.inf)
+        ref = whitened(W, np.diag(s64) @ R.T @ omw)
+        env = alpha / math.sqrt(8 * math.pi ** 3 * det_sigma) * math.sqrt(2 * math.pi / (v @ Sinv @ v))
+        assert abs(got - ref) <= 1e-10 * env
+        Wl = R.T @ np.diag(1 / s64)
+        lit = whitened(Wl, Wl @ omw)
+        if abs(lit - got) > 1e-6 * env:
+            literal_bad += 1
+    assert literal_bad >= 10
+
+
+def _clip_chord(Sinv, m, o, v, k, tmin, tmax):
+    d = o - m
+    a = v @ Sinv @ v; beta = v @ Sinv @ d
+    ts = -beta / a
+    pp = d + ts * v
+    r2 = pp @ Sinv @ pp
+    if r2 >= k * k:
+        return None
+    hw = math.sqrt((k * k - r2) / a)
+    lo, hi = max(ts - hw, tmin), min(ts + hw, tmax)
+    return (lo, hi, a, beta, d @ Sinv @ d) if lo < hi else None
+
+
+def test_zero_frequency_erf_form():
+    """omega = 0, k = 3: the truncated chord integral equals the real-erf closed form."""
+    rng = np.random.default_rng(3)
+    for trial in range(24):
+        mu, q, s, _, _, w = _rand_prim(rng)
+        f, p = _single(mu, q, s, (0, 0, 0), 0.0, w, k=3.0)
+        Sinv, _, _ = _geom(p)
+        m = p["mu"][0].astype(np.float64)
+        o, v = _ray_near(rng, m, 0.04)
+        tmin, tmax = (0.0, np.inf) if trial % 2 == 0 else (0.9, 1.02)
+        cc = _clip_chord(Sinv, m, o, v, 3.0, tmin, tmax)
+        has, lo, hi = f.chord(0, o, v, tmin, tmax)
+        assert has == (cc is not None)
+        if cc is None:
+            continue
+        lo_r, hi_r, a, beta, gamma = cc
+        assert abs(lo - lo_r) < 1e-12 and abs(hi - hi_r) < 1e-12
+        amp = float(p["weight"][0])
+        sa = math.sqrt(a / 2)
+        exact = amp * math.sqrt(math.pi / (2 * a)) * math.exp(-0.5 * (gamma - beta ** 2 / a)) * (
+            math.erf(sa * (hi_r + beta / a)) - math.erf(sa * (lo_r + beta / a)))
+        got = f.chord_integral(0, o, v, tmin, tmax)
+        assert abs(got - exact) <= 1e-12 * amp * math.sqrt(2 * math.pi / a)
+
+
+def test_finite_segment_complex_erf_appendix_a3():
+    """omega != 0, k = 3: the truncated chord integral equals the finite-domain
+    complex-erf closed form of App. A.3 (scipy's complex erf)."""
+    rng = np.random.default_rng(4)
+    checked = 0
+    for trial in range(40):
+        mu, q, s, om, ph, w = _rand_prim(rng, omega_scale=15.0)
+        f, p = _single(mu, q, s, om, ph, w, k=3.0)
+        Sinv, _, _ = _geom(p)
+        m = p["mu"][0].astype(np.float64)
+        o, v = _ray_near(rng, m, 0.04)
+        cc = _clip_chord(Sinv, m, o, v, 3.0, 0.0, np.inf)
+        if cc is None:
+            continue
+        lo, hi, a, beta, gamma = cc
+        omw = p["omega"][0].astype(np.float64)
+        B = omw @ v
+        delta = omw @ (o - m) + float(p["phase"][0])
+        if abs(B) / math.sqrt(a) > 4.0:
+            continue
+        amp = float(p["weight"][0])
+        al = math.sqrt(a / 2)
+        zeta = (-beta + 1j * B) / math.sqrt(2 * a)
+        r2 = gamma - beta ** 2 / a
+        pref = amp * math.sqrt(math.pi / (2 * a)) * math.exp(-0.5 * r2 - B * B / (2 * a))
+        val = pref * (np.exp(1j * (delta - beta * B / a)) *
+                      (special.erf(al * hi - zeta) - special.erf(al * lo - zeta))).real
+        got = f.chord_integral(0, o, v, 0.0, np.inf)
+        assert abs(got - val) <= 1e-11 * amp * math.sqrt(2 * math.pi / a), (trial, got, val)
+        checked += 1
+    assert checked >= 10
+
+
+def test_chord_matches_brute_force_sampling():
+    """Chord endpoints equal the extent of {t : q(t) <= k^2} sampled on a fine grid."""
+    rng = np.random.default_rng(5)
+    for trial in range(20):
+        mu, q, s, om, ph, w = _rand_prim(rng)
+        f, p = _single(mu, q, s, om, ph, w, k=3.0)
+        Sinv, _, _ = _geom(p)
+        m = p["mu"][0].astype(np.float64)
+        o, v = _ray_near(rng, m, 0.05)
+        ts = np.linspace(0.0, 2.0, 400001)
+        y = o[None, :] + ts[:, None] * v[None, :] - m[None, :]
+        qq = np.einsum("ni,ij,nj->n", y, Sinv, y)
+        inside = np.nonzero(qq <= 9.0)[0]
+        has, lo, hi = f.chord(0, o, v, 0.0, 2.0)
+        assert has == (inside.size > 0)
+        if has:
+            dt = ts[1] - ts[0]
+            assert abs(ts[inside[0]] - lo) <= dt and abs(ts[inside[-1]] - hi) <= dt
+
+
+# --------------------------------------------------------------------------- invariants
+def _small_octave(n=340, octaves=4, seed=7):
+    p = synth.octave_field(n, octaves, seed=seed)
+    return oracle.Field(p, weight_mode="peak", omega_frame="local"), p
+
+
+def test_band_densities_sum_to_full_density():
+    f, p = _small_octave()
+    occ, _ = f.cells()
+    _, _, cell = f.labels()
+    rng = np.random.default_rng(8)
+    for _ in range(30):
+        x = rng.random(3)
+        full = f.density(x)
+        acc = 0.0
+        for b in range(8):
+            bits = 0
+            for c in range(64):
+                if (occ >> c) & 1 and ((c == 0 and b == 0) or (c > 0 and (c - 1) // 8 + 1 == b)):
+                    bits |= 1 << c
+            if bits:
+                acc += f.density(x, mask=bits)
+        assert abs(acc - full) <= 1e-12 * (1 + abs(full))
+
+
+def test_tau_is_sum_of_per_primitive_integrals_and_cutoffs_nest():
+    """Eq. 3: tau = sum_i tau_i; band cutoffs add whole bands."""
+    f, p = _small_octave()
+    o, d, tr = synth.random_rays(16, seed=3)
+    T_all, tau_all = f.transmittance(o, d, tr, mode="det")
+    band = p["band"]
+    per = np.zeros((16, f.n))
+    for r in range(16):
+        for i in range(f.n):
+            per[r, i] = f.chord_integral(i, o[r], d[r], tr[r, 0], tr[r, 1])
+    assert np.allclose(tau_all, per.sum(1), rtol=0, atol=1e-11)
+    assert np.allclose(T_all, np.exp(-tau_all), rtol=1e-14, atol=0)
+    prev = np.zeros(16)
+    for b in range(4):
+        _, tau_b = f.transmittance(o, d, tr, mode="det", lod=oracle.Lod(1, b, 0))
+        assert np.allclose(tau_b - prev, per[:, band == b].sum(1), atol=1e-11)
+        prev = tau_b
+    _, tau_cv = f.transmittance(o, d, tr, mode="det", lod=oracle.Lod(1, 7, 0))
+    assert np.allclose(tau_cv, tau_all, atol=1e-12)
+
+
+def test_phase_shift_by_pi_inverts_transmittance():
+    rng = np.random.default_rng(9)
+    for _ in range(8):
+        mu, q, s, om, ph, w = _rand_prim(rng)
+        f1, p1 = _single(mu, q, s, om, ph, w)
+        f2, p2 = _single(mu, q, s, om, ph + math.pi, w)
+        o, v = _ray_near(rng, p1["mu"][0], 0.03)
+        T1, _ = f1.transmittance(o[None], v[None], None, mode="det")
+        T2, _ = f2.transmittance(o[None], v[None], None, mode="det")
+        # phases are float32 inputs: allow the rounding of ph + pi
+        assert abs(T1[0] * T2[0] - 1.0) < 1e-5
+
+
+def test_rotation_invariance():
+    """Rotating the field (means, orientations, world carriers) and the rays
+    together leaves every transmittance unchanged."""
+    p = synth.absorption_field(64, seed=11)
+    f = oracle.Field(p)
+    o, d, tr = synth.random_rays(24, seed=5)
+    T0, tau0 = f.transmittance(o, d, tr, mode="det")
+    Q = Rotation.from_rotvec([0.3, -1.1, 0.7])
+    c = np.array([0.5, 0.5, 0.5])
+    p2 = dict(p)
+    p2["mu"] = (Q.apply(p["mu"].astype(np.float64) - c) + c).astype(np.float32)
+    qi = p["quat"].astype(np.float64)
+    rq = Q * Rotation.from_quat(np.stack([qi[:, 1], qi[:, 2], qi[:, 3], qi[:, 0]], 1))
+    xyzw = rq.as_quat()
+    p2["quat"] = np.stack([xyzw[:, 3], xyzw[:, 0], xyzw[:, 1], xyzw[:, 2]], 1).astype(np.float32)
+    p2["omega"] = Q.apply(p["omega"].astype(np.float64)).astype(np.float32)
+    f2 = oracle.Field(p2)
+    o2 = (Q.apply(o.astype(np.float64) - c) + c).astype(np.float32)
+    d2 = Q.apply(d.astype(np.float64)).astype(np.float32)
+    T1, tau1 = f2.transmittance(o2, d2, tr, mode="det")
+    # float32 rounding of the rotated inputs perturbs positions by ~1e-7
+    assert np.max(np.abs(tau1 - tau0)) < 2e-4
+    assert np.max(np.abs(tau0)) > 0.05
+
+
+# --------------------------------------------------------------------------- mask sampler
+def test_mask_weights_are_reciprocal_probabilities():
+    """Sum over outcomes of p * w * 1[cell selected] = 1 (App. B tables), checked
+    by Monte Carlo frequencies against the stated probabilities."""
+    f, p = _small_octave(n=5460, octaves=6)
+    occ, kbar = f.cells()
+    lod = oracle.Lod(2, 7, 1)  # uniform + control variate, importance-sampled cones
+    v = np.array([0.3, -0.5, 0.81]); v /= np.linalg.norm(v)
+    n = 40000
+    acc = np.zeros(64)
+    picks = np.zeros(64)
+    for r in range(n):
+        m, w = f.sample_mask(lod, v, seed=3, ray=r, sample=0, bounce=0, tag=oracle.TAG_MASK)
+        bits = np.array([(m >> c) & 1 for c in range(64)], bool)
+        acc += np.where(bits, w, 0.0)
+        picks += bits
+    cells = [c for c in range(64) if (occ >> c) & 1]
+    assert acc[0] / n == pytest.approx(1.0, abs=1e-12)  # Gaussian band always, weight 1
+    # expected frequency of each Gabor cell: 1/G * w_c / W_band
+    axes = []
+    for k in range(8):
+        z = 1 - (k + 0.5) / 8; r_ = math.sqrt(1 - z * z); ph = k * math.pi * (3 - math.sqrt(5))
+        axes.append((r_ * math.cos(ph), r_ * math.sin(ph), z))
+    G = 5
+    for c in cells:
+        if c == 0:
+            continue
+        b = (c - 1) // 8 + 1
+        band_cells = [cc for cc in cells if cc > 0 and (cc - 1) // 8 + 1 == b]
+        wts = {cc: math.exp(-0.5 * kbar[cc] ** 2 * abs(np.dot(v, axes[(cc - 1) % 8])) ** 2)
+               for cc in band_cells}
+        pexp = wts[c] / sum(wts.values()) / G
+        sd = math.sqrt(pexp * (1 - pexp) / n)
+        assert abs(picks[c] / n - pexp) < 5 * sd + 1e-9
+        est = acc[c] / n
+        sd_w = (1.0 / pexp) * sd
+        assert abs(est - 1.0) < 5 * sd_w
+
+
+# --------------------------------------------------------------------------- estimators
+def _three_gabors():
+    p = {"mu": np.array([[0.45, 0.5, 0.5], [0.55, 0.52, 0.45], [0.5, 0.47, 0.6]], np.float32),
+         "quat": np.array([[1, 0.2, 0.1, 0], [0.9, 0, 0.3, 0.2], [0.7, 0.1, 0, 0.6]], np.float32),
+         "log_scale": np.log(np.array([[0.08, 0.06, 0.1], [0.05, 0.09, 0.07], [0.1, 0.1, 0.06]])).astype(np.float32),
+         "omega": np.array([[0, 0, 0], [20, -10, 5], [-8, 12, 30]], np.float32),
+         "phase": np.array([0.0, 1.0, 4.0], np.float32),
+         "weight": np.array([6.0, 3.0, 2.5], np.float32)}
+    return p
+
+
+def test_ratio_tracking_is_unbiased_for_transmittance():
+    p = _three_gabors()
+    f = oracle.Field(p)
+    o = np.array([[0.5, 0.5, -0.5], [0.47, 0.52, -0.5], [0.55, 0.45, -0.5]], np.float32)
+    d = np.tile(np.array([0, 0, 1], np.float32), (3, 1))
+    T_det, _ = f.transmittance(o, d, None, mode="det")
+    blocks = np.array([f.transmittance(o, d, None, mode="rt", spp=4000, seed=s)[0]
+                       for s in range(20)])
+    mean = blocks.mean(0)
+    se = blocks.std(0, ddof=1) / math.sqrt(blocks.shape[0])
+    assert np.all(np.abs(mean - T_det) < 4.5 * se + 1e-4), (mean, T_det, se)
+    assert np.all(T_det < 0.95)
+
+
+def test_majorant_bounds_density_and_drives_points():
+    """kappa_bar >= |kappa| on the ray, and the tentative points of one chord form a
+    Poisson process with intensity equal to that chord's majorant."""
+    p = _three_gabors()
+    f = oracle.Field(p)
+    o = np.array([0.5, 0.5, -0.5]); v = np.array([0.0, 0.0, 1.0])
+    ts = np.linspace(0.7, 1.3, 3001)
+    for t in ts:
+        x = o + t * v
+        assert f.majorant(o, v, t) >= abs(f.density(x)) - 1e-12
+    # one chord: counts in bins vs integral of its own majorant
+    fi = oracle.Field({k: p[k][1:2] for k in ("mu", "quat", "log_scale", "omega", "phase", "weight")})
+    has, lo, hi = fi.chord(0, o, v)
+    assert has
+    edges = np.linspace(lo, hi, 9)
+    grid = np.linspace(lo, hi, 40001)
+    maj = np.array([fi.majorant(o, v, t) for t in grid])
+    expect = np.array([np.trapezoid(maj[(grid >= a) & (grid <= b)], grid[(grid >= a) & (grid <= b)])
+                       for a, b in zip(edges[:-1], edges[1:])])
+    counts = np.zeros(8)
+    nrep = 6000
+    for w in range(nrep):
+        t, _ = fi.chord_points(0, o, v, seed=1, ray=0, word=w)
+        counts += np.histogram(t, edges)[0]
+    exp_counts = expect * nrep
+    chi2 = np.sum((counts - exp_counts) ** 2 / exp_counts)
+    assert chi2 < stats.chi2.ppf(0.9999, 8)
+
+
+def _gauss_only():
+    p = _three_gabors()
+    p = dict(p)
+    p["omega"] = np.zeros((3, 3), np.float32)
+    p["phase"] = np.zeros(3, np.float32)
+    return p
+
+
+@pytest.mark.parametrize("kind", ["gauss", "gabor"])
+def test_delta_tracking_collision_distribution(kind):
+    """Collision CDF is 1 - exp(-int_0^t max(kappa,0)) (Woodcock tracking of the
+    clamped extinction)."""
+    p = _gauss_only() if kind == "gauss" else _three_gabors()
+    f = oracle.Field(p)
+    o = np.array([0.5, 0.5, -0.5]); v = np.array([0.0, 0.0, 1.0])
+    grid = np.linspace(0.0, 2.0, 40001)
+    kap = np.array([f.density(o + t * v) for t in grid])
+    cum = np.concatenate([[0.0], np.cumsum(0.5 * (np.maximum(kap[1:], 0) + np.maximum(kap[:-1], 0)) * np.diff(grid))])
+    if kind == "gauss":
+        T_det, tau = f.transmittance(o[None].astype(np.float32), v[None].astype(np.float32), None)
+        # the trapezoid rule is first order at the k-sigma cut-offs
+        assert abs(cum[-1] - tau[0]) < 2e-5
+    edges = np.linspace(0.6, 1.4, 17)
+    Fe = 1 - np.exp(-np.interp(edges, grid, cum))
+    probs = np.concatenate([[Fe[0]], np.diff(Fe), [1 - Fe[-1]]])
+    n = 6000
+    hits = []
+    for r in range(n):
+        h, t = f.delta_track(o, v, seed=2, ray=r, word=oracle.stream_word(0, 0, oracle.TAG_TRACK))
+        hits.append(t if h else np.inf)
+    hits = np.array(hits)
+    counts = np.concatenate([[np.sum(hits < edges[0])], np.histogram(hits, edges)[0],
+                             [np.sum(hits >= edges[-1])]])
+    keep = probs * n > 5
+    chi2 = np.sum((counts[keep] - n * probs[keep]) ** 2 / (n * probs[keep]))
+    assert chi2 < stats.chi2.ppf(0.9999, keep.sum() - 1)
+
+
+def test_masked_optical_depth_is_unbiased_and_jensen_bias():
+    """E[tau_hat] = tau under uniform + control variate masking with importance-
+    sampled cones (Sec. 4.5, per segment unbiased); E[exp(-tau_hat)] equals the
+    enumeration over masks and exceeds exp(-tau) (Sec. 4.5.3)."""
+    f, p = _small_octave(n=1365, octaves=5, seed=12)
+    o, d, tr = synth.random_rays(6, seed=21)
+    _, tau = f.transmittance(o, d, tr, mode="det")
+    lod = oracle.Lod(2, 7, 1)
+    blocks = np.array([f.transmittance(o, d, tr, mode="det", spp=200, seed=s, lod=lod)[1]
+                       for s in range(16)])
+    mean = blocks.mean(0)
+    se = blocks.std(0, ddof=1) / 4.0
+    assert np.all(np.abs(mean - tau) < 4.5 * se + 1e-9), (mean, tau, se)
+    # Jensen with whole-band masking (cones all): enumerate the G equally likely masks
+    lod_b = oracle.Lod(2, 7, 0)
+    band_tau = []
+    prev = np.zeros(6)
+    for b in range(5):
+        _, tb = f.transmittance(o, d, tr, mode="det", lod=oracle.Lod(1, b, 0))
+        band_tau.append(tb - prev)
+        prev = tb
+    G = 4
+    enum = np.mean([np.exp(-(band_tau[0] + G * band_tau[b])) for b in range(1, 5)], axis=0)
+    samples = np.array([np.exp(-f.transmittance(o, d, tr, mode="det", spp=1, seed=s, lod=lod_b)[1])
+                        for s in range(3000)])
+    se2 = samples.std(0, ddof=1) / math.sqrt(3000)
+    assert np.all(np.abs(samples.mean(0) - enum) < 4.5 * se2 + 1e-12)
+    assert np.all(enum >= np.exp(-tau) - 1e-15)
+    var = np.mean([(band_tau[0] + G * band_tau[b] - tau) ** 2 for b in range(1, 5)], axis=0)
+    small = var < 0.05
+    if small.any():
+        approx = 0.5 * var * np.exp(-tau)
+        assert np.all(np.abs((enum - np.exp(-tau))[small] - approx[small]) <= 0.5 * approx[small] + 1e-6)
+
+
+def test_single_scatter_mean_matches_nested_quadrature():
+    """Mean single-scattering radiance of one pixel equals
+    albedo E/(4 pi) int kappa(t) exp(-tau(0,t)) T_light(x(t)) dt (Gaussian field)."""
+    p = _gauss_only()
+    f = oracle.Field(p)
+    cam = oracle.camera((0.5, 0.5, -1.0), (0.5, 0.5, 0.5), (0, 1, 0), 45.0, 64, 64)
+    ro = oracle.render_opts("scatter", spp=20000, max_bounces=1, albedo=0.8)
+    px, py = 32, 31
+    smp = f.render(cam, ro, seed=5, crop=(px, py, 1, 1), samples=True).ravel()
+    # reference: nested quadrature with per-sample jittered rays averaged
+    ref = []
+    rng_idx = range(0, 20000, 500)
+    light = np.array([1.0, 1.0, -1.0]) / math.sqrt(3.0)
+    for s in rng_idx:
+        o, v = oracle.camera_ray(cam, 5, px, py, s)
+        grid = np.linspace(0.9, 2.1, 1201)
+        kap = np.array([f.density(o + t * v) for t in grid])
+        cum = np.concatenate([[0.0], np.cumsum(0.5 * (kap[1:] + kap[:-1]) * np.diff(grid))])
+        xs = o[None] + grid[:, None] * v[None]
+        Tl, _ = f.transmittance(xs.astype(np.float32), np.tile(light, (len(grid), 1)).astype(np.float32),
+                                None, mode="det")
+        ref.append(0.8 / (4 * math.pi) * np.trapezoid(kap * np.exp(-cum) * Tl, grid))
+    ref_mean = float(np.mean(ref))
+    # the jitter varies the reference slightly: compare the sample mean with the
+    # mean of the per-jitter references, within MC error plus the jitter spread
+    se = smp.std(ddof=1) / math.sqrt(smp.size) + np.std(ref) / math.sqrt(len(ref))
+    assert abs(smp.mean() - ref_mean) < 4.5 * se
+    assert ref_mean > 1e-3
+
+
+# --------------------------------------------------------------------------- gradient
+def test_tomography_gradient_matches_central_differences():
+    p = _three_gabors()
+    p["phase"] = np.array([0.3, 1.0, 4.0], np.float32)
+    cam = oracle.camera((0.5, 0.5, -1.0), (0.5, 0.5, 0.5), (0, 1, 0), 12.0, 6, 6)
+    spp = 2
+    f = oracle.Field(p)
+    target = f.tomo_image(cam, spp, 3) * 0.9 + 0.02
+    L, g = f.tomo_loss_grad(cam, spp, 3, target)
+    N = 3
+    offs = {"mu": 0, "quat": 3 * N, "log_scale": 7 * N, "omega": 10 * N, "phase": 13 * N,
+            "weight": 14 * N}
+    rng = np.random.default_rng(0)
+    checked = 0
+    for key, off in offs.items():
+        arr = p[key].reshape(-1)
+        for j in range(arr.size):
+            base = float(arr[j])
+            # small steps: finite differences across a tangent chord are biased
+            h = 1e-5 * max(abs(base), 0.5)
+            pp = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in p.items()}
+            pm = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in p.items()}
+            pp[key].reshape(-1)[j] = np.float32(base + h)
+            pm[key].reshape(-1)[j] = np.float32(base - h)
+            step = float(pp[key].reshape(-1)[j]) - float(pm[key].reshape(-1)[j])
+            Lp, _ = oracle.Field(pp).tomo_loss_grad(cam, spp, 3, target)
+            Lm, _ = oracle.Field(pm).tomo_loss_grad(cam, spp, 3, target)
+            fd = (Lp - Lm) / step
+            an = g[off + j]
+            assert abs(fd - an) <= 2e-3 * abs(an) + 1e-5 * np.max(np.abs(g)), (key, j, fd, an)
+            checked += 1
+    assert checked == 45
