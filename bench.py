@@ -1,0 +1,315 @@
+#!/usr/bin/env python
+"""Benchmark: single-scattering renders of a 100k-primitive Gabor field.
+
+Workload (one step): a 4-octave synthetic field of 100,000 Gabor primitives in
+the unit cube (the octave generator of synth.octave_field, seed 0), a 512x512
+pinhole camera, 16 samples per pixel, one directional light, isotropic phase,
+albedo 0.8, single scattering, rendered at the 4 LoD band cutoffs (all bands,
+<= 1/2, <= 1/4 and <= 1/8 of the highest band): 4 renders per step.
+
+Prints one JSON line: Mrays/s (traced path segments: camera rays + NEE rays),
+Gabor evaluations/s, render p50/p99 ms, the roofline of the render kernel, an
+end-to-end figure through the C ABI with host buffers, the FP64 oracle timed
+on the host cores, and the SM clocks sampled during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+N_PRIMS = 100_000
+OCTAVES = 4
+RES = 512
+SPP = 16
+CUTOFFS = (3, 2, 1, 0)
+# smaller launches of the same kernel for profiling captures (--res / --spp)
+SEED = 1
+METRIC = "Mrays/s and Gabor evals/s at fixed RMSE vs FP64 oracle; render p50/p99 ms"
+WORKLOAD = ("single scattering, 100k-primitive 4-octave Gabor field, 512x512, 16 spp, "
+            "4 LoD band cutoffs (all, <=1/2, <=1/4, <=1/8)")
+MUFU_PER_SM_CLK = 16  # SFU results per SM per clock
+MUFU_PER_EVAL = 2     # ex2 + cos per Gabor evaluation
+
+
+def config(extra=None):
+    c = {"workload": WORKLOAD, "primitives": N_PRIMS, "octaves": OCTAVES, "image": [RES, RES],
+         "spp": SPP, "lod_cutoffs": list(CUTOFFS), "integrator": "single scattering (delta + ratio tracking)",
+         "storage": "fp32 records", "l2": "flushed between timed steps (256 MiB write)",
+         "parallelism": "replicas"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(prefix="gf_clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--id=%d" % gpu_index, "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(seconds, cutoffs=CUTOFFS, crop=4):
+    """Time the FP64 oracle on crops of the same workload for ~`seconds`."""
+    import oracle
+    p = synth.octave_field(N_PRIMS, OCTAVES, seed=0)
+    f = oracle.Field(p, omega_frame="local")
+    c = synth.DEFAULT_CAMERA
+    cam = oracle.camera(c["eye"], c["look_at"], c["up"], c["vfov_deg"], RES, RES)
+    ro = oracle.render_opts("scatter", SPP, 1, 0.8, synth.LIGHT_DIR, 1.0)
+    rng = np.random.default_rng(0)
+    oracle.rays_traced(reset=True)
+    t0 = time.perf_counter()
+    crops = 0
+    while True:
+        for cut in cutoffs:
+            lod = oracle.Lod(1, cut, 0)
+            x, y = (int(v) for v in rng.integers(0, RES - crop, 2))
+            f.render(cam, ro, SEED, lod=lod, lod_nee=lod, crop=(x, y, crop, crop))
+            crops += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    rays = oracle.rays_traced(reset=True)
+    return {"value": rays / dt / 1e6, "unit": "Mrays/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%d crops of %dx%d px x %d spp over the 4 cutoffs, %d rays, %.1f s"
+                      % (crops, crop, crop, SPP, rays, dt)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle  # noqa: F401
+    per_step = max(2.0, 20.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample(per_step / 4, crop=2)
+    vals = [oracle_sample(per_step, crop=2) for _ in range(args.steps)]
+    rays_per_s = statistics.mean(v["value"] for v in vals)
+    cb = dict(vals[-1])
+    cb["value"] = rays_per_s
+    line = {"impl": "reference", "metric": METRIC, "value": rays_per_s, "unit": "Mrays/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config({"engine": "FP64 CPU oracle (OpenMP)"}), "cpu_baseline": cb,
+            "e2e": {"value": rays_per_s, "unit": "Mrays/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world):
+    import torch
+    import torch.distributed as dist
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2602_05081_gb300 import _abi, api
+
+    ctx = api.Context(local)
+    p = synth.octave_field(N_PRIMS, OCTAVES, seed=0)
+    field = api.Field(ctx, p)
+    c = synth.DEFAULT_CAMERA
+    cam = api.camera(c["eye"], c["look_at"], c["up"], c["vfov_deg"], RES, RES)
+    ro = api.render_opts("scatter", SPP, 1, 0.8, synth.LIGHT_DIR, 1.0)
+    out = torch.empty(RES, RES, dtype=torch.float32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+    stream = torch.cuda.current_stream()
+    lods = [api.lod("cutoff", k) for k in CUTOFFS]
+
+    def step(evs=None):
+        for j, lo in enumerate(lods):
+            field.set_lod(lo)
+            if evs is not None:
+                evs[j][0].record(stream)
+            _abi.gf_render(field.h, cam, ro, SEED, out, stream)
+            if evs is not None:
+                evs[j][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    field.sync(stream)
+    field.stats(reset=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    render_ms = []
+    step_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in lods]
+        step(evs)
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        render_ms.append(ms)
+        step_ms.append(sum(ms))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    field.sync(stream)
+    st = field.stats(reset=True)
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms, st["rays"], st["evals"]], dtype=torch.float64, device=dev)
+    if world > 1:
+        tmax = t[0:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        sums = t[1:3].clone()
+        dist.all_reduce(sums, op=dist.ReduceOp.SUM)
+        total_ms_max = float(tmax[0])
+        rays_all, evals_all = float(sums[0]), float(sums[1])
+    else:
+        total_ms_max, rays_all, evals_all = total_ms, float(st["rays"]), float(st["evals"])
+    # end to end through the C ABI with a host (pinned) output buffer
+    host = torch.empty(RES, RES, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    field.stats(reset=True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for lo in lods:
+            field.set_lod(lo)
+            _abi.gf_render(field.h, cam, ro, SEED, host, stream)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    st_e2e = field.stats(reset=True)
+    if rank != 0:
+        return
+    import ctypes
+    flat = [m for s in render_ms for m in s]
+    peaks, peak_kind = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_geval = sm_count * MUFU_PER_SM_CLK / MUFU_PER_EVAL * peaks.get("sm_max_mhz", 2070.0) * 1e-3
+    achieved = (st["evals"] / (4 * args.steps)) / (statistics.mean(flat) * 1e-3) * 1e-9
+    traffic = None
+    value = rays_all / (total_ms_max * 1e-3) / 1e6
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": config(),
+        "gabor_evals_per_s": evals_all / (total_ms_max * 1e-3),
+        "render_ms_p50": float(np.percentile(flat, 50)),
+        "render_ms_p99": float(np.percentile(flat, 99)),
+        "render_ms_by_cutoff": {str(k): statistics.mean(s[j] for s in render_ms)
+                                for j, k in enumerate(CUTOFFS)},
+        "rays_per_step": st["rays"] / args.steps,
+        "evals_per_step": st["evals"] / args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_geval, "unit": "Geval/s",
+                     "frac": achieved / peak_geval, "traffic": traffic,
+                     "kernel": "k_render<true> (delta + ratio tracking)",
+                     "peak_basis": "%d SMs x %d SFU/clk / %d SFU per eval x %.0f MHz (%s clock)"
+                                   % (sm_count, MUFU_PER_SM_CLK, MUFU_PER_EVAL,
+                                      peaks.get("sm_max_mhz", 2070.0), peak_kind)},
+        "e2e": {"value": st_e2e["rays"] / e2e_s / 1e6, "unit": "Mrays/s",
+                "h2d_bytes_per_step": 4 * (ctypes.sizeof(_abi.gf_camera) + ctypes.sizeof(_abi.gf_render_opts)),
+                "d2h_bytes_per_step": 4 * RES * RES * 4},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clk,
+    }
+    line["counters_per_ray"] = {k: st[k] / max(1, st["rays"])
+                                for k in ("chords", "evals", "nodes", "points", "windows", "steps", "leaves")}
+    if any(st["cycles"]):
+        line["phase_cycles_share"] = dict(zip(("traversal", "points", "evaluation", "mask", "path"),
+                                              (c / max(1, st["cycles"][4]) for c in st["cycles"])))
+    if world == 1 and args.cpu_seconds > 0:
+        line["cpu_baseline"] = oracle_sample(args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--res", type=int, default=RES, help="profiling only: image size")
+    ap.add_argument("--spp", type=int, default=SPP, help="profiling only: samples per pixel")
+    args = ap.parse_args()
+    globals()["RES"], globals()["SPP"] = args.res, args.spp
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

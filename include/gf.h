@@ -1,0 +1,243 @@
+/*
+ * gf.h -- C ABI of the GB300 Gabor-field renderer (libgf.so).
+ *
+ * The library renders a density field made of anisotropic 3D Gabor kernels
+ * (Condor, Hermann, Yurtsever et al., "Gabor Fields: Orientation-Selective
+ * Level-of-Detail for Volume Rendering", arXiv 2602.05081):
+ *
+ *   kappa(x) = sum_i w_cell(i) A_i exp(-q_i(x)/2) cos(omega_i.(x-mu_i) + phi_i) 1[q_i(x) <= k^2]
+ *   q_i(x)   = (x-mu_i)^T Sigma_i^-1 (x-mu_i),  Sigma_i = R_i S_i S_i^T R_i^T
+ *
+ * (Sec. 3 Eq. 1, Sec. 4.2 Eq. 6; the k-sigma ellipsoid support of Sec. 3; the
+ * level-of-detail cell weights w of Sec. 4.5-4.6).  A phase phi_i generalises
+ * the paper's zero-phase carrier (phi = 0 reproduces it).
+ *
+ * General conventions
+ *  - Every call returns a gf_status; GF_OK is 0.  No exception crosses the ABI.
+ *    gf_last_error() returns a thread-local message for the last failure.
+ *  - Compute calls are asynchronous on the caller's CUDA stream (gf_stream is a
+ *    cudaStream_t; NULL means the legacy default stream).  Device-side
+ *    failures (a traversal stack or window that overflows, a bounded loop
+ *    that gives up) set an error word in the field; gf_sync() waits on the
+ *    stream and maps it to GF_EOVERFLOW / GF_ETIMEOUT.
+ *  - Array arguments are plain pointers.  Unless stated, a pointer may be
+ *    device memory or host memory (pageable or pinned); host buffers are
+ *    staged through library-owned device memory and the call then
+ *    synchronises the stream before returning.  The caller owns every
+ *    input and output buffer; the library owns packed records, the BVH and
+ *    scratch, all released by gf_field_free / gf_destroy.
+ *  - Layouts are structure-of-arrays, float32, row-major per element.
+ *  - Random numbers: Philox4x32-10 (Salmon et al. 2011) keyed by the 64-bit
+ *    seed, counter = (draw, primitive index or 0xFFFFFFFF, ray or pixel
+ *    index, (sample << 12) | (bounce << 8) | stream tag); uniforms are
+ *    (x >> 8) * 2^-24.  Results depend only on these counters, never on
+ *    scheduling.
+ */
+#ifndef GF_H
+#define GF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gf_status {
+  GF_OK = 0,
+  GF_EINVAL = 1,    /* invalid argument (null, non-finite, out of range) */
+  GF_ENOMEM = 2,    /* device allocation failed */
+  GF_ECUDA = 3,     /* a CUDA runtime call failed */
+  GF_EOVERFLOW = 4, /* a bounded device buffer overflowed (stack, window, points) */
+  GF_ETIMEOUT = 5,  /* a bounded device wait or loop gave up */
+  GF_ESTATE = 6     /* call out of order (e.g. render before gf_build_bvh) */
+} gf_status;
+
+typedef struct gf_ctx gf_ctx;
+typedef struct gf_field gf_field;
+typedef void* gf_stream; /* cudaStream_t */
+
+/* Primitive parameters, N entries each (Sec. 4.2; App. D lists the same set:
+   mean, rotation quaternion, scales, carrier, weight, plus a phase).
+   mu[3N]; quat[4N] as (w,x,y,z), normalised by the library; log_scale[3N]
+   (natural log of the per-axis standard deviations); omega[3N] (see
+   gf_field_opts.omega_frame); phase[N] (radians); weight[N]; band[N]
+   optional octave label 0..7 (0 = the Gaussian low-pass band, Sec. 4.3),
+   NULL derives floor(log2(1 + |omega|/(2 pi))) in FP32. */
+typedef struct gf_params {
+  int64_t n;
+  const float* mu;
+  const float* quat;
+  const float* log_scale;
+  const float* omega;
+  const float* phase;
+  const float* weight;
+  const uint8_t* band;
+} gf_params;
+
+enum { GF_PREC_FP32 = 0, GF_PREC_FP16 = 1, GF_PREC_BF16 = 2 };
+/* PEAK: A = weight (peak density).  NORMALIZED: A = weight / sqrt(8 pi^3 |Sigma|) (Eq. 6). */
+enum { GF_WEIGHT_PEAK = 0, GF_WEIGHT_NORMALIZED = 1 };
+/* WORLD: omega is the world-space carrier in rad/unit.  LOCAL: omega holds the
+   whitened-frame carrier k_W and the world carrier is R S^-1 k_W; the paper's
+   tied form (Sec. 4.2) is k_W = (w, w, w). */
+enum { GF_OMEGA_WORLD = 0, GF_OMEGA_LOCAL = 1 };
+
+typedef struct gf_field_opts {
+  int precision;   /* GF_PREC_*: storage of the packed records (math is FP32) */
+  int weight_mode; /* GF_WEIGHT_* */
+  int omega_frame; /* GF_OMEGA_* */
+  float k_sigma;   /* support radius in sigma units, (0, 6]; the paper uses 3 */
+} gf_field_opts;
+
+/* Level-of-detail mask (Sec. 4.5.1-4.5.2, 4.6; strategy tables of App. B).
+   Cells: cell 0 = Gaussian band; cell 1 + 8 (band-1) + cone for Gabor bands,
+   cone = the nearest of 8 fixed orientation axes to the carrier direction.
+   freq_policy: ALL every band weight 1; CUTOFF bands <= max_band weight 1;
+   UNIF_CV Gaussians weight 1 plus one Gabor band (<= max_band) chosen
+   uniformly, weight P-1; UNIFORM one band (<= max_band) uniformly, weight P.
+   cone_policy (applied inside every selected Gabor band): ALL; IS one cone
+   with probability w(a)/W, w(a) = exp(-kbar^2 a^2/2), a = |v.o_c|, weight
+   W/w(a) (Eq. 17); UNIFORM one cone, weight K.  A new mask is drawn for
+   every path segment (per bounce) and every NEE ray. */
+enum { GF_FREQ_ALL = 0, GF_FREQ_CUTOFF = 1, GF_FREQ_UNIF_CV = 2, GF_FREQ_UNIFORM = 3 };
+enum { GF_CONE_ALL = 0, GF_CONE_IS = 1, GF_CONE_UNIFORM = 2 };
+typedef struct gf_lod_desc {
+  int freq_policy;
+  int max_band;
+  int cone_policy;
+} gf_lod_desc;
+
+enum { GF_TR_DETERMINISTIC = 0, GF_TR_RATIO_TRACKING = 1 };
+
+/* Pinhole camera: pixel (px,py) of a width x height image (py = 0 at the top)
+   looks along normalize(f + sx r + sy u) with f = normalize(look_at - eye),
+   r = normalize(up x f), u = f x r, sx = (2(px+jx)/W - 1) tan(vfov/2) W/H,
+   sy = (1 - 2(py+jy)/H) tan(vfov/2); (jx, jy) from the camera stream. */
+typedef struct gf_camera {
+  float eye[3], look_at[3], up[3];
+  float vfov_deg;
+  int width, height;
+} gf_camera;
+
+/* TOMO: image = mean over samples of exp(-tau) along the camera ray (Sec. 4.6,
+   tomography).  SCATTER: delta tracking to a collision, weight albedo,
+   next-event estimation to a directional light by ratio tracking with an
+   isotropic phase 1/(4 pi), isotropic re-emission, up to max_bounces
+   collisions (1 = single scattering). */
+enum { GF_INTEG_TOMO = 0, GF_INTEG_SCATTER = 1 };
+typedef struct gf_render_opts {
+  int integrator;
+  int spp;
+  int max_bounces;
+  float albedo;
+  float light_dir[3]; /* direction towards the light, normalised by the library */
+  float light_irradiance;
+} gf_render_opts;
+
+/* Work counters accumulated by the kernels since the last reset. */
+typedef struct gf_stats {
+  uint64_t rays;   /* traced rays: camera segments, bounce segments, NEE rays, API rays */
+  uint64_t chords; /* chord set-ups (ray x primitive overlaps, per window) */
+  uint64_t evals;  /* Gabor evaluations A exp(-q/2) cos(theta) */
+  uint64_t nodes;  /* BVH node visits */
+  uint64_t points; /* tentative collision points */
+  uint64_t windows; /* BVH traversals (one per ray window) */
+  uint64_t steps;  /* warp traversal steps (up to 32 nodes each) */
+  uint64_t leaves; /* leaves reached (ellipsoid chord tests) */
+  uint64_t cycles[5]; /* SM clock cycles per phase (traversal, tentative points, evaluation,
+                         mask sampling, whole path), summed over warps; zero unless the
+                         library was built with GF_PHASE_TIMERS */
+} gf_stats;
+
+/* Context on one CUDA device (cudaSetDevice(device) is made current by every
+   call that takes the context or a field created from it).  Computes the
+   Gauss-Legendre tables.  GF_ECUDA if the device is missing or not sm_103. */
+gf_status gf_create(int device, gf_ctx** out);
+gf_status gf_destroy(gf_ctx* ctx);
+
+/* Pack the primitives (Sec. 4.2 parameters -> Sigma^-1, world carrier, amplitude,
+   band/cone/cell labels; load-time binning of Sec. 4.6).  params arrays may be
+   host or device memory.  Validates on the host/device: n >= 1, finite values,
+   |quat| > 0, k_sigma in (0,6], band labels <= 7 (GF_EINVAL).  The field keeps a
+   copy of the raw parameters for gf_render_backward. */
+gf_status gf_load_field(gf_ctx* ctx, const gf_params* params, const gf_field_opts* opts,
+                        gf_stream stream, gf_field** out);
+gf_status gf_field_free(gf_field* field);
+
+/* Build the BVH over the k-sigma ellipsoid bounds (Sec. 3; the per-level
+   acceleration structures of Sec. 4.6 become one radix tree whose top levels
+   split by cell, every node carrying the 64-bit OR of its cells).
+   Reorders the packed records along the tree. */
+gf_status gf_build_bvh(gf_field* field, gf_stream stream);
+
+/* Set the LoD mask used by subsequent calls: primary rays (camera and bounce
+   segments, transmittance API) and NEE rays (nee may be NULL = same as primary). */
+gf_status gf_set_lod_mask(gf_field* field, const gf_lod_desc* primary, const gf_lod_desc* nee);
+
+/* Transmittance of n_rays rays x(t) = o + t d, t in [trange[2r], trange[2r+1]]
+   (trange NULL: [0, inf)); d is normalised by the library.
+   DETERMINISTIC: tau = sum over chords of the chord integral (Eq. 2), each by
+   Gauss-Legendre quadrature with a node count set by the chord's whitened
+   length and carrier phase span, FP32 with compensated summation; with a
+   stochastic mask tau is averaged over spp mask draws (Sec. 4.6 tomography);
+   out_T = exp(-tau), out_tau = tau (nullable).
+   RATIO_TRACKING: out_T = mean over spp samples of prod (1 - kappa/kappa_bar)
+   over the tentative points (per-segment majorants, see gf_render);
+   out_tau is not written.  Signed kappa (absorption only).
+   o, d: float[3n]; trange: float[2n]; out_T, out_tau: float[n]. */
+gf_status gf_transmittance(gf_field* field, const float* o, const float* d, const float* trange,
+                           int64_t n_rays, int mode, int spp, uint64_t seed, float* out_T,
+                           float* out_tau, gf_stream stream);
+
+/* Render width x height floats (row-major) into out_image.  Per path segment
+   the ray is cut into segments at every chord entry/exit and wherever the
+   whitened distance to a kernel's envelope peak crosses an integer; each
+   segment carries the majorant kappa_bar = sum w|A| exp(-(r^2+n^2)/2) over
+   the chords active on it, which bounds |kappa|; its tentative points are
+   drawn chord by chord (a superposition of Poisson processes) and accepted
+   with probability max(kappa,0)/kappa_bar (delta tracking) or weighted by
+   1 - max(kappa,0)/kappa_bar (ratio tracking for NEE). */
+gf_status gf_render(gf_field* field, const gf_camera* camera, const gf_render_opts* opts,
+                    uint64_t seed, float* out_image, gf_stream stream);
+
+/* Adjoint of the TOMO integrator with all cells: given dL/dI (float[W*H]),
+   accumulate dL/dparam into grad (float[15 N], SoA like gf_params: mu[3N],
+   quat[4N], log_scale[3N], omega[3N] in the input frame, phase[N],
+   weight[N]); grad is overwritten.  Per ray the chords are recomputed
+   (no stored paths); dtau/dtheta = integral of d(integrand)/dtheta plus the
+   Leibniz terms of the chord ends on the ellipsoid. */
+gf_status gf_render_backward(gf_field* field, const gf_camera* camera,
+                             const gf_render_opts* opts, uint64_t seed,
+                             const float* dL_dimage, float* grad, gf_stream stream);
+
+/* Labels of every primitive (original order): band, cone, cell (uint8[N] each,
+   nullable; host or device).  Synchronises the stream. */
+gf_status gf_field_labels(gf_field* field, uint8_t* band, uint8_t* cone, uint8_t* cell,
+                          gf_stream stream);
+
+/* Chord sets for testing: for each ray, the primitives (original indices) whose
+   ellipsoid the ray crosses inside trange under the current primary mask
+   (deterministic policies only), with FP32 entry/exit t.  counts int32[n];
+   prims int32[n*cap]; t_in, t_out float[n*cap] (nullable).  Rays with more
+   than cap chords report the full count and the first cap entries found. */
+gf_status gf_ray_chords(gf_field* field, const float* o, const float* d, const float* trange,
+                        int64_t n_rays, int cap, int32_t* counts, int32_t* prims, float* t_in,
+                        float* t_out, gf_stream stream);
+
+/* Raw Philox4x32-10 blocks for testing: out[4n] from ctr[4n], key[2n]
+   (uint32, host or device). */
+gf_status gf_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n,
+                    gf_stream stream);
+
+gf_status gf_get_stats(gf_field* field, gf_stats* out, int reset);
+/* Wait for the stream, then report (and clear) any device-side error of the field. */
+gf_status gf_sync(gf_field* field, gf_stream stream);
+/* Number of primitives, precision, occupied cell mask. */
+gf_status gf_field_info(gf_field* field, int64_t* n, int* precision, uint64_t* occupied);
+const char* gf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GF_H */

@@ -101,6 +101,8 @@ def _load():
         lib.or_tomo_loss_grad.argtypes = [C.POINTER(FieldDesc), C.POINTER(Camera), i32, u64, vp,
                                           vp, i32]
         lib.or_tomo_image.argtypes = [C.POINTER(FieldDesc), C.POINTER(Camera), i32, u64, vp, i32]
+        lib.or_rays_traced.restype = C.c_longlong
+        lib.or_rays_traced.argtypes = [i32]
         _lib = lib
         return lib
 
@@ -273,6 +275,11 @@ def render_opts(integrator="scatter", spp=1, max_bounces=1, albedo=0.8,
                 light_dir=(1.0, 1.0, -1.0), light_irradiance=1.0):
     return RenderOpts(0 if integrator == "tomo" else 1, int(spp), int(max_bounces), float(albedo),
                       (C.c_float * 3)(*light_dir), float(light_irradiance))
+
+
+def rays_traced(reset=False):
+    """Rays (camera, bounce and NEE segments) traced by the render calls since the last reset."""
+    return int(_load().or_rays_traced(int(bool(reset))))
 
 
 def stream_word(sample, bounce, tag):

@@ -785,6 +785,23 @@ void or_camera_ray(const or_camera* C, uint64_t seed, int px, int py, int s, dou
    directional light by ratio tracking, isotropic phase 1/(4 pi), then an
    isotropic new direction; the LoD mask is redrawn at every bounce
    (Sec. 4.5, per path segment; Sec. 4.6 pipeline steps 1-6). */
+/* traced rays (camera, bounce and NEE segments) since the last reset */
+static long long g_rays = 0;
+long long or_rays_traced(int reset) {
+  long long r;
+#pragma omp atomic read
+  r = g_rays;
+  if (reset) {
+#pragma omp atomic write
+    g_rays = 0;
+  }
+  return r;
+}
+static void count_ray(void) {
+#pragma omp atomic
+  g_rays += 1;
+}
+
 static double path_sample(const or_field* f, const or_lod* lod, const or_lod* lodn,
                           const or_camera* C, const or_render_opts* ro, uint64_t seed, int px,
                           int py, int s) {
@@ -795,6 +812,7 @@ static double path_sample(const or_field* f, const or_lod* lod, const or_lod* lo
     uint64_t mask;
     double w64[OR_MAX_CELLS];
     or_sample_mask(f, lod, v, seed, pix, (uint32_t)s, 0, OR_TAG_MASK, &mask, w64);
+    count_ray();
     return exp(-det_tau(f, o, v, 0.0, INFINITY, mask, w64));
   }
   double l[3] = {ro->light_dir[0], ro->light_dir[1], ro->light_dir[2]};
@@ -805,6 +823,7 @@ static double path_sample(const or_field* f, const or_lod* lod, const or_lod* lo
     double w64[OR_MAX_CELLS];
     or_sample_mask(f, lod, v, seed, pix, (uint32_t)s, (uint32_t)b, OR_TAG_MASK, &mask, w64);
     double th;
+    count_ray();
     if (!or_delta_track(f, o, v, 0.0, INFINITY, mask, w64, seed, pix,
                         stream_word((uint32_t)s, (uint32_t)b, OR_TAG_TRACK), &th))
       break;
@@ -813,6 +832,7 @@ static double path_sample(const or_field* f, const or_lod* lod, const or_lod* lo
     uint64_t nmask;
     double nw[OR_MAX_CELLS];
     or_sample_mask(f, lodn, l, seed, pix, (uint32_t)s, (uint32_t)b, OR_TAG_NEE_MASK, &nmask, nw);
+    count_ray();
     double Tl = ratio_track(f, x, l, 0.0, INFINITY, nmask, nw, seed, pix,
                             stream_word((uint32_t)s, (uint32_t)b, OR_TAG_NEE), 1);
     L += thr * ro->light_irradiance * Tl / (4.0 * OR_PI);

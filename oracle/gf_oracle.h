@@ -125,6 +125,9 @@ void or_render_samples(const or_field* f, const or_lod* lod, const or_lod* lod_n
                        const or_camera* cam, const or_render_opts* ro, uint64_t seed, int x0,
                        int y0, int w, int h, double* out, int n_threads);
 
+/* rays traced by or_render / or_render_samples since the last reset */
+long long or_rays_traced(int reset);
+
 /* camera ray of pixel (px,py), sample s */
 void or_camera_ray(const or_camera* cam, uint64_t seed, int px, int py, int s, double o[3],
                    double v[3]);

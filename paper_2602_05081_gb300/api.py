@@ -1,0 +1,176 @@
+"""Conveniences over the C ABI (marshalling only; the work runs in libgf.so).
+
+``Field`` packs a primitive set on the GPU (gf_load_field + gf_build_bvh) and
+forwards the rendering calls; ``TomoRender`` is a torch.autograd.Function whose
+backward is the hand-written adjoint kernel (gf_render_backward).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _abi as A
+
+_KEYS = ("mu", "quat", "log_scale", "omega", "phase", "weight")
+_FRAMES = {"world": A.GF_OMEGA_WORLD, "local": A.GF_OMEGA_LOCAL}
+_WMODES = {"peak": A.GF_WEIGHT_PEAK, "normalized": A.GF_WEIGHT_NORMALIZED}
+_PRECS = {"fp32": A.GF_PREC_FP32, "fp16": A.GF_PREC_FP16, "bf16": A.GF_PREC_BF16}
+
+
+class Context:
+    def __init__(self, device: int = 0):
+        self.device = int(device)
+        self.h = A.gf_create(self.device)
+
+    def close(self):
+        if getattr(self, "h", None):
+            A.gf_destroy(self.h)
+            self.h = None
+
+
+def _as_tensor(x, device, dtype=torch.float32):
+    if isinstance(x, torch.Tensor):
+        return x.detach().to(device=device, dtype=dtype).contiguous()
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device=device).contiguous()
+
+
+def lod(freq="all", max_band=7, cone="all"):
+    f = {"all": A.GF_FREQ_ALL, "cutoff": A.GF_FREQ_CUTOFF, "unif_cv": A.GF_FREQ_UNIF_CV,
+         "uniform": A.GF_FREQ_UNIFORM}[freq]
+    c = {"all": A.GF_CONE_ALL, "is": A.GF_CONE_IS, "uniform": A.GF_CONE_UNIFORM}[cone]
+    return A.gf_lod_desc(f, int(max_band), c)
+
+
+def camera(eye, look_at, up, vfov_deg, width, height):
+    return A.gf_camera((C.c_float * 3)(*eye), (C.c_float * 3)(*look_at), (C.c_float * 3)(*up),
+                       float(vfov_deg), int(width), int(height))
+
+
+def render_opts(integrator="scatter", spp=1, max_bounces=1, albedo=0.8,
+                light_dir=(1.0, 1.0, -1.0), light_irradiance=1.0):
+    return A.gf_render_opts(A.GF_INTEG_TOMO if integrator == "tomo" else A.GF_INTEG_SCATTER,
+                            int(spp), int(max_bounces), float(albedo),
+                            (C.c_float * 3)(*light_dir), float(light_irradiance))
+
+
+class Field:
+    """A packed primitive set with its BVH on one GPU."""
+
+    def __init__(self, ctx: Context, params: dict, precision="fp32", weight_mode=None,
+                 omega_frame=None, k_sigma=3.0, stream=None, device_inputs=True):
+        self.ctx = ctx
+        dev = torch.device("cuda", ctx.device) if device_inputs else torch.device("cpu")
+        self._keep = {k: _as_tensor(params[k], dev) for k in _KEYS}
+        band = params.get("band")
+        self._keep["band"] = None if band is None else _as_tensor(band, dev, torch.uint8)
+        self.n = int(self._keep["phase"].numel())
+        p = A.gf_params(self.n, *(A.ptr(self._keep[k]) for k in _KEYS),
+                        A.ptr(self._keep["band"]))
+        wm = weight_mode or params.get("weight_mode", "peak")
+        fr = omega_frame or params.get("omega_frame", "world")
+        opts = A.gf_field_opts(_PRECS[precision], _WMODES[wm], _FRAMES[fr], float(k_sigma))
+        self.h = A.gf_load_field(ctx.h, p, opts, stream)
+        A.gf_build_bvh(self.h, stream)
+        if not device_inputs:
+            self._keep = None
+
+    def free(self):
+        if getattr(self, "h", None):
+            A.gf_field_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def set_lod(self, primary=None, nee=None):
+        A.gf_set_lod_mask(self.h, primary if primary is not None else lod(), nee)
+
+    def transmittance(self, o, d, trange=None, mode="det", spp=1, seed=0, out_T=None,
+                      out_tau=None, stream=None):
+        n = int(o.shape[0])
+        if out_T is None:
+            dev = o.device if isinstance(o, torch.Tensor) else torch.device("cpu")
+            out_T = torch.empty(n, dtype=torch.float32, device=dev)
+            if mode == "det" and out_tau is None:
+                out_tau = torch.empty(n, dtype=torch.float32, device=dev)
+        m = A.GF_TR_DETERMINISTIC if mode == "det" else A.GF_TR_RATIO_TRACKING
+        A.gf_transmittance(self.h, o, d, trange, n, m, spp, seed, out_T, out_tau, stream)
+        return out_T, out_tau
+
+    def render(self, cam, opts, seed=0, out=None, stream=None):
+        if out is None:
+            out = torch.empty(cam.height, cam.width, dtype=torch.float32,
+                              device=torch.device("cuda", self.ctx.device))
+        A.gf_render(self.h, cam, opts, seed, out, stream)
+        return out
+
+    def render_backward(self, cam, opts, seed, dL_dimage, grad=None, stream=None):
+        if grad is None:
+            grad = torch.empty(15 * self.n, dtype=torch.float32, device=dL_dimage.device)
+        A.gf_render_backward(self.h, cam, opts, seed, dL_dimage, grad, stream)
+        return grad
+
+    def labels(self):
+        b = np.zeros(self.n, np.uint8); c = np.zeros(self.n, np.uint8); e = np.zeros(self.n, np.uint8)
+        A.gf_field_labels(self.h, b, c, e)
+        return b, c, e
+
+    def chords(self, o, d, trange=None, cap=512):
+        n = int(o.shape[0])
+        counts = np.zeros(n, np.int32)
+        prims = np.zeros(n * cap, np.int32)
+        tin = np.zeros(n * cap, np.float32)
+        tout = np.zeros(n * cap, np.float32)
+        A.gf_ray_chords(self.h, o, d, trange, n, cap, counts, prims, tin, tout)
+        return counts, prims.reshape(n, cap), tin.reshape(n, cap), tout.reshape(n, cap)
+
+    def stats(self, reset=False):
+        return A.gf_get_stats(self.h, reset)
+
+    def sync(self, stream=None):
+        A.gf_sync(self.h, stream)
+
+    def info(self):
+        return A.gf_field_info(self.h)
+
+
+def split_grad(g: torch.Tensor, n: int) -> dict:
+    """SoA gradient (15 N floats) -> per-parameter tensors shaped like the inputs."""
+    return {"mu": g[0:3 * n].view(n, 3), "quat": g[3 * n:7 * n].view(n, 4),
+            "log_scale": g[7 * n:10 * n].view(n, 3), "omega": g[10 * n:13 * n].view(n, 3),
+            "phase": g[13 * n:14 * n], "weight": g[14 * n:15 * n]}
+
+
+class TomoRender(torch.autograd.Function):
+    """I = tomography image of the field given by the parameter tensors.
+
+    Forward packs the field and renders (GF_INTEG_TOMO, all cells); backward
+    runs the adjoint kernel with per-ray recomputation.
+    """
+
+    @staticmethod
+    def forward(ctx_, mu, quat, log_scale, omega, phase, weight, gctx, cam, spp, seed,
+                omega_frame, weight_mode, k_sigma):
+        params = {"mu": mu, "quat": quat, "log_scale": log_scale, "omega": omega,
+                  "phase": phase, "weight": weight}
+        f = Field(gctx, params, omega_frame=omega_frame, weight_mode=weight_mode,
+                  k_sigma=k_sigma)
+        opts = render_opts("tomo", spp=spp)
+        img = f.render(cam, opts, seed)
+        ctx_.field = f
+        ctx_.cam, ctx_.opts, ctx_.seed = cam, opts, seed
+        return img
+
+    @staticmethod
+    def backward(ctx_, g_img):
+        f = ctx_.field
+        g = f.render_backward(ctx_.cam, ctx_.opts, ctx_.seed, g_img.contiguous())
+        parts = split_grad(g, f.n)
+        f.free()
+        return (parts["mu"], parts["quat"], parts["log_scale"], parts["omega"], parts["phase"],
+                parts["weight"], None, None, None, None, None, None, None)

@@ -1,0 +1,587 @@
+// gf_api.cu -- the C ABI of include/gf.h: argument checks, memory ownership,
+// host-buffer staging and error mapping around the kernels.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gf_host.h"
+#include "gf_trace.cuh"
+
+using namespace gf;
+
+struct gf_ctx {
+  Ctx c;
+};
+struct gf_field {
+  Field f;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+gf_status fail(gf_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+gf_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(e == cudaErrorMemoryAllocation ? GF_ENOMEM : GF_ECUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define GF_CUDA(call, where)                   \
+  do {                                         \
+    cudaError_t _e = (call);                   \
+    if (_e != cudaSuccess) return cuda_fail(_e, where); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Gauss-Legendre nodes/weights on [-1,1] by Newton iteration on the
+// three-term Legendre recurrence (double precision)
+void gauss_legendre(int n, double* x, double* w) {
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n + 0.5)), dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+void cone_axes(float axes[kCones][3]) {
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k < kCones; ++k) {
+    double z = 1.0 - (k + 0.5) / kCones;
+    double r = std::sqrt(1.0 - z * z);
+    double ph = k * pi * (3.0 - std::sqrt(5.0));
+    axes[k][0] = (float)(r * std::cos(ph));
+    axes[k][1] = (float)(r * std::sin(ph));
+    axes[k][2] = (float)z;
+  }
+}
+
+struct Staging {
+  std::vector<std::pair<void*, const void*>> back;  // device -> host copies
+};
+
+// device view of a caller buffer: the pointer itself, or a slice of the
+// field's staging area (copied in when `in`)
+gf_status stage(Field& F, const void* p, size_t bytes, bool in, cudaStream_t s, size_t& off,
+                void** out) {
+  if (!p || is_device_ptr(p)) {
+    *out = const_cast<void*>(p);
+    return GF_OK;
+  }
+  size_t need = off + ((bytes + 255) & ~size_t(255));
+  if (need > F.stage_bytes) return fail(GF_ESTATE, "staging area too small");
+  void* d = (char*)F.stage + off;
+  off = need;
+  if (in) GF_CUDA(cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, s), "stage in");
+  *out = d;
+  return GF_OK;
+}
+
+gf_status ensure_stage(Field& F, size_t bytes) {
+  if (bytes <= F.stage_bytes) return GF_OK;
+  if (F.stage) cudaFree(F.stage);
+  F.stage = nullptr;
+  F.stage_bytes = 0;
+  GF_CUDA(cudaMalloc(&F.stage, bytes), "staging alloc");
+  F.stage_bytes = bytes;
+  return GF_OK;
+}
+
+bool lod_ok(const gf_lod_desc* l) {
+  return l && l->freq_policy >= 0 && l->freq_policy <= 3 && l->cone_policy >= 0 &&
+         l->cone_policy <= 2 && l->max_band >= 0 && l->max_band <= 7;
+}
+
+gf_status camera_params(const gf_camera* c, const gf_render_opts* o, uint64_t seed,
+                        const Field& F, PathParams& P) {
+  if (!c || !o) return fail(GF_EINVAL, "camera/opts null");
+  if (c->width < 1 || c->height < 1 || (int64_t)c->width * c->height > (1ll << 31) - 1)
+    return fail(GF_EINVAL, "bad image size");
+  if (o->spp < 1 || o->spp > (1 << 20)) return fail(GF_EINVAL, "spp must be in [1, 2^20]");
+  if (o->max_bounces < 0 || o->max_bounces > 15) return fail(GF_EINVAL, "max_bounces in [0, 15]");
+  if (o->integrator != GF_INTEG_TOMO && o->integrator != GF_INTEG_SCATTER)
+    return fail(GF_EINVAL, "bad integrator");
+  if (!(c->vfov_deg > 0.f && c->vfov_deg < 180.f)) return fail(GF_EINVAL, "vfov in (0,180)");
+  double e[3] = {c->eye[0], c->eye[1], c->eye[2]};
+  double f[3] = {c->look_at[0] - e[0], c->look_at[1] - e[1], c->look_at[2] - e[2]};
+  double fn = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+  if (!(fn > 0)) return fail(GF_EINVAL, "eye == look_at");
+  for (double& x : f) x /= fn;
+  double u[3] = {c->up[0], c->up[1], c->up[2]};
+  double r[3] = {u[1] * f[2] - u[2] * f[1], u[2] * f[0] - u[0] * f[2], u[0] * f[1] - u[1] * f[0]};
+  double rn = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  if (!(rn > 0)) return fail(GF_EINVAL, "up parallel to view direction");
+  for (double& x : r) x /= rn;
+  double uv[3] = {f[1] * r[2] - f[2] * r[1], f[2] * r[0] - f[0] * r[2], f[0] * r[1] - f[1] * r[0]};
+  P.cam.eye = make_float3((float)e[0], (float)e[1], (float)e[2]);
+  P.cam.fw = make_float3((float)f[0], (float)f[1], (float)f[2]);
+  P.cam.rt = make_float3((float)r[0], (float)r[1], (float)r[2]);
+  P.cam.up = make_float3((float)uv[0], (float)uv[1], (float)uv[2]);
+  P.cam.tanh = (float)std::tan(0.5 * (double)c->vfov_deg * 3.14159265358979323846 / 180.0);
+  P.cam.aspect = (float)((double)c->width / (double)c->height);
+  P.cam.W = c->width;
+  P.cam.H = c->height;
+  P.integrator = o->integrator;
+  P.spp = o->spp;
+  P.max_bounces = o->max_bounces;
+  P.albedo = o->albedo;
+  P.irradiance = o->light_irradiance;
+  double l[3] = {o->light_dir[0], o->light_dir[1], o->light_dir[2]};
+  double ln = std::sqrt(l[0] * l[0] + l[1] * l[1] + l[2] * l[2]);
+  if (o->integrator == GF_INTEG_SCATTER && !(ln > 0)) return fail(GF_EINVAL, "light_dir zero");
+  if (!(ln > 0)) ln = 1.0;
+  P.light = make_float3((float)(l[0] / ln), (float)(l[1] / ln), (float)(l[2] / ln));
+  P.seed = seed;
+  P.lod = F.lod;
+  P.lod_nee = F.lod_nee;
+  return GF_OK;
+}
+
+void free_field(Field& F) {
+  void* ptrs[] = {F.p_mu, F.p_quat, F.p_ls, F.p_om, F.p_ph, F.p_w, F.rec_orig, F.box_orig,
+                  F.kw_orig, F.rec, F.rec16, F.nodes, F.sorted_orig, F.labels, F.err,
+                  F.stats, F.counter, F.cell_acc, F.stage};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gf_last_error(void) { return g_err.c_str(); }
+
+gf_status gf_create(int device, gf_ctx** out) {
+  if (!out) return fail(GF_EINVAL, "out null");
+  *out = nullptr;
+  int ndev = 0;
+  GF_CUDA(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
+  if (device < 0 || device >= ndev) return fail(GF_EINVAL, "no such device");
+  GF_CUDA(cudaSetDevice(device), "cudaSetDevice");
+  cudaDeviceProp prop;
+  GF_CUDA(cudaGetDeviceProperties(&prop, device), "cudaGetDeviceProperties");
+  if (!(prop.major == 10 && prop.minor == 3))
+    return fail(GF_ECUDA, "libgf is built for sm_103a (GB300); device is sm_" +
+                              std::to_string(prop.major) + std::to_string(prop.minor));
+  std::vector<float> x(kGLTotal), w(kGLTotal);
+  for (int r = 0; r < kNumRules; ++r) {
+    int n = gl_n(r), off = gl_off(r);
+    std::vector<double> xd(n), wd(n);
+    gauss_legendre(n, xd.data(), wd.data());
+    for (int k = 0; k < n; ++k) {
+      x[off + k] = (float)xd[k];
+      w[off + k] = (float)wd[k];
+    }
+  }
+  float* gl = nullptr;
+  GF_CUDA(cudaMalloc((void**)&gl, 2 * kGLTotal * sizeof(float)), "alloc GL tables");
+  GF_CUDA(cudaMemcpy(gl, x.data(), kGLTotal * sizeof(float), cudaMemcpyHostToDevice), "GL tables");
+  GF_CUDA(cudaMemcpy(gl + kGLTotal, w.data(), kGLTotal * sizeof(float), cudaMemcpyHostToDevice),
+          "GL tables");
+  gf_ctx* c = new gf_ctx;
+  c->c.gl = gl;
+  c->c.device = device;
+  c->c.sm_count = prop.multiProcessorCount;
+  c->c.cc_major = prop.major;
+  c->c.cc_minor = prop.minor;
+  *out = c;
+  return GF_OK;
+}
+
+gf_status gf_destroy(gf_ctx* ctx) {
+  if (ctx) {
+    cudaSetDevice(ctx->c.device);
+    cudaFree(ctx->c.gl);
+  }
+  delete ctx;
+  return GF_OK;
+}
+
+gf_status gf_load_field(gf_ctx* ctx, const gf_params* p, const gf_field_opts* opts,
+                        gf_stream stream, gf_field** out) {
+  if (!ctx || !p || !opts || !out) return fail(GF_EINVAL, "null argument");
+  *out = nullptr;
+  if (p->n < 1 || p->n > (1ll << 30)) return fail(GF_EINVAL, "n must be in [1, 2^30]");
+  if (!p->mu || !p->quat || !p->log_scale || !p->omega || !p->phase || !p->weight)
+    return fail(GF_EINVAL, "parameter array null");
+  if (!(opts->k_sigma > 0.f && opts->k_sigma <= 6.f)) return fail(GF_EINVAL, "k_sigma in (0,6]");
+  if (opts->precision < 0 || opts->precision > 2) return fail(GF_EINVAL, "bad precision");
+  if (opts->weight_mode < 0 || opts->weight_mode > 1) return fail(GF_EINVAL, "bad weight_mode");
+  if (opts->omega_frame < 0 || opts->omega_frame > 1) return fail(GF_EINVAL, "bad omega_frame");
+  GF_CUDA(cudaSetDevice(ctx->c.device), "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  gf_field* h = new gf_field;
+  Field& F = h->f;
+  F.ctx = &ctx->c;
+  F.n = p->n;
+  F.opts = *opts;
+  const int64_t n = p->n;
+  auto A = [&](void** q, size_t bytes) { return cudaMalloc(q, bytes ? bytes : 16); };
+  cudaError_t e = cudaSuccess;
+  void* band_dev = nullptr;
+  do {
+    if ((e = A((void**)&F.p_mu, 3 * n * 4)) || (e = A((void**)&F.p_quat, 4 * n * 4)) ||
+        (e = A((void**)&F.p_ls, 3 * n * 4)) || (e = A((void**)&F.p_om, 3 * n * 4)) ||
+        (e = A((void**)&F.p_ph, n * 4)) || (e = A((void**)&F.p_w, n * 4)) ||
+        (e = A((void**)&F.rec_orig, 64 * n)) || (e = A((void**)&F.box_orig, 24 * n)) ||
+        (e = A((void**)&F.kw_orig, 4 * n)) || (e = A((void**)&F.labels, 3 * n)) ||
+        (e = A((void**)&F.err, 4)) || (e = A((void**)&F.stats, 8 * kNumStats)) ||
+        (e = A((void**)&F.counter, 16)) || (e = A((void**)&F.cell_acc, 128 * 4)))
+      break;
+    if (p->band && (e = A(&band_dev, n))) break;
+    auto cp = [&](void* dst, const void* src, size_t bytes) {
+      return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
+    };
+    if ((e = cp(F.p_mu, p->mu, 3 * n * 4)) || (e = cp(F.p_quat, p->quat, 4 * n * 4)) ||
+        (e = cp(F.p_ls, p->log_scale, 3 * n * 4)) || (e = cp(F.p_om, p->omega, 3 * n * 4)) ||
+        (e = cp(F.p_ph, p->phase, n * 4)) || (e = cp(F.p_w, p->weight, n * 4)))
+      break;
+    if (p->band && (e = cp(band_dev, p->band, n))) break;
+    if ((e = cudaMemsetAsync(F.err, 0, 4, s)) || (e = cudaMemsetAsync(F.stats, 0, 8 * kNumStats, s)) ||
+        (e = cudaMemsetAsync(F.cell_acc, 0, 512, s)))
+      break;
+  } while (0);
+  if (e != cudaSuccess) {
+    free_field(F);
+    if (band_dev) cudaFree(band_dev);
+    delete h;
+    return cuda_fail(e, "gf_load_field alloc/copy");
+  }
+  cone_axes(F.dev.axes);
+  gf_params dp = *p;
+  dp.mu = F.p_mu;
+  dp.quat = F.p_quat;
+  dp.log_scale = F.p_ls;
+  dp.omega = F.p_om;
+  dp.phase = F.p_ph;
+  dp.weight = F.p_w;
+  dp.band = (const uint8_t*)band_dev;
+  e = launch_pack(F, dp, s);
+  int herr = 0;
+  float acc[128];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, F.err, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(acc, F.cell_acc, 512, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (band_dev) cudaFree(band_dev);
+  if (e != cudaSuccess) {
+    free_field(F);
+    delete h;
+    return cuda_fail(e, "gf_load_field pack");
+  }
+  if (herr) {
+    free_field(F);
+    delete h;
+    return fail(GF_EINVAL, "non-finite parameter, zero quaternion or band label > 7");
+  }
+  F.dev.n = n;
+  F.dev.precision = opts->precision;
+  F.dev.ksig = opts->k_sigma;
+  F.dev.k2 = opts->k_sigma * opts->k_sigma;
+  F.dev.occupied = 0;
+  for (int c = 0; c < kMaxCells; ++c) {
+    float cnt = acc[64 + c];
+    if (cnt > 0.f) F.dev.occupied |= 1ull << c;
+    F.dev.kbar[c] = cnt > 0.f ? acc[c] / cnt : 0.f;
+  }
+  for (int k = 0; k < 8; ++k) F.dev.env[k] = (float)std::exp(-0.5 * k * k);
+  F.dev.err = F.err;
+  F.dev.stats = F.stats;
+  F.dev.gl = ctx->c.gl;
+  F.dev.root = -1;
+  *out = h;
+  return GF_OK;
+}
+
+gf_status gf_field_free(gf_field* h) {
+  if (!h) return GF_OK;
+  cudaSetDevice(h->f.ctx->device);
+  free_field(h->f);
+  delete h;
+  return GF_OK;
+}
+
+gf_status gf_build_bvh(gf_field* h, gf_stream stream) {
+  if (!h) return fail(GF_EINVAL, "field null");
+  Field& F = h->f;
+  GF_CUDA(cudaSetDevice(F.ctx->device), "cudaSetDevice");
+  if (F.built) return GF_OK;
+  if (F.opts.precision != GF_PREC_FP32)
+    return fail(GF_EINVAL, "reduced-precision records are not available in this build");
+  const int64_t n = F.n;
+  GF_CUDA(cudaMalloc((void**)&F.rec, 64 * n), "alloc records");
+  GF_CUDA(cudaMalloc((void**)&F.nodes, n > 1 ? (n - 1) * sizeof(Node) : 16), "alloc nodes");
+  GF_CUDA(cudaMalloc((void**)&F.sorted_orig, 4 * n), "alloc order");
+  GF_CUDA(build_bvh(F, (cudaStream_t)stream), "build_bvh");
+  cudaFree(F.rec_orig);
+  F.rec_orig = nullptr;
+  cudaFree(F.box_orig);
+  F.box_orig = nullptr;
+  F.built = true;
+  return GF_OK;
+}
+
+gf_status gf_set_lod_mask(gf_field* h, const gf_lod_desc* primary, const gf_lod_desc* nee) {
+  if (!h || !lod_ok(primary) || (nee && !lod_ok(nee))) return fail(GF_EINVAL, "bad lod descriptor");
+  h->f.lod = LodDev{primary->freq_policy, primary->max_band, primary->cone_policy};
+  const gf_lod_desc* n2 = nee ? nee : primary;
+  h->f.lod_nee = LodDev{n2->freq_policy, n2->max_band, n2->cone_policy};
+  return GF_OK;
+}
+
+gf_status gf_transmittance(gf_field* h, const float* o, const float* d, const float* trange,
+                           int64_t n_rays, int mode, int spp, uint64_t seed, float* out_T,
+                           float* out_tau, gf_stream stream) {
+  if (!h || !o || !d || !out_T) return fail(GF_EINVAL, "null argument");
+  Field& F = h->f;
+  if (!F.built) return fail(GF_ESTATE, "gf_build_bvh has not run");
+  if (n_rays < 0 || n_rays > (1ll << 31) - 1) return fail(GF_EINVAL, "n_rays out of range");
+  if (mode != GF_TR_DETERMINISTIC && mode != GF_TR_RATIO_TRACKING) return fail(GF_EINVAL, "bad mode");
+  if (spp < 1 || spp > (1 << 20)) return fail(GF_EINVAL, "spp in [1, 2^20]");
+  if (n_rays == 0) return GF_OK;
+  GF_CUDA(cudaSetDevice(F.ctx->device), "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  size_t n = (size_t)n_rays;
+  gf_status st = ensure_stage(F, 256 * 6 + n * 4 * (3 + 3 + 2 + 1 + 1));
+  if (st) return st;
+  size_t off = 0;
+  void *od, *dd, *td, *Td, *taud;
+  if ((st = stage(F, o, 12 * n, true, s, off, &od)) || (st = stage(F, d, 12 * n, true, s, off, &dd)) ||
+      (st = stage(F, trange, 8 * n, true, s, off, &td)) ||
+      (st = stage(F, out_T, 4 * n, false, s, off, &Td)) ||
+      (st = stage(F, mode == GF_TR_DETERMINISTIC ? out_tau : nullptr, 4 * n, false, s, off, &taud)))
+    return st;
+  TrParams P;
+  P.o = (const float*)od;
+  P.d = (const float*)dd;
+  P.trange = (const float*)td;
+  P.n = n_rays;
+  P.mode = mode;
+  P.spp = spp;
+  P.seed = seed;
+  P.lod = F.lod;
+  P.out_T = (float*)Td;
+  P.out_tau = (float*)taud;
+  P.counter = F.counter;
+  GF_CUDA(launch_transmittance(F, P, s), "transmittance launch");
+  bool sync = false;
+  if (Td != out_T) {
+    GF_CUDA(cudaMemcpyAsync(out_T, Td, 4 * n, cudaMemcpyDeviceToHost, s), "copy T");
+    sync = true;
+  }
+  if (out_tau && taud && taud != out_tau) {
+    GF_CUDA(cudaMemcpyAsync(out_tau, taud, 4 * n, cudaMemcpyDeviceToHost, s), "copy tau");
+    sync = true;
+  }
+  if (sync) GF_CUDA(cudaStreamSynchronize(s), "sync");
+  return GF_OK;
+}
+
+gf_status gf_render(gf_field* h, const gf_camera* camera, const gf_render_opts* opts,
+                    uint64_t seed, float* out_image, gf_stream stream) {
+  if (!h || !out_image) return fail(GF_EINVAL, "null argument");
+  Field& F = h->f;
+  if (!F.built) return fail(GF_ESTATE, "gf_build_bvh has not run");
+  PathParams P;
+  gf_status st = camera_params(camera, opts, seed, F, P);
+  if (st) return st;
+  GF_CUDA(cudaSetDevice(F.ctx->device), "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  size_t bytes = (size_t)P.cam.W * P.cam.H * 4;
+  void* od = out_image;
+  if (!is_device_ptr(out_image)) {
+    if ((st = ensure_stage(F, bytes + 256))) return st;
+    od = F.stage;
+  }
+  GF_CUDA(launch_render(F, P, (float*)od, s), "render launch");
+  if (od != out_image) {
+    GF_CUDA(cudaMemcpyAsync(out_image, od, bytes, cudaMemcpyDeviceToHost, s), "copy image");
+    GF_CUDA(cudaStreamSynchronize(s), "sync");
+  }
+  return GF_OK;
+}
+
+gf_status gf_render_backward(gf_field* h, const gf_camera* camera, const gf_render_opts* opts,
+                             uint64_t seed, const float* dL_dimage, float* grad,
+                             gf_stream stream) {
+  if (!h || !dL_dimage || !grad) return fail(GF_EINVAL, "null argument");
+  Field& F = h->f;
+  if (!F.built) return fail(GF_ESTATE, "gf_build_bvh has not run");
+  PathParams P;
+  gf_status st = camera_params(camera, opts, seed, F, P);
+  if (st) return st;
+  if (opts->integrator != GF_INTEG_TOMO)
+    return fail(GF_EINVAL, "the adjoint covers the tomography integrator");
+  GF_CUDA(cudaSetDevice(F.ctx->device), "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  size_t npix = (size_t)P.cam.W * P.cam.H;
+  size_t gbytes = (size_t)F.n * 15 * 4;
+  if ((st = ensure_stage(F, npix * 4 + gbytes + 512))) return st;
+  size_t off = 0;
+  void *dl, *gd;
+  if ((st = stage(F, dL_dimage, npix * 4, true, s, off, &dl)) ||
+      (st = stage(F, grad, gbytes, false, s, off, &gd)))
+    return st;
+  GF_CUDA(cudaMemsetAsync(gd, 0, gbytes, s), "zero grad");
+  GF_CUDA(launch_tomo_backward(F, P, (const float*)dl, (float*)gd, s), "backward launch");
+  if (gd != grad) {
+    GF_CUDA(cudaMemcpyAsync(grad, gd, gbytes, cudaMemcpyDeviceToHost, s), "copy grad");
+    GF_CUDA(cudaStreamSynchronize(s), "sync");
+  }
+  return GF_OK;
+}
+
+gf_status gf_field_labels(gf_field* h, uint8_t* band, uint8_t* cone, uint8_t* cell,
+                          gf_stream stream) {
+  if (!h) return fail(GF_EINVAL, "field null");
+  Field& F = h->f;
+  GF_CUDA(cudaSetDevice(F.ctx->device), "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  size_t n = (size_t)F.n;
+  if (band) GF_CUDA(cudaMemcpyAsync(band, F.labels, n, cudaMemcpyDefault, s), "labels");
+  if (cone) GF_CUDA(cudaMemcpyAsync(cone, F.labels + n, n, cudaMemcpyDefault, s), "labels");
+  if (cell) GF_CUDA(cudaMemcpyAsync(cell, F.labels + 2 * n, n, cudaMemcpyDefault, s), "labels");
+  GF_CUDA(cudaStreamSynchronize(s), "sync");
+  return GF_OK;
+}
+
+gf_status gf_ray_chords(gf_field* h, const float* o, const float* d, const float* trange,
+                        int64_t n_rays, int cap, int32_t* counts, int32_t* prims, float* t_in,
+                        float* t_out, gf_stream stream) {
+  if (!h || !o || !d || !counts || !prims || cap < 1) return fail(GF_EINVAL, "bad argument");
+  Field& F = h->f;
+  if (!F.built) return fail(GF_ESTATE, "gf_build_bvh has not run");
+  if (!lod_is_deterministic(F.lod)) return fail(GF_EINVAL, "chord lists need a deterministic mask");
+  if (n_rays <= 0) return GF_OK;
+  GF_CUDA(cudaSetDevice(F.ctx->device), "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  size_t n = (size_t)n_rays, nc = n * (size_t)cap;
+  gf_status st = ensure_stage(F, 256 * 8 + n * 4 * 9 + nc * 12);
+  if (st) return st;
+  size_t off = 0;
+  void *od, *dd, *td, *cd, *pd, *tid, *tod;
+  if ((st = stage(F, o, 12 * n, true, s, off, &od)) || (st = stage(F, d, 12 * n, true, s, off, &dd)) ||
+      (st = stage(F, trange, 8 * n, true, s, off, &td)) ||
+      (st = stage(F, counts, 4 * n, false, s, off, &cd)) ||
+      (st = stage(F, prims, 4 * nc, false, s, off, &pd)) ||
+      (st = stage(F, t_in, 4 * nc, false, s, off, &tid)) ||
+      (st = stage(F, t_out, 4 * nc, false, s, off, &tod)))
+    return st;
+  ChordParams P;
+  P.o = (const float*)od;
+  P.d = (const float*)dd;
+  P.trange = (const float*)td;
+  P.n = n_rays;
+  P.cap = cap;
+  P.lod = F.lod;
+  P.counts = (int*)cd;
+  P.prims = (int*)pd;
+  P.tin = (float*)tid;
+  P.tout = (float*)tod;
+  P.counter = F.counter;
+  GF_CUDA(launch_ray_chords(F, P, s), "chords launch");
+  if (cd != counts) GF_CUDA(cudaMemcpyAsync(counts, cd, 4 * n, cudaMemcpyDeviceToHost, s), "copy");
+  if (pd != prims) GF_CUDA(cudaMemcpyAsync(prims, pd, 4 * nc, cudaMemcpyDeviceToHost, s), "copy");
+  if (t_in && tid != t_in) GF_CUDA(cudaMemcpyAsync(t_in, tid, 4 * nc, cudaMemcpyDeviceToHost, s), "copy");
+  if (t_out && tod != t_out) GF_CUDA(cudaMemcpyAsync(t_out, tod, 4 * nc, cudaMemcpyDeviceToHost, s), "copy");
+  GF_CUDA(cudaStreamSynchronize(s), "sync");
+  return GF_OK;
+}
+
+gf_status gf_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n,
+                    gf_stream stream) {
+  if (!ctr || !key || !out || n < 0) return fail(GF_EINVAL, "bad argument");
+  if (n == 0) return GF_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  bool host = !is_device_ptr(ctr) || !is_device_ptr(key) || !is_device_ptr(out);
+  if (!host) {
+    GF_CUDA(launch_philox(ctr, key, out, n, s), "philox launch");
+    return GF_OK;
+  }
+  uint32_t *c = nullptr, *k = nullptr, *r = nullptr;
+  GF_CUDA(cudaMalloc((void**)&c, 16 * n), "alloc");
+  GF_CUDA(cudaMalloc((void**)&k, 8 * n), "alloc");
+  GF_CUDA(cudaMalloc((void**)&r, 16 * n), "alloc");
+  cudaError_t e = cudaMemcpyAsync(c, ctr, 16 * n, cudaMemcpyDefault, s);
+  if (!e) e = cudaMemcpyAsync(k, key, 8 * n, cudaMemcpyDefault, s);
+  if (!e) e = launch_philox(c, k, r, n, s);
+  if (!e) e = cudaMemcpyAsync(out, r, 16 * n, cudaMemcpyDefault, s);
+  if (!e) e = cudaStreamSynchronize(s);
+  cudaFree(c);
+  cudaFree(k);
+  cudaFree(r);
+  if (e) return cuda_fail(e, "gf_philox");
+  return GF_OK;
+}
+
+gf_status gf_get_stats(gf_field* h, gf_stats* out, int reset) {
+  if (!h || !out) return fail(GF_EINVAL, "null argument");
+  Field& F = h->f;
+  GF_CUDA(cudaSetDevice(F.ctx->device), "cudaSetDevice");
+  unsigned long long v[kNumStats];
+  GF_CUDA(cudaDeviceSynchronize(), "sync");
+  GF_CUDA(cudaMemcpy(v, F.stats, sizeof(v), cudaMemcpyDeviceToHost), "stats");
+  out->rays = v[ST_RAYS];
+  out->chords = v[ST_CHORDS];
+  out->evals = v[ST_EVALS];
+  out->nodes = v[ST_NODES];
+  out->points = v[ST_POINTS];
+  out->windows = v[ST_WINDOWS];
+  out->steps = v[ST_STEPS];
+  out->leaves = v[ST_LEAVES];
+  for (int k = 0; k < 5; ++k) out->cycles[k] = v[ST_CYC_TRAV + k];
+  if (reset) GF_CUDA(cudaMemset(F.stats, 0, sizeof(v)), "reset stats");
+  return GF_OK;
+}
+
+gf_status gf_sync(gf_field* h, gf_stream stream) {
+  if (!h) return fail(GF_EINVAL, "field null");
+  Field& F = h->f;
+  GF_CUDA(cudaSetDevice(F.ctx->device), "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  GF_CUDA(cudaStreamSynchronize(s), "stream sync");
+  int err = 0;
+  GF_CUDA(cudaMemcpy(&err, F.err, 4, cudaMemcpyDeviceToHost), "read error word");
+  if (!err) return GF_OK;
+  GF_CUDA(cudaMemset(F.err, 0, 4), "clear error word");
+  if (err & (ERR_STACK | ERR_WINDOW | ERR_POINTS))
+    return fail(GF_EOVERFLOW, "device buffer overflow (code " + std::to_string(err) + ")");
+  if (err & ERR_GUARD) return fail(GF_ETIMEOUT, "bounded device loop gave up");
+  return fail(GF_EINVAL, "device-side input error (code " + std::to_string(err) + ")");
+}
+
+gf_status gf_field_info(gf_field* h, int64_t* n, int* precision, uint64_t* occupied) {
+  if (!h) return fail(GF_EINVAL, "field null");
+  if (n) *n = h->f.n;
+  if (precision) *precision = h->f.opts.precision;
+  if (occupied) *occupied = h->f.dev.occupied;
+  return GF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,383 @@
+// gf_bvh.cu -- primitive packing (load-time binning of Sec. 4.6) and the BVH
+// over the k-sigma ellipsoid bounds (Sec. 3): Morton codes under a cell
+// prefix, radix sort, Karras's binary radix tree, bottom-up box/mask refit.
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include <cub/device/device_radix_sort.cuh>
+
+#include "gf_host.h"
+
+namespace gf {
+
+// ---------------------------------------------------------------------------
+// pack: parameters -> Sigma^-1, world carrier, amplitude, labels, boxes
+// ---------------------------------------------------------------------------
+struct PackArgs {
+  gf_params p;
+  int weight_mode, omega_frame;
+  float ksig;
+  float axes[kCones][3];
+  float4* rec;
+  float* box;
+  float* kw;
+  uint8_t* labels;  // band[N], cone[N], cell[N]
+  float* cell_acc;  // sum |k_W| [64], count [64]
+  int* err;
+};
+
+__global__ void k_pack(const __grid_constant__ PackArgs A) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.p.n) return;
+  float mu[3], q[4], ls[3], om_in[3];
+  for (int j = 0; j < 3; ++j) {
+    mu[j] = A.p.mu[3 * i + j];
+    ls[j] = A.p.log_scale[3 * i + j];
+    om_in[j] = A.p.omega[3 * i + j];
+  }
+  for (int j = 0; j < 4; ++j) q[j] = A.p.quat[4 * i + j];
+  float phi = A.p.phase[i], wt = A.p.weight[i];
+  bool finite = isfinite(phi) && isfinite(wt);
+  for (int j = 0; j < 3; ++j) finite = finite && isfinite(mu[j]) && isfinite(ls[j]) && isfinite(om_in[j]);
+  for (int j = 0; j < 4; ++j) finite = finite && isfinite(q[j]);
+  float qn = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  if (!finite || !(qn > 0.f)) {
+    atomicOr(A.err, ERR_INPUT);
+    qn = 1.f;
+    q[0] = 1.f; q[1] = q[2] = q[3] = 0.f;
+  }
+  float w = q[0] / qn, x = q[1] / qn, y = q[2] / qn, z = q[3] / qn;
+  float R[3][3] = {{1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y)},
+                   {2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x)},
+                   {2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)}};
+  float s[3] = {expf(ls[0]), expf(ls[1]), expf(ls[2])};
+  float is2[3] = {1.f / (s[0] * s[0]), 1.f / (s[1] * s[1]), 1.f / (s[2] * s[2])};
+  float P[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      P[a][b] = R[a][0] * R[b][0] * is2[0] + R[a][1] * R[b][1] * is2[1] + R[a][2] * R[b][2] * is2[2];
+  float om[3], kw[3];
+  if (A.omega_frame == GF_OMEGA_LOCAL) {
+    for (int a = 0; a < 3; ++a)
+      om[a] = R[a][0] * om_in[0] / s[0] + R[a][1] * om_in[1] / s[1] + R[a][2] * om_in[2] / s[2];
+    for (int j = 0; j < 3; ++j) kw[j] = om_in[j];
+  } else {
+    for (int a = 0; a < 3; ++a) om[a] = om_in[a];
+    for (int j = 0; j < 3; ++j) kw[j] = s[j] * (R[0][j] * om[0] + R[1][j] * om[1] + R[2][j] * om[2]);
+  }
+  float amp = wt;
+  if (A.weight_mode == GF_WEIGHT_NORMALIZED) amp = wt / (15.749609945722419f * s[0] * s[1] * s[2]);
+  // band: caller's octave label, else floor(log2(1 + |omega|/(2 pi))) decided in FP32
+  int band;
+  if (A.p.band) {
+    band = A.p.band[i];
+    if (band > 7) {
+      atomicOr(A.err, ERR_INPUT);
+      band = 7;
+    }
+  } else {
+    float n2 = __fadd_rn(__fadd_rn(__fmul_rn(om[0], om[0]), __fmul_rn(om[1], om[1])), __fmul_rn(om[2], om[2]));
+    float onef = __fadd_rn(1.0f, __fdiv_rn(__fsqrt_rn(n2), 6.28318530717958647692f));
+    band = 0;
+    for (int j = 1; j <= 7; ++j)
+      if (onef >= (float)(1 << j)) band = j;
+  }
+  // orientation bin: argmax |omega . o_k| in FP32, ties to the lowest k
+  int cone = 0;
+  if (band > 0) {
+    float bv = -1.f;
+    for (int k = 0; k < kCones; ++k) {
+      float d = fabsf(__fadd_rn(__fadd_rn(__fmul_rn(om[0], A.axes[k][0]), __fmul_rn(om[1], A.axes[k][1])),
+                                __fmul_rn(om[2], A.axes[k][2])));
+      if (d > bv) {
+        bv = d;
+        cone = k;
+      }
+    }
+  }
+  int cell = band == 0 ? 0 : 1 + kCones * (band - 1) + cone;
+  float4* r = A.rec + 4 * i;
+  r[0] = make_float4(mu[0], mu[1], mu[2], amp);
+  r[1] = make_float4(P[0][0], P[0][1], P[0][2], P[1][1]);
+  r[2] = make_float4(P[1][2], P[2][2], phi, __uint_as_float((uint32_t)cell));
+  r[3] = make_float4(om[0], om[1], om[2], __uint_as_float((uint32_t)i));
+  // box of the k-sigma ellipsoid: half-extent k sqrt(Sigma_jj), padded
+  for (int a = 0; a < 3; ++a) {
+    float sjj = R[a][0] * R[a][0] * s[0] * s[0] + R[a][1] * R[a][1] * s[1] * s[1] +
+                R[a][2] * R[a][2] * s[2] * s[2];
+    float hw = A.ksig * sqrtf(sjj);
+    float pad = 1e-5f * hw + 1e-6f * (1.f + fabsf(mu[a]));
+    A.box[6 * i + a] = mu[a] - hw - pad;
+    A.box[6 * i + 3 + a] = mu[a] + hw + pad;
+  }
+  float kn = sqrtf(kw[0] * kw[0] + kw[1] * kw[1] + kw[2] * kw[2]);
+  A.kw[i] = kn;
+  A.labels[i] = (uint8_t)band;
+  A.labels[A.p.n + i] = (uint8_t)cone;
+  A.labels[2 * A.p.n + i] = (uint8_t)cell;
+  atomicAdd(A.cell_acc + cell, kn);
+  atomicAdd(A.cell_acc + 64 + cell, 1.f);
+}
+
+cudaError_t launch_pack(Field& F, const gf_params& P, cudaStream_t s) {
+  PackArgs A;
+  A.p = P;
+  A.weight_mode = F.opts.weight_mode;
+  A.omega_frame = F.opts.omega_frame;
+  A.ksig = F.opts.k_sigma;
+  for (int k = 0; k < kCones; ++k)
+    for (int j = 0; j < 3; ++j) A.axes[k][j] = F.dev.axes[k][j];
+  A.rec = F.rec_orig;
+  A.box = F.box_orig;
+  A.kw = F.kw_orig;
+  A.labels = F.labels;
+  A.cell_acc = F.cell_acc;
+  A.err = F.err;
+  int64_t blocks = (P.n + 127) / 128;
+  k_pack<<<(unsigned)blocks, 128, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// BVH build
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned int ord_enc(float f) {
+  unsigned int u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord_dec(unsigned int u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
+}
+
+// bounds[0..2] box min, [3..5] box max, [6..8] centre min, [9..11] centre max (ordered ints)
+__global__ void k_bounds(const float* box, const float4* rec, int64_t n, unsigned int* bounds) {
+  float v[12];
+  for (int j = 0; j < 3; ++j) {
+    v[j] = INFINITY; v[3 + j] = -INFINITY; v[6 + j] = INFINITY; v[9 + j] = -INFINITY;
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float4 r0 = rec[4 * i];
+    float m[3] = {r0.x, r0.y, r0.z};
+    for (int j = 0; j < 3; ++j) {
+      v[j] = fminf(v[j], box[6 * i + j]);
+      v[3 + j] = fmaxf(v[3 + j], box[6 * i + 3 + j]);
+      v[6 + j] = fminf(v[6 + j], m[j]);
+      v[9 + j] = fmaxf(v[9 + j], m[j]);
+    }
+  }
+  for (int j = 0; j < 12; ++j) {
+    float x = v[j];
+    bool mn = (j < 3) || (j >= 6 && j < 9);
+    for (int o = 16; o > 0; o >>= 1) {
+      float y = __shfl_xor_sync(kFull, x, o);
+      x = mn ? fminf(x, y) : fmaxf(x, y);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      if (mn) atomicMin(bounds + j, ord_enc(x));
+      else atomicMax(bounds + j, ord_enc(x));
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned int spread10(unsigned int x) {
+  x &= 1023u;
+  x = (x | (x << 16)) & 0x030000FFu;
+  x = (x | (x << 8)) & 0x0300F00Fu;
+  x = (x | (x << 4)) & 0x030C30C3u;
+  x = (x | (x << 2)) & 0x09249249u;
+  return x;
+}
+
+__global__ void k_morton(const float4* rec, int64_t n, const unsigned int* bounds,
+                         unsigned long long* keys, int* idx) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float lo[3], hi[3];
+  for (int j = 0; j < 3; ++j) {
+    lo[j] = ord_dec(bounds[6 + j]);
+    hi[j] = ord_dec(bounds[9 + j]);
+  }
+  float4 r0 = rec[4 * i];
+  uint32_t cell = __float_as_uint(rec[4 * i + 2].w);
+  float m[3] = {r0.x, r0.y, r0.z};
+  unsigned int c[3];
+  for (int j = 0; j < 3; ++j) {
+    float ext = hi[j] - lo[j];
+    float u = ext > 0.f ? (m[j] - lo[j]) / ext : 0.5f;
+    u = fminf(fmaxf(u, 0.f), 1.f);
+    c[j] = (unsigned int)fminf(u * 1024.f, 1023.f);
+  }
+  unsigned int mc = (spread10(c[0]) << 2) | (spread10(c[1]) << 1) | spread10(c[2]);
+  keys[i] = ((unsigned long long)cell << 30) | mc;
+  idx[i] = (int)i;
+}
+
+__global__ void k_gather(const float4* rec_in, const float* box_in, const int* idx, int64_t n,
+                         float4* rec_out, float* box_out, int* sorted_orig) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  int i = idx[j];
+  for (int k = 0; k < 4; ++k) rec_out[4 * j + k] = rec_in[4 * (int64_t)i + k];
+  for (int k = 0; k < 6; ++k) box_out[6 * j + k] = box_in[6 * (int64_t)i + k];
+  sorted_orig[j] = i;
+}
+
+__device__ __forceinline__ int delta_key(const unsigned long long* k, int64_t n, int64_t i, int64_t j) {
+  if (j < 0 || j >= n) return -1;
+  unsigned long long a = k[i], b = k[j];
+  if (a == b) return 64 + __clz((unsigned int)(i ^ j));
+  return __clzll(a ^ b);
+}
+
+// Karras (HPG 2012): internal node i covers [min(i,j), max(i,j)], split at gamma
+__global__ void k_karras(const unsigned long long* keys, int64_t n, Node* nodes, int* leaf_parent) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  int d = (delta_key(keys, n, i, i + 1) - delta_key(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+  int dmin = delta_key(keys, n, i, i - d);
+  int64_t lmax = 2;
+  while (delta_key(keys, n, i, i + lmax * d) > dmin) lmax *= 2;
+  int64_t l = 0;
+  for (int64_t t = lmax / 2; t >= 1; t /= 2)
+    if (delta_key(keys, n, i, i + (l + t) * d) > dmin) l += t;
+  int64_t j = i + l * d;
+  int dnode = delta_key(keys, n, i, j);
+  int64_t s = 0;
+  int64_t t = l;
+  do {
+    t = (t + 1) / 2;
+    if (delta_key(keys, n, i, i + (s + t) * d) > dnode) s += t;
+  } while (t > 1);
+  int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
+  int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+  int left = (lo == gamma) ? ~(int)gamma : (int)gamma;
+  int right = (hi == gamma + 1) ? ~(int)(gamma + 1) : (int)(gamma + 1);
+  nodes[i].d.x = left;
+  nodes[i].d.y = right;
+  if (left >= 0) nodes[left].d.z = (int)i; else leaf_parent[gamma] = (int)i;
+  if (right >= 0) nodes[right].d.z = (int)i; else leaf_parent[gamma + 1] = (int)i;
+  if (i == 0) nodes[0].d.z = -1;
+}
+
+__device__ __forceinline__ void write_slot(Node* nd, int slot, const float* b, unsigned long long m) {
+  volatile float* a = reinterpret_cast<volatile float*>(&nd->a);
+  volatile unsigned int* e = reinterpret_cast<volatile unsigned int*>(&nd->e);
+  if (slot == 0) {
+    a[0] = b[0]; a[1] = b[1]; a[2] = b[2]; a[3] = b[3]; a[4] = b[4]; a[5] = b[5];
+    e[0] = (unsigned int)m; e[1] = (unsigned int)(m >> 32);
+  } else {
+    a[6] = b[0]; a[7] = b[1]; a[8] = b[2]; a[9] = b[3]; a[10] = b[4]; a[11] = b[5];
+    e[2] = (unsigned int)m; e[3] = (unsigned int)(m >> 32);
+  }
+}
+
+// bottom-up refit: the second child to arrive at a node merges both slots
+__global__ void k_refit(const float* box, const float4* rec, int64_t n, Node* nodes,
+                        const int* leaf_parent, int* flags) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  float b[6];
+  for (int k = 0; k < 6; ++k) b[k] = box[6 * j + k];
+  unsigned long long m = 1ull << (__float_as_uint(rec[4 * j + 2].w) & 63u);
+  int child = ~(int)j;
+  int node = leaf_parent[j];
+  for (int guard = 0; node >= 0 && guard < 4096; ++guard) {
+    Node* nd = nodes + node;
+    int slot = (nd->d.x == child) ? 0 : 1;
+    write_slot(nd, slot, b, m);
+    __threadfence();
+    if (atomicAdd(flags + node, 1) == 0) return;
+    __threadfence();
+    volatile float* a = reinterpret_cast<volatile float*>(&nd->a);
+    volatile unsigned int* e = reinterpret_cast<volatile unsigned int*>(&nd->e);
+    b[0] = fminf(a[0], a[6]); b[1] = fminf(a[1], a[7]); b[2] = fminf(a[2], a[8]);
+    b[3] = fmaxf(a[3], a[9]); b[4] = fmaxf(a[4], a[10]); b[5] = fmaxf(a[5], a[11]);
+    m = ((unsigned long long)e[0] | ((unsigned long long)e[1] << 32)) |
+        ((unsigned long long)e[2] | ((unsigned long long)e[3] << 32));
+    child = node;
+    node = nd->d.z;
+  }
+}
+
+static cudaError_t dalloc(void** p, size_t bytes) { return cudaMalloc(p, bytes ? bytes : 16); }
+
+cudaError_t build_bvh(Field& F, cudaStream_t s) {
+  const int64_t n = F.n;
+  cudaError_t e = cudaSuccess;
+  unsigned int* bounds = nullptr;
+  unsigned long long *keys = nullptr, *keys2 = nullptr;
+  int *idx = nullptr, *idx2 = nullptr, *leaf_parent = nullptr, *flags = nullptr;
+  float* box_sorted = nullptr;
+  void* tmp = nullptr;
+  size_t tmp_bytes = 0;
+  unsigned int hb[12];
+#define GF_TRY(x) do { e = (x); if (e != cudaSuccess) goto done; } while (0)
+  GF_TRY(dalloc((void**)&bounds, 12 * sizeof(unsigned int)));
+  GF_TRY(dalloc((void**)&keys, n * sizeof(unsigned long long)));
+  GF_TRY(dalloc((void**)&keys2, n * sizeof(unsigned long long)));
+  GF_TRY(dalloc((void**)&idx, n * sizeof(int)));
+  GF_TRY(dalloc((void**)&idx2, n * sizeof(int)));
+  GF_TRY(dalloc((void**)&leaf_parent, n * sizeof(int)));
+  GF_TRY(dalloc((void**)&flags, n * sizeof(int)));
+  GF_TRY(dalloc((void**)&box_sorted, n * 6 * sizeof(float)));
+  {
+    unsigned int init[12];
+    for (int j = 0; j < 12; ++j) {
+      bool mn = (j < 3) || (j >= 6 && j < 9);
+      init[j] = mn ? 0xFFFFFFFFu : 0u;
+    }
+    GF_TRY(cudaMemcpyAsync(bounds, init, sizeof(init), cudaMemcpyHostToDevice, s));
+  }
+  {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    k_bounds<<<blocks, 256, 0, s>>>(F.box_orig, F.rec_orig, n, bounds);
+    GF_TRY(cudaGetLastError());
+    k_morton<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(F.rec_orig, n, bounds, keys, idx);
+    GF_TRY(cudaGetLastError());
+  }
+  GF_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys, keys2, idx, idx2, (int)n, 0, 36, s));
+  GF_TRY(dalloc(&tmp, tmp_bytes));
+  GF_TRY(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys, keys2, idx, idx2, (int)n, 0, 36, s));
+  k_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(F.rec_orig, F.box_orig, idx2, n, F.rec,
+                                                      box_sorted, F.sorted_orig);
+  GF_TRY(cudaGetLastError());
+  if (n >= 2) {
+    GF_TRY(cudaMemsetAsync(F.nodes, 0, (n - 1) * sizeof(Node), s));
+    GF_TRY(cudaMemsetAsync(flags, 0, n * sizeof(int), s));
+    k_karras<<<(unsigned)((n - 1 + 255) / 256), 256, 0, s>>>(keys2, n, F.nodes, leaf_parent);
+    GF_TRY(cudaGetLastError());
+    k_refit<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(box_sorted, F.rec, n, F.nodes, leaf_parent, flags);
+    GF_TRY(cudaGetLastError());
+  }
+  GF_TRY(cudaMemcpyAsync(hb, bounds, sizeof(hb), cudaMemcpyDeviceToHost, s));
+  GF_TRY(cudaStreamSynchronize(s));
+  {
+    auto dec = [](unsigned int u) {
+      unsigned int b = (u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u;
+      float f;
+      memcpy(&f, &b, 4);
+      return f;
+    };
+    F.dev.lo = make_float3(dec(hb[0]), dec(hb[1]), dec(hb[2]));
+    F.dev.hi = make_float3(dec(hb[3]), dec(hb[4]), dec(hb[5]));
+  }
+  F.dev.rec = F.rec;
+  F.dev.nodes = F.nodes;
+  F.dev.root = n >= 2 ? 0 : -1;
+done:
+#undef GF_TRY
+  cudaFree(bounds);
+  cudaFree(keys);
+  cudaFree(keys2);
+  cudaFree(idx);
+  cudaFree(idx2);
+  cudaFree(leaf_parent);
+  cudaFree(flags);
+  cudaFree(box_sorted);
+  cudaFree(tmp);
+  return e;
+}
+
+}  // namespace gf

@@ -1,0 +1,381 @@
+// gf_device.cuh -- device-side data structures and helpers of the Gabor-field
+// renderer (sm_103a).  Notation follows arXiv 2602.05081: mu, Sigma, omega,
+// the per-ray quadratic q(t) = a t^2 + 2 beta t + gamma and phase B t + delta
+// of App. A.1, the k-sigma support of Sec. 3.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gf {
+
+constexpr int kMaxCells = 64;
+constexpr int kCones = 8;
+constexpr uint32_t kNoPrim = 0xFFFFFFFFu;
+constexpr unsigned kFull = 0xffffffffu;
+
+enum : uint32_t {
+  TAG_CAMERA = 1,
+  TAG_MASK = 2,
+  TAG_TRACK = 3,
+  TAG_NEE = 4,
+  TAG_NEE_MASK = 5,
+  TAG_SCATTER = 6
+};
+
+enum : int { ERR_STACK = 1, ERR_WINDOW = 2, ERR_POINTS = 4, ERR_GUARD = 8, ERR_INPUT = 16 };
+
+// Binary BVH node holding the boxes, children and cell masks of both children
+// (one 80-byte fetch tests two boxes).  child >= 0: internal node; child < 0:
+// leaf of the sorted primitive ~child.
+struct __align__(16) Node {
+  float4 a;  // c0.lo.xyz, c0.hi.x
+  float4 b;  // c0.hi.yz, c1.lo.xy
+  float4 c;  // c1.lo.z, c1.hi.xyz
+  int4 d;    // child0, child1, parent (build only), unused
+  uint4 e;   // cell mask of child0 (lo, hi), child1 (lo, hi)
+};
+
+struct LodDev {
+  int freq_policy, max_band, cone_policy;
+};
+
+// Everything a kernel needs to read a packed field; passed by value.
+struct DevField {
+  const float4* rec;       // FP32 records: 4 x float4 per primitive, BVH order
+  const uint4* rec16;      // FP16/BF16 records: 2 x uint4 per primitive, BVH order
+  const Node* nodes;
+  int64_t n;
+  int root;                // internal root node, -1 when n == 1
+  int precision;           // 0 FP32, 1 FP16, 2 BF16
+  float ksig, k2;
+  float3 lo, hi;           // scene bounds (union of all ellipsoid boxes)
+  unsigned long long occupied;
+  float kbar[kMaxCells];   // mean |k_W| per cell
+  float axes[kCones][3];   // orientation-bin axes
+  float env[8];            // exp(-n^2/2), n = 0..7
+  float dec_scale[3];      // FP16 record: cell box extent per unit of u16 code (unused)
+  const float* gl;         // Gauss-Legendre nodes then weights (2 x kGLTotal)
+  int* err;
+  unsigned long long* stats;  // rays, chords, evals, nodes, points
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11), written from the published round
+// function: 10 rounds, Weyl key bump between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+__device__ __forceinline__ uint4 rng4(uint64_t seed, uint32_t draw, uint32_t prim, uint32_t ray,
+                                      uint32_t word) {
+  return philox(make_uint4(draw, prim, ray, word),
+                make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+__device__ __forceinline__ float u01(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+__device__ __forceinline__ uint32_t stream_word(uint32_t sample, uint32_t bounce, uint32_t tag) {
+  return (sample << 12) | ((bounce & 15u) << 8) | (tag & 255u);
+}
+
+// ---------------------------------------------------------------------------
+// fast math: MUFU exp2 and cos
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float ex2f(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float cosf_fast(float x) { return __cosf(x); }
+
+// phase reduction to [-pi, pi]: x - 2 pi rint(x / 2 pi) with 2 pi split into a
+// short head (exact product with small integers) and a tail (Cody-Waite)
+__device__ __forceinline__ float reduce_2pi(float x) {
+  const float kInv2Pi = 0.15915494309189535f;
+  const float kHead = 6.28125f;                 // 2 pi rounded to 7 significant bits
+  const float kTail = 1.9353071795864769e-3f;   // 2 pi - kHead
+  float k = rintf(x * kInv2Pi);
+  float r = fmaf(-k, kHead, x);
+  return fmaf(-k, kTail, r);
+}
+
+constexpr float kLog2e = 1.4426950408889634f;
+
+// ---------------------------------------------------------------------------
+// warp helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  return x;
+}
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// Neumaier accumulation of x into (s, c)
+__device__ __forceinline__ void neumaier_add(float& s, float& c, float x) {
+  float t = __fadd_rn(s, x);
+  if (fabsf(s) >= fabsf(x))
+    c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, t), x));
+  else
+    c = __fadd_rn(c, __fadd_rn(__fsub_rn(x, t), s));
+  s = t;
+}
+// compensated warp sum of (s + c) pairs; every lane receives the total
+__device__ __forceinline__ float warp_sum_comp(float s, float c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float so = __shfl_xor_sync(kFull, s, o), co = __shfl_xor_sync(kFull, c, o);
+    float t, e;
+    two_sum(s, so, t, e);
+    s = t;
+    c = __fadd_rn(__fadd_rn(c, co), e);
+  }
+  return __fadd_rn(s, c);
+}
+
+// ---------------------------------------------------------------------------
+// records
+// FP32 record (64 B): {mu.xyz, A}, {P00, P01, P02, P11}, {P12, P22, phi, cell},
+// {omega.xyz, orig index}, P = Sigma^-1.
+// ---------------------------------------------------------------------------
+struct Prim {
+  float3 mu;
+  float A;
+  float p00, p01, p02, p11, p12, p22;
+  float phi;
+  uint32_t cell;
+  float3 om;
+  uint32_t orig;
+};
+
+__device__ __forceinline__ Prim load_prim(const DevField& F, int j) {
+  Prim P;
+  const float4* r = F.rec + 4 * (int64_t)j;
+  float4 r0 = __ldg(r), r1 = __ldg(r + 1), r2 = __ldg(r + 2), r3 = __ldg(r + 3);
+  P.mu = make_float3(r0.x, r0.y, r0.z);
+  P.A = r0.w;
+  P.p00 = r1.x; P.p01 = r1.y; P.p02 = r1.z; P.p11 = r1.w;
+  P.p12 = r2.x; P.p22 = r2.y; P.phi = r2.z; P.cell = __float_as_uint(r2.w);
+  P.om = make_float3(r3.x, r3.y, r3.z);
+  P.orig = __float_as_uint(r3.w);
+  return P;
+}
+
+// Per-(ray, primitive) chord in coordinates dt = t - tc around a reference tc
+// near the envelope peak.  Along the ray the kernel is
+//   A exp(-(a dt^2 + 2 b dt + g)/2) cos(B dt + delta)
+// (App. A.1 with the origin moved to tc); the chord is where the quadratic is
+// <= k^2, clipped to the ray's [tmin, tmax].
+struct Chord {
+  float tc;          // reference t (absolute)
+  float dtin, dtout; // clipped chord, relative to tc
+  float a, b, g;     // quadratic coefficients in dt
+  float B, delta;    // phase slope and phase at tc, delta in [-pi, pi]
+  float absA;        // |A| (the sign of A is folded into delta)
+  float qmin, dts;   // minimum of the quadratic and its position (relative to tc)
+  float hw;          // half-width of the unclipped chord
+  float3 p;          // o + tc v - mu (compensated)
+  uint32_t cell, orig;
+};
+
+__device__ __forceinline__ bool chord_setup(const Prim& P, float3 o, float3 v, float tmin,
+                                            float tmax, float k2, Chord& c) {
+  // u = Sigma^-1 v, a = v^T Sigma^-1 v
+  float ux = fmaf(P.p00, v.x, fmaf(P.p01, v.y, P.p02 * v.z));
+  float uy = fmaf(P.p01, v.x, fmaf(P.p11, v.y, P.p12 * v.z));
+  float uz = fmaf(P.p02, v.x, fmaf(P.p12, v.y, P.p22 * v.z));
+  float a = fmaf(v.x, ux, fmaf(v.y, uy, v.z * uz));
+  // d0 = o - mu, error-free split; reference tc = -(d0 . u)/a
+  float d0x = __fsub_rn(o.x, P.mu.x), d0y = __fsub_rn(o.y, P.mu.y), d0z = __fsub_rn(o.z, P.mu.z);
+  float tc = -fmaf(d0x, ux, fmaf(d0y, uy, d0z * uz)) / a;
+  // p = (o - mu) + tc v with compensated arithmetic (positions ~1, offsets ~sigma)
+  float ex, ey, ez;
+  {
+    float s, bb;
+    s = d0x; bb = __fsub_rn(s, o.x); ex = __fsub_rn(__fsub_rn(o.x, __fsub_rn(s, bb)), __fadd_rn(P.mu.x, bb));
+    s = d0y; bb = __fsub_rn(s, o.y); ey = __fsub_rn(__fsub_rn(o.y, __fsub_rn(s, bb)), __fadd_rn(P.mu.y, bb));
+    s = d0z; bb = __fsub_rn(s, o.z); ez = __fsub_rn(__fsub_rn(o.z, __fsub_rn(s, bb)), __fadd_rn(P.mu.z, bb));
+  }
+  float prx = __fmul_rn(tc, v.x), pry = __fmul_rn(tc, v.y), prz = __fmul_rn(tc, v.z);
+  float erx = fmaf(tc, v.x, -prx), ery = fmaf(tc, v.y, -pry), erz = fmaf(tc, v.z, -prz);
+  float px = __fadd_rn(__fadd_rn(d0x, prx), __fadd_rn(ex, erx));
+  float py = __fadd_rn(__fadd_rn(d0y, pry), __fadd_rn(ey, ery));
+  float pz = __fadd_rn(__fadd_rn(d0z, prz), __fadd_rn(ez, erz));
+  // b = v^T Sigma^-1 p (~0), g = p^T Sigma^-1 p
+  float b = fmaf(ux, px, fmaf(uy, py, uz * pz));
+  float qx = fmaf(P.p00, px, fmaf(P.p01, py, P.p02 * pz));
+  float qy = fmaf(P.p01, px, fmaf(P.p11, py, P.p12 * pz));
+  float qz = fmaf(P.p02, px, fmaf(P.p12, py, P.p22 * pz));
+  float g = fmaf(px, qx, fmaf(py, qy, pz * qz));
+  float dts = -b / a;
+  float qmin = fmaf(b, dts, g);
+  float disc = k2 - qmin;
+  if (!(disc > 0.0f)) return false;
+  float hw = sqrtf(disc / a);
+  float lo = fmaxf(dts - hw, tmin - tc);
+  float hi = fminf(dts + hw, tmax - tc);
+  if (!(lo < hi)) return false;
+  c.tc = tc;
+  c.dtin = lo;
+  c.dtout = hi;
+  c.a = a;
+  c.b = b;
+  c.g = g;
+  c.B = fmaf(P.om.x, v.x, fmaf(P.om.y, v.y, P.om.z * v.z));
+  float ph = fmaf(P.om.x, px, fmaf(P.om.y, py, fmaf(P.om.z, pz, P.phi)));
+  if (P.A < 0.0f) ph += 3.14159265358979f;
+  c.delta = reduce_2pi(ph);
+  c.absA = fabsf(P.A);
+  c.qmin = qmin;
+  c.dts = dts;
+  c.hw = hw;
+  c.p = make_float3(px, py, pz);
+  c.cell = P.cell;
+  c.orig = P.orig;
+  return true;
+}
+
+// ray-box slab test over [t0, t1]
+__device__ __forceinline__ bool slab(float3 o, float3 inv, float lx, float ly, float lz, float hx,
+                                     float hy, float hz, float t0, float t1) {
+  float tx0 = (lx - o.x) * inv.x, tx1 = (hx - o.x) * inv.x;
+  float ty0 = (ly - o.y) * inv.y, ty1 = (hy - o.y) * inv.y;
+  float tz0 = (lz - o.z) * inv.z, tz1 = (hz - o.z) * inv.z;
+  float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), t0));
+  float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), t1));
+  return tn <= tf;
+}
+
+__device__ __forceinline__ float3 safe_inv(float3 v) {
+  const float tiny = 1e-30f;
+  float x = fabsf(v.x) < tiny ? copysignf(tiny, v.x) : v.x;
+  float y = fabsf(v.y) < tiny ? copysignf(tiny, v.y) : v.y;
+  float z = fabsf(v.z) < tiny ? copysignf(tiny, v.z) : v.z;
+  return make_float3(1.0f / x, 1.0f / y, 1.0f / z);
+}
+
+// entry/exit of the scene box; returns false if missed
+__device__ __forceinline__ bool scene_span(const DevField& F, float3 o, float3 inv, float tmin,
+                                           float tmax, float& t0, float& t1) {
+  float tx0 = (F.lo.x - o.x) * inv.x, tx1 = (F.hi.x - o.x) * inv.x;
+  float ty0 = (F.lo.y - o.y) * inv.y, ty1 = (F.hi.y - o.y) * inv.y;
+  float tz0 = (F.lo.z - o.z) * inv.z, tz1 = (F.hi.z - o.z) * inv.z;
+  t0 = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tmin));
+  t1 = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+  return t0 <= t1;
+}
+
+__device__ __forceinline__ void set_err(const DevField& F, int code) { atomicOr(F.err, code); }
+
+// ---------------------------------------------------------------------------
+// Per-thread traversal of one ray under a cell mask: every lane of a warp owns
+// its own ray, so a warp advances 32 independent rays per step.  One 80-byte
+// fetch gives both child boxes of a node; test(tn, tf) decides whether a child
+// whose box spans [tn, tf] along the ray can matter (the test may tighten as
+// the traversal proceeds); hit leaves go to leaf(j) at once; the nearer
+// internal child is visited first and the other pushed on a per-thread stack
+// together with its entry t, re-tested when popped.
+// ---------------------------------------------------------------------------
+constexpr int kStack = 64;
+
+__device__ __forceinline__ void slab_interval(float3 o, float3 inv, float lx, float ly, float lz,
+                                              float hx, float hy, float hz, float& tn, float& tf) {
+  float tx0 = (lx - o.x) * inv.x, tx1 = (hx - o.x) * inv.x;
+  float ty0 = (ly - o.y) * inv.y, ty1 = (hy - o.y) * inv.y;
+  float tz0 = (lz - o.z) * inv.z, tz1 = (hz - o.z) * inv.z;
+  tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fminf(tz0, tz1));
+  tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
+}
+
+template <class TestFn, class LeafFn>
+__device__ __forceinline__ void traverse_ray(const DevField& F, float3 o, float3 inv,
+                                             unsigned long long mask, TestFn& test, LeafFn& leaf,
+                                             unsigned long long& nvis,
+                                             unsigned long long& nleaves) {
+  if (F.root < 0) {
+    ++nleaves;
+    leaf(0);
+    return;
+  }
+  int st_node[kStack];
+  float st_tn[kStack];
+  int sp = 0;
+  int node = F.root;           // next internal node, -1 once the tree is exhausted
+  int pend0 = -1, pend1 = -1;  // queued leaves
+  // each internal node is fetched at most once per traversal
+  const long long max_steps = F.n + 64;
+  long long steps = 0;
+  for (;;) {
+    // while-while: traverse until a leaf is queued or the tree is exhausted; the
+    // lanes of a warp reconverge after this loop and process their leaves together
+    while (node >= 0 && pend0 < 0) {
+      if (++steps > max_steps) {
+        set_err(F, ERR_GUARD);
+        node = -1;
+        break;
+      }
+      const Node* N = F.nodes + node;
+      const float4 a = __ldg(&N->a), b = __ldg(&N->b), c = __ldg(&N->c);
+      const int4 d = __ldg(&N->d);
+      const uint4 e = __ldg(&N->e);
+      ++nvis;
+      const unsigned long long m0 = (unsigned long long)e.x | ((unsigned long long)e.y << 32);
+      const unsigned long long m1 = (unsigned long long)e.z | ((unsigned long long)e.w << 32);
+      float tn0, tf0, tn1, tf1;
+      slab_interval(o, inv, a.x, a.y, a.z, a.w, b.x, b.y, tn0, tf0);
+      slab_interval(o, inv, b.z, b.w, c.x, c.y, c.z, c.w, tn1, tf1);
+      const bool h0 = (m0 & mask) && test(tn0, tf0);
+      const bool h1 = (m1 & mask) && test(tn1, tf1);
+      const int c0 = d.x, c1 = d.y;
+      if (h0 && c0 < 0) pend0 = ~c0;
+      if (h1 && c1 < 0) {
+        if (pend0 < 0) pend0 = ~c1;
+        else pend1 = ~c1;
+      }
+      const bool g0 = h0 && c0 >= 0, g1 = h1 && c1 >= 0;
+      if (g0 && g1) {
+        const bool first0 = tn0 <= tn1;
+        if (sp < kStack) {
+          st_node[sp] = first0 ? c1 : c0;
+          st_tn[sp] = first0 ? tn1 : tn0;
+          ++sp;
+        } else {
+          set_err(F, ERR_STACK);
+        }
+        node = first0 ? c0 : c1;
+      } else if (g0) {
+        node = c0;
+      } else if (g1) {
+        node = c1;
+      } else {
+        // pop, skipping entries the (possibly tightened) test now rejects
+        node = -1;
+        while (sp > 0) {
+          --sp;
+          if (test(st_tn[sp], INFINITY)) {
+            node = st_node[sp];
+            break;
+          }
+        }
+      }
+    }
+    if (pend0 < 0) return;
+    ++nleaves;
+    leaf(pend0);
+    pend0 = pend1;
+    pend1 = -1;
+  }
+}
+
+}  // namespace gf

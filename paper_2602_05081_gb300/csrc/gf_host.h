@@ -1,0 +1,90 @@
+// gf_host.h -- host-side structures shared by the translation units of libgf.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/gf.h"
+#include "gf_device.cuh"
+#include "gf_trace.cuh"
+
+namespace gf {
+
+struct Ctx {
+  int device = 0;
+  int sm_count = 0;
+  int cc_major = 0, cc_minor = 0;
+  float* gl = nullptr;  // device Gauss-Legendre tables
+};
+
+struct TrParams {
+  const float* o;
+  const float* d;
+  const float* trange;
+  int64_t n;
+  int mode, spp;
+  uint64_t seed;
+  LodDev lod;
+  float* out_T;
+  float* out_tau;
+  int* counter;
+};
+
+struct ChordParams {
+  const float* o;
+  const float* d;
+  const float* trange;
+  int64_t n;
+  int cap;
+  LodDev lod;
+  int* counts;
+  int* prims;
+  float* tin;
+  float* tout;
+  int* counter;
+};
+
+struct Field {
+  Ctx* ctx = nullptr;
+  int64_t n = 0;
+  gf_field_opts opts{};
+  // raw parameters (device copies, original order) for the adjoint
+  float* p_mu = nullptr;
+  float* p_quat = nullptr;
+  float* p_ls = nullptr;
+  float* p_om = nullptr;
+  float* p_ph = nullptr;
+  float* p_w = nullptr;
+  // packed data
+  float4* rec_orig = nullptr;   // FP32 records in original order (until the build)
+  float* box_orig = nullptr;    // 6 floats per primitive
+  float* kw_orig = nullptr;     // |k_W| per primitive
+  float4* rec = nullptr;        // FP32 records in BVH order
+  uint4* rec16 = nullptr;       // reduced-precision records in BVH order
+  Node* nodes = nullptr;
+  int* sorted_orig = nullptr;   // BVH position -> original index
+  uint8_t* labels = nullptr;    // band, cone, cell per primitive (3N, original order)
+  int* err = nullptr;
+  unsigned long long* stats = nullptr;
+  int* counter = nullptr;
+  float* cell_acc = nullptr;    // per-cell |k_W| sums (64) and counts (64)
+  bool built = false;
+  DevField dev{};
+  LodDev lod{0, 7, 0}, lod_nee{0, 7, 0};
+  // staging for host buffers
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+};
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_transmittance(const Field& F, const TrParams& P, cudaStream_t s);
+cudaError_t launch_render(const Field& F, const PathParams& P, float* out, cudaStream_t s);
+cudaError_t launch_ray_chords(const Field& F, const ChordParams& P, cudaStream_t s);
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n,
+                          cudaStream_t s);
+cudaError_t launch_pack(Field& F, const gf_params& P, cudaStream_t s);
+cudaError_t build_bvh(Field& F, cudaStream_t s);
+cudaError_t launch_tomo_backward(const Field& F, const PathParams& P, const float* dLdI,
+                                 float* grad, cudaStream_t s);
+
+}  // namespace gf

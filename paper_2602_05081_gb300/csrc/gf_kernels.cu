@@ -1,0 +1,229 @@
+// gf_kernels.cu -- render, transmittance and test kernels of the Gabor-field
+// renderer.  Persistent warps pull work tiles from a global counter: 32 rays,
+// or an 8x4 block of pixels, per warp; each lane owns one ray or pixel
+// (gf_trace.cuh).
+#include <cuda_runtime.h>
+
+#include "gf_host.h"
+#include "gf_trace.cuh"
+
+namespace gf {
+
+constexpr int kBlock = 128;
+constexpr int kTileW = 8, kTileH = 4;
+
+struct BlockTables {
+  float glx[kGLTotal], glw[kGLTotal];
+  float env[8];
+};
+
+__device__ __forceinline__ void init_tables(BlockTables& sm, const DevField& F) {
+  for (int i = threadIdx.x; i < kGLTotal; i += blockDim.x) {
+    sm.glx[i] = F.gl[i];
+    sm.glw[i] = F.gl[kGLTotal + i];
+  }
+  if (threadIdx.x < 8) sm.env[threadIdx.x] = F.env[threadIdx.x];
+  __syncthreads();
+}
+
+__device__ __forceinline__ int next_tile(int* counter, uint32_t lane) {
+  int it = 0;
+  if (lane == 0) it = atomicAdd(counter, 1);
+  return __shfl_sync(kFull, it, 0);
+}
+
+// ---------------------------------------------------------------------------
+// transmittance: deterministic quadrature or ratio tracking, one ray per lane
+// ---------------------------------------------------------------------------
+template <bool TRACK>
+__global__ void __launch_bounds__(kBlock)
+    k_transmittance(const __grid_constant__ DevField F, const TrParams P) {
+  __shared__ BlockTables sm;
+  init_tables(sm, F);
+  const uint32_t lane = threadIdx.x & 31u;
+  Counters cnt;
+  const bool det_mask = lod_is_deterministic(P.lod);
+  for (;;) {
+    const int tile = next_tile(P.counter, lane);
+    if ((int64_t)tile * 32 >= P.n) break;
+    const int64_t r = (int64_t)tile * 32 + lane;
+    if (r < P.n) {
+      const float3 o = make_float3(P.o[3 * r], P.o[3 * r + 1], P.o[3 * r + 2]);
+      const float3 v = normalize3(make_float3(P.d[3 * r], P.d[3 * r + 1], P.d[3 * r + 2]));
+      const float tmin = P.trange ? P.trange[2 * r] : 0.f;
+      const float tmax = P.trange ? P.trange[2 * r + 1] : INFINITY;
+      if (!TRACK) {
+        const int spp = det_mask ? 1 : P.spp;
+        float s_acc = 0.f, c_acc = 0.f;
+        for (int s = 0; s < spp; ++s) {
+          const Mask m = sample_mask(F, P.lod, v, P.seed, (uint32_t)r, (uint32_t)s, 0, TAG_MASK);
+          cnt.rays += 1;
+          neumaier_add(s_acc, c_acc, det_tau(F, m, o, v, tmin, tmax, sm.glx, sm.glw, cnt));
+        }
+        const float tau = __fadd_rn(s_acc, c_acc) / (float)spp;
+        P.out_T[r] = expf(-tau);
+        if (P.out_tau) P.out_tau[r] = tau;
+      } else {
+        float acc = 0.f;
+        for (int s = 0; s < P.spp; ++s) {
+          const Mask m = sample_mask(F, P.lod, v, P.seed, (uint32_t)r, (uint32_t)s, 0, TAG_MASK);
+          cnt.rays += 1;
+          acc += track<false>(F, m, o, v, tmin, tmax, false, P.seed, (uint32_t)r,
+                              stream_word((uint32_t)s, 0, TAG_TRACK), sm.env, cnt, nullptr);
+        }
+        P.out_T[r] = acc / (float)P.spp;
+      }
+    }
+  }
+  flush_counters(F, cnt, lane);
+}
+
+// ---------------------------------------------------------------------------
+// render: each lane owns one pixel of an 8x4 tile and runs its samples in
+// order (deterministic per pixel)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock)
+    k_render(const __grid_constant__ DevField F, const PathParams P, float* out, int* counter) {
+  __shared__ BlockTables sm;
+  init_tables(sm, F);
+  const uint32_t lane = threadIdx.x & 31u;
+  Counters cnt;
+  const int tiles_x = (P.cam.W + kTileW - 1) / kTileW;
+  const int tiles_y = (P.cam.H + kTileH - 1) / kTileH;
+  for (;;) {
+    const int tile = next_tile(counter, lane);
+    if (tile >= tiles_x * tiles_y) break;
+    const int px = (tile % tiles_x) * kTileW + (int)(lane % kTileW);
+    const int py = (tile / tiles_x) * kTileH + (int)(lane / kTileW);
+    if (px < P.cam.W && py < P.cam.H) {
+      float acc = 0.f;
+      for (int s = 0; s < P.spp; ++s) acc += path_sample(F, P, px, py, s, sm.glx, sm.glw, sm.env, cnt);
+      out[(int64_t)py * P.cam.W + px] = acc / (float)P.spp;
+    }
+  }
+  flush_counters(F, cnt, lane);
+}
+
+// ---------------------------------------------------------------------------
+// chord sets (testing)
+// ---------------------------------------------------------------------------
+struct ListLeaf {
+  const DevField* F;
+  const Mask* M;
+  float3 o, v;
+  float tmin, tmax;
+  const ChordParams* P;
+  int64_t r;
+  int n = 0;
+  __device__ __forceinline__ void operator()(int j) {
+    const Prim Pr = load_prim(*F, j);
+    if (!(mask_weight(*M, Pr.cell & 63u) > 0.f)) return;
+    Chord ch;
+    if (!chord_setup(Pr, o, v, tmin, tmax, F->k2, ch)) return;
+    if (n < P->cap) {
+      const int64_t at = r * P->cap + n;
+      P->prims[at] = (int)ch.orig;
+      if (P->tin) P->tin[at] = ch.tc + ch.dtin;
+      if (P->tout) P->tout[at] = ch.tc + ch.dtout;
+    }
+    ++n;
+  }
+};
+
+__global__ void __launch_bounds__(kBlock) k_ray_chords(const __grid_constant__ DevField F,
+                                                       const ChordParams P) {
+  const uint32_t lane = threadIdx.x & 31u;
+  for (;;) {
+    const int tile = next_tile(P.counter, lane);
+    if ((int64_t)tile * 32 >= P.n) break;
+    const int64_t r = (int64_t)tile * 32 + lane;
+    if (r >= P.n) continue;  // next_tile below is reached by every lane
+    const float3 o = make_float3(P.o[3 * r], P.o[3 * r + 1], P.o[3 * r + 2]);
+    const float3 v = normalize3(make_float3(P.d[3 * r], P.d[3 * r + 1], P.d[3 * r + 2]));
+    const float tmin = P.trange ? P.trange[2 * r] : 0.f;
+    const float tmax = P.trange ? P.trange[2 * r + 1] : INFINITY;
+    const Mask m = sample_mask(F, P.lod, v, 0, (uint32_t)r, 0, 0, TAG_MASK);
+    const float3 inv = safe_inv(v);
+    float t0, t1;
+    int n = 0;
+    if (m.bits && scene_span(F, o, inv, tmin, tmax, t0, t1)) {
+      ListLeaf leaf;
+      leaf.F = &F;
+      leaf.M = &m;
+      leaf.o = o;
+      leaf.v = v;
+      leaf.tmin = tmin;
+      leaf.tmax = tmax;
+      leaf.P = &P;
+      leaf.r = r;
+      SpanTest test{t0, t1};
+      unsigned long long nv = 0, nl = 0;
+      traverse_ray(F, o, inv, m.bits, test, leaf, nv, nl);
+      n = leaf.n;
+    }
+    P.counts[r] = n;
+  }
+}
+
+__global__ void k_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+  const uint2 k = make_uint2(key[2 * i], key[2 * i + 1]);
+  const uint4 r = philox(c, k);
+  out[4 * i] = r.x;
+  out[4 * i + 1] = r.y;
+  out[4 * i + 2] = r.z;
+  out[4 * i + 3] = r.w;
+}
+
+// ---------------------------------------------------------------------------
+// launchers: persistent grids of (resident blocks per SM) x SMs
+// ---------------------------------------------------------------------------
+template <class K>
+static int persistent_grid(const Field& F, K kernel, int64_t warps_of_work) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
+  if (per_sm < 1) per_sm = 1;
+  const int64_t need = (warps_of_work + kBlock / 32 - 1) / (kBlock / 32);
+  int64_t g = (int64_t)F.ctx->sm_count * per_sm;
+  if (need < g) g = need;
+  return (int)(g < 1 ? 1 : g);
+}
+
+cudaError_t launch_transmittance(const Field& F, const TrParams& P, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(P.counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = (P.n + 31) / 32;
+  if (P.mode == GF_TR_DETERMINISTIC) {
+    k_transmittance<false><<<persistent_grid(F, k_transmittance<false>, tiles), kBlock, 0, s>>>(F.dev, P);
+  } else {
+    k_transmittance<true><<<persistent_grid(F, k_transmittance<true>, tiles), kBlock, 0, s>>>(F.dev, P);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_render(const Field& F, const PathParams& P, float* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(F.counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = (int64_t)((P.cam.W + kTileW - 1) / kTileW) * ((P.cam.H + kTileH - 1) / kTileH);
+  k_render<<<persistent_grid(F, k_render, tiles), kBlock, 0, s>>>(F.dev, P, out, F.counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ray_chords(const Field& F, const ChordParams& P, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(P.counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  k_ray_chords<<<persistent_grid(F, k_ray_chords, (P.n + 31) / 32), kBlock, 0, s>>>(F.dev, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n,
+                          cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = (n + 255) / 256;
+  k_philox<<<(unsigned)blocks, 256, 0, s>>>(ctr, key, out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace gf

@@ -1,0 +1,613 @@
+// gf_trace.cuh -- per-ray work shared by the render, transmittance and server
+// kernels: LoD mask sampling, deterministic optical depth, tentative points,
+// ratio and delta tracking, path samples.  One thread owns one ray (or one
+// pixel's paths); a warp advances 32 rays.
+#pragma once
+#include "gf_device.cuh"
+
+namespace gf {
+
+// Gauss-Legendre rules: n in {8,12,16,20,24,32,48,64}, flattened
+constexpr int kNumRules = 8;
+constexpr int kGLTotal = 8 + 12 + 16 + 20 + 24 + 32 + 48 + 64;
+__host__ __device__ constexpr int gl_n(int r) {
+  return r == 0 ? 8 : r == 1 ? 12 : r == 2 ? 16 : r == 3 ? 20 : r == 4 ? 24 : r == 5 ? 32 : r == 6 ? 48 : 64;
+}
+__host__ __device__ constexpr int gl_off(int r) {
+  return r == 0 ? 0 : gl_off(r - 1) + gl_n(r - 1);
+}
+// node count from the chord's whitened length plus half its carrier phase span
+// (radians): the smallest rule whose error stays below 1e-8 of the envelope
+// integral for Gaussian x cosine integrands of that size
+__device__ __forceinline__ int gl_rule(float m) {
+  return m < 2.f ? 0 : m < 6.f ? 1 : m < 10.f ? 2 : m < 18.f ? 3 : m < 24.f ? 4 : m < 40.f ? 5 : m < 56.f ? 6 : 7;
+}
+
+// tentative points held per thread per window
+constexpr int kPts = 8;
+
+// Work counters, per thread; flush sums them over the warp.
+constexpr int kNumStats = 16;
+enum : int {
+  ST_RAYS = 0, ST_CHORDS, ST_EVALS, ST_NODES, ST_POINTS, ST_WINDOWS, ST_STEPS, ST_LEAVES,
+  ST_CYC_TRAV, ST_CYC_GEN, ST_CYC_EVAL, ST_CYC_MASK, ST_CYC_TOTAL
+};
+struct Counters {
+  unsigned long long rays = 0, chords = 0, evals = 0, nodes = 0, points = 0, windows = 0,
+                     steps = 0, leaves = 0;
+  unsigned long long cyc[5] = {0, 0, 0, 0, 0};  // pass 1, pass 2, (unused), mask, whole path
+};
+
+#ifdef GF_PHASE_TIMERS
+#define GF_TIC(v) long long v = clock64()
+#define GF_TOC(cnt, k, v) (cnt).cyc[k] += (unsigned long long)(clock64() - (v))
+#else
+#define GF_TIC(v)
+#define GF_TOC(cnt, k, v)
+#endif
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  return x;
+}
+// counters -> global stats; called by all 32 lanes of the warp
+__device__ __forceinline__ void flush_counters(const DevField& F, Counters& c, uint32_t lane) {
+  unsigned long long v[8] = {c.rays, c.chords, c.evals, c.nodes, c.points, c.windows, c.steps,
+                             c.leaves};
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = warp_sum_u64(v[k]);
+#ifdef GF_PHASE_TIMERS
+  unsigned long long y[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) y[k] = warp_sum_u64(c.cyc[k]);
+#endif
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) atomicAdd(F.stats + k, v[k]);
+#ifdef GF_PHASE_TIMERS
+#pragma unroll
+    for (int k = 0; k < 5; ++k) atomicAdd(F.stats + ST_CYC_TRAV + k, y[k]);
+#endif
+  }
+  c = Counters();
+}
+
+// ---------------------------------------------------------------------------
+// LoD mask (Sec. 4.5.1, 4.5.2, 4.6; App. B strategy tables).  Within a band
+// either every occupied cone is selected with one weight or exactly one cone
+// is, so a mask is its cell bits plus one weight per band.
+// ---------------------------------------------------------------------------
+struct Mask {
+  unsigned long long bits;
+  float bw[8];
+};
+
+__device__ __forceinline__ float mask_weight(const Mask& m, uint32_t cell) {
+  if (!(m.bits >> cell & 1ull)) return 0.f;
+  const int b = cell == 0 ? 0 : (int)((cell - 1u) >> 3) + 1;
+  float w = m.bw[0];
+#pragma unroll
+  for (int k = 1; k < 8; ++k) w = (b == k) ? m.bw[k] : w;
+  return w;
+}
+
+__device__ __forceinline__ unsigned band_cells8(unsigned long long occ, int b) {
+  return b == 0 ? (unsigned)(occ & 1ull) : (unsigned)((occ >> (1 + kCones * (b - 1))) & 0xFFull);
+}
+// position of the (j+1)-th set bit of m (m has more than j set bits)
+__device__ __forceinline__ int nth_bit(unsigned m, int j) { return (int)__fns(m, 0, j + 1); }
+
+__host__ __device__ __forceinline__ bool lod_is_deterministic(const LodDev& L) {
+  return (L.freq_policy == 0 || L.freq_policy == 1) && L.cone_policy == 0;
+}
+
+static __device__ Mask sample_mask(const DevField& F, const LodDev& L, float3 v, uint64_t seed,
+                                   uint32_t ray, uint32_t sample, uint32_t bounce, uint32_t tag) {
+  Mask M;
+  M.bits = 0;
+  const int maxb = L.freq_policy == 0 ? 7 : L.max_band;
+  unsigned occ = 0;
+#pragma unroll
+  for (int b = 0; b < 8; ++b)
+    if (b <= maxb && band_cells8(F.occupied, b)) occ |= 1u << b;
+  float bw[8];
+  unsigned sel = 0;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) bw[b] = 0.f;
+  const uint32_t word = stream_word(sample, bounce, tag);
+  if (L.freq_policy == 0 || L.freq_policy == 1) {
+    sel = occ;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) bw[b] = 1.f;
+  } else {
+    const uint32_t x24 = rng4(seed, 0, kNoPrim, ray, word).x >> 8;
+    int pickb = -1;
+    float wb = 0.f;
+    if (L.freq_policy == 2) {
+      // Gaussians always (weight 1) + one Gabor band uniformly (weight P-1)
+      if (occ & 1u) {
+        sel |= 1u;
+        bw[0] = 1.f;
+      }
+      const unsigned gab = occ & ~1u;
+      const int G = __popc(gab);
+      if (G > 0) {
+        pickb = nth_bit(gab, (int)(((unsigned long long)x24 * (unsigned)G) >> 24));
+        wb = (float)G;
+      }
+    } else {
+      // one band out of P uniformly (weight P)
+      const int Q = __popc(occ);
+      if (Q > 0) {
+        pickb = nth_bit(occ, (int)(((unsigned long long)x24 * (unsigned)Q) >> 24));
+        wb = (float)Q;
+      }
+    }
+    if (pickb >= 0) {
+      sel |= 1u << pickb;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) bw[b] = (b == pickb) ? wb : bw[b];
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    M.bw[b] = bw[b];
+    if (!(sel >> b & 1u)) continue;
+    const unsigned cells = band_cells8(F.occupied, b);
+    if (b == 0) {
+      M.bits |= (unsigned long long)cells;
+      continue;
+    }
+    if (L.cone_policy == 0) {
+      M.bits |= (unsigned long long)cells << (1 + kCones * (b - 1));
+      continue;
+    }
+    const uint32_t y = rng4(seed, (uint32_t)(1 + b), kNoPrim, ray, word).x;
+    const int nc = __popc(cells);
+    int k;
+    float cf;
+    if (L.cone_policy == 2) {
+      // one cone uniformly, weight K
+      k = nth_bit(cells, (int)(((unsigned long long)(y >> 8) * (unsigned)nc) >> 24));
+      cf = (float)nc;
+    } else {
+      // importance sampling: p = w(a)/W with w(a) = exp(-kbar^2 a^2 / 2), weight W/w(a)
+      float wc[kCones], W = 0.f;
+#pragma unroll
+      for (int c = 0; c < kCones; ++c) {
+        wc[c] = 0.f;
+        if (cells >> c & 1u) {
+          const float a = fabsf(v.x * F.axes[c][0] + v.y * F.axes[c][1] + v.z * F.axes[c][2]);
+          const float kb = F.kbar[1 + kCones * (b - 1) + c];
+          wc[c] = expf(-0.5f * kb * kb * a * a);
+          W += wc[c];
+        }
+      }
+      const float target = u01(y) * W;
+      float acc = 0.f, wk = 0.f;
+      k = -1;
+      int last = 0;
+      float wlast = 0.f;
+#pragma unroll
+      for (int c = 0; c < kCones; ++c) {
+        if (cells >> c & 1u) {
+          last = c;
+          wlast = wc[c];
+          acc += wc[c];
+          if (k < 0 && target < acc) {
+            k = c;
+            wk = wc[c];
+          }
+        }
+      }
+      if (k < 0) {
+        k = last;
+        wk = wlast;
+      }
+      cf = W / wk;
+    }
+    M.bw[b] = bw[b] * cf;
+    M.bits |= 1ull << (1 + kCones * (b - 1) + k);
+  }
+  return M;
+}
+
+// ---------------------------------------------------------------------------
+// deterministic optical depth along one ray (Eq. 2-3): every chord is
+// integrated by Gauss-Legendre as soon as its leaf is reached; FP32 with an
+// accurate cosine, Neumaier compensation across chords.
+// ---------------------------------------------------------------------------
+struct SpanTest {
+  float t0, t1;
+  __device__ __forceinline__ bool operator()(float tn, float tf) const {
+    return fmaxf(tn, t0) <= fminf(tf, t1);
+  }
+};
+
+__device__ __forceinline__ void gl_pick(int r, int& n, int& off) {
+  n = gl_n(7);
+  off = gl_off(7);
+#pragma unroll
+  for (int q = 6; q >= 0; --q)
+    if (r <= q) {
+      n = gl_n(q);
+      off = gl_off(q);
+    }
+}
+
+struct DetLeaf {
+  const DevField* F;
+  const Mask* M;
+  float3 o, v;
+  float tmin, tmax;
+  const float* glx;
+  const float* glw;
+  float s = 0.f, c = 0.f;
+  unsigned long long nch = 0, nev = 0;
+  __device__ __forceinline__ void operator()(int j) {
+    const Prim P = load_prim(*F, j);
+    const float w = mask_weight(*M, P.cell & 63u);
+    if (!(w > 0.f)) return;
+    Chord ch;
+    if (!chord_setup(P, o, v, tmin, tmax, F->k2, ch)) return;
+    ++nch;
+    const float len = ch.dtout - ch.dtin;
+    int n, off;
+    gl_pick(gl_rule(sqrtf(ch.a) * len + 0.5f * fabsf(ch.B) * len), n, off);
+    const float mid = 0.5f * (ch.dtin + ch.dtout), hl = 0.5f * len;
+    const float y2 = -0.5f * kLog2e * ch.a, y1 = -kLog2e * ch.b, y0 = -0.5f * kLog2e * ch.g;
+    float acc = 0.f;
+    for (int k = 0; k < n; ++k) {
+      const float dt = fmaf(hl, glx[off + k], mid);
+      const float y = fmaf(fmaf(y2, dt, y1), dt, y0);
+      acc = fmaf(glw[off + k] * ex2f(y), cosf(fmaf(ch.B, dt, ch.delta)), acc);
+    }
+    nev += (unsigned long long)n;
+    neumaier_add(s, c, w * ch.absA * hl * acc);
+  }
+};
+
+__device__ __forceinline__ float det_tau(const DevField& F, const Mask& M, float3 o, float3 v,
+                                         float tmin, float tmax, const float* glx,
+                                         const float* glw, Counters& cnt) {
+  const float3 inv = safe_inv(v);
+  float t0, t1;
+  if (M.bits == 0ull || !scene_span(F, o, inv, tmin, tmax, t0, t1)) return 0.f;
+  DetLeaf leaf;
+  leaf.F = &F;
+  leaf.M = &M;
+  leaf.o = o;
+  leaf.v = v;
+  leaf.tmin = tmin;
+  leaf.tmax = tmax;
+  leaf.glx = glx;
+  leaf.glw = glw;
+  SpanTest test{t0, t1};
+  traverse_ray(F, o, inv, M.bits, test, leaf, cnt.nodes, cnt.leaves);
+  cnt.windows += 1;
+  cnt.chords += leaf.nch;
+  cnt.evals += leaf.nev;
+  return __fadd_rn(leaf.s, leaf.c);
+}
+
+// ---------------------------------------------------------------------------
+// Tracking.  The majorant is constant on every segment between consecutive
+// chord ends and whitened-distance integers: kappa_bar = sum over the active
+// chords of w|A| exp(-(r^2 + n^2)/2), n = floor(sqrt(a)|t - t*|).  Its
+// Poisson process of tentative points is drawn chord by chord (superposition),
+// each chord from its own Philox stream (counter = draw, primitive, ray, word;
+// x.x -> exponential step, x.y -> acceptance uniform).
+//
+// Window by window, pass 1 traverses the ray and keeps the kPts smallest-t
+// points beyond the window start in registers, pruning boxes that start past
+// the current kPts-th point; pass 2 traverses only boxes containing one of
+// those points and sums kappa and kappa_bar there.  The estimate depends only
+// on the chords and their streams, never on the windows.
+// ---------------------------------------------------------------------------
+struct PointBuf {
+  float t[kPts], u[kPts];
+};
+
+struct CollectLeaf {
+  const DevField* F;
+  const Mask* M;
+  float3 o, v;
+  float tmin, tmax;
+  float ta;     // window start: points must be > ta (>= ta in the first window)
+  bool first;
+  float bound;  // points beyond are not needed: min(t1, kPts-th point so far)
+  PointBuf* B;
+  uint64_t seed;
+  uint32_t ray, word;
+  const float* env;
+  unsigned long long nch = 0;
+  __device__ __forceinline__ void insert(float t, float u) {
+#pragma unroll
+    for (int i = 0; i < kPts; ++i) {
+      const bool sw = t < B->t[i];
+      const float tt = B->t[i], uu = B->u[i];
+      B->t[i] = sw ? t : tt;
+      B->u[i] = sw ? u : uu;
+      t = sw ? tt : t;
+      u = sw ? uu : u;
+    }
+    bound = fminf(bound, B->t[kPts - 1]);
+  }
+  __device__ void operator()(int j) {
+    const Prim P = load_prim(*F, j);
+    const float w = mask_weight(*M, P.cell & 63u);
+    if (!(w > 0.f)) return;
+    Chord ch;
+    if (!chord_setup(P, o, v, tmin, tmax, F->k2, ch)) return;
+    if (!(ch.tc + ch.dtin <= bound && ch.tc + ch.dtout >= ta)) return;
+    ++nch;
+    // piecewise rate h exp(-n^2/2) on whitened-distance pieces of the chord
+    const float h = w * ch.absA * expf(-0.5f * ch.qmin);
+    const float sa = sqrtf(ch.a), invs = 1.0f / sa, dts = ch.dts, dtout = ch.dtout;
+    int J = (int)ceilf(sa * ch.hw) - 1;
+    J = J < 0 ? 0 : (J > 6 ? 6 : J);
+    float dt = ch.dtin;
+    int p = 0;
+    while (p < 2 * J) {
+      const float bp = p < J ? dts - (float)(J - p) * invs : dts + (float)(p - J + 1) * invs;
+      if (bp <= dt) ++p;
+      else break;
+    }
+    for (uint32_t draw = 0; draw < (1u << 16); ++draw) {
+      const uint4 x = rng4(seed, draw, ch.orig, ray, word);
+      float z = -logf(1.0f - u01(x.x));
+      bool emit = false;
+      for (int q = 0; q < 2 * J + 2; ++q) {
+        const float bp = p < J ? dts - (float)(J - p) * invs : dts + (float)(p - J + 1) * invs;
+        const float end = p < 2 * J ? fminf(bp, dtout) : dtout;
+        const int nn = p < J ? J - p : p - J;
+        const float lam = h * env[nn];
+        const float capz = lam * (end - dt);
+        if (z < capz) {
+          dt += z / lam;
+          emit = true;
+          break;
+        }
+        z -= capz;
+        dt = end;
+        if (dt >= dtout) return;
+        ++p;
+      }
+      if (!emit) return;
+      const float t = ch.tc + dt;
+      if (t > bound) return;
+      if (first ? t >= ta : t > ta) insert(t, u01(x.y));
+    }
+    set_err(*F, ERR_GUARD);
+  }
+};
+
+struct CollectTest {
+  const float* ta;
+  const float* bound;
+  __device__ __forceinline__ bool operator()(float tn, float tf) const {
+    return fmaxf(tn, *ta) <= fminf(tf, *bound);
+  }
+};
+
+struct PointTest {
+  const PointBuf* B;
+  int n;
+  __device__ __forceinline__ bool operator()(float tn, float tf) const {
+    bool hit = false;
+#pragma unroll
+    for (int i = 0; i < kPts; ++i) hit |= (i < n) && B->t[i] >= tn && B->t[i] <= tf;
+    return hit;
+  }
+};
+
+struct AccumLeaf {
+  const DevField* F;
+  const Mask* M;
+  float3 o, v;
+  float tmin, tmax;
+  const PointBuf* B;
+  int n;
+  const float* env;
+  float kap[kPts], kb[kPts];
+  unsigned long long nev = 0;
+  __device__ void operator()(int j) {
+    const Prim P = load_prim(*F, j);
+    const float w = mask_weight(*M, P.cell & 63u);
+    if (!(w > 0.f)) return;
+    Chord ch;
+    if (!chord_setup(P, o, v, tmin, tmax, F->k2, ch)) return;
+    const float tin = ch.tc + ch.dtin, tout = ch.tc + ch.dtout;
+    const float wa = w * ch.absA;
+    const float y2 = -0.5f * kLog2e * ch.a, y1 = -kLog2e * ch.b;
+    const float y0 = fmaf(-0.5f * kLog2e, ch.g, log2f(wa));
+    const float h = wa * expf(-0.5f * ch.qmin);
+    const float sa = sqrtf(ch.a);
+#pragma unroll
+    for (int i = 0; i < kPts; ++i) {
+      const float t = B->t[i];
+      if (i < n && t >= tin && t <= tout) {
+        const float dt = t - ch.tc;
+        const float y = fmaf(fmaf(y2, dt, y1), dt, y0);
+        kap[i] = fmaf(ex2f(y), cosf_fast(fmaf(ch.B, dt, ch.delta)), kap[i]);
+        int m = (int)(fabsf(dt - ch.dts) * sa);
+        m = m > 7 ? 7 : m;
+        kb[i] = fmaf(h, env[m], kb[i]);
+        ++nev;
+      }
+    }
+  }
+};
+
+// Ratio tracking (DELTA = false): returns prod (1 - kappa/kappa_bar).
+// Delta tracking (DELTA = true): returns 1 and *t_hit at the first accepted
+// point (probability max(kappa,0)/kappa_bar), else 0.
+template <bool DELTA>
+__device__ float track(const DevField& F, const Mask& M, float3 o, float3 v, float tmin,
+                       float tmax, bool clamp_neg, uint64_t seed, uint32_t ray, uint32_t word,
+                       const float* env, Counters& cnt, float* t_hit) {
+  const float3 inv = safe_inv(v);
+  float t0, t1;
+  float Tr = 1.f;
+  if (M.bits == 0ull || !scene_span(F, o, inv, tmin, tmax, t0, t1)) return DELTA ? 0.f : 1.f;
+  float ta = t0;
+  bool first = true;
+  for (int guard = 0; guard < (1 << 16); ++guard) {
+    PointBuf B;
+#pragma unroll
+    for (int i = 0; i < kPts; ++i) {
+      B.t[i] = INFINITY;
+      B.u[i] = 0.f;
+    }
+    GF_TIC(c0);
+    CollectLeaf cl;
+    cl.F = &F;
+    cl.M = &M;
+    cl.o = o;
+    cl.v = v;
+    cl.tmin = tmin;
+    cl.tmax = tmax;
+    cl.ta = ta;
+    cl.first = first;
+    cl.bound = t1;
+    cl.B = &B;
+    cl.seed = seed;
+    cl.ray = ray;
+    cl.word = word;
+    cl.env = env;
+    CollectTest ctest{&cl.ta, &cl.bound};
+    traverse_ray(F, o, inv, M.bits, ctest, cl, cnt.nodes, cnt.leaves);
+    GF_TOC(cnt, 0, c0);
+    cnt.windows += 1;
+    cnt.chords += cl.nch;
+    int n = 0;
+#pragma unroll
+    for (int i = 0; i < kPts; ++i) n += B.t[i] < INFINITY ? 1 : 0;
+    cnt.points += (unsigned long long)n;
+    if (n == 0) break;
+    GF_TIC(c1);
+    AccumLeaf al;
+    al.F = &F;
+    al.M = &M;
+    al.o = o;
+    al.v = v;
+    al.tmin = tmin;
+    al.tmax = tmax;
+    al.B = &B;
+    al.n = n;
+    al.env = env;
+#pragma unroll
+    for (int i = 0; i < kPts; ++i) {
+      al.kap[i] = 0.f;
+      al.kb[i] = 0.f;
+    }
+    PointTest ptest{&B, n};
+    traverse_ray(F, o, inv, M.bits, ptest, al, cnt.nodes, cnt.leaves);
+    GF_TOC(cnt, 1, c1);
+    cnt.windows += 1;
+    cnt.evals += al.nev;
+    if (DELTA) {
+#pragma unroll
+      for (int i = 0; i < kPts; ++i) {
+        if (i < n && B.u[i] * al.kb[i] < fmaxf(al.kap[i], 0.f)) {
+          *t_hit = B.t[i];
+          return 1.f;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < kPts; ++i) {
+        if (i < n && al.kb[i] > 0.f) {
+          const float k = clamp_neg ? fmaxf(al.kap[i], 0.f) : al.kap[i];
+          Tr *= 1.f - k / al.kb[i];
+        }
+      }
+    }
+    if (n < kPts) break;  // every point of the ray has been used
+    ta = B.t[kPts - 1];
+    first = false;
+  }
+  return DELTA ? 0.f : Tr;
+}
+
+// ---------------------------------------------------------------------------
+// camera and path samples
+// ---------------------------------------------------------------------------
+struct CamDev {
+  float3 eye, fw, rt, up;
+  float tanh, aspect;
+  int W, H;
+};
+
+__device__ __forceinline__ float3 normalize3(float3 a) {
+  const float n = sqrtf(a.x * a.x + a.y * a.y + a.z * a.z);
+  return make_float3(a.x / n, a.y / n, a.z / n);
+}
+
+__device__ __forceinline__ void camera_ray(const CamDev& C, uint64_t seed, int px, int py, int s,
+                                           float3& o, float3& v) {
+  const uint32_t pix = (uint32_t)py * (uint32_t)C.W + (uint32_t)px;
+  const uint4 x = rng4(seed, 0, kNoPrim, pix, stream_word((uint32_t)s, 0, TAG_CAMERA));
+  const float jx = u01(x.x), jy = u01(x.y);
+  const float sx = (2.0f * ((float)px + jx) / (float)C.W - 1.0f) * C.tanh * C.aspect;
+  const float sy = (1.0f - 2.0f * ((float)py + jy) / (float)C.H) * C.tanh;
+  const float3 d = make_float3(C.fw.x + sx * C.rt.x + sy * C.up.x, C.fw.y + sx * C.rt.y + sy * C.up.y,
+                               C.fw.z + sx * C.rt.z + sy * C.up.z);
+  v = normalize3(d);
+  o = C.eye;
+}
+
+struct PathParams {
+  CamDev cam;
+  int integrator, spp, max_bounces;
+  float albedo, irradiance;
+  float3 light;
+  uint64_t seed;
+  LodDev lod, lod_nee;
+};
+
+// one sample of pixel (px, py): tomography exp(-tau) or scattering radiance
+static __device__ float path_sample(const DevField& F, const PathParams& P, int px, int py, int s,
+                                    const float* glx, const float* glw, const float* env,
+                                    Counters& cnt) {
+  float3 o, v;
+  camera_ray(P.cam, P.seed, px, py, s, o, v);
+  const uint32_t pix = (uint32_t)py * (uint32_t)P.cam.W + (uint32_t)px;
+  if (P.integrator == 0) {
+    const Mask m = sample_mask(F, P.lod, v, P.seed, pix, (uint32_t)s, 0, TAG_MASK);
+    cnt.rays += 1;
+    return expf(-det_tau(F, m, o, v, 0.f, INFINITY, glx, glw, cnt));
+  }
+  float thr = 1.f, Lsum = 0.f;
+  GF_TIC(ct);
+  for (int b = 0; b < P.max_bounces; ++b) {
+    GF_TIC(cm);
+    const Mask m = sample_mask(F, P.lod, v, P.seed, pix, (uint32_t)s, (uint32_t)b, TAG_MASK);
+    GF_TOC(cnt, 3, cm);
+    float th = 0.f;
+    cnt.rays += 1;
+    const float hit = track<true>(F, m, o, v, 0.f, INFINITY, true, P.seed, pix,
+                                  stream_word((uint32_t)s, (uint32_t)b, TAG_TRACK), env, cnt, &th);
+    if (hit == 0.f) break;
+    const float3 x = make_float3(o.x + th * v.x, o.y + th * v.y, o.z + th * v.z);
+    thr *= P.albedo;
+    const Mask mn = sample_mask(F, P.lod_nee, P.light, P.seed, pix, (uint32_t)s, (uint32_t)b,
+                                TAG_NEE_MASK);
+    cnt.rays += 1;
+    const float Tl = track<false>(F, mn, x, P.light, 0.f, INFINITY, true, P.seed, pix,
+                                  stream_word((uint32_t)s, (uint32_t)b, TAG_NEE), env, cnt, nullptr);
+    Lsum += thr * P.irradiance * Tl * (0.25f / 3.14159265358979f);
+    const uint4 y = rng4(P.seed, 0, kNoPrim, pix, stream_word((uint32_t)s, (uint32_t)b, TAG_SCATTER));
+    const float z = 1.0f - 2.0f * u01(y.x);
+    const float rr = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+    float sn, cs;
+    sincosf(2.0f * 3.14159265358979f * u01(y.y), &sn, &cs);
+    v = make_float3(rr * cs, rr * sn, z);
+    o = x;
+  }
+  GF_TOC(cnt, 4, ct);
+  return Lsum;
+}
+
+}  // namespace gf

@@ -1,0 +1,337 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI (GPU).
+
+Tolerances: |T_gpu - T_oracle| <= 1e-5 on deterministic transmittance (FP32
+storage); images under shared Philox streams within 1% of the oracle's Monte
+Carlo noise, RMS_pixels(I_gpu - I_oracle) <= 0.01 RMS_pixels(sigma_MC); bit
+equality for integer work (Philox blocks, labels, chord sets).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2602_05081_gb300 import api as _api
+    return _api
+
+
+@pytest.fixture(scope="module")
+def ctx(api):
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+DEV = "cuda"
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _cam_pair(api, w, h):
+    c = synth.DEFAULT_CAMERA
+    return (api.camera(c["eye"], c["look_at"], c["up"], c["vfov_deg"], w, h),
+            oracle.camera(c["eye"], c["look_at"], c["up"], c["vfov_deg"], w, h))
+
+
+# --------------------------------------------------------------------------- integers
+def test_philox_blocks_equal_oracle(api):
+    from paper_2602_05081_gb300 import _abi
+    rng = np.random.default_rng(0)
+    n = 2048
+    ctr = rng.integers(0, 2 ** 32, (n, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, (n, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0; key[0] = 0
+    out = np.zeros((n, 4), np.uint32)
+    _abi.gf_philox(ctr, key, out, n)
+    ref = np.stack([oracle.philox4x32_10(ctr[i], key[i]) for i in range(n)])
+    assert np.array_equal(out, ref)
+    assert [hex(x) for x in out[0]] == ["0x6627e8d5", "0xe169c58d", "0xbc57ac4c", "0x9b00dbd8"]
+
+
+@pytest.mark.parametrize("which", ["absorption", "octave"])
+def test_labels_equal_oracle(api, ctx, which):
+    p = synth.absorption_field(4096, seed=3) if which == "absorption" else synth.octave_field(21000, 5, seed=3)
+    f = api.Field(ctx, p)
+    b, c, e = f.labels()
+    ob, oc, oe = oracle.Field(p, omega_frame=p["omega_frame"]).labels()
+    assert np.array_equal(b, ob)
+    mism = np.nonzero(c != oc)[0]
+    assert mism.size <= 2, mism  # only exact near-ties may flip (FP32 carrier vs FP64)
+    assert np.array_equal(e == oe, c == oc)
+
+
+def test_chord_sets_equal_oracle(api, ctx):
+    p = synth.octave_field(5000, 4, seed=5)
+    f = api.Field(ctx, p)
+    orc = oracle.Field(p, omega_frame="local")
+    o, d, tr = synth.random_rays(48, seed=9)
+    counts, prims, tin, tout = f.chords(_t(o), _t(d), _t(tr), cap=1024)
+    f.sync()
+    for r in range(48):
+        got = {int(x): (float(a), float(b)) for x, a, b in
+               zip(prims[r, :counts[r]], tin[r, :counts[r]], tout[r, :counts[r]])}
+        assert counts[r] == len(got)
+        ref = {}
+        for i in range(orc.n):
+            has, lo, hi = orc.chord(i, o[r].astype(np.float64), d[r].astype(np.float64), tr[r, 0], tr[r, 1])
+            if has:
+                ref[i] = (lo, hi)
+        for i in set(got) ^ set(ref):  # only tangent chords may differ
+            lo, hi = ref.get(i, got.get(i))
+            assert hi - lo < 2e-4, (r, i, lo, hi)
+        for i in set(got) & set(ref):
+            assert abs(got[i][0] - ref[i][0]) < 2e-5 and abs(got[i][1] - ref[i][1]) < 2e-5
+
+
+# --------------------------------------------------------------------------- transmittance
+def test_deterministic_transmittance_absorption_64x64(api, ctx):
+    """256 Gabor primitives, 64x64 orthographic rays along +z: |dT| <= 1e-5."""
+    p = synth.absorption_field(256, seed=0)
+    f = api.Field(ctx, p)
+    o, d, tr = synth.orthographic_rays(64)
+    T, tau = f.transmittance(_t(o), _t(d), _t(tr), mode="det")
+    f.sync()
+    T_ref, tau_ref = oracle.Field(p).transmittance(o, d, tr, mode="det")
+    err = np.abs(T.cpu().numpy() - T_ref)
+    assert err.max() <= 1e-5, err.max()
+    assert np.abs(tau.cpu().numpy() - tau_ref).max() <= 1e-5 * max(1.0, np.abs(tau_ref).max())
+    assert np.abs(tau_ref).max() > 0.2  # non-trivial optical depths
+
+
+def test_deterministic_transmittance_edges(api, ctx):
+    """Clipped ranges, rays that miss, one- and two-primitive fields, host buffers."""
+    p = synth.absorption_field(256, seed=1)
+    f = api.Field(ctx, p)
+    orc = oracle.Field(p)
+    o, d, tr = synth.random_rays(300, seed=2)
+    rng = np.random.default_rng(3)
+    tr = tr.copy()
+    tr[:100, 0] = rng.uniform(0.5, 1.5, 100).astype(np.float32)
+    tr[:100, 1] = tr[:100, 0] + rng.uniform(0.0, 0.6, 100).astype(np.float32)
+    tr[100:110, 1] = tr[100:110, 0]  # empty ranges
+    d[110:130] = -d[110:130]  # rays pointing away from the cube
+    T, _ = f.transmittance(_t(o), _t(d), _t(tr), mode="det")
+    f.sync()
+    T_ref, _ = orc.transmittance(o, d, tr, mode="det")
+    assert np.abs(T.cpu().numpy() - T_ref).max() <= 1e-5
+    assert np.all(T.cpu().numpy()[110:130] == 1.0)
+    # host buffers through the same entry point
+    Th = np.zeros(300, np.float32)
+    f.transmittance(o, d, tr, mode="det", out_T=Th, out_tau=np.zeros(300, np.float32))
+    assert np.array_equal(Th, T.cpu().numpy())
+    for n in (1, 2):
+        q = {k: (v[:n] if isinstance(v, np.ndarray) else v) for k, v in p.items()}
+        g = api.Field(ctx, q)
+        oo = np.tile(q["mu"][0] - np.array([0, 0, 1.0], np.float32), (8, 1)).astype(np.float32)
+        oo[:, :2] += np.linspace(-0.05, 0.05, 8, dtype=np.float32)[:, None]
+        dd = np.tile(np.array([0, 0, 1.0], np.float32), (8, 1))
+        Tg, _ = g.transmittance(_t(oo), _t(dd), None, mode="det")
+        g.sync()
+        Tr, _ = oracle.Field(q).transmittance(oo, dd, None, mode="det")
+        assert np.abs(Tg.cpu().numpy() - Tr).max() <= 1e-5
+
+
+def test_deterministic_transmittance_lod_masks(api, ctx):
+    """Band cutoffs and the stochastic (uniform + control variate, importance-
+    sampled cones) mask averaged over spp draws, same Philox draws as the oracle."""
+    p = synth.octave_field(21000, 5, seed=4)
+    f = api.Field(ctx, p)
+    orc = oracle.Field(p, omega_frame="local")
+    o, d, tr = synth.random_rays(96, seed=6)
+    for cut in range(5):
+        f.set_lod(api.lod("cutoff", cut))
+        T, tau = f.transmittance(_t(o), _t(d), _t(tr), mode="det")
+        f.sync()
+        T_ref, tau_ref = orc.transmittance(o, d, tr, mode="det", lod=oracle.Lod(1, cut, 0))
+        assert np.abs(T.cpu().numpy() - T_ref).max() <= 1e-5, cut
+    f.set_lod(api.lod("unif_cv", 7, "is"))
+    T, tau = f.transmittance(_t(o), _t(d), _t(tr), mode="det", spp=16, seed=11)
+    f.sync()
+    T_ref, tau_ref = orc.transmittance(o, d, tr, mode="det", spp=16, seed=11, lod=oracle.Lod(2, 7, 1))
+    # masked weights up to ~W/w(a) amplify absolute rounding; compare tau relative to its scale
+    assert np.abs(tau.cpu().numpy() - tau_ref).max() <= 2e-5 * max(1.0, np.abs(tau_ref).max())
+
+
+def test_ratio_tracking_same_streams(api, ctx):
+    """1 spp ratio tracking: each ray's estimate equals the oracle's under the
+    shared Philox streams, except for rare FP32 decision flips."""
+    p = synth.absorption_field(256, seed=0)
+    f = api.Field(ctx, p)
+    o, d, tr = synth.orthographic_rays(64)
+    T, _ = f.transmittance(_t(o), _t(d), _t(tr), mode="rt", spp=1, seed=7)
+    f.sync()
+    T_ref, _ = oracle.Field(p).transmittance(o, d, tr, mode="rt", spp=1, seed=7)
+    err = np.abs(T.cpu().numpy() - T_ref)
+    assert np.mean(err > 1e-4) <= 0.002, np.sort(err)[-10:]
+    assert np.median(err) <= 1e-6
+    # and the estimator is unbiased for exp(-tau): many spp against the quadrature
+    T8, _ = f.transmittance(_t(o[:256]), _t(d[:256]), _t(tr[:256]), mode="rt", spp=4096, seed=8)
+    Td, _ = f.transmittance(_t(o[:256]), _t(d[:256]), _t(tr[:256]), mode="det")
+    f.sync()
+    z = (T8 - Td).cpu().numpy()
+    assert abs(z.mean()) < 5 * z.std() / math.sqrt(256) + 1e-4
+
+
+# --------------------------------------------------------------------------- images
+def _mc_parity(api, f, orc, cam_g, cam_o, ro_g, ro_o, seed, lod_o=None, lodn_o=None, crop=None):
+    img = f.render(cam_g, ro_g, seed=seed)
+    f.sync()
+    g = img.cpu().numpy()
+    smp = orc.render(cam_o, ro_o, seed=seed, lod=lod_o, lod_nee=lodn_o, crop=crop, samples=True)
+    ref = smp.mean(-1)
+    sig = smp.std(-1, ddof=1) / math.sqrt(smp.shape[-1])
+    if crop is not None:
+        x0, y0, w, h = crop
+        g = g[y0:y0 + h, x0:x0 + w]
+    diff = np.sqrt(np.mean((g - ref) ** 2))
+    noise = np.sqrt(np.mean(sig ** 2))
+    return diff, noise, ref
+
+
+def test_single_scatter_render_parity(api, ctx):
+    p = synth.octave_field(3000, 4, seed=8)
+    f = api.Field(ctx, p)
+    orc = oracle.Field(p, omega_frame="local")
+    cg, co = _cam_pair(api, 24, 24)
+    for cut in (3, 1):
+        f.set_lod(api.lod("cutoff", cut))
+        lo = oracle.Lod(1, cut, 0)
+        diff, noise, ref = _mc_parity(api, f, orc, cg, co, api.render_opts("scatter", 8, 1),
+                                      oracle.render_opts("scatter", 8, 1), 2, lo, lo)
+        assert ref.max() > 1e-3
+        assert diff <= 0.01 * noise, (cut, diff, noise)
+
+
+def test_multiple_scatter_stochastic_mask_parity(api, ctx):
+    p = synth.octave_field(5460, 6, seed=9)
+    f = api.Field(ctx, p)
+    orc = oracle.Field(p, omega_frame="local")
+    cg, co = _cam_pair(api, 16, 16)
+    f.set_lod(api.lod("unif_cv", 7, "is"), api.lod("unif_cv", 7, "is"))
+    lo = oracle.Lod(2, 7, 1)
+    diff, noise, ref = _mc_parity(api, f, orc, cg, co, api.render_opts("scatter", 8, 4),
+                                  oracle.render_opts("scatter", 8, 4), 3, lo, lo)
+    assert ref.max() > 1e-3
+    assert diff <= 0.01 * noise, (diff, noise)
+
+
+def test_tomography_render_parity(api, ctx):
+    """Tomography image: per camera ray |dT| <= 1e-5 on identical float rays, and
+    the rendered image within 1% of the MC noise of its jittered samples.  The
+    image's own rays are built in FP32 on the GPU: a position rounding of
+    ~1e-7 times carriers of ~1e3 rad/unit moves phases by ~1e-4, which is why
+    the image is held to the Monte Carlo criterion and T to the ray-exact one."""
+    p = synth.octave_field(3000, 4, seed=10)
+    f = api.Field(ctx, p)
+    orc = oracle.Field(p, omega_frame="local")
+    cg, co = _cam_pair(api, 32, 32)
+    rays = [oracle.camera_ray(co, 4, x, y, s) for y in range(0, 32, 3) for x in range(0, 32, 3)
+            for s in range(2)]
+    o = np.array([r[0] for r in rays], np.float32)
+    d = np.array([r[1] for r in rays], np.float32)
+    T, _ = f.transmittance(_t(o), _t(d), None, mode="det")
+    f.sync()
+    T_ref, _ = orc.transmittance(o, d, None, mode="det")
+    assert np.abs(T.cpu().numpy() - T_ref).max() <= 1e-5
+    diff, noise, ref = _mc_parity(api, f, orc, cg, co, api.render_opts("tomo", 4),
+                                  oracle.render_opts("tomo", 4), 4)
+    assert diff <= 0.01 * noise, (diff, noise)
+
+
+def test_full_size_single_scatter_sampled_pixels(api, ctx):
+    """100k-primitive 4-octave field, 512x512, 16 spp, the band cutoffs timed by
+    the benchmark: sampled pixels against the oracle computed pixel by pixel."""
+    p = synth.octave_field(100_000, 4, seed=0)
+    f = api.Field(ctx, p)
+    orc = oracle.Field(p, omega_frame="local")
+    cg, co = _cam_pair(api, 512, 512)
+    rng = np.random.default_rng(12)
+    pix = rng.integers(0, 512, (12, 2))
+    for cut in (3, 0):
+        f.set_lod(api.lod("cutoff", cut))
+        img = f.render(cg, api.render_opts("scatter", 16, 1), seed=1)
+        f.sync()
+        g = img.cpu().numpy()
+        lo = oracle.Lod(1, cut, 0)
+        diffs, sigs = [], []
+        for x, y in pix:
+            smp = orc.render(co, oracle.render_opts("scatter", 16, 1), seed=1, lod=lo, lod_nee=lo,
+                             crop=(int(x), int(y), 1, 1), samples=True).ravel()
+            diffs.append(g[y, x] - smp.mean())
+            sigs.append(smp.std(ddof=1) / 4.0)
+        diffs, sigs = np.array(diffs), np.array(sigs)
+        assert np.sqrt(np.mean(diffs ** 2)) <= 0.01 * np.sqrt(np.mean(sigs ** 2)) + 1e-7, (cut, diffs)
+
+
+# --------------------------------------------------------------------------- adjoint
+def test_tomography_gradient_matches_oracle(api, ctx):
+    p = synth.octave_field(340, 4, seed=13)
+    f = api.Field(ctx, p)
+    orc = oracle.Field(p, omega_frame="local")
+    cg, co = _cam_pair(api, 32, 32)
+    ro = api.render_opts("tomo", 1)
+    img = f.render(cg, ro, seed=5)
+    target = (img * 0.97 + 0.01).detach()
+    q = synth.perturb(p, 0.01, seed=2)
+    g = api.Field(ctx, q)
+    img2 = g.render(cg, ro, seed=5)
+    dL = (2.0 * (img2 - target)).contiguous()
+    grad = g.render_backward(cg, ro, 5, dL)
+    g.sync()
+    L_ref, grad_ref = oracle.Field(q, omega_frame="local").tomo_loss_grad(co, 1, 5, target.cpu().numpy())
+    gg = grad.cpu().numpy().astype(np.float64)
+    scale = np.abs(grad_ref).max()
+    bad = np.abs(gg - grad_ref) > 1e-2 * np.abs(grad_ref) + 1e-3 * scale
+    assert bad.mean() < 0.002, (np.nonzero(bad)[0][:10], gg[bad][:5], grad_ref[bad][:5])
+
+
+def test_autograd_function_uses_the_adjoint(api, ctx):
+    p = synth.absorption_field(64, seed=14)
+    cg, _ = _cam_pair(api, 16, 16)
+    ts = {k: torch.tensor(p[k], device=DEV, requires_grad=True)
+          for k in ("mu", "quat", "log_scale", "omega", "phase", "weight")}
+    img = api.TomoRender.apply(ts["mu"], ts["quat"], ts["log_scale"], ts["omega"], ts["phase"],
+                               ts["weight"], ctx, cg, 1, 3, "world", "peak", 3.0)
+    loss = (img ** 2).sum()
+    loss.backward()
+    f = api.Field(ctx, p)
+    g = f.render_backward(cg, api.render_opts("tomo", 1), 3, (2 * img).detach().contiguous())
+    parts = api.split_grad(g, 64)
+    for k in ts:
+        assert torch.allclose(ts[k].grad, parts[k].view_as(ts[k].grad), rtol=1e-5, atol=1e-6)
+
+
+# --------------------------------------------------------------------------- errors
+def test_invalid_inputs_are_rejected(api, ctx):
+    from paper_2602_05081_gb300 import _abi
+    p = synth.absorption_field(16, seed=0)
+    bad = dict(p)
+    bad["mu"] = p["mu"].copy()
+    bad["mu"][3, 1] = np.nan
+    with pytest.raises(_abi.GfError) as e:
+        api.Field(ctx, bad)
+    assert e.value.status == _abi.GF_EINVAL
+    with pytest.raises(_abi.GfError):
+        api.Field(ctx, p, k_sigma=0.0)
+    f = api.Field(ctx, p)
+    o, d, tr = synth.orthographic_rays(4)
+    with pytest.raises(_abi.GfError):
+        f.transmittance(_t(o), _t(d), _t(tr), mode="det", spp=0)
+    cg, _ = _cam_pair(api, 4, 4)
+    with pytest.raises(_abi.GfError):
+        f.render(cg, api.render_opts("scatter", 0, 1))
+    f.sync()
