@@ -308,6 +308,9 @@ __device__ __forceinline__ void traverse_ray(const DevField& F, float3 o, float3
     leaf(0);
     return;
   }
+  // lanes that entered together stay together: they reconverge after every
+  // traversal burst and leave the loop only when all of them are done
+  const unsigned am = __activemask();
   int st_node[kStack];
   float st_tn[kStack];
   int sp = 0;
@@ -318,7 +321,7 @@ __device__ __forceinline__ void traverse_ray(const DevField& F, float3 o, float3
   long long steps = 0;
   for (;;) {
     // while-while: traverse until a leaf is queued or the tree is exhausted; the
-    // lanes of a warp reconverge after this loop and process their leaves together
+    // lanes then process their leaves together
     while (node >= 0 && pend0 < 0) {
       if (++steps > max_steps) {
         set_err(F, ERR_GUARD);
@@ -370,11 +373,14 @@ __device__ __forceinline__ void traverse_ray(const DevField& F, float3 o, float3
         }
       }
     }
-    if (pend0 < 0) return;
-    ++nleaves;
-    leaf(pend0);
-    pend0 = pend1;
-    pend1 = -1;
+    __syncwarp(am);
+    if (pend0 >= 0) {
+      ++nleaves;
+      leaf(pend0);
+      pend0 = pend1;
+      pend1 = -1;
+    }
+    if (!__any_sync(am, node >= 0 || pend0 >= 0)) return;
   }
 }
 

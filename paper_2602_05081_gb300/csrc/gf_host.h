@@ -79,6 +79,7 @@ struct Field {
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_transmittance(const Field& F, const TrParams& P, cudaStream_t s);
 cudaError_t launch_render(const Field& F, const PathParams& P, float* out, cudaStream_t s);
+cudaError_t launch_render_scatter(const Field& F, const PathParams& P, float* out, cudaStream_t s);
 cudaError_t launch_ray_chords(const Field& F, const ChordParams& P, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n,
                           cudaStream_t s);

@@ -95,11 +95,11 @@ __global__ void __launch_bounds__(kBlock)
     if (tile >= tiles_x * tiles_y) break;
     const int px = (tile % tiles_x) * kTileW + (int)(lane % kTileW);
     const int py = (tile / tiles_x) * kTileH + (int)(lane / kTileW);
-    if (px < P.cam.W && py < P.cam.H) {
-      float acc = 0.f;
-      for (int s = 0; s < P.spp; ++s) acc += path_sample(F, P, px, py, s, sm.glx, sm.glw, sm.env, cnt);
-      out[(int64_t)py * P.cam.W + px] = acc / (float)P.spp;
-    }
+    const bool active = px < P.cam.W && py < P.cam.H;
+    float acc = 0.f;
+    for (int s = 0; s < P.spp; ++s)
+      acc += path_sample(F, P, active, px, py, s, sm.glx, sm.glw, sm.env, cnt);
+    if (active) out[(int64_t)py * P.cam.W + px] = acc / (float)P.spp;
   }
   flush_counters(F, cnt, lane);
 }
@@ -206,6 +206,7 @@ cudaError_t launch_transmittance(const Field& F, const TrParams& P, cudaStream_t
 cudaError_t launch_render(const Field& F, const PathParams& P, float* out, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(F.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
+  if (P.integrator == GF_INTEG_SCATTER) return launch_render_scatter(F, P, out, s);
   const int64_t tiles = (int64_t)((P.cam.W + kTileW - 1) / kTileW) * ((P.cam.H + kTileH - 1) / kTileH);
   k_render<<<persistent_grid(F, k_render, tiles), kBlock, 0, s>>>(F.dev, P, out, F.counter);
   return cudaGetLastError();

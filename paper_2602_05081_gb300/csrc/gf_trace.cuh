@@ -447,13 +447,18 @@ template <bool DELTA>
 __device__ float track(const DevField& F, const Mask& M, float3 o, float3 v, float tmin,
                        float tmax, bool clamp_neg, uint64_t seed, uint32_t ray, uint32_t word,
                        const float* env, Counters& cnt, float* t_hit) {
+  const unsigned am = __activemask();
   const float3 inv = safe_inv(v);
-  float t0, t1;
-  float Tr = 1.f;
-  if (M.bits == 0ull || !scene_span(F, o, inv, tmin, tmax, t0, t1)) return DELTA ? 0.f : 1.f;
+  float t0 = 0.f, t1 = 0.f;
+  float Tr = 1.f, hit = 0.f;
+  // `more`: this lane still has windows to process; all lanes that entered
+  // iterate together until none has
+  bool more = M.bits != 0ull && scene_span(F, o, inv, tmin, tmax, t0, t1);
   float ta = t0;
   bool first = true;
   for (int guard = 0; guard < (1 << 16); ++guard) {
+    if (!__any_sync(am, more)) break;
+    if (!more) continue;
     PointBuf B;
 #pragma unroll
     for (int i = 0; i < kPts; ++i) {
@@ -485,7 +490,10 @@ __device__ float track(const DevField& F, const Mask& M, float3 o, float3 v, flo
 #pragma unroll
     for (int i = 0; i < kPts; ++i) n += B.t[i] < INFINITY ? 1 : 0;
     cnt.points += (unsigned long long)n;
-    if (n == 0) break;
+    if (n == 0) {
+      more = false;
+      continue;
+    }
     GF_TIC(c1);
     AccumLeaf al;
     al.F = &F;
@@ -508,12 +516,18 @@ __device__ float track(const DevField& F, const Mask& M, float3 o, float3 v, flo
     cnt.windows += 1;
     cnt.evals += al.nev;
     if (DELTA) {
+      bool found = false;
 #pragma unroll
       for (int i = 0; i < kPts; ++i) {
-        if (i < n && B.u[i] * al.kb[i] < fmaxf(al.kap[i], 0.f)) {
+        if (!found && i < n && B.u[i] * al.kb[i] < fmaxf(al.kap[i], 0.f)) {
           *t_hit = B.t[i];
-          return 1.f;
+          found = true;
         }
+      }
+      if (found) {
+        hit = 1.f;
+        more = false;
+        continue;
       }
     } else {
 #pragma unroll
@@ -524,11 +538,14 @@ __device__ float track(const DevField& F, const Mask& M, float3 o, float3 v, flo
         }
       }
     }
-    if (n < kPts) break;  // every point of the ray has been used
+    if (n < kPts) {  // every point of the ray has been used
+      more = false;
+      continue;
+    }
     ta = B.t[kPts - 1];
     first = false;
   }
-  return DELTA ? 0.f : Tr;
+  return DELTA ? hit : Tr;
 }
 
 // ---------------------------------------------------------------------------
@@ -567,44 +584,60 @@ struct PathParams {
   LodDev lod, lod_nee;
 };
 
-// one sample of pixel (px, py): tomography exp(-tau) or scattering radiance
-static __device__ float path_sample(const DevField& F, const PathParams& P, int px, int py, int s,
-                                    const float* glx, const float* glw, const float* env,
-                                    Counters& cnt) {
-  float3 o, v;
-  camera_ray(P.cam, P.seed, px, py, s, o, v);
+// One sample of pixel (px, py): tomography exp(-tau) or scattering radiance.
+// Called by all lanes of a warp together (inactive lanes with active = false):
+// every phase (camera tracking, NEE, scattering) runs with the lanes that need
+// it converged, and the lanes regroup after each phase.
+static __device__ float path_sample(const DevField& F, const PathParams& P, bool active, int px,
+                                    int py, int s, const float* glx, const float* glw,
+                                    const float* env, Counters& cnt) {
+  float3 o = make_float3(0.f, 0.f, 0.f), v = make_float3(0.f, 0.f, 1.f);
+  if (active) camera_ray(P.cam, P.seed, px, py, s, o, v);
   const uint32_t pix = (uint32_t)py * (uint32_t)P.cam.W + (uint32_t)px;
   if (P.integrator == 0) {
-    const Mask m = sample_mask(F, P.lod, v, P.seed, pix, (uint32_t)s, 0, TAG_MASK);
-    cnt.rays += 1;
-    return expf(-det_tau(F, m, o, v, 0.f, INFINITY, glx, glw, cnt));
+    float T = 0.f;
+    if (active) {
+      const Mask m = sample_mask(F, P.lod, v, P.seed, pix, (uint32_t)s, 0, TAG_MASK);
+      cnt.rays += 1;
+      T = expf(-det_tau(F, m, o, v, 0.f, INFINITY, glx, glw, cnt));
+    }
+    __syncwarp();
+    return T;
   }
   float thr = 1.f, Lsum = 0.f;
+  bool alive = active;
   GF_TIC(ct);
   for (int b = 0; b < P.max_bounces; ++b) {
-    GF_TIC(cm);
-    const Mask m = sample_mask(F, P.lod, v, P.seed, pix, (uint32_t)s, (uint32_t)b, TAG_MASK);
-    GF_TOC(cnt, 3, cm);
-    float th = 0.f;
-    cnt.rays += 1;
-    const float hit = track<true>(F, m, o, v, 0.f, INFINITY, true, P.seed, pix,
-                                  stream_word((uint32_t)s, (uint32_t)b, TAG_TRACK), env, cnt, &th);
-    if (hit == 0.f) break;
+    float th = 0.f, hit = 0.f;
+    if (alive) {
+      GF_TIC(cm);
+      const Mask m = sample_mask(F, P.lod, v, P.seed, pix, (uint32_t)s, (uint32_t)b, TAG_MASK);
+      GF_TOC(cnt, 3, cm);
+      cnt.rays += 1;
+      hit = track<true>(F, m, o, v, 0.f, INFINITY, true, P.seed, pix,
+                        stream_word((uint32_t)s, (uint32_t)b, TAG_TRACK), env, cnt, &th);
+    }
+    __syncwarp();
+    alive = alive && hit != 0.f;
     const float3 x = make_float3(o.x + th * v.x, o.y + th * v.y, o.z + th * v.z);
-    thr *= P.albedo;
-    const Mask mn = sample_mask(F, P.lod_nee, P.light, P.seed, pix, (uint32_t)s, (uint32_t)b,
-                                TAG_NEE_MASK);
-    cnt.rays += 1;
-    const float Tl = track<false>(F, mn, x, P.light, 0.f, INFINITY, true, P.seed, pix,
-                                  stream_word((uint32_t)s, (uint32_t)b, TAG_NEE), env, cnt, nullptr);
-    Lsum += thr * P.irradiance * Tl * (0.25f / 3.14159265358979f);
-    const uint4 y = rng4(P.seed, 0, kNoPrim, pix, stream_word((uint32_t)s, (uint32_t)b, TAG_SCATTER));
-    const float z = 1.0f - 2.0f * u01(y.x);
-    const float rr = sqrtf(fmaxf(0.0f, 1.0f - z * z));
-    float sn, cs;
-    sincosf(2.0f * 3.14159265358979f * u01(y.y), &sn, &cs);
-    v = make_float3(rr * cs, rr * sn, z);
-    o = x;
+    if (alive) {
+      thr *= P.albedo;
+      const Mask mn = sample_mask(F, P.lod_nee, P.light, P.seed, pix, (uint32_t)s, (uint32_t)b,
+                                  TAG_NEE_MASK);
+      cnt.rays += 1;
+      const float Tl = track<false>(F, mn, x, P.light, 0.f, INFINITY, true, P.seed, pix,
+                                    stream_word((uint32_t)s, (uint32_t)b, TAG_NEE), env, cnt, nullptr);
+      Lsum += thr * P.irradiance * Tl * (0.25f / 3.14159265358979f);
+      const uint4 y = rng4(P.seed, 0, kNoPrim, pix, stream_word((uint32_t)s, (uint32_t)b, TAG_SCATTER));
+      const float z = 1.0f - 2.0f * u01(y.x);
+      const float rr = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+      float sn, cs;
+      sincosf(2.0f * 3.14159265358979f * u01(y.y), &sn, &cs);
+      v = make_float3(rr * cs, rr * sn, z);
+      o = x;
+    }
+    __syncwarp();
+    if (!__any_sync(kFull, alive)) break;
   }
   GF_TOC(cnt, 4, ct);
   return Lsum;
