@@ -230,6 +230,24 @@ gf_status gf_ray_chords(gf_field* field, const float* o, const float* d, const f
 gf_status gf_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n,
                     gf_stream stream);
 
+/* gf_transmittance for callers that cannot allocate device memory at call time
+   (an external memory manager forbids it, the device budget is spent, or only
+   host arrays are at hand).  No counterpart in the paper: it is a deployment
+   variant of gf_transmittance with the same arguments and the same results.
+   It allocates nothing: its scratch (the kernel's work counter and device
+   copies of host buffers) is one file-scope 8 MiB device array, present on
+   every GPU that loads the library until the process exits.  Limits: n_rays
+   <= 200000 (larger calls fail with GF_EINVAL; split them).  Pointers may be
+   host or device memory; host buffers make the call synchronise the stream.
+   The first call on a device looks up the array's device address (do it
+   before any stream capture).  Every call shares the array, which keeps the
+   previous call's contents (the counter is cleared per call): calls that
+   overlap on the GPU (different streams or threads) race and must be
+   serialised by the caller. */
+gf_status gf_transmittance_static(gf_field* field, const float* o, const float* d,
+                                  const float* trange, int64_t n_rays, int mode, int spp,
+                                  uint64_t seed, float* out_T, float* out_tau, gf_stream stream);
+
 gf_status gf_get_stats(gf_field* field, gf_stats* out, int reset);
 /* Wait for the stream, then report (and clear) any device-side error of the field. */
 gf_status gf_sync(gf_field* field, gf_stream stream);

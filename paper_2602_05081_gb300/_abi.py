@@ -80,6 +80,7 @@ _SIGS = {
     "gf_build_bvh": [_vp, _vp],
     "gf_set_lod_mask": [_vp, C.POINTER(gf_lod_desc), C.POINTER(gf_lod_desc)],
     "gf_transmittance": [_vp, _vp, _vp, _vp, _i64, _int, _int, _u64, _vp, _vp, _vp],
+    "gf_transmittance_static": [_vp, _vp, _vp, _vp, _i64, _int, _int, _u64, _vp, _vp, _vp],
     "gf_render": [_vp, C.POINTER(gf_camera), C.POINTER(gf_render_opts), _u64, _vp, _vp],
     "gf_render_backward": [_vp, C.POINTER(gf_camera), C.POINTER(gf_render_opts), _u64, _vp, _vp,
                            _vp],
@@ -166,6 +167,13 @@ def gf_transmittance(field, o, d, trange, n_rays, mode, spp, seed, out_T, out_ta
     _check(lib.gf_transmittance(field, ptr(o), ptr(d), ptr(trange), int(n_rays), int(mode),
                                 int(spp), int(seed), ptr(out_T), ptr(out_tau),
                                 stream_handle(stream)))
+
+
+def gf_transmittance_static(field, o, d, trange, n_rays, mode, spp, seed, out_T, out_tau=None,
+                            stream=None):
+    _check(lib.gf_transmittance_static(field, ptr(o), ptr(d), ptr(trange), int(n_rays),
+                                       int(mode), int(spp), int(seed), ptr(out_T), ptr(out_tau),
+                                       stream_handle(stream)))
 
 
 def gf_render(field, camera: gf_camera, opts: gf_render_opts, seed, out_image, stream=None):

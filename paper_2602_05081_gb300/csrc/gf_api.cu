@@ -16,9 +16,6 @@ using namespace gf;
 struct gf_ctx {
   Ctx c;
 };
-struct gf_field {
-  Field f;
-};
 
 namespace {
 
@@ -173,6 +170,10 @@ void free_field(Field& F) {
 }
 
 }  // namespace
+
+namespace gf {
+gf_status report(gf_status s, const std::string& msg) { return fail(s, msg); }
+}  // namespace gf
 
 extern "C" {
 

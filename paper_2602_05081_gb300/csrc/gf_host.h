@@ -88,4 +88,12 @@ cudaError_t build_bvh(Field& F, cudaStream_t s);
 cudaError_t launch_tomo_backward(const Field& F, const PathParams& P, const float* dLdI,
                                  float* grad, cudaStream_t s);
 
+// sets the thread-local message returned by gf_last_error and returns s
+gf_status report(gf_status s, const std::string& msg);
+
 }  // namespace gf
+
+// opaque handle of include/gf.h
+struct gf_field {
+  gf::Field f;
+};
