@@ -277,8 +277,10 @@ def run_ours(args, rank, world):
     line["counters_per_ray"] = {k: st[k] / max(1, st["rays"])
                                 for k in ("chords", "evals", "nodes", "points", "windows", "steps", "leaves")}
     if any(st["cycles"]):
-        line["phase_cycles_share"] = dict(zip(("traversal", "points", "evaluation", "mask", "path"),
-                                              (c / max(1, st["cycles"][4]) for c in st["cycles"])))
+        tot = max(1, sum(st["cycles"]))
+        line["phase_cycles_share"] = dict(zip(("traversal_steps", "leaf_rounds_pass1", "chord_walks",
+                                               "leaf_rounds_pass2", "decisions"),
+                                              (c / tot for c in st["cycles"])))
     if world == 1 and args.cpu_seconds > 0:
         line["cpu_baseline"] = oracle_sample(args.cpu_seconds)
     print(json.dumps(line), flush=True)

@@ -211,6 +211,7 @@ __global__ void __launch_bounds__(kBackBlock)
 
 cudaError_t launch_tomo_backward(const Field& F, const PathParams& P, const float* dLdI,
                                  float* grad, cudaStream_t s) {
+  (void)cudaGetLastError();  // a stale error of an unrelated call is not ours
   cudaError_t e = cudaMemsetAsync(F.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   BackArgs B;
@@ -223,11 +224,12 @@ cudaError_t launch_tomo_backward(const Field& F, const PathParams& P, const floa
   B.n = F.n;
   B.grad = grad;
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tomo_backward, kBackBlock, 0);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tomo_backward, kBackBlock, 0) != cudaSuccess)
+    (void)cudaGetLastError();
   if (per_sm < 1) per_sm = 1;
   const int64_t tiles = (int64_t)((P.cam.W + 7) / 8) * ((P.cam.H + 3) / 4);
   const int64_t need = (tiles + kBackBlock / 32 - 1) / (kBackBlock / 32);
-  int64_t g = (int64_t)F.ctx->sm_count * per_sm;
+  int64_t g = (int64_t)F.ctx.sm_count * per_sm;
   if (need < g) g = need;
   k_tomo_backward<<<(unsigned)(g < 1 ? 1 : g), kBackBlock, 0, s>>>(F.dev, P, B, dLdI, F.counter);
   return cudaGetLastError();

@@ -164,7 +164,7 @@ gf_status camera_params(const gf_camera* c, const gf_render_opts* o, uint64_t se
 void free_field(Field& F) {
   void* ptrs[] = {F.p_mu, F.p_quat, F.p_ls, F.p_om, F.p_ph, F.p_w, F.rec_orig, F.box_orig,
                   F.kw_orig, F.rec, F.rec16, F.nodes, F.sorted_orig, F.labels, F.err,
-                  F.stats, F.counter, F.cell_acc, F.stage};
+                  F.stats, F.counter, F.cell_acc, F.stage, F.wscratch, F.gl};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -240,7 +240,7 @@ gf_status gf_load_field(gf_ctx* ctx, const gf_params* p, const gf_field_opts* op
   cudaStream_t s = (cudaStream_t)stream;
   gf_field* h = new gf_field;
   Field& F = h->f;
-  F.ctx = &ctx->c;
+  F.ctx = ctx->c;
   F.n = p->n;
   F.opts = *opts;
   const int64_t n = p->n;
@@ -254,7 +254,11 @@ gf_status gf_load_field(gf_ctx* ctx, const gf_params* p, const gf_field_opts* op
         (e = A((void**)&F.rec_orig, 64 * n)) || (e = A((void**)&F.box_orig, 24 * n)) ||
         (e = A((void**)&F.kw_orig, 4 * n)) || (e = A((void**)&F.labels, 3 * n)) ||
         (e = A((void**)&F.err, 4)) || (e = A((void**)&F.stats, 8 * kNumStats)) ||
-        (e = A((void**)&F.counter, 16)) || (e = A((void**)&F.cell_acc, 128 * 4)))
+        (e = A((void**)&F.counter, 16)) || (e = A((void**)&F.cell_acc, 128 * 4)) ||
+        (e = A((void**)&F.gl, 2 * kGLTotal * sizeof(float))))
+      break;
+    if ((e = cudaMemcpyAsync(F.gl, ctx->c.gl, 2 * kGLTotal * sizeof(float),
+                             cudaMemcpyDeviceToDevice, s)))
       break;
     if (p->band && (e = A(&band_dev, n))) break;
     auto cp = [&](void* dst, const void* src, size_t bytes) {
@@ -314,7 +318,7 @@ gf_status gf_load_field(gf_ctx* ctx, const gf_params* p, const gf_field_opts* op
   for (int k = 0; k < 8; ++k) F.dev.env[k] = (float)std::exp(-0.5 * k * k);
   F.dev.err = F.err;
   F.dev.stats = F.stats;
-  F.dev.gl = ctx->c.gl;
+  F.dev.gl = F.gl;
   F.dev.root = -1;
   *out = h;
   return GF_OK;
@@ -322,7 +326,7 @@ gf_status gf_load_field(gf_ctx* ctx, const gf_params* p, const gf_field_opts* op
 
 gf_status gf_field_free(gf_field* h) {
   if (!h) return GF_OK;
-  cudaSetDevice(h->f.ctx->device);
+  cudaSetDevice(h->f.ctx.device);
   free_field(h->f);
   delete h;
   return GF_OK;
@@ -331,7 +335,7 @@ gf_status gf_field_free(gf_field* h) {
 gf_status gf_build_bvh(gf_field* h, gf_stream stream) {
   if (!h) return fail(GF_EINVAL, "field null");
   Field& F = h->f;
-  GF_CUDA(cudaSetDevice(F.ctx->device), "cudaSetDevice");
+  GF_CUDA(cudaSetDevice(F.ctx.device), "cudaSetDevice");
   if (F.built) return GF_OK;
   if (F.opts.precision != GF_PREC_FP32)
     return fail(GF_EINVAL, "reduced-precision records are not available in this build");
@@ -366,7 +370,7 @@ gf_status gf_transmittance(gf_field* h, const float* o, const float* d, const fl
   if (mode != GF_TR_DETERMINISTIC && mode != GF_TR_RATIO_TRACKING) return fail(GF_EINVAL, "bad mode");
   if (spp < 1 || spp > (1 << 20)) return fail(GF_EINVAL, "spp in [1, 2^20]");
   if (n_rays == 0) return GF_OK;
-  GF_CUDA(cudaSetDevice(F.ctx->device), "cudaSetDevice");
+  GF_CUDA(cudaSetDevice(F.ctx.device), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
   size_t n = (size_t)n_rays;
   gf_status st = ensure_stage(F, 256 * 6 + n * 4 * (3 + 3 + 2 + 1 + 1));
@@ -412,7 +416,7 @@ gf_status gf_render(gf_field* h, const gf_camera* camera, const gf_render_opts* 
   PathParams P;
   gf_status st = camera_params(camera, opts, seed, F, P);
   if (st) return st;
-  GF_CUDA(cudaSetDevice(F.ctx->device), "cudaSetDevice");
+  GF_CUDA(cudaSetDevice(F.ctx.device), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
   size_t bytes = (size_t)P.cam.W * P.cam.H * 4;
   void* od = out_image;
@@ -439,7 +443,7 @@ gf_status gf_render_backward(gf_field* h, const gf_camera* camera, const gf_rend
   if (st) return st;
   if (opts->integrator != GF_INTEG_TOMO)
     return fail(GF_EINVAL, "the adjoint covers the tomography integrator");
-  GF_CUDA(cudaSetDevice(F.ctx->device), "cudaSetDevice");
+  GF_CUDA(cudaSetDevice(F.ctx.device), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
   size_t npix = (size_t)P.cam.W * P.cam.H;
   size_t gbytes = (size_t)F.n * 15 * 4;
@@ -462,7 +466,7 @@ gf_status gf_field_labels(gf_field* h, uint8_t* band, uint8_t* cone, uint8_t* ce
                           gf_stream stream) {
   if (!h) return fail(GF_EINVAL, "field null");
   Field& F = h->f;
-  GF_CUDA(cudaSetDevice(F.ctx->device), "cudaSetDevice");
+  GF_CUDA(cudaSetDevice(F.ctx.device), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
   size_t n = (size_t)F.n;
   if (band) GF_CUDA(cudaMemcpyAsync(band, F.labels, n, cudaMemcpyDefault, s), "labels");
@@ -480,7 +484,7 @@ gf_status gf_ray_chords(gf_field* h, const float* o, const float* d, const float
   if (!F.built) return fail(GF_ESTATE, "gf_build_bvh has not run");
   if (!lod_is_deterministic(F.lod)) return fail(GF_EINVAL, "chord lists need a deterministic mask");
   if (n_rays <= 0) return GF_OK;
-  GF_CUDA(cudaSetDevice(F.ctx->device), "cudaSetDevice");
+  GF_CUDA(cudaSetDevice(F.ctx.device), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
   size_t n = (size_t)n_rays, nc = n * (size_t)cap;
   gf_status st = ensure_stage(F, 256 * 8 + n * 4 * 9 + nc * 12);
@@ -544,7 +548,7 @@ gf_status gf_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int
 gf_status gf_get_stats(gf_field* h, gf_stats* out, int reset) {
   if (!h || !out) return fail(GF_EINVAL, "null argument");
   Field& F = h->f;
-  GF_CUDA(cudaSetDevice(F.ctx->device), "cudaSetDevice");
+  GF_CUDA(cudaSetDevice(F.ctx.device), "cudaSetDevice");
   unsigned long long v[kNumStats];
   GF_CUDA(cudaDeviceSynchronize(), "sync");
   GF_CUDA(cudaMemcpy(v, F.stats, sizeof(v), cudaMemcpyDeviceToHost), "stats");
@@ -564,7 +568,7 @@ gf_status gf_get_stats(gf_field* h, gf_stats* out, int reset) {
 gf_status gf_sync(gf_field* h, gf_stream stream) {
   if (!h) return fail(GF_EINVAL, "field null");
   Field& F = h->f;
-  GF_CUDA(cudaSetDevice(F.ctx->device), "cudaSetDevice");
+  GF_CUDA(cudaSetDevice(F.ctx.device), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
   GF_CUDA(cudaStreamSynchronize(s), "stream sync");
   int err = 0;

@@ -121,6 +121,7 @@ __global__ void k_pack(const __grid_constant__ PackArgs A) {
 }
 
 cudaError_t launch_pack(Field& F, const gf_params& P, cudaStream_t s) {
+  (void)cudaGetLastError();  // a stale error of an unrelated call is not ours
   PackArgs A;
   A.p = P;
   A.weight_mode = F.opts.weight_mode;
@@ -303,6 +304,7 @@ __global__ void k_refit(const float* box, const float4* rec, int64_t n, Node* no
 static cudaError_t dalloc(void** p, size_t bytes) { return cudaMalloc(p, bytes ? bytes : 16); }
 
 cudaError_t build_bvh(Field& F, cudaStream_t s) {
+  (void)cudaGetLastError();  // a stale error of an unrelated call is not ours
   const int64_t n = F.n;
   cudaError_t e = cudaSuccess;
   unsigned int* bounds = nullptr;

@@ -45,7 +45,8 @@ struct ChordParams {
 };
 
 struct Field {
-  Ctx* ctx = nullptr;
+  Ctx ctx;                     // copy: a field outlives the gf_ctx it came from
+  float* gl = nullptr;         // the field's own Gauss-Legendre tables
   int64_t n = 0;
   gf_field_opts opts{};
   // raw parameters (device copies, original order) for the adjoint
@@ -74,6 +75,9 @@ struct Field {
   // staging for host buffers
   void* stage = nullptr;
   size_t stage_bytes = 0;
+  // per-warp chord store of the scattering renderer (grows on demand)
+  mutable float4* wscratch = nullptr;
+  mutable size_t wscratch_bytes = 0;
 };
 
 // launchers (return cudaError_t of the launch)

@@ -183,15 +183,17 @@ __global__ void k_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out
 template <class K>
 static int persistent_grid(const Field& F, K kernel, int64_t warps_of_work) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0) != cudaSuccess)
+    (void)cudaGetLastError();
   if (per_sm < 1) per_sm = 1;
   const int64_t need = (warps_of_work + kBlock / 32 - 1) / (kBlock / 32);
-  int64_t g = (int64_t)F.ctx->sm_count * per_sm;
+  int64_t g = (int64_t)F.ctx.sm_count * per_sm;
   if (need < g) g = need;
   return (int)(g < 1 ? 1 : g);
 }
 
 cudaError_t launch_transmittance(const Field& F, const TrParams& P, cudaStream_t s) {
+  (void)cudaGetLastError();  // a stale error of an unrelated call is not ours
   cudaError_t e = cudaMemsetAsync(P.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   const int64_t tiles = (P.n + 31) / 32;
@@ -204,6 +206,7 @@ cudaError_t launch_transmittance(const Field& F, const TrParams& P, cudaStream_t
 }
 
 cudaError_t launch_render(const Field& F, const PathParams& P, float* out, cudaStream_t s) {
+  (void)cudaGetLastError();  // a stale error of an unrelated call is not ours
   cudaError_t e = cudaMemsetAsync(F.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   if (P.integrator == GF_INTEG_SCATTER) return launch_render_scatter(F, P, out, s);
@@ -213,6 +216,7 @@ cudaError_t launch_render(const Field& F, const PathParams& P, float* out, cudaS
 }
 
 cudaError_t launch_ray_chords(const Field& F, const ChordParams& P, cudaStream_t s) {
+  (void)cudaGetLastError();  // a stale error of an unrelated call is not ours
   cudaError_t e = cudaMemsetAsync(P.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   k_ray_chords<<<persistent_grid(F, k_ray_chords, (P.n + 31) / 32), kBlock, 0, s>>>(F.dev, P);
@@ -221,6 +225,7 @@ cudaError_t launch_ray_chords(const Field& F, const ChordParams& P, cudaStream_t
 
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n,
                           cudaStream_t s) {
+  (void)cudaGetLastError();  // a stale error of an unrelated call is not ours
   if (n <= 0) return cudaSuccess;
   const int64_t blocks = (n + 255) / 256;
   k_philox<<<(unsigned)blocks, 256, 0, s>>>(ctr, key, out, n);

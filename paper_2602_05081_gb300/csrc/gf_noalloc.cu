@@ -60,7 +60,7 @@ extern "C" gf_status gf_transmittance_static(gf_field* h, const float* o, const 
   if (mode != GF_TR_DETERMINISTIC && mode != GF_TR_RATIO_TRACKING) return report(GF_EINVAL, "bad mode");
   if (spp < 1 || spp > (1 << 20)) return report(GF_EINVAL, "spp in [1, 2^20]");
   if (n_rays == 0) return GF_OK;
-  const int dev = F.ctx->device;
+  const int dev = F.ctx.device;
   if (dev < 0 || dev >= 64) return report(GF_EINVAL, "device index beyond 63");
   cudaError_t e = cudaSetDevice(dev);
   if (e != cudaSuccess) return report(GF_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));

@@ -28,6 +28,7 @@ constexpr int kWWarps = 4;      // warps per block
 constexpr int kLeafQ = 96;      // queued leaves per warp (<= 31 left + 64 new)
 constexpr int kChordQ = 64;     // queued chords per warp (<= 31 left + 32 new)
 constexpr int kPK = 8;          // tentative points per lane and window
+constexpr int kSlotCh = 256;    // stored chords per lane and window (global scratch)
 
 // One slot per lane, 89 words: an odd stride keeps same-field accesses of the
 // 32 slots in distinct shared-memory banks.
@@ -38,7 +39,7 @@ struct LaneRay {
   float bw[8];                  // LoD band weights
   uint32_t mask_lo, mask_hi;    // LoD cell bits
   int npts;                     // points emitted in the window (may exceed kPK)
-  int ovf;                      // ordered encoding of the smallest dropped t
+  int nch;                      // chords stored for the window (may exceed kSlotCh)
   float pt[kPK], pu[kPK], kap[kPK], kb[kPK];
 };
 static_assert(sizeof(LaneRay) % 8 == 4, "odd word stride");
@@ -136,11 +137,10 @@ __device__ __forceinline__ void walk_chord(const DevField& F, WarpQ& Q, const Ch
 // One traversal phase for the slots with want = true.  The warp shares one
 // stack of (node, slot) entries: every step pops up to 32 entries from the
 // frontiers of all its rays, so lanes stay busy while 32 rays are in flight.
-// PASS 1 collects the tentative points of each slot's window; PASS 2 sums
-// kappa and kappa_bar at them.
-template <int PASS>
+// It collects the tentative points of each slot's window and stores the
+// window's chords for their evaluation.
 __device__ void warp_phase(const DevField& F, WarpQ& Q, bool want, uint32_t lane, uint64_t seed,
-                           const float* env, Counters& cnt) {
+                           const float* env, float4* wch, Counters& cnt) {
   const unsigned lt = (1u << lane) - 1u;
   int sp = 0, lq_n = 0, cq_n = 0;  // warp-uniform sizes
   {
@@ -165,6 +165,7 @@ __device__ void warp_phase(const DevField& F, WarpQ& Q, bool want, uint32_t lane
       break;
     }
     // ---------------- one traversal step: up to 32 (node, slot) entries
+    GF_TIC(t_step);
     int take = sp < 32 ? sp : 32;
     if (sp > kWStack - 96) take = 1;  // near capacity: depth first
     int ent = (int)lane < take ? Q.stk[sp - take + (int)lane] : -1;
@@ -189,20 +190,8 @@ __device__ void warp_phase(const DevField& F, WarpQ& Q, bool want, uint32_t lane
       float tn0, tf0, tn1, tf1;
       slab_interval(o, inv, a.x, a.y, a.z, a.w, b.x, b.y, tn0, tf0);
       slab_interval(o, inv, b.z, b.w, c.x, c.y, c.z, c.w, tn1, tf1);
-      bool h0, h1;
-      if (PASS == 1) {
-        h0 = fmaxf(tn0, R.ta) <= fminf(tf0, R.te);
-        h1 = fmaxf(tn1, R.ta) <= fminf(tf1, R.te);
-      } else {
-        h0 = false;
-        h1 = false;
-        const int np = R.npts;
-        for (int i = 0; i < np; ++i) {
-          const float t = R.pt[i];
-          h0 |= t >= tn0 && t <= tf0;
-          h1 |= t >= tn1 && t <= tf1;
-        }
-      }
+      bool h0 = fmaxf(tn0, R.ta) <= fminf(tf0, R.te);
+      bool h1 = fmaxf(tn1, R.ta) <= fminf(tf1, R.te);
       h0 = h0 && (m0 & mask);
       h1 = h1 && (m1 & mask);
       c0 = d.x;
@@ -239,6 +228,7 @@ __device__ void warp_phase(const DevField& F, WarpQ& Q, bool want, uint32_t lane
       __syncwarp();
     }
     const bool any_trav = sp > 0;
+    if (lane == 0) GF_TOC(cnt, 0, t_step);
     // ---------------- leaf rounds: 32 leaves of any slots' rays at a time
     while (lq_n >= 32 || (!any_trav && lq_n > 0)) {
       const int tk = lq_n < 32 ? lq_n : 32;
@@ -251,75 +241,59 @@ __device__ void warp_phase(const DevField& F, WarpQ& Q, bool want, uint32_t lane
       __syncwarp();
       lq_n -= tk;
       cnt.leaves += have ? 1ull : 0ull;
-      if (PASS == 1) {
-        bool ok = false;
-        ChordItem ci;
-        if (have) {
-          const LaneRay& R = Q.r[own];
-          Prim P;
-          Chord ch;
-          float w;
-          if (slot_chord(F, R, j, P, ch, w)) {
-            const float tin = ch.tc + ch.dtin, tout = ch.tc + ch.dtout;
-            if (tin < R.te && tout >= R.ta) {
-              ok = true;
-              ci.tc = ch.tc;
-              ci.dtin = ch.dtin;
-              ci.dtout = ch.dtout;
-              ci.h = w * ch.absA * expf(-0.5f * ch.qmin);
-              ci.sa = sqrtf(ch.a);
-              ci.dts = ch.dts;
-              ci.smax = ci.sa * ch.hw;
-              ci.orig = ch.orig;
-              ci.owner = own;
-            }
-          }
-        }
-        const unsigned bc = __ballot_sync(kFull, ok);
-        if (ok) Q.cq[cq_n + __popc(bc & lt)] = ci;
-        cq_n += __popc(bc);
-        cnt.chords += ok ? 1ull : 0ull;
-        __syncwarp();
-        while (cq_n >= 32) {
-          const bool hv = true;
-          ChordItem cw = Q.cq[cq_n - 32 + (int)lane];
-          __syncwarp();
-          cq_n -= 32;
-          if (hv) walk_chord(F, Q, cw, seed, env, cnt.points);
-          __syncwarp();
-        }
-      } else {
-        if (have) {
-          LaneRay& R = Q.r[own];
-          Prim P;
-          Chord ch;
-          float w;
-          if (slot_chord(F, R, j, P, ch, w)) {
-            const float tin = ch.tc + ch.dtin, tout = ch.tc + ch.dtout;
+      GF_TIC(t_leaf);
+      bool ok = false;
+      ChordItem ci;
+      if (have) {
+        const LaneRay& R = Q.r[own];
+        Prim P;
+        Chord ch;
+        float w;
+        if (slot_chord(F, R, j, P, ch, w)) {
+          const float tin = ch.tc + ch.dtin, tout = ch.tc + ch.dtout;
+          if (tin < R.te && tout >= R.ta) {
+            ok = true;
             const float wa = w * ch.absA;
-            const float y2 = -0.5f * kLog2e * ch.a, y1 = -kLog2e * ch.b;
-            const float y0 = fmaf(-0.5f * kLog2e, ch.g, log2f(wa));
-            const float h = wa * expf(-0.5f * ch.qmin);
-            const float sa = sqrtf(ch.a);
-            const int n = R.npts;
-            for (int i = 0; i < n; ++i) {
-              const float t = R.pt[i];
-              if (t >= tin && t <= tout) {
-                const float dt = t - ch.tc;
-                const float y = fmaf(fmaf(y2, dt, y1), dt, y0);
-                atomicAdd(&R.kap[i], ex2f(y) * cosf_fast(fmaf(ch.B, dt, ch.delta)));
-                int m = (int)(fabsf(dt - ch.dts) * sa);
-                m = m > 7 ? 7 : m;
-                atomicAdd(&R.kb[i], h * env[m]);
-                ++cnt.evals;
-              }
+            const float h = wa * expf(-0.5f * ch.qmin), sa = sqrtf(ch.a);
+            // evaluation record for the points of this window
+            const int k = atomicAdd(&Q.r[own].nch, 1);
+            if (k < kSlotCh) {
+              float4* dst = wch + ((size_t)own * kSlotCh + k) * 3;
+              dst[0] = make_float4(ch.tc, tin, tout, ch.B);
+              dst[1] = make_float4(-0.5f * kLog2e * ch.a, -kLog2e * ch.b,
+                                   fmaf(-0.5f * kLog2e, ch.g, log2f(wa)), ch.delta);
+              dst[2] = make_float4(h, sa, ch.dts, 0.f);
             }
+            ci.tc = ch.tc;
+            ci.dtin = ch.dtin;
+            ci.dtout = ch.dtout;
+            ci.h = h;
+            ci.sa = sa;
+            ci.dts = ch.dts;
+            ci.smax = ci.sa * ch.hw;
+            ci.orig = ch.orig;
+            ci.owner = own;
           }
         }
+      }
+      const unsigned bc = __ballot_sync(kFull, ok);
+      if (ok) Q.cq[cq_n + __popc(bc & lt)] = ci;
+      cq_n += __popc(bc);
+      cnt.chords += ok ? 1ull : 0ull;
+      __syncwarp();
+      if (lane == 0) GF_TOC(cnt, 1, t_leaf);
+      GF_TIC(t_walk);
+      while (cq_n >= 32) {
+        const bool hv = true;
+        ChordItem cw = Q.cq[cq_n - 32 + (int)lane];
+        __syncwarp();
+        cq_n -= 32;
+        if (hv) walk_chord(F, Q, cw, seed, env, cnt.points);
         __syncwarp();
       }
+      if (lane == 0) GF_TOC(cnt, 2, t_walk);
     }
-    if (PASS == 1 && !any_trav && lq_n == 0) {
+    if (!any_trav && lq_n == 0) {
       // traversal over and no leaf left: walk the remaining chords
       while (cq_n > 0) {
         const int tk = cq_n < 32 ? cq_n : 32;
@@ -384,9 +358,56 @@ __device__ __forceinline__ bool start_ray(const DevField& F, LaneRay& R, PathSta
   return true;
 }
 
+// kappa and kappa_bar at the points of every slot, from the chords pass 1
+// stored: the warp scans each slot's list (lanes over chords), then reduces.
+__device__ void eval_stored(WarpQ& Q, const float4* wch, const float* env, uint32_t lane,
+                            Counters& cnt) {
+  for (int s = 0; s < 32; ++s) {
+    LaneRay& R = Q.r[s];
+    const int ns = R.npts;
+    if (ns <= 0) continue;  // uniform: every lane reads the same slot
+    const int mc = R.nch;
+    float pt[kPK], kap[kPK], kb[kPK];
+#pragma unroll
+    for (int i = 0; i < kPK; ++i) {
+      pt[i] = i < ns ? R.pt[i] : INFINITY;
+      kap[i] = 0.f;
+      kb[i] = 0.f;
+    }
+    const float4* base = wch + (size_t)s * kSlotCh * 3;
+    for (int c = (int)lane; c < mc; c += 32) {
+      const float4 a = base[3 * c], b = base[3 * c + 1], e = base[3 * c + 2];
+#pragma unroll
+      for (int i = 0; i < kPK; ++i) {
+        const float t = pt[i];
+        if (t >= a.y && t <= a.z) {
+          const float dt = t - a.x;
+          const float y = fmaf(fmaf(b.x, dt, b.y), dt, b.z);
+          kap[i] = fmaf(ex2f(y), cosf_fast(fmaf(a.w, dt, b.w)), kap[i]);
+          int m = (int)(fabsf(dt - e.z) * e.y);
+          m = m > 7 ? 7 : m;
+          kb[i] = fmaf(e.x, env[m], kb[i]);
+          ++cnt.evals;
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kPK; ++i) {
+      if (i < ns) {
+        const float k1 = warp_sum(kap[i]), k2 = warp_sum(kb[i]);
+        if (lane == 0) {
+          R.kap[i] = k1;
+          R.kb[i] = k2;
+        }
+      }
+    }
+  }
+  __syncwarp();
+}
+
 __global__ void __launch_bounds__(kWWarps * 32)
     k_render_scatter(const __grid_constant__ DevField F, const PathParams P, float* out,
-                     int* counter) {
+                     int* counter, float4* chord_store) {
   extern __shared__ __align__(16) unsigned char smraw[];
   float* env = reinterpret_cast<float*>(smraw);
   WarpQ* Qs = reinterpret_cast<WarpQ*>(smraw + 64);
@@ -395,6 +416,7 @@ __global__ void __launch_bounds__(kWWarps * 32)
   const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
   WarpQ& Q = Qs[wid];
   LaneRay& R = Q.r[lane];
+  float4* wch = chord_store + ((size_t)blockIdx.x * kWWarps + wid) * 32 * kSlotCh * 3;
   Counters cnt;
   const int npix = P.cam.W * P.cam.H;
   const float inv4pi = 0.25f / 3.14159265358979f;
@@ -493,15 +515,15 @@ __global__ void __launch_bounds__(kWWarps * 32)
     if (!__any_sync(kFull, want)) break;
     // ---- pass 1: tentative points of the window
     R.npts = 0;
-    R.ovf = INT_MAX;
+    R.nch = 0;
     __syncwarp();
-    warp_phase<1>(F, Q, want, lane, P.seed, env, cnt);
+    warp_phase(F, Q, want, lane, P.seed, env, wch, cnt);
     // owner: a window whose points overflowed the slots is halved and redone;
     // otherwise its points are sorted by t for the decisions
     int n = 0;
     bool ovf = false;
     if (want) {
-      ovf = R.npts > kPK;
+      ovf = R.npts > kPK || R.nch > kSlotCh;
       n = ovf ? 0 : R.npts;
       for (int k = 1; k < n; ++k) {
         const float t = R.pt[k], u = R.pu[k];
@@ -522,10 +544,10 @@ __global__ void __launch_bounds__(kWWarps * 32)
     }
     cnt.windows += want ? 1ull : 0ull;
     __syncwarp();
-    // ---- pass 2: kappa and kappa_bar at the points
-    const bool want2 = want && n > 0;
-    if (__any_sync(kFull, want2)) warp_phase<2>(F, Q, want2, lane, P.seed, env, cnt);
+    // ---- kappa and kappa_bar at the points, from the stored chords
+    if (__any_sync(kFull, want && n > 0)) eval_stored(Q, wch, env, lane, cnt);
     // ---- decisions
+    GF_TIC(t_dec);
     if (want) {
       const bool last = R.te >= S.t1;
       if (ovf) {
@@ -570,6 +592,7 @@ __global__ void __launch_bounds__(kWWarps * 32)
       }
     }
     __syncwarp();
+    if (lane == 0) GF_TOC(cnt, 4, t_dec);
   }
   flush_counters(F, cnt, lane);
 }
@@ -577,19 +600,32 @@ __global__ void __launch_bounds__(kWWarps * 32)
 size_t scatter_smem_bytes() { return 64 + sizeof(WarpQ) * kWWarps; }
 
 cudaError_t launch_render_scatter(const Field& F, const PathParams& P, float* out, cudaStream_t s) {
+  (void)cudaGetLastError();  // a stale error of an unrelated call is not ours
   cudaError_t e = cudaMemsetAsync(F.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   const size_t smem = scatter_smem_bytes();
   e = cudaFuncSetAttribute(k_render_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_scatter, kWWarps * 32, smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_scatter, kWWarps * 32, smem) != cudaSuccess)
+    (void)cudaGetLastError();
   if (per_sm < 1) per_sm = 1;
   const int64_t npix = (int64_t)P.cam.W * P.cam.H;
   const int64_t need = (npix + kWWarps * 32 - 1) / (kWWarps * 32);
-  int64_t g = (int64_t)F.ctx->sm_count * per_sm;
+  int64_t g = (int64_t)F.ctx.sm_count * per_sm;
   if (need < g) g = need;
-  k_render_scatter<<<(unsigned)(g < 1 ? 1 : g), kWWarps * 32, smem, s>>>(F.dev, P, out, F.counter);
+  if (g < 1) g = 1;
+  // per-warp chord store: 32 slots x kSlotCh records of 3 float4
+  const size_t store = (size_t)g * kWWarps * 32 * kSlotCh * 3 * sizeof(float4);
+  if (F.wscratch_bytes < store) {
+    if (F.wscratch) cudaFree(F.wscratch);
+    F.wscratch = nullptr;
+    F.wscratch_bytes = 0;
+    e = cudaMalloc((void**)&F.wscratch, store);
+    if (e != cudaSuccess) return e;
+    F.wscratch_bytes = store;
+  }
+  k_render_scatter<<<(unsigned)g, kWWarps * 32, smem, s>>>(F.dev, P, out, F.counter, F.wscratch);
   return cudaGetLastError();
 }
 
