@@ -240,6 +240,25 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     st_e2e = field.stats(reset=True)
+    # the same step with 32-byte FP16 / BF16 records (FP32 math)
+    prec_ms = {"fp32": sum(step_ms) / len(step_ms)}
+    for prec in ("fp16", "bf16"):
+        fr = api.Field(ctx, p, precision=prec)
+        for _ in range(max(1, args.warmup)):
+            for lo in lods:
+                fr.set_lod(lo)
+                _abi.gf_render(fr.h, cam, ro, SEED, out, stream)
+        flush.fill_(1.0)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for lo in lods:
+            fr.set_lod(lo)
+            _abi.gf_render(fr.h, cam, ro, SEED, out, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        fr.sync(stream)
+        prec_ms[prec] = ev0.elapsed_time(ev1)
+        fr.free()
     if rank != 0:
         return
     import ctypes
@@ -264,7 +283,7 @@ def run_ours(args, rank, world):
         "evals_per_step": st["evals"] / args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_geval, "unit": "Geval/s",
                      "frac": achieved / peak_geval, "traffic": traffic,
-                     "kernel": "k_render<true> (delta + ratio tracking)",
+                     "kernel": "k_render_scatter (delta + ratio tracking)",
                      "peak_basis": "%d SMs x %d SFU/clk / %d SFU per eval x %.0f MHz (%s clock)"
                                    % (sm_count, MUFU_PER_SM_CLK, MUFU_PER_EVAL,
                                       peaks.get("sm_max_mhz", 2070.0), peak_kind)},
@@ -272,6 +291,7 @@ def run_ours(args, rank, world):
                 "h2d_bytes_per_step": 4 * (ctypes.sizeof(_abi.gf_camera) + ctypes.sizeof(_abi.gf_render_opts)),
                 "d2h_bytes_per_step": 4 * RES * RES * 4},
         "gpu_launches": 4 * args.steps,
+        "storage_ms_per_step": prec_ms,
         "clocks": clk,
     }
     line["counters_per_ray"] = {k: st[k] / max(1, st["rays"])

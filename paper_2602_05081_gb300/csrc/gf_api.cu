@@ -111,6 +111,10 @@ gf_status ensure_stage(Field& F, size_t bytes) {
   return GF_OK;
 }
 
+}  // namespace
+
+namespace gf {
+
 bool lod_ok(const gf_lod_desc* l) {
   return l && l->freq_policy >= 0 && l->freq_policy <= 3 && l->cone_policy >= 0 &&
          l->cone_policy <= 2 && l->max_band >= 0 && l->max_band <= 7;
@@ -160,6 +164,10 @@ gf_status camera_params(const gf_camera* c, const gf_render_opts* o, uint64_t se
   P.lod_nee = F.lod_nee;
   return GF_OK;
 }
+
+}  // namespace gf
+
+namespace {
 
 void free_field(Field& F) {
   void* ptrs[] = {F.p_mu, F.p_quat, F.p_ls, F.p_om, F.p_ph, F.p_w, F.rec_orig, F.box_orig,
@@ -337,8 +345,6 @@ gf_status gf_build_bvh(gf_field* h, gf_stream stream) {
   Field& F = h->f;
   GF_CUDA(cudaSetDevice(F.ctx.device), "cudaSetDevice");
   if (F.built) return GF_OK;
-  if (F.opts.precision != GF_PREC_FP32)
-    return fail(GF_EINVAL, "reduced-precision records are not available in this build");
   const int64_t n = F.n;
   GF_CUDA(cudaMalloc((void**)&F.rec, 64 * n), "alloc records");
   GF_CUDA(cudaMalloc((void**)&F.nodes, n > 1 ? (n - 1) * sizeof(Node) : 16), "alloc nodes");
@@ -348,6 +354,24 @@ gf_status gf_build_bvh(gf_field* h, gf_stream stream) {
   F.rec_orig = nullptr;
   cudaFree(F.box_orig);
   F.box_orig = nullptr;
+  if (F.opts.precision != GF_PREC_FP32) {
+    // 32-byte records replace the 64-byte ones on the rendering path
+    GF_CUDA(cudaMalloc((void**)&F.rec16, 32 * n), "alloc reduced records");
+    cudaStream_t s = (cudaStream_t)stream;
+    int herr = 0;
+    GF_CUDA(launch_pack16(F, s), "pack reduced records");
+    GF_CUDA(cudaMemcpyAsync(&herr, F.err, 4, cudaMemcpyDeviceToHost, s), "read error word");
+    GF_CUDA(cudaStreamSynchronize(s), "sync");
+    if (herr) {
+      cudaMemset(F.err, 0, 4);
+      return fail(GF_EINVAL, "amplitude outside the FP16 range: use BF16 records");
+    }
+    F.dev.rec16 = F.rec16;
+    F.dev.orig16 = F.sorted_orig;
+    cudaFree(F.rec);  // the 64-byte records are not read again
+    F.rec = nullptr;
+    F.dev.rec = nullptr;
+  }
   F.built = true;
   return GF_OK;
 }
@@ -443,6 +467,8 @@ gf_status gf_render_backward(gf_field* h, const gf_camera* camera, const gf_rend
   if (st) return st;
   if (opts->integrator != GF_INTEG_TOMO)
     return fail(GF_EINVAL, "the adjoint covers the tomography integrator");
+  if (F.opts.precision != GF_PREC_FP32)
+    return fail(GF_EINVAL, "the adjoint needs FP32 records");
   GF_CUDA(cudaSetDevice(F.ctx.device), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
   size_t npix = (size_t)P.cam.W * P.cam.H;

@@ -5,6 +5,9 @@
 
 #include <cstring>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <cub/device/device_radix_sort.cuh>
 
 #include "gf_host.h"
@@ -16,7 +19,7 @@ namespace gf {
 // ---------------------------------------------------------------------------
 struct PackArgs {
   gf_params p;
-  int weight_mode, omega_frame;
+  int weight_mode, omega_frame, precision;
   float ksig;
   float axes[kCones][3];
   float4* rec;
@@ -107,7 +110,10 @@ __global__ void k_pack(const __grid_constant__ PackArgs A) {
     float sjj = R[a][0] * R[a][0] * s[0] * s[0] + R[a][1] * R[a][1] * s[1] * s[1] +
                 R[a][2] * R[a][2] * s[2] * s[2];
     float hw = A.ksig * sqrtf(sjj);
-    float pad = 1e-5f * hw + 1e-6f * (1.f + fabsf(mu[a]));
+    // reduced-precision records move the decoded ellipsoid by up to ~5e-4 (FP16)
+    // or ~4e-3 (BF16) of its size and the mean by half a u16 step: pad for it
+    const float rel = A.precision == GF_PREC_BF16 ? 1e-2f : (A.precision == GF_PREC_FP16 ? 2e-3f : 1e-5f);
+    float pad = rel * hw + (A.precision == GF_PREC_FP32 ? 1e-6f : 1e-4f) * (1.f + fabsf(mu[a]));
     A.box[6 * i + a] = mu[a] - hw - pad;
     A.box[6 * i + 3 + a] = mu[a] + hw + pad;
   }
@@ -126,6 +132,7 @@ cudaError_t launch_pack(Field& F, const gf_params& P, cudaStream_t s) {
   A.p = P;
   A.weight_mode = F.opts.weight_mode;
   A.omega_frame = F.opts.omega_frame;
+  A.precision = F.opts.precision;
   A.ksig = F.opts.k_sigma;
   for (int k = 0; k < kCones; ++k)
     for (int j = 0; j < 3; ++j) A.axes[k][j] = F.dev.axes[k][j];
@@ -364,6 +371,10 @@ cudaError_t build_bvh(Field& F, cudaStream_t s) {
     };
     F.dev.lo = make_float3(dec(hb[0]), dec(hb[1]), dec(hb[2]));
     F.dev.hi = make_float3(dec(hb[3]), dec(hb[4]), dec(hb[5]));
+    for (int k = 0; k < 3; ++k) {
+      F.mu_lo[k] = dec(hb[6 + k]);
+      F.mu_hi[k] = dec(hb[9 + k]);
+    }
   }
   F.dev.rec = F.rec;
   F.dev.nodes = F.nodes;
@@ -380,6 +391,108 @@ done:
   cudaFree(box_sorted);
   cudaFree(tmp);
   return e;
+}
+
+// ---------------------------------------------------------------------------
+// reduced-precision records (layout in gf_device.cuh), BVH order
+// ---------------------------------------------------------------------------
+struct Pack16Args {
+  const float *mu, *quat, *ls, *om, *ph, *w;
+  const uint8_t* cell;  // per original index
+  const int* sorted_orig;
+  int64_t n;
+  int prec, omega_frame, weight_mode;
+  float3 lo, scale;
+  uint4* out;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t to_half_bits(float x, int prec) {
+  return prec == GF_PREC_BF16 ? (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x))
+                              : (uint32_t)__half_as_ushort(__float2half_rn(x));
+}
+
+__global__ void k_pack16(const __grid_constant__ Pack16Args A) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= A.n) return;
+  const int64_t i = A.sorted_orig[j];
+  uint32_t mc[3];
+  const float lo[3] = {A.lo.x, A.lo.y, A.lo.z}, sc[3] = {A.scale.x, A.scale.y, A.scale.z};
+  for (int k = 0; k < 3; ++k) {
+    const float c = rintf((A.mu[3 * i + k] - lo[k]) / sc[k]);
+    mc[k] = (uint32_t)fminf(fmaxf(c, 0.f), 65535.f);
+  }
+  float q[4];
+  float qn = 0.f;
+  for (int k = 0; k < 4; ++k) {
+    q[k] = A.quat[4 * i + k];
+    qn += q[k] * q[k];
+  }
+  qn = rsqrtf(qn);
+  int qs[4];
+  for (int k = 0; k < 4; ++k) qs[k] = (int)rintf(q[k] * qn * 32767.f);
+  float s[3];
+  for (int k = 0; k < 3; ++k) s[k] = expf(A.ls[3 * i + k]);
+  const float w = q[0] * qn, x = q[1] * qn, y = q[2] * qn, z = q[3] * qn;
+  const float R[3][3] = {{1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y)},
+                         {2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x)},
+                         {2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)}};
+  float kw[3];
+  for (int k = 0; k < 3; ++k) {
+    if (A.omega_frame == GF_OMEGA_LOCAL) {
+      kw[k] = A.om[3 * i + k];
+    } else {
+      kw[k] = s[k] * (R[0][k] * A.om[3 * i] + R[1][k] * A.om[3 * i + 1] + R[2][k] * A.om[3 * i + 2]);
+    }
+  }
+  float amp = A.w[i];
+  if (A.weight_mode == GF_WEIGHT_NORMALIZED) amp = amp / (15.749609945722419f * s[0] * s[1] * s[2]);
+  if (A.prec == GF_PREC_FP16 && !(fabsf(amp) <= 65504.f)) atomicOr(A.err, ERR_INPUT);
+  float ph = fmodf(A.ph[i], 6.28318530717958647692f);
+  if (ph < 0.f) ph += 6.28318530717958647692f;
+  const uint32_t pc = (uint32_t)rintf(ph * (65536.0f / 6.28318530717958647692f)) & 0xFFFFu;
+  const uint32_t cell = A.cell[i];
+  uint4 r0, r1;
+  r0.x = mc[0] | (mc[1] << 16);
+  r0.y = mc[2] | ((uint32_t)(qs[0] & 0xFFFF) << 16);
+  r0.z = (uint32_t)(qs[1] & 0xFFFF) | ((uint32_t)(qs[2] & 0xFFFF) << 16);
+  r0.w = (uint32_t)(qs[3] & 0xFFFF) | (to_half_bits(1.f / s[0], A.prec) << 16);
+  r1.x = to_half_bits(1.f / s[1], A.prec) | (to_half_bits(1.f / s[2], A.prec) << 16);
+  r1.y = to_half_bits(kw[0], A.prec) | (to_half_bits(kw[1], A.prec) << 16);
+  r1.z = to_half_bits(kw[2], A.prec) | (to_half_bits(amp, A.prec) << 16);
+  r1.w = pc | (cell << 16);
+  A.out[2 * j] = r0;
+  A.out[2 * j + 1] = r1;
+}
+
+cudaError_t launch_pack16(Field& F, cudaStream_t s) {
+  (void)cudaGetLastError();  // a stale error of an unrelated call is not ours
+  Pack16Args A;
+  A.mu = F.p_mu;
+  A.quat = F.p_quat;
+  A.ls = F.p_ls;
+  A.om = F.p_om;
+  A.ph = F.p_ph;
+  A.w = F.p_w;
+  A.cell = F.labels + 2 * F.n;
+  A.sorted_orig = F.sorted_orig;
+  A.n = F.n;
+  A.prec = F.opts.precision;
+  A.omega_frame = F.opts.omega_frame;
+  A.weight_mode = F.opts.weight_mode;
+  float sc[3];
+  for (int k = 0; k < 3; ++k) {
+    const float ext = F.mu_hi[k] - F.mu_lo[k];
+    sc[k] = ext > 0.f ? ext / 65535.f : 1.f;
+  }
+  A.lo = make_float3(F.mu_lo[0], F.mu_lo[1], F.mu_lo[2]);
+  A.scale = make_float3(sc[0], sc[1], sc[2]);
+  A.out = F.rec16;
+  A.err = F.err;
+  F.dev.qlo = A.lo;
+  F.dev.qscale = A.scale;
+  k_pack16<<<(unsigned)((F.n + 255) / 256), 256, 0, s>>>(A);
+  return cudaGetLastError();
 }
 
 }  // namespace gf

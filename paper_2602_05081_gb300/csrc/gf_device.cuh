@@ -3,6 +3,7 @@
 // the per-ray quadratic q(t) = a t^2 + 2 beta t + gamma and phase B t + delta
 // of App. A.1, the k-sigma support of Sec. 3.
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -53,7 +54,8 @@ struct DevField {
   float kbar[kMaxCells];   // mean |k_W| per cell
   float axes[kCones][3];   // orientation-bin axes
   float env[8];            // exp(-n^2/2), n = 0..7
-  float dec_scale[3];      // FP16 record: cell box extent per unit of u16 code (unused)
+  const int* orig16;       // reduced-precision records: BVH position -> original index
+  float3 qlo, qscale;      // reduced-precision records: mean = qlo + code * qscale
   const float* gl;         // Gauss-Legendre nodes then weights (2 x kGLTotal)
   int* err;
   unsigned long long* stats;  // rays, chords, evals, nodes, points
@@ -244,6 +246,126 @@ __device__ __forceinline__ bool chord_setup(const Prim& P, float3 o, float3 v, f
   c.cell = P.cell;
   c.orig = P.orig;
   return true;
+}
+
+// ---------------------------------------------------------------------------
+// Reduced-precision record (32 B = 2 x uint4), BVH order:
+//   x0 = mu.x | mu.y << 16            (u16 fixed point in the means' box)
+//   y0 = mu.z | q.w << 16             (quaternion as snorm16)
+//   z0 = q.x  | q.y << 16
+//   w0 = q.z  | 1/s0 << 16            (1/s, k_W and A as FP16 or BF16)
+//   x1 = 1/s1 | 1/s2 << 16
+//   y1 = kW.x | kW.y << 16
+//   z1 = kW.z | A << 16
+//   w1 = phase | cell << 16           (phase as u16 in [0, 2 pi))
+// Decoded to FP32; the chord is set up in the whitened frame W = S^-1 R^T
+// (Sec. 4.4): u = W v, p_W = W (o + tc v - mu), phase k_W . p_W + phi.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float half_bits_to_float(uint32_t h, int prec) {
+  return prec == 2 ? __uint_as_float(h << 16) : __half2float(__ushort_as_half((unsigned short)h));
+}
+
+__device__ __forceinline__ bool chord_setup16(const DevField& F, uint4 r0, uint4 r1, int j,
+                                              float3 o, float3 v, float tmin, float tmax,
+                                              Chord& c) {
+  const int prec = F.precision;
+  const float3 mu = make_float3(fmaf((float)(r0.x & 0xFFFFu), F.qscale.x, F.qlo.x),
+                                fmaf((float)(r0.x >> 16), F.qscale.y, F.qlo.y),
+                                fmaf((float)(r0.y & 0xFFFFu), F.qscale.z, F.qlo.z));
+  const float qw = (float)(short)(r0.y >> 16), qx = (float)(short)(r0.z & 0xFFFFu);
+  const float qy = (float)(short)(r0.z >> 16), qz = (float)(short)(r0.w & 0xFFFFu);
+  const float is0 = half_bits_to_float(r0.w >> 16, prec);
+  const float is1 = half_bits_to_float(r1.x & 0xFFFFu, prec);
+  const float is2 = half_bits_to_float(r1.x >> 16, prec);
+  const float k0 = half_bits_to_float(r1.y & 0xFFFFu, prec);
+  const float k1 = half_bits_to_float(r1.y >> 16, prec);
+  const float k2 = half_bits_to_float(r1.z & 0xFFFFu, prec);
+  const float A = half_bits_to_float(r1.z >> 16, prec);
+  const float phi = (float)(r1.w & 0xFFFFu) * (6.28318530717958647692f / 65536.0f);
+  // rotation of the unnormalised quaternion: R = M(q) / |q|^2
+  const float n2 = qw * qw + qx * qx + qy * qy + qz * qz;
+  const float in2 = 1.0f / n2;
+  const float R00 = (qw * qw + qx * qx - qy * qy - qz * qz) * in2;
+  const float R01 = 2.f * (qx * qy - qw * qz) * in2, R02 = 2.f * (qx * qz + qw * qy) * in2;
+  const float R10 = 2.f * (qx * qy + qw * qz) * in2;
+  const float R11 = (qw * qw - qx * qx + qy * qy - qz * qz) * in2;
+  const float R12 = 2.f * (qy * qz - qw * qx) * in2, R20 = 2.f * (qx * qz - qw * qy) * in2;
+  const float R21 = 2.f * (qy * qz + qw * qx) * in2;
+  const float R22 = (qw * qw - qx * qx - qy * qy + qz * qz) * in2;
+  // whitened direction and offset
+  const float ux = is0 * fmaf(R00, v.x, fmaf(R10, v.y, R20 * v.z));
+  const float uy = is1 * fmaf(R01, v.x, fmaf(R11, v.y, R21 * v.z));
+  const float uz = is2 * fmaf(R02, v.x, fmaf(R12, v.y, R22 * v.z));
+  const float a = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+  const float d0x = __fsub_rn(o.x, mu.x), d0y = __fsub_rn(o.y, mu.y), d0z = __fsub_rn(o.z, mu.z);
+  const float w0x = is0 * fmaf(R00, d0x, fmaf(R10, d0y, R20 * d0z));
+  const float w0y = is1 * fmaf(R01, d0x, fmaf(R11, d0y, R21 * d0z));
+  const float w0z = is2 * fmaf(R02, d0x, fmaf(R12, d0y, R22 * d0z));
+  const float tc = -fmaf(ux, w0x, fmaf(uy, w0y, uz * w0z)) / a;
+  // offset at tc in world space with compensated arithmetic, then whitened
+  float ex, ey, ez;
+  {
+    float sx = d0x, bb = __fsub_rn(sx, o.x);
+    ex = __fsub_rn(__fsub_rn(o.x, __fsub_rn(sx, bb)), __fadd_rn(mu.x, bb));
+    sx = d0y; bb = __fsub_rn(sx, o.y);
+    ey = __fsub_rn(__fsub_rn(o.y, __fsub_rn(sx, bb)), __fadd_rn(mu.y, bb));
+    sx = d0z; bb = __fsub_rn(sx, o.z);
+    ez = __fsub_rn(__fsub_rn(o.z, __fsub_rn(sx, bb)), __fadd_rn(mu.z, bb));
+  }
+  const float prx = __fmul_rn(tc, v.x), pry = __fmul_rn(tc, v.y), prz = __fmul_rn(tc, v.z);
+  const float px = __fadd_rn(__fadd_rn(d0x, prx), __fadd_rn(ex, fmaf(tc, v.x, -prx)));
+  const float py = __fadd_rn(__fadd_rn(d0y, pry), __fadd_rn(ey, fmaf(tc, v.y, -pry)));
+  const float pz = __fadd_rn(__fadd_rn(d0z, prz), __fadd_rn(ez, fmaf(tc, v.z, -prz)));
+  const float pwx = is0 * fmaf(R00, px, fmaf(R10, py, R20 * pz));
+  const float pwy = is1 * fmaf(R01, px, fmaf(R11, py, R21 * pz));
+  const float pwz = is2 * fmaf(R02, px, fmaf(R12, py, R22 * pz));
+  const float b = fmaf(ux, pwx, fmaf(uy, pwy, uz * pwz));
+  const float g = fmaf(pwx, pwx, fmaf(pwy, pwy, pwz * pwz));
+  const float dts = -b / a;
+  const float qmin = fmaf(b, dts, g);
+  const float disc = F.k2 - qmin;
+  if (!(disc > 0.0f)) return false;
+  const float hw = sqrtf(disc / a);
+  const float lo = fmaxf(dts - hw, tmin - tc);
+  const float hi = fminf(dts + hw, tmax - tc);
+  if (!(lo < hi)) return false;
+  c.tc = tc;
+  c.dtin = lo;
+  c.dtout = hi;
+  c.a = a;
+  c.b = b;
+  c.g = g;
+  c.B = fmaf(k0, ux, fmaf(k1, uy, k2 * uz));
+  float ph = fmaf(k0, pwx, fmaf(k1, pwy, fmaf(k2, pwz, phi)));
+  if (A < 0.0f) ph += 3.14159265358979f;
+  c.delta = reduce_2pi(ph);
+  c.absA = fabsf(A);
+  c.qmin = qmin;
+  c.dts = dts;
+  c.hw = hw;
+  c.p = make_float3(px, py, pz);
+  c.cell = (r1.w >> 16) & 63u;
+  c.orig = (uint32_t)__ldg(F.orig16 + j);
+  return true;
+}
+
+// Chord of BVH primitive j for either record precision; `weight(cell)` is the
+// LoD weight of the primitive's cell (no chord when it is 0).
+template <class WeightFn>
+__device__ __forceinline__ bool prim_chord(const DevField& F, int j, float3 o, float3 v,
+                                           float tmin, float tmax, WeightFn weight, float& w,
+                                           Chord& ch) {
+  if (F.precision == 0) {
+    const Prim P = load_prim(F, j);
+    w = weight(P.cell & 63u);
+    if (!(w > 0.f)) return false;
+    return chord_setup(P, o, v, tmin, tmax, F.k2, ch);
+  }
+  const uint4* r = F.rec16 + 2 * (int64_t)j;
+  const uint4 r0 = __ldg(r), r1 = __ldg(r + 1);
+  w = weight((r1.w >> 16) & 63u);
+  if (!(w > 0.f)) return false;
+  return chord_setup16(F, r0, r1, j, o, v, tmin, tmax, ch);
 }
 
 // ray-box slab test over [t0, t1]

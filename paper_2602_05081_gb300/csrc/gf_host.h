@@ -70,6 +70,7 @@ struct Field {
   int* counter = nullptr;
   float* cell_acc = nullptr;    // per-cell |k_W| sums (64) and counts (64)
   bool built = false;
+  float mu_lo[3] = {0, 0, 0}, mu_hi[3] = {0, 0, 0};  // box of the means (from the build)
   DevField dev{};
   LodDev lod{0, 7, 0}, lod_nee{0, 7, 0};
   // staging for host buffers
@@ -78,6 +79,28 @@ struct Field {
   // per-warp chord store of the scattering renderer (grows on demand)
   mutable float4* wscratch = nullptr;
   mutable size_t wscratch_bytes = 0;
+};
+
+// Render server batch (one launch of k_render_server): items of many requests
+// on several fields.  Item i covers pixels [pix0, pix0 + npix) of request
+// req and the batch's flat pixel numbers [base, base + npix); bases ascend.
+struct ServerItem {
+  int req, pix0, npix, base;
+};
+struct ServerReqDev {
+  PathParams P;
+  float* fb;   // device framebuffer of the request (W x H floats)
+  int asset;   // index into ServerLaunch::fields
+  int pad_;
+};
+struct ServerLaunch {
+  const DevField* fields;  // device array, one per asset (err/stats point at the server's)
+  int64_t max_n;           // largest primitive count over the assets
+  const ServerItem* items;
+  int n_items;
+  int total;               // pixels in the batch
+  const ServerReqDev* reqs;
+  int* counter;            // zero at launch
 };
 
 // launchers (return cudaError_t of the launch)
@@ -89,11 +112,20 @@ cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* ou
                           cudaStream_t s);
 cudaError_t launch_pack(Field& F, const gf_params& P, cudaStream_t s);
 cudaError_t build_bvh(Field& F, cudaStream_t s);
+cudaError_t launch_pack16(Field& F, cudaStream_t s);
+size_t scatter_store_bytes(int64_t grid);
+cudaError_t server_grid(int sm_count, int64_t& grid);
+cudaError_t launch_render_server(const ServerLaunch& L, int64_t grid, float4* chord_store,
+                                 cudaStream_t s);
 cudaError_t launch_tomo_backward(const Field& F, const PathParams& P, const float* dLdI,
                                  float* grad, cudaStream_t s);
 
 // sets the thread-local message returned by gf_last_error and returns s
 gf_status report(gf_status s, const std::string& msg);
+// camera and integrator options -> kernel parameters (LoD from the field)
+gf_status camera_params(const gf_camera* c, const gf_render_opts* o, uint64_t seed, const Field& F,
+                        PathParams& P);
+bool lod_ok(const gf_lod_desc* l);
 
 }  // namespace gf
 

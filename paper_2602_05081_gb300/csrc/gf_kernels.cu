@@ -116,10 +116,11 @@ struct ListLeaf {
   int64_t r;
   int n = 0;
   __device__ __forceinline__ void operator()(int j) {
-    const Prim Pr = load_prim(*F, j);
-    if (!(mask_weight(*M, Pr.cell & 63u) > 0.f)) return;
+    const Mask& Mk = *M;
     Chord ch;
-    if (!chord_setup(Pr, o, v, tmin, tmax, F->k2, ch)) return;
+    float w;
+    if (!prim_chord(*F, j, o, v, tmin, tmax, [&](uint32_t c) { return mask_weight(Mk, c); }, w, ch))
+      return;
     if (n < P->cap) {
       const int64_t at = r * P->cap + n;
       P->prims[at] = (int)ch.orig;

@@ -246,11 +246,11 @@ struct DetLeaf {
   float s = 0.f, c = 0.f;
   unsigned long long nch = 0, nev = 0;
   __device__ __forceinline__ void operator()(int j) {
-    const Prim P = load_prim(*F, j);
-    const float w = mask_weight(*M, P.cell & 63u);
-    if (!(w > 0.f)) return;
+    const Mask& Mk = *M;
     Chord ch;
-    if (!chord_setup(P, o, v, tmin, tmax, F->k2, ch)) return;
+    float w;
+    if (!prim_chord(*F, j, o, v, tmin, tmax, [&](uint32_t c) { return mask_weight(Mk, c); }, w, ch))
+      return;
     ++nch;
     const float len = ch.dtout - ch.dtin;
     int n, off;
@@ -335,11 +335,11 @@ struct CollectLeaf {
     bound = fminf(bound, B->t[kPts - 1]);
   }
   __device__ void operator()(int j) {
-    const Prim P = load_prim(*F, j);
-    const float w = mask_weight(*M, P.cell & 63u);
-    if (!(w > 0.f)) return;
+    const Mask& Mk = *M;
     Chord ch;
-    if (!chord_setup(P, o, v, tmin, tmax, F->k2, ch)) return;
+    float w;
+    if (!prim_chord(*F, j, o, v, tmin, tmax, [&](uint32_t c) { return mask_weight(Mk, c); }, w, ch))
+      return;
     if (!(ch.tc + ch.dtin <= bound && ch.tc + ch.dtout >= ta)) return;
     ++nch;
     // piecewise rate h exp(-n^2/2) on whitened-distance pieces of the chord
@@ -413,11 +413,11 @@ struct AccumLeaf {
   float kap[kPts], kb[kPts];
   unsigned long long nev = 0;
   __device__ void operator()(int j) {
-    const Prim P = load_prim(*F, j);
-    const float w = mask_weight(*M, P.cell & 63u);
-    if (!(w > 0.f)) return;
+    const Mask& Mk = *M;
     Chord ch;
-    if (!chord_setup(P, o, v, tmin, tmax, F->k2, ch)) return;
+    float w;
+    if (!prim_chord(*F, j, o, v, tmin, tmax, [&](uint32_t c) { return mask_weight(Mk, c); }, w, ch))
+      return;
     const float tin = ch.tc + ch.dtin, tout = ch.tc + ch.dtout;
     const float wa = w * ch.absA;
     const float y2 = -0.5f * kLog2e * ch.a, y1 = -kLog2e * ch.b;

@@ -1,20 +1,24 @@
 // gf_wavefront.cu -- scattering renderer: lanes traverse, the warp processes.
 //
-// Every lane of a warp owns one path (one pixel's samples in order) and
-// traverses its current ray's BVH on its own.  Leaves that a lane reaches are
-// not processed by that lane: they go to a per-warp queue in shared memory,
-// and whenever 32 are queued the whole warp tests them at once (chord set-up
-// of the owning lane's ray).  Chords that can hold tentative points go to a
-// second queue and are walked 32 at a time (Philox draws of Sec. 3's
-// per-segment majorant, drawn chord by chord).  Tentative points land in the
-// owner's buffer through shared-memory atomics.  A second traversal sums
-// kappa and kappa_bar at those points (again through the warp's leaf queue),
-// after which each lane takes its delta-tracking or ratio-tracking decision
-// and moves its path on (camera ray -> collision -> NEE -> scattering).
+// Every lane of a warp owns one path (one pixel's samples in order).  The
+// warp traverses the BVH for all 32 current rays together: one shared stack
+// of (node, lane) entries, from which every step pops up to 32 entries, so the
+// lanes stay busy while rays of different lengths are in flight.  Leaves that
+// are reached go to a per-warp queue in shared memory, and whenever 32 are
+// queued the whole warp sets up their chords at once (chord set-up on the
+// owning lane's ray).  Each chord that overlaps the owner's window [ta, te)
+// is stored (its evaluation record, in a per-warp global store) and queued;
+// queued chords are walked 32 at a time, drawing the chord's tentative points
+// of Sec. 3's per-segment majorant from its own Philox stream.  Points land in
+// the owner's buffer through shared-memory atomics.  kappa and kappa_bar at
+// the points are then summed from the stored records (the warp scans each
+// lane's list and reduces by shuffles), after which each lane takes its
+// delta-tracking or ratio-tracking decision and moves its path on (camera
+// ray -> collision -> NEE -> scattering).
 //
 // The tentative points are a function of the chords and their Philox streams
-// only, so results equal the per-thread formulation up to floating-point
-// summation order (kappa sums are accumulated with atomics).
+// only, so results equal a per-ray formulation up to floating-point summation
+// order.
 #include <cuda_runtime.h>
 
 #include <climits>

@@ -335,3 +335,68 @@ def test_invalid_inputs_are_rejected(api, ctx):
     with pytest.raises(_abi.GfError):
         f.render(cg, api.render_opts("scatter", 0, 1))
     f.sync()
+
+
+# --------------------------------------------------------------------------- reduced precision
+@pytest.mark.parametrize("prec,u", [("fp16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
+def test_reduced_precision_transmittance(api, ctx, prec, u):
+    """32-byte records against the FP64 oracle, within a bound derived from
+    every rounding the record applies (FP32 math after decoding).
+
+    With z the whitened offset (|z| <= k inside the support) the integrand is
+    A exp(-|z|^2/2) cos(k_W . z + phi).  The record perturbs
+      z      by dz <= k u (1/s rounded) + sqrt(3) h_mu / s_min (u16 means,
+             half step h_mu) + (2/32767) k s_max / s_min (snorm16 quaternion:
+             rotation angle error <= 2 |dq|),
+      A      by u A,  k_W by u |k_W|,  phi by pi/65536 (u16 phase),
+    so |d integrand| <= A exp(-q/2) [u + k dz + k u |k_W| + |k_W| dz + pi/65536]
+    and, summed over a ray's chords, |d tau| <= C E with E the envelope
+    integral.  The k-sigma cut moves too: a chord end shifts by at most
+    2 s_max sqrt(2 k dz) where the integrand is at most A e^{-k^2/2}, which
+    adds that much per chord."""
+    p = synth.absorption_field(256, seed=0)
+    f = api.Field(ctx, p, precision=prec)
+    orc = oracle.Field(p)
+    o, d, tr = synth.orthographic_rays(32)
+    T, tau = f.transmittance(_t(o), _t(d), _t(tr), mode="det")
+    f.sync()
+    _, tau_ref = orc.transmittance(o, d, tr, mode="det")
+    env = dict(p)
+    env["omega"] = np.zeros_like(p["omega"])
+    env["phase"] = np.zeros_like(p["phase"])
+    _, E = oracle.Field(env).transmittance(o, d, tr, mode="det")
+    k = 3.0
+    s = np.exp(p["log_scale"].astype(np.float64))
+    s_min, s_max = s.min(), s.max()
+    mu = p["mu"].astype(np.float64)
+    h_mu = (mu.max(0) - mu.min(0)).max() / 65535.0 / 2.0
+    kw = np.max(np.linalg.norm(p["omega"], axis=1) * s.max(1))
+    dz = k * u + np.sqrt(3.0) * h_mu / s_min + (2.0 / 32767.0) * k * s_max / s_min
+    C_rel = u + k * dz + k * u * kw + kw * dz + np.pi / 65536.0
+    n_ch = np.zeros(o.shape[0])
+    for r in range(o.shape[0]):
+        v = d[r] / np.linalg.norm(d[r])
+        n_ch[r] = sum(orc.chord(i, o[r], v, tr[r, 0], tr[r, 1])[0] for i in range(256))
+    edge = np.max(np.abs(p["weight"])) * np.exp(-k * k / 2) * 2.0 * s_max * np.sqrt(2 * k * dz)
+    bound = C_rel * E + edge * n_ch + 2e-6
+    err = np.abs(tau.cpu().numpy() - tau_ref)
+    assert np.all(err <= bound), (err.max(), (err / bound).max())
+    assert f.info()[1] == {"fp16": 1, "bf16": 2}[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_reduced_precision_image_rmse(api, ctx, prec):
+    """Equal image RMSE: RMSE(I_reduced, I_ref) <= 1.01 RMSE(I_oracle, I_ref) at
+    equal spp and seed, I_ref an independent 16x-spp oracle render."""
+    p = synth.octave_field(3000, 4, seed=8)
+    f = api.Field(ctx, p, precision=prec)
+    orc = oracle.Field(p, omega_frame="local")
+    cg, co = _cam_pair(api, 16, 16)
+    img = f.render(cg, api.render_opts("scatter", 8, 1), seed=2)
+    f.sync()
+    mine = img.cpu().numpy()
+    same = orc.render(co, oracle.render_opts("scatter", 8, 1), seed=2)
+    ref = orc.render(co, oracle.render_opts("scatter", 128, 1), seed=99)
+    r_red = np.sqrt(np.mean((mine - ref) ** 2))
+    r_orc = np.sqrt(np.mean((same - ref) ** 2))
+    assert r_red <= 1.01 * r_orc, (r_red, r_orc)
