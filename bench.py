@@ -140,6 +140,83 @@ def oracle_sample(seconds, cutoffs=CUTOFFS, crop=4):
                       % (crops, crop, crop, SPP, rays, dt)}
 
 
+SERVER_ASSETS = ((50_000, 4), (200_000, 4), (1_000_000, 6), (2_000_000, 6))
+
+
+def server_leg(api, ctx, n_requests, load=0.7):
+    """Render server on a Poisson stream of mixed requests over 4 resident assets.
+
+    The first n_requests of the seeded request stream (resolution uniform over
+    128^2..1024^2, spp over {1,4,16,64}, LoD over the 4 band cutoffs, random
+    cameras on a sphere) are first submitted all at once to measure the
+    saturated request rate, then replayed at load x that rate as Poisson
+    arrivals; latency = submit -> image in the caller's (pinned host) buffer.
+    """
+    fields = [api.Field(ctx, synth.octave_field(n, o, seed=10 + k))
+              for k, (n, o) in enumerate(SERVER_ASSETS)]
+    stream = synth.request_stream(n_requests, 1.0, seed=0, lods=(0, 1, 2, 3))
+    srv = api.Server(ctx, fields, mem_budget=256 << 20, max_inflight=32, max_queue=100000)
+    c = synth.DEFAULT_CAMERA
+
+    def submit(r):
+        eye = r["eye"]
+        d = np.subtract(c["look_at"], eye)
+        up = (0.0, 1.0, 0.0) if abs(d[1]) < 0.99 * np.linalg.norm(d) else (0.0, 0.0, 1.0)
+        cam = api.camera(eye, c["look_at"], up, c["vfov_deg"], r["res"], r["res"])
+        ro = api.render_opts("scatter", r["spp"], 1, 0.8, synth.LIGHT_DIR, 1.0)
+        top = SERVER_ASSETS[r["asset"]][1] - 1
+        lo = api.lod("cutoff", top - r["lod"])
+        t, _ = srv.submit(r["asset"], cam, ro, lo, lo, r["seed"])
+        return t
+
+    try:
+        # saturated throughput: the whole sample queued at once
+        s0 = srv.stats()
+        t0 = time.perf_counter()
+        tk = [submit(r) for r in stream]
+        for t in tk:
+            srv.wait(t)
+        sat_s = time.perf_counter() - t0
+        s1 = srv.stats()
+        rate = load * n_requests / sat_s
+        # Poisson arrivals at `load` of the saturated rate
+        t0 = time.perf_counter()
+        tk = []
+        for r in stream:
+            due = t0 + r["t_arrive"] / rate
+            while True:
+                now = time.perf_counter()
+                if now >= due:
+                    break
+                time.sleep(min(0.002, due - now))
+            tk.append(submit(r))
+        res = [srv.wait(t) for t in tk]
+        span_s = time.perf_counter() - t0
+        s2 = srv.stats()
+    finally:
+        srv.close()
+        for f in fields:
+            f.free()
+    lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in res])
+    wait = np.array([r["t_admit_ms"] - r["t_submit_ms"] for r in res])
+    samples = sum(r["res"] ** 2 * r["spp"] for r in stream)
+    rays = s2["work"]["rays"] - s1["work"]["rays"]
+    return {
+        "requests": n_requests, "sample": "first %d requests of the seeded 2000-request stream"
+                                          % n_requests,
+        "assets": [n for n, _ in SERVER_ASSETS], "failed": int(s2["failed"]),
+        "saturated_requests_per_s": n_requests / sat_s,
+        "saturated_mrays_per_s": (s1["work"]["rays"] - s0["work"]["rays"]) / sat_s / 1e6,
+        "poisson_rate_per_s": rate, "load": load,
+        "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+        "queue_wait_ms_p50": float(np.percentile(wait, 50)),
+        "mrays_per_s": rays / span_s / 1e6, "msamples_per_s": samples / span_s / 1e6,
+        "launches": int(s2["launches"] - s1["launches"]),
+        "gpu_busy_frac": (s2["busy_ms"] - s1["busy_ms"]) / (span_s * 1e3),
+        "max_inflight_seen": int(s2["max_inflight_seen"]),
+    }
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -159,6 +236,21 @@ def run_reference(args, rank, world):
             "e2e": {"value": rays_per_s, "unit": "Mrays/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def combine_ranks(total_ms, rays, evals, world, device):
+    """Whole-job figures of N replicas: the slowest rank's timed milliseconds
+    and the work summed over ranks (one all-reduce each; no data-path
+    collective exists, every rank renders its own copy of the workload)."""
+    if world <= 1:
+        return float(total_ms), float(rays), float(evals)
+    import torch
+    import torch.distributed as dist
+    tmax = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    sums = torch.tensor([float(rays), float(evals)], dtype=torch.float64, device=device)
+    dist.all_reduce(sums, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(sums[0]), float(sums[1])
 
 
 def run_ours(args, rank, world):
@@ -217,17 +309,8 @@ def run_ours(args, rank, world):
     clk = clocks.stop()
     field.sync(stream)
     st = field.stats(reset=True)
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms, st["rays"], st["evals"]], dtype=torch.float64, device=dev)
-    if world > 1:
-        tmax = t[0:1].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        sums = t[1:3].clone()
-        dist.all_reduce(sums, op=dist.ReduceOp.SUM)
-        total_ms_max = float(tmax[0])
-        rays_all, evals_all = float(sums[0]), float(sums[1])
-    else:
-        total_ms_max, rays_all, evals_all = total_ms, float(st["rays"]), float(st["evals"])
+    total_ms_max, rays_all, evals_all = combine_ranks(sum(step_ms), st["rays"], st["evals"],
+                                                      world, dev)
     # end to end through the C ABI with a host (pinned) output buffer
     host = torch.empty(RES, RES, dtype=torch.float32).pin_memory()
     torch.cuda.synchronize()
@@ -301,6 +384,8 @@ def run_ours(args, rank, world):
         line["phase_cycles_share"] = dict(zip(("traversal_steps", "leaf_rounds_pass1", "chord_walks",
                                                "leaf_rounds_pass2", "decisions"),
                                               (c / tot for c in st["cycles"])))
+    if world == 1 and args.server_requests > 0:
+        line["server"] = server_leg(api, ctx, args.server_requests)
     if world == 1 and args.cpu_seconds > 0:
         line["cpu_baseline"] = oracle_sample(args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -313,6 +398,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--server-requests", type=int, default=16,
+                    help="requests of the render-server leg (0: skip)")
     ap.add_argument("--res", type=int, default=RES, help="profiling only: image size")
     ap.add_argument("--spp", type=int, default=SPP, help="profiling only: samples per pixel")
     args = ap.parse_args()

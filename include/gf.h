@@ -158,7 +158,7 @@ gf_status gf_destroy(gf_ctx* ctx);
 
 /* Pack the primitives (Sec. 4.2 parameters -> Sigma^-1, world carrier, amplitude,
    band/cone/cell labels; load-time binning of Sec. 4.6).  params arrays may be
-   host or device memory.  Validates on the host/device: n >= 1, finite values,
+   host or device memory.  Validates on the host/device: 1 <= n < 2^26, finite values,
    |quat| > 0, k_sigma in (0,6], band labels <= 7 (GF_EINVAL).  The field keeps a
    copy of the raw parameters for gf_render_backward. */
 gf_status gf_load_field(gf_ctx* ctx, const gf_params* params, const gf_field_opts* opts,
@@ -247,6 +247,83 @@ gf_status gf_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int
 gf_status gf_transmittance_static(gf_field* field, const float* o, const float* d,
                                   const float* trange, int64_t n_rays, int mode, int spp,
                                   uint64_t seed, float* out_T, float* out_tau, gf_stream stream);
+
+/* ------------------------------------------------------------------------
+   Render server: continuous batching of scattering renders over resident
+   fields.  No counterpart in the paper (a serving layer around gf_render).
+
+   Requests queue in arrival order.  A request is admitted when one of
+   max_inflight slots is free and its framebuffer (width x height floats,
+   256-byte aligned) fits in the server's device pool of mem_budget bytes;
+   the head of the queue waits for memory (no overtaking).  Every batched
+   launch gives each admitted request an equal share of batch_samples pixel
+   samples (at least 32 pixels), taken as its next contiguous pixel range;
+   one kernel launch renders the ranges of all admitted requests on all
+   fields together, and two launches are kept in flight on two streams so
+   that one launch's tail overlaps the next launch.  Requests admitted while
+   launches run join the next launch.  A pixel is rendered by one lane from
+   its first sample to its last, so a request's image does not depend on
+   what it was batched with (up to FP32 summation order inside the
+   majorant sums, as between two gf_render calls).  When a request's last
+   range completes, its framebuffer is copied to request.out (host or device)
+   and its memory and slot are released; then it is DONE.
+   A scheduler thread inside the library drives the device; submit, poll and
+   wait may be called from any thread.  The fields must outlive the server. */
+typedef struct gf_server gf_server;
+typedef struct gf_server_opts {
+  size_t mem_budget;     /* device bytes for request framebuffers (admission by memory) */
+  int max_inflight;      /* requests admitted at once, 1..1024 */
+  int max_queue;         /* pending requests beyond which submit fails with GF_EOVERFLOW */
+  int64_t batch_samples; /* pixel samples per batched launch (0: 16 per resident lane) */
+} gf_server_opts;
+typedef struct gf_request {
+  int asset;             /* index into the fields given to gf_server_create */
+  gf_camera camera;
+  gf_render_opts opts;   /* integrator must be GF_INTEG_SCATTER */
+  gf_lod_desc lod;       /* primary rays */
+  gf_lod_desc lod_nee;   /* NEE rays */
+  uint64_t seed;
+  float* out;            /* width*height floats, host or device, owned by the caller */
+} gf_request;
+enum { GF_REQ_QUEUED = 0, GF_REQ_RUNNING = 1, GF_REQ_DONE = 2, GF_REQ_FAILED = 3 };
+typedef struct gf_result {
+  int state;             /* GF_REQ_* */
+  int status;            /* gf_status of a FAILED request, else GF_OK */
+  double t_submit_ms;    /* server clock: ms since gf_server_create */
+  double t_admit_ms;     /* admitted (slot and memory granted); 0 while queued */
+  double t_done_ms;      /* image in request.out; 0 until DONE */
+  int64_t launches;      /* batched launches that carried pixels of the request */
+} gf_result;
+typedef struct gf_server_stats {
+  int64_t submitted, completed, failed;
+  int64_t launches;          /* batched kernel launches */
+  int64_t items;             /* (request, pixel range) items over all launches */
+  int max_inflight_seen;     /* most requests admitted at once */
+  int64_t max_bytes_seen;    /* most framebuffer bytes in use at once */
+  double busy_ms;            /* sum of launch durations (CUDA events) */
+  gf_stats work;             /* kernel work counters over all launches */
+} gf_server_stats;
+
+/* Create a server over n_fields built fields of one context (the fields stay
+   owned by the caller).  Allocates the framebuffer pool, per-launch scratch
+   for two launches in flight and the batch buffers, then starts the
+   scheduler thread.  GF_EINVAL for bad options, GF_ESTATE for an unbuilt
+   field, GF_ENOMEM if the pool does not fit. */
+gf_status gf_server_create(gf_ctx* ctx, gf_field* const* fields, int n_fields,
+                           const gf_server_opts* opts, gf_server** out);
+/* Queue a request; *ticket identifies it.  Validated here: asset index,
+   camera and options as for gf_render, LoD descriptors, a framebuffer that
+   fits the pool at all (GF_EINVAL); a full queue gives GF_EOVERFLOW. */
+gf_status gf_server_submit(gf_server* server, const gf_request* request, uint64_t* ticket);
+/* State and timestamps of a request (GF_EINVAL for an unknown ticket). */
+gf_status gf_server_poll(gf_server* server, uint64_t ticket, gf_result* out);
+/* Block until the request is DONE or FAILED, or timeout_ms passes
+   (GF_ETIMEOUT; the request keeps running). */
+gf_status gf_server_wait(gf_server* server, uint64_t ticket, double timeout_ms, gf_result* out);
+gf_status gf_server_get_stats(gf_server* server, gf_server_stats* out);
+/* Stop admitting, fail the requests still queued, finish the admitted ones,
+   stop the scheduler thread and free the server's memory. */
+gf_status gf_server_destroy(gf_server* server);
 
 gf_status gf_get_stats(gf_field* field, gf_stats* out, int reset);
 /* Wait for the stream, then report (and clear) any device-side error of the field. */

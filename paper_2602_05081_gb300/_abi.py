@@ -66,6 +66,31 @@ class gf_stats(C.Structure):
                 ("steps", C.c_uint64), ("leaves", C.c_uint64), ("cycles", C.c_uint64 * 5)]
 
 
+GF_REQ_QUEUED, GF_REQ_RUNNING, GF_REQ_DONE, GF_REQ_FAILED = range(4)
+
+
+class gf_server_opts(C.Structure):
+    _fields_ = [("mem_budget", C.c_size_t), ("max_inflight", C.c_int), ("max_queue", C.c_int),
+                ("batch_samples", C.c_int64)]
+
+
+class gf_request(C.Structure):
+    _fields_ = [("asset", C.c_int), ("camera", gf_camera), ("opts", gf_render_opts),
+                ("lod", gf_lod_desc), ("lod_nee", gf_lod_desc), ("seed", C.c_uint64),
+                ("out", C.c_void_p)]
+
+
+class gf_result(C.Structure):
+    _fields_ = [("state", C.c_int), ("status", C.c_int), ("t_submit_ms", C.c_double),
+                ("t_admit_ms", C.c_double), ("t_done_ms", C.c_double), ("launches", C.c_int64)]
+
+
+class gf_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("launches", C.c_int64), ("items", C.c_int64), ("max_inflight_seen", C.c_int),
+                ("max_bytes_seen", C.c_int64), ("busy_ms", C.c_double), ("work", gf_stats)]
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError("libgf.so is not built (%s); run paper_2602_05081_gb300.build.build()"
                       % LIB_PATH)
@@ -90,6 +115,12 @@ _SIGS = {
     "gf_get_stats": [_vp, C.POINTER(gf_stats), _int],
     "gf_sync": [_vp, _vp],
     "gf_field_info": [_vp, C.POINTER(_i64), C.POINTER(_int), C.POINTER(_u64)],
+    "gf_server_create": [_vp, C.POINTER(_vp), _int, C.POINTER(gf_server_opts), C.POINTER(_vp)],
+    "gf_server_submit": [_vp, C.POINTER(gf_request), C.POINTER(_u64)],
+    "gf_server_poll": [_vp, _u64, C.POINTER(gf_result)],
+    "gf_server_wait": [_vp, _u64, C.c_double, C.POINTER(gf_result)],
+    "gf_server_get_stats": [_vp, C.POINTER(gf_server_stats)],
+    "gf_server_destroy": [_vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(lib, _name)
@@ -218,6 +249,49 @@ def gf_field_info(field):
     n = _i64(); p = _int(); occ = _u64()
     _check(lib.gf_field_info(field, C.byref(n), C.byref(p), C.byref(occ)))
     return int(n.value), int(p.value), int(occ.value)
+
+
+def _result(r: gf_result) -> dict:
+    return {k: (float(getattr(r, k)) if k.startswith("t_") else int(getattr(r, k)))
+            for k, _ in gf_result._fields_}
+
+
+def gf_server_create(ctx, fields, opts: gf_server_opts):
+    arr = (_vp * len(fields))(*[f.value if isinstance(f, _vp) else f for f in fields])
+    h = _vp()
+    _check(lib.gf_server_create(ctx, arr, len(fields), C.byref(opts), C.byref(h)))
+    return h
+
+
+def gf_server_submit(server, request: gf_request) -> int:
+    t = _u64()
+    _check(lib.gf_server_submit(server, C.byref(request), C.byref(t)))
+    return int(t.value)
+
+
+def gf_server_poll(server, ticket) -> dict:
+    r = gf_result()
+    _check(lib.gf_server_poll(server, int(ticket), C.byref(r)))
+    return _result(r)
+
+
+def gf_server_wait(server, ticket, timeout_ms=60000.0) -> dict:
+    r = gf_result()
+    _check(lib.gf_server_wait(server, int(ticket), float(timeout_ms), C.byref(r)))
+    return _result(r)
+
+
+def gf_server_get_stats(server) -> dict:
+    s = gf_server_stats()
+    _check(lib.gf_server_get_stats(server, C.byref(s)))
+    out = {k: (float(getattr(s, k)) if k == "busy_ms" else int(getattr(s, k)))
+           for k, _ in gf_server_stats._fields_ if k != "work"}
+    out["work"] = {k: int(getattr(s.work, k)) for k, _ in gf_stats._fields_ if k != "cycles"}
+    return out
+
+
+def gf_server_destroy(server):
+    _check(lib.gf_server_destroy(server))
 
 
 EXPORTED = tuple(_SIGS) + ("gf_last_error",)

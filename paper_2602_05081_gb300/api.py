@@ -2,7 +2,8 @@
 
 ``Field`` packs a primitive set on the GPU (gf_load_field + gf_build_bvh) and
 forwards the rendering calls; ``TomoRender`` is a torch.autograd.Function whose
-backward is the hand-written adjoint kernel (gf_render_backward).
+backward is the hand-written adjoint kernel (gf_render_backward); ``Server``
+wraps the continuous-batching render server (gf_server_*).
 """
 from __future__ import annotations
 
@@ -174,3 +175,49 @@ class TomoRender(torch.autograd.Function):
         f.free()
         return (parts["mu"], parts["quat"], parts["log_scale"], parts["omega"], parts["phase"],
                 parts["weight"], None, None, None, None, None, None, None)
+
+
+class Server:
+    """Continuous-batching render server over resident fields (gf_server_*)."""
+
+    def __init__(self, ctx: Context, fields, mem_budget=256 << 20, max_inflight=32,
+                 max_queue=4096, batch_samples=0):
+        self.ctx = ctx
+        self.fields = list(fields)  # the fields must outlive the server
+        opts = A.gf_server_opts(int(mem_budget), int(max_inflight), int(max_queue),
+                                int(batch_samples))
+        self.h = A.gf_server_create(ctx.h, [f.h for f in self.fields], opts)
+        self._outs = {}
+
+    def submit(self, asset, cam, opts, lod_primary=None, lod_nee=None, seed=0, out=None):
+        """Queue a render; returns (ticket, out).  out defaults to a pinned host tensor."""
+        if out is None:
+            out = torch.empty(cam.height, cam.width, dtype=torch.float32).pin_memory()
+        lp = lod_primary if lod_primary is not None else lod()
+        ln = lod_nee if lod_nee is not None else lp
+        rq = A.gf_request(int(asset), cam, opts, lp, ln, int(seed), A.ptr(out))
+        t = A.gf_server_submit(self.h, rq)
+        self._outs[t] = out  # keep the buffer alive until the request finishes
+        return t, out
+
+    def poll(self, ticket):
+        return A.gf_server_poll(self.h, ticket)
+
+    def wait(self, ticket, timeout_ms=600000.0):
+        r = A.gf_server_wait(self.h, ticket, timeout_ms)
+        return r
+
+    def stats(self):
+        return A.gf_server_get_stats(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            A.gf_server_destroy(self.h)
+            self.h = None
+            self._outs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

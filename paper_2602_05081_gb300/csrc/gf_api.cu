@@ -13,10 +13,6 @@
 
 using namespace gf;
 
-struct gf_ctx {
-  Ctx c;
-};
-
 namespace {
 
 thread_local std::string g_err;
@@ -171,7 +167,7 @@ namespace {
 
 void free_field(Field& F) {
   void* ptrs[] = {F.p_mu, F.p_quat, F.p_ls, F.p_om, F.p_ph, F.p_w, F.rec_orig, F.box_orig,
-                  F.kw_orig, F.rec, F.rec16, F.nodes, F.sorted_orig, F.labels, F.err,
+                  F.kw_orig, F.rec, F.rec16, F.nodes, F.nodes4, F.sorted_orig, F.labels, F.err,
                   F.stats, F.counter, F.cell_acc, F.stage, F.wscratch, F.gl};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -237,7 +233,8 @@ gf_status gf_load_field(gf_ctx* ctx, const gf_params* p, const gf_field_opts* op
                         gf_stream stream, gf_field** out) {
   if (!ctx || !p || !opts || !out) return fail(GF_EINVAL, "null argument");
   *out = nullptr;
-  if (p->n < 1 || p->n > (1ll << 30)) return fail(GF_EINVAL, "n must be in [1, 2^30]");
+  // node and primitive indices share a 32-bit word with a 5-bit lane index
+  if (p->n < 1 || p->n >= (1ll << 26)) return fail(GF_EINVAL, "n must be in [1, 2^26)");
   if (!p->mu || !p->quat || !p->log_scale || !p->omega || !p->phase || !p->weight)
     return fail(GF_EINVAL, "parameter array null");
   if (!(opts->k_sigma > 0.f && opts->k_sigma <= 6.f)) return fail(GF_EINVAL, "k_sigma in (0,6]");

@@ -9,6 +9,7 @@
 #include <cuda_fp16.h>
 
 #include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
 
 #include "gf_host.h"
 
@@ -308,6 +309,96 @@ __global__ void k_refit(const float* box, const float4* rec, int64_t n, Node* no
   }
 }
 
+// ---------------------------------------------------------------------------
+// Four-wide collapse: binary nodes at even depth become Node4s whose children
+// are their children's children (a leaf child stays a leaf).
+// ---------------------------------------------------------------------------
+__global__ void k_depth_parity(const Node* nodes, int64_t m, int* even) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  int d = 0;
+  int v = (int)i;
+  for (int g = 0; g < 4096 && v > 0; ++g) {  // node 0 is the root
+    v = nodes[v].d.z;
+    ++d;
+  }
+  even[i] = (d & 1) == 0 ? 1 : 0;
+}
+
+__device__ __forceinline__ void node_slot(const Node& N, int slot, float* b, unsigned long long& m,
+                                          int& child) {
+  const float* a = reinterpret_cast<const float*>(&N.a);
+  const int o = slot == 0 ? 0 : 6;
+  for (int k = 0; k < 6; ++k) b[k] = a[o + k];
+  m = slot == 0 ? ((unsigned long long)N.e.x | ((unsigned long long)N.e.y << 32))
+                : ((unsigned long long)N.e.z | ((unsigned long long)N.e.w << 32));
+  child = slot == 0 ? N.d.x : N.d.y;
+}
+
+__global__ void k_collapse4(const Node* nodes, int64_t m, const int* even, const int* map,
+                            Node4* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m || !even[i]) return;
+  float box[4][6];
+  unsigned long long mk[4] = {0, 0, 0, 0};
+  int ch[4] = {0, 0, 0, 0};
+  int nc = 0;
+  const Node& N = nodes[i];
+  for (int s = 0; s < 2; ++s) {
+    float b[6];
+    unsigned long long mm;
+    int c;
+    node_slot(N, s, b, mm, c);
+    if (c < 0) {
+      for (int k = 0; k < 6; ++k) box[nc][k] = b[k];
+      mk[nc] = mm;
+      ch[nc++] = c;
+      continue;
+    }
+    const Node& C = nodes[c];
+    for (int t = 0; t < 2; ++t) {
+      int cc;
+      node_slot(C, t, box[nc], mk[nc], cc);
+      ch[nc++] = cc < 0 ? cc : map[cc];
+    }
+  }
+  float lo[3], hi[3], sc[3];
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = box[0][a];
+    hi[a] = box[0][3 + a];
+    for (int k = 1; k < nc; ++k) {
+      lo[a] = fminf(lo[a], box[k][a]);
+      hi[a] = fmaxf(hi[a], box[k][3 + a]);
+    }
+    // grid step: lo + 255 s >= hi (upward rounding), never zero
+    sc[a] = __fdiv_ru(__fsub_ru(hi[a], lo[a]), 255.0f);
+    const float floor_s = fmaxf(fabsf(lo[a]), fabsf(hi[a])) * 1e-7f + 1e-30f;
+    sc[a] = fmaxf(sc[a], floor_s);
+  }
+  uint32_t ql[3] = {0, 0, 0}, qh[3] = {0, 0, 0};
+  for (int k = 0; k < nc; ++k) {
+    for (int a = 0; a < 3; ++a) {
+      // conservative codes, checked with the decoding formula of the traversal
+      float fl = floorf((box[k][a] - lo[a]) / sc[a]);
+      int cl = (int)fminf(fmaxf(fl, 0.f), 255.f);
+      while (cl > 0 && fmaf((float)cl, sc[a], lo[a]) > box[k][a]) --cl;
+      float fh = ceilf((box[k][3 + a] - lo[a]) / sc[a]);
+      int chh = (int)fminf(fmaxf(fh, 0.f), 255.f);
+      while (chh < 255 && fmaf((float)chh, sc[a], lo[a]) < box[k][3 + a]) ++chh;
+      ql[a] |= (uint32_t)cl << (8 * k);
+      qh[a] |= (uint32_t)chh << (8 * k);
+    }
+  }
+  Node4 o;
+  o.v0 = make_float4(lo[0], lo[1], lo[2], sc[0]);
+  o.v1 = make_float4(sc[1], sc[2], __uint_as_float(ql[0]), __uint_as_float(ql[1]));
+  o.q = make_uint4(ql[2], qh[0], qh[1], qh[2]);
+  o.child = make_int4(ch[0], ch[1], ch[2], ch[3]);
+  o.m01 = make_uint4((uint32_t)mk[0], (uint32_t)(mk[0] >> 32), (uint32_t)mk[1], (uint32_t)(mk[1] >> 32));
+  o.m23 = make_uint4((uint32_t)mk[2], (uint32_t)(mk[2] >> 32), (uint32_t)mk[3], (uint32_t)(mk[3] >> 32));
+  out[map[i]] = o;
+}
+
 static cudaError_t dalloc(void** p, size_t bytes) { return cudaMalloc(p, bytes ? bytes : 16); }
 
 cudaError_t build_bvh(Field& F, cudaStream_t s) {
@@ -359,6 +450,29 @@ cudaError_t build_bvh(Field& F, cudaStream_t s) {
     GF_TRY(cudaGetLastError());
     k_refit<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(box_sorted, F.rec, n, F.nodes, leaf_parent, flags);
     GF_TRY(cudaGetLastError());
+    // four-wide collapse (flags become even-depth markers, leaf_parent their scan)
+    const int64_t m = n - 1;
+    k_depth_parity<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(F.nodes, m, flags);
+    GF_TRY(cudaGetLastError());
+    size_t sb = 0;
+    GF_TRY(cub::DeviceScan::ExclusiveSum(nullptr, sb, flags, leaf_parent, (int)m, s));
+    if (sb > tmp_bytes) {
+      cudaFree(tmp);
+      tmp = nullptr;
+      GF_TRY(dalloc(&tmp, sb));
+      tmp_bytes = sb;
+    }
+    GF_TRY(cub::DeviceScan::ExclusiveSum(tmp, sb, flags, leaf_parent, (int)m, s));
+    int last[2] = {0, 0};
+    GF_TRY(cudaMemcpyAsync(&last[0], leaf_parent + (m - 1), sizeof(int), cudaMemcpyDeviceToHost, s));
+    GF_TRY(cudaMemcpyAsync(&last[1], flags + (m - 1), sizeof(int), cudaMemcpyDeviceToHost, s));
+    GF_TRY(cudaStreamSynchronize(s));
+    const int64_t m4 = (int64_t)last[0] + last[1];
+    if (F.nodes4) cudaFree(F.nodes4);
+    F.nodes4 = nullptr;
+    GF_TRY(dalloc((void**)&F.nodes4, (size_t)m4 * sizeof(Node4)));
+    k_collapse4<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(F.nodes, m, flags, leaf_parent, F.nodes4);
+    GF_TRY(cudaGetLastError());
   }
   GF_TRY(cudaMemcpyAsync(hb, bounds, sizeof(hb), cudaMemcpyDeviceToHost, s));
   GF_TRY(cudaStreamSynchronize(s));
@@ -378,6 +492,7 @@ cudaError_t build_bvh(Field& F, cudaStream_t s) {
   }
   F.dev.rec = F.rec;
   F.dev.nodes = F.nodes;
+  F.dev.nodes4 = F.nodes4;
   F.dev.root = n >= 2 ? 0 : -1;
 done:
 #undef GF_TRY

@@ -36,6 +36,22 @@ struct __align__(16) Node {
   uint4 e;   // cell mask of child0 (lo, hi), child1 (lo, hi)
 };
 
+// Four-wide node of the scattering renderer's BVH, collapsed from the binary
+// tree (every even-depth binary node with its children's children).  Child
+// boxes are 8-bit codes on a per-node grid: box = lo + code * s per axis,
+// floor/ceil rounded on the builder and checked with the decoding formula so
+// that each decoded box contains the exact child box.  Unused children have
+// an empty code box and a zero cell mask.  child >= 0: four-wide node;
+// child < 0: leaf of the sorted primitive ~child.
+struct __align__(16) Node4 {
+  float4 v0;  // lo.xyz, s.x
+  float4 v1;  // s.yz, bits: qlo.x (4 children x u8), qlo.y
+  uint4 q;    // qlo.z, qhi.x, qhi.y, qhi.z (4 children x u8 each)
+  int4 child;
+  uint4 m01;  // cell masks of children 0, 1 (lo, hi)
+  uint4 m23;  // cell masks of children 2, 3
+};
+
 struct LodDev {
   int freq_policy, max_band, cone_policy;
 };
@@ -45,6 +61,7 @@ struct DevField {
   const float4* rec;       // FP32 records: 4 x float4 per primitive, BVH order
   const uint4* rec16;      // FP16/BF16 records: 2 x uint4 per primitive, BVH order
   const Node* nodes;
+  const Node4* nodes4;     // four-wide collapse of nodes (root 0 when n >= 2)
   int64_t n;
   int root;                // internal root node, -1 when n == 1
   int precision;           // 0 FP32, 1 FP16, 2 BF16
@@ -115,6 +132,11 @@ constexpr float kLog2e = 1.4426950408889634f;
 // warp helpers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  return x;
+}
+__device__ __forceinline__ long long warp_sum_ll(long long x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
   return x;

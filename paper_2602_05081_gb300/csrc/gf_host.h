@@ -63,6 +63,7 @@ struct Field {
   float4* rec = nullptr;        // FP32 records in BVH order
   uint4* rec16 = nullptr;       // reduced-precision records in BVH order
   Node* nodes = nullptr;
+  Node4* nodes4 = nullptr;      // four-wide collapse (built by gf_build_bvh)
   int* sorted_orig = nullptr;   // BVH position -> original index
   uint8_t* labels = nullptr;    // band, cone, cell per primitive (3N, original order)
   int* err = nullptr;
@@ -129,7 +130,10 @@ bool lod_ok(const gf_lod_desc* l);
 
 }  // namespace gf
 
-// opaque handle of include/gf.h
+// opaque handles of include/gf.h
+struct gf_ctx {
+  gf::Ctx c;
+};
 struct gf_field {
   gf::Field f;
 };

@@ -29,21 +29,24 @@
 namespace gf {
 
 constexpr int kWWarps = 4;      // warps per block
-constexpr int kLeafQ = 96;      // queued leaves per warp (<= 31 left + 64 new)
+constexpr int kLeafQ = 160;     // queued leaves per warp (<= 31 left + 128 new)
 constexpr int kChordQ = 64;     // queued chords per warp (<= 31 left + 32 new)
 constexpr int kPK = 8;          // tentative points per lane and window
 constexpr int kSlotCh = 256;    // stored chords per lane and window (global scratch)
 
-// One slot per lane, 89 words: an odd stride keeps same-field accesses of the
+// One slot per lane, 61 words: an odd stride keeps same-field accesses of the
 // 32 slots in distinct shared-memory banks.
 struct LaneRay {
   float o[3], v[3], inv[3];
-  float tmin, tmax, ta, te;     // ray range and window [ta, te)
+  float ta, te;                 // window [ta, te) of the ray (which spans t >= 0)
   uint32_t ray, word;
+  uint32_t seed_lo, seed_hi;    // Philox key of the path's render
+  int asset;                    // field of the path
   float bw[8];                  // LoD band weights
   uint32_t mask_lo, mask_hi;    // LoD cell bits
   int npts;                     // points emitted in the window (may exceed kPK)
   int nch;                      // chords stored for the window (may exceed kSlotCh)
+  int hmax;                     // bits of the largest chord peak h of the window (h >= 0)
   float pt[kPK], pu[kPK], kap[kPK], kb[kPK];
 };
 static_assert(sizeof(LaneRay) % 8 == 4, "odd word stride");
@@ -52,12 +55,17 @@ struct ChordItem {
   uint32_t orig;
   int owner;
 };
-constexpr int kWStack = 1024;   // shared (node, slot) stack entries per warp
+// Shared (node, slot) stack entries per warp.  A step pushes at most 128
+// entries (32 four-wide nodes); above kWStack - kStackMargin the warp goes
+// depth first (one entry per step, net growth <= 3 per tree level), so the
+// stack holds a full step plus 40 levels of descent.  Four blocks of four
+// warps fit one SM.
+constexpr int kWStack = 848;
+constexpr int kStackMargin = 248;
 struct WarpQ {
   LaneRay r[32];
-  int stk[kWStack];
-  int lq_prim[kLeafQ];
-  int lq_own[kLeafQ];
+  int stk[kWStack];   // (node << 5) | slot
+  int lq[kLeafQ];     // (sorted primitive << 5) | slot
   ChordItem cq[kChordQ];
 };
 
@@ -76,20 +84,22 @@ __device__ __forceinline__ float ray_weight(const LaneRay& R, uint32_t cell) {
   return R.bw[b];
 }
 
+__device__ __forceinline__ uint64_t slot_seed(const LaneRay& R) {
+  return (uint64_t)R.seed_lo | ((uint64_t)R.seed_hi << 32);
+}
+
 // chord of sorted primitive j on the ray of slot R
-__device__ __forceinline__ bool slot_chord(const DevField& F, const LaneRay& R, int j, Prim& P,
-                                           Chord& ch, float& w) {
-  P = load_prim(F, j);
-  w = ray_weight(R, P.cell & 63u);
-  if (!(w > 0.f)) return false;
-  return chord_setup(P, make_float3(R.o[0], R.o[1], R.o[2]), make_float3(R.v[0], R.v[1], R.v[2]),
-                     R.tmin, R.tmax, F.k2, ch);
+__device__ __forceinline__ bool slot_chord(const DevField& F, const LaneRay& R, int j, Chord& ch,
+                                           float& w) {
+  return prim_chord(F, j, make_float3(R.o[0], R.o[1], R.o[2]), make_float3(R.v[0], R.v[1], R.v[2]),
+                    0.f, INFINITY, [&](uint32_t c) { return ray_weight(R, c); }, w, ch);
 }
 
 // walk one queued chord: emit its tentative points in [ta, te) to the owner
 __device__ __forceinline__ void walk_chord(const DevField& F, WarpQ& Q, const ChordItem& c,
-                                           uint64_t seed, const float* env, unsigned long long& npt) {
+                                           const float* env, unsigned long long& npt) {
   LaneRay& R = Q.r[c.owner];
+  const uint64_t seed = slot_seed(R);
   const float ta = R.ta, te = R.te;
   const float invs = 1.0f / c.sa;
   int J = (int)ceilf(c.smax) - 1;
@@ -143,40 +153,38 @@ __device__ __forceinline__ void walk_chord(const DevField& F, WarpQ& Q, const Ch
 // frontiers of all its rays, so lanes stay busy while 32 rays are in flight.
 // It collects the tentative points of each slot's window and stores the
 // window's chords for their evaluation.
-__device__ void warp_phase(const DevField& F, WarpQ& Q, bool want, uint32_t lane, uint64_t seed,
-                           const float* env, float4* wch, Counters& cnt) {
+template <class Work>
+__device__ void warp_phase(const Work& Wk, WarpQ& Q, bool want, uint32_t lane, const float* env,
+                           float4* wch, Counters& cnt) {
   const unsigned lt = (1u << lane) - 1u;
   int sp = 0, lq_n = 0, cq_n = 0;  // warp-uniform sizes
   {
-    const unsigned bal = __ballot_sync(kFull, want);
-    const int idx = __popc(bal & lt);
-    if (F.root >= 0) {
-      if (want) Q.stk[idx] = (F.root << 5) | (int)lane;
-      sp = __popc(bal);
-    } else {  // a one-primitive field has no internal node: queue its leaf
-      if (want) {
-        Q.lq_prim[idx] = 0;
-        Q.lq_own[idx] = (int)lane;
-      }
-      lq_n = __popc(bal);
-    }
+    // a one-primitive field has no internal node: its leaf is queued instead
+    const int root = want ? Wk.field(Q.r[lane].asset).root : -1;
+    const unsigned bs = __ballot_sync(kFull, want && root >= 0);
+    const unsigned bl = __ballot_sync(kFull, want && root < 0);
+    if (want && root >= 0) Q.stk[__popc(bs & lt)] = (root << 5) | (int)lane;
+    if (want && root < 0) Q.lq[__popc(bl & lt)] = (0 << 5) | (int)lane;
+    sp = __popc(bs);
+    lq_n = __popc(bl);
     __syncwarp();
   }
-  const long long max_it = 4 * (F.n + 64) * 32 / 32 + 4096;
+  const long long max_it = 4 * (Wk.max_n() + 64) + 4096;
   for (long long it = 0;; ++it) {
     if (it > max_it * 32) {
-      if (lane == 0) set_err(F, ERR_GUARD);
+      if (lane == 0) set_err(Wk.err_field(), ERR_GUARD);
       break;
     }
-    // ---------------- one traversal step: up to 32 (node, slot) entries
+    // ---------------- one traversal step: up to 32 (four-wide node, slot) entries
     GF_TIC(t_step);
     int take = sp < 32 ? sp : 32;
-    if (sp > kWStack - 96) take = 1;  // near capacity: depth first
-    int ent = (int)lane < take ? Q.stk[sp - take + (int)lane] : -1;
+    if (sp > kWStack - kStackMargin) take = 1;  // near capacity: depth first
+    const int ent = (int)lane < take ? Q.stk[sp - take + (int)lane] : -1;
     __syncwarp();
     sp -= take;
-    int c0 = 0, c1 = 0, l0 = -1, l1 = -1, slot = 0;
-    bool g0 = false, g1 = false;
+    int slot = 0;
+    int ch[4] = {0, 0, 0, 0};
+    unsigned hit = 0u;  // bit k: child k overlaps the window and the ray's cells
     if (ent >= 0) {
       const int node = ent >> 5;
       slot = ent & 31;
@@ -184,51 +192,70 @@ __device__ void warp_phase(const DevField& F, WarpQ& Q, bool want, uint32_t lane
       const float3 o = make_float3(R.o[0], R.o[1], R.o[2]);
       const float3 inv = make_float3(R.inv[0], R.inv[1], R.inv[2]);
       const unsigned long long mask = slot_mask(R);
-      const Node* N = F.nodes + node;
-      const float4 a = __ldg(&N->a), b = __ldg(&N->b), c = __ldg(&N->c);
-      const int4 d = __ldg(&N->d);
-      const uint4 e = __ldg(&N->e);
+      const Node4* N = Wk.field(R.asset).nodes4 + node;
+      const float4 v0 = __ldg(&N->v0), v1 = __ldg(&N->v1);
+      const uint4 q = __ldg(&N->q);
+      const int4 c4 = __ldg(&N->child);
+      const uint4 m01 = __ldg(&N->m01), m23 = __ldg(&N->m23);
       ++cnt.nodes;
-      const unsigned long long m0 = (unsigned long long)e.x | ((unsigned long long)e.y << 32);
-      const unsigned long long m1 = (unsigned long long)e.z | ((unsigned long long)e.w << 32);
-      float tn0, tf0, tn1, tf1;
-      slab_interval(o, inv, a.x, a.y, a.z, a.w, b.x, b.y, tn0, tf0);
-      slab_interval(o, inv, b.z, b.w, c.x, c.y, c.z, c.w, tn1, tf1);
-      bool h0 = fmaxf(tn0, R.ta) <= fminf(tf0, R.te);
-      bool h1 = fmaxf(tn1, R.ta) <= fminf(tf1, R.te);
-      h0 = h0 && (m0 & mask);
-      h1 = h1 && (m1 & mask);
-      c0 = d.x;
-      c1 = d.y;
-      if (h0 && c0 < 0) l0 = ~c0;
-      if (h1 && c1 < 0) l1 = ~c1;
-      g0 = h0 && c0 >= 0;
-      g1 = h1 && c1 >= 0;
+      const uint32_t qlx = __float_as_uint(v1.z), qly = __float_as_uint(v1.w);
+      const unsigned long long mk[4] = {
+          (unsigned long long)m01.x | ((unsigned long long)m01.y << 32),
+          (unsigned long long)m01.z | ((unsigned long long)m01.w << 32),
+          (unsigned long long)m23.x | ((unsigned long long)m23.y << 32),
+          (unsigned long long)m23.z | ((unsigned long long)m23.w << 32)};
+      ch[0] = c4.x;
+      ch[1] = c4.y;
+      ch[2] = c4.z;
+      ch[3] = c4.w;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int sh = 8 * k;
+        const float x0 = fmaf((float)((qlx >> sh) & 255u), v0.w, v0.x);
+        const float y0 = fmaf((float)((qly >> sh) & 255u), v1.x, v0.y);
+        const float z0 = fmaf((float)((q.x >> sh) & 255u), v1.y, v0.z);
+        const float x1 = fmaf((float)((q.y >> sh) & 255u), v0.w, v0.x);
+        const float y1 = fmaf((float)((q.z >> sh) & 255u), v1.x, v0.y);
+        const float z1 = fmaf((float)((q.w >> sh) & 255u), v1.y, v0.z);
+        float tn, tf;
+        slab_interval(o, inv, x0, y0, z0, x1, y1, z1, tn, tf);
+        if ((mk[k] & mask) && fmaxf(tn, R.ta) <= fminf(tf, R.te)) hit |= 1u << k;
+      }
     }
-    // ---------------- push internal children, queue leaves
+    // ---------------- push internal children, queue leaves (one warp scan)
     {
-      const unsigned p0 = __ballot_sync(kFull, g0), p1 = __ballot_sync(kFull, g1);
-      const int np0 = __popc(p0), np1 = __popc(p1);
-      if (sp + np0 + np1 > kWStack) {
-        if (lane == 0) set_err(F, ERR_STACK);
-      } else {
-        if (g0) Q.stk[sp + __popc(p0 & lt)] = (c0 << 5) | slot;
-        if (g1) Q.stk[sp + np0 + __popc(p1 & lt)] = (c1 << 5) | slot;
-        sp += np0 + np1;
+      int np = 0, nl = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (hit >> k & 1u) {
+          if (ch[k] >= 0) ++np;
+          else ++nl;
+        }
       }
-      const unsigned b0 = __ballot_sync(kFull, l0 >= 0), b1 = __ballot_sync(kFull, l1 >= 0);
-      const int n0 = __popc(b0);
-      if (l0 >= 0) {
-        const int idx = lq_n + __popc(b0 & lt);
-        Q.lq_prim[idx] = l0;
-        Q.lq_own[idx] = slot;
+      int inc = np | (nl << 16);
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, inc, o);
+        if ((int)lane >= o) inc += y;
       }
-      if (l1 >= 0) {
-        const int idx = lq_n + n0 + __popc(b1 & lt);
-        Q.lq_prim[idx] = l1;
-        Q.lq_own[idx] = slot;
+      const int tot = __shfl_sync(kFull, inc, 31);
+      const int tp = tot & 0xFFFF, tl = tot >> 16;
+      int pp = sp + (inc & 0xFFFF) - np;
+      int pl = lq_n + (inc >> 16) - nl;
+      const bool room = sp + tp <= kWStack;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (hit >> k & 1u) {
+          if (ch[k] >= 0) {
+            if (room) Q.stk[pp++] = (ch[k] << 5) | slot;
+          } else {
+            Q.lq[pl++] = (~ch[k] << 5) | slot;
+          }
+        }
       }
-      lq_n += n0 + __popc(b1);
+      if (room) sp += tp;
+      else if (lane == 0) set_err(Wk.err_field(), ERR_STACK);
+      lq_n += tl;
       __syncwarp();
     }
     const bool any_trav = sp > 0;
@@ -239,8 +266,9 @@ __device__ void warp_phase(const DevField& F, WarpQ& Q, bool want, uint32_t lane
       const bool have = (int)lane < tk;
       int j = 0, own = 0;
       if (have) {
-        j = Q.lq_prim[lq_n - tk + (int)lane];
-        own = Q.lq_own[lq_n - tk + (int)lane];
+        const int e = Q.lq[lq_n - tk + (int)lane];
+        j = e >> 5;
+        own = e & 31;
       }
       __syncwarp();
       lq_n -= tk;
@@ -250,16 +278,16 @@ __device__ void warp_phase(const DevField& F, WarpQ& Q, bool want, uint32_t lane
       ChordItem ci;
       if (have) {
         const LaneRay& R = Q.r[own];
-        Prim P;
         Chord ch;
         float w;
-        if (slot_chord(F, R, j, P, ch, w)) {
+        if (slot_chord(Wk.field(R.asset), R, j, ch, w)) {
           const float tin = ch.tc + ch.dtin, tout = ch.tc + ch.dtout;
           if (tin < R.te && tout >= R.ta) {
             ok = true;
             const float wa = w * ch.absA;
             const float h = wa * expf(-0.5f * ch.qmin), sa = sqrtf(ch.a);
             // evaluation record for the points of this window
+            atomicMax(&Q.r[own].hmax, __float_as_int(h));
             const int k = atomicAdd(&Q.r[own].nch, 1);
             if (k < kSlotCh) {
               float4* dst = wch + ((size_t)own * kSlotCh + k) * 3;
@@ -292,7 +320,7 @@ __device__ void warp_phase(const DevField& F, WarpQ& Q, bool want, uint32_t lane
         ChordItem cw = Q.cq[cq_n - 32 + (int)lane];
         __syncwarp();
         cq_n -= 32;
-        if (hv) walk_chord(F, Q, cw, seed, env, cnt.points);
+        if (hv) walk_chord(Wk.err_field(), Q, cw, env, cnt.points);
         __syncwarp();
       }
       if (lane == 0) GF_TOC(cnt, 2, t_walk);
@@ -306,7 +334,7 @@ __device__ void warp_phase(const DevField& F, WarpQ& Q, bool want, uint32_t lane
         if (hv) cw = Q.cq[cq_n - tk + (int)lane];
         __syncwarp();
         cq_n -= tk;
-        if (hv) walk_chord(F, Q, cw, seed, env, cnt.points);
+        if (hv) walk_chord(Wk.err_field(), Q, cw, env, cnt.points);
         __syncwarp();
       }
     }
@@ -317,6 +345,7 @@ __device__ void warp_phase(const DevField& F, WarpQ& Q, bool want, uint32_t lane
 
 // per-lane path state
 struct PathState {
+  int rq;         // request of the pixel (0 for a single render)
   int pix;        // -1: no pixel
   int s, b;       // sample, bounce
   int kind;       // 0 idle, 1 delta tracking, 2 ratio tracking (NEE)
@@ -332,8 +361,6 @@ __device__ __forceinline__ void set_slot(LaneRay& R, float3 o, float3 v, const M
   R.v[0] = v.x; R.v[1] = v.y; R.v[2] = v.z;
   const float3 iv = safe_inv(v);
   R.inv[0] = iv.x; R.inv[1] = iv.y; R.inv[2] = iv.z;
-  R.tmin = 0.f;
-  R.tmax = INFINITY;
   R.ray = ray;
   R.word = word;
   R.mask_lo = (uint32_t)m.bits;
@@ -364,6 +391,13 @@ __device__ __forceinline__ bool start_ray(const DevField& F, LaneRay& R, PathSta
 
 // kappa and kappa_bar at the points of every slot, from the chords pass 1
 // stored: the warp scans each slot's list (lanes over chords), then reduces.
+// The sums are exact in 64-bit fixed point: a term is at most the peak h of
+// its chord, so with H the largest peak of the slot's window and at most
+// kSlotCh = 2^8 chords, scaling by 2^(54 - e) (H < 2^e) keeps every partial
+// sum below 2^62.  Each term is rounded once (to 2^(e-54), far below FP32
+// resolution); the integer sum does not depend on the order in which the
+// chords were stored, so a path's decisions do not depend on which other
+// rays shared its warp.
 __device__ void eval_stored(WarpQ& Q, const float4* wch, const float* env, uint32_t lane,
                             Counters& cnt) {
   for (int s = 0; s < 32; ++s) {
@@ -371,12 +405,17 @@ __device__ void eval_stored(WarpQ& Q, const float4* wch, const float* env, uint3
     const int ns = R.npts;
     if (ns <= 0) continue;  // uniform: every lane reads the same slot
     const int mc = R.nch;
-    float pt[kPK], kap[kPK], kb[kPK];
+    int ex = ((R.hmax >> 23) & 0xFF) - 126;  // H < 2^ex
+    ex = ex < -70 ? -70 : ex;
+    const float S = __int_as_float((127 + 54 - ex) << 23);     // 2^(54 - ex)
+    const float invS = __int_as_float((127 - 54 + ex) << 23);  // 2^(ex - 54)
+    float pt[kPK];
+    long long kap[kPK], kb[kPK];
 #pragma unroll
     for (int i = 0; i < kPK; ++i) {
       pt[i] = i < ns ? R.pt[i] : INFINITY;
-      kap[i] = 0.f;
-      kb[i] = 0.f;
+      kap[i] = 0;
+      kb[i] = 0;
     }
     const float4* base = wch + (size_t)s * kSlotCh * 3;
     for (int c = (int)lane; c < mc; c += 32) {
@@ -387,10 +426,10 @@ __device__ void eval_stored(WarpQ& Q, const float4* wch, const float* env, uint3
         if (t >= a.y && t <= a.z) {
           const float dt = t - a.x;
           const float y = fmaf(fmaf(b.x, dt, b.y), dt, b.z);
-          kap[i] = fmaf(ex2f(y), cosf_fast(fmaf(a.w, dt, b.w)), kap[i]);
+          kap[i] += __float2ll_rn(ex2f(y) * cosf_fast(fmaf(a.w, dt, b.w)) * S);
           int m = (int)(fabsf(dt - e.z) * e.y);
           m = m > 7 ? 7 : m;
-          kb[i] = fmaf(e.x, env[m], kb[i]);
+          kb[i] += __float2ll_rn(e.x * env[m] * S);
           ++cnt.evals;
         }
       }
@@ -398,10 +437,10 @@ __device__ void eval_stored(WarpQ& Q, const float4* wch, const float* env, uint3
 #pragma unroll
     for (int i = 0; i < kPK; ++i) {
       if (i < ns) {
-        const float k1 = warp_sum(kap[i]), k2 = warp_sum(kb[i]);
+        const long long k1 = warp_sum_ll(kap[i]), k2 = warp_sum_ll(kb[i]);
         if (lane == 0) {
-          R.kap[i] = k1;
-          R.kb[i] = k2;
+          R.kap[i] = __ll2float_rn(k1) * invS;
+          R.kb[i] = __ll2float_rn(k2) * invS;
         }
       }
     }
@@ -409,23 +448,70 @@ __device__ void eval_stored(WarpQ& Q, const float4* wch, const float* env, uint3
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(kWWarps * 32)
-    k_render_scatter(const __grid_constant__ DevField F, const PathParams P, float* out,
-                     int* counter, float4* chord_store) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  float* env = reinterpret_cast<float*>(smraw);
-  WarpQ* Qs = reinterpret_cast<WarpQ*>(smraw + 64);
-  if (threadIdx.x < 8) env[threadIdx.x] = F.env[threadIdx.x];
-  __syncthreads();
-  const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-  WarpQ& Q = Qs[wid];
+// ---------------------------------------------------------------------------
+// Work sources.  A lane takes pixels one at a time; a pixel belongs to a
+// request (its camera, LoD descriptors, seed and framebuffer) and a request to
+// a field.  A single render is one request on one field; the render server
+// hands the kernel a batch of items from many requests on several fields.
+// ---------------------------------------------------------------------------
+struct ImageWork {
+  const DevField* F;
+  const PathParams* P;
+  float* out;
+  int* counter;
+  int npix;
+  __device__ const DevField& field(int) const { return *F; }
+  __device__ const DevField& err_field() const { return *F; }
+  __device__ int64_t max_n() const { return F->n; }
+  __device__ const PathParams& params(int) const { return *P; }
+  __device__ int asset(int) const { return 0; }
+  __device__ bool next(int& rq, int& pix) const {
+    pix = atomicAdd(counter, 1);
+    rq = 0;
+    return pix < npix;
+  }
+  __device__ void write(int, int pix, float v) const { out[pix] = v; }
+};
+
+struct ServerWork {
+  const ServerLaunch* L;
+  __device__ const DevField& field(int a) const { return L->fields[a]; }
+  __device__ const DevField& err_field() const { return L->fields[0]; }
+  __device__ int64_t max_n() const { return L->max_n; }
+  __device__ const PathParams& params(int rq) const { return L->reqs[rq].P; }
+  __device__ int asset(int rq) const { return L->reqs[rq].asset; }
+  // the batch's pixels are numbered 0..total-1 item after item; a lane takes
+  // the next number and finds its item by binary search over the item bases
+  __device__ bool next(int& rq, int& pix) const {
+    const int f = atomicAdd(L->counter, 1);
+    if (f >= L->total) return false;
+    int lo = 0, hi = L->n_items - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (L->items[mid].base <= f) lo = mid;
+      else hi = mid - 1;
+    }
+    const ServerItem it = L->items[lo];
+    rq = it.req;
+    pix = it.pix0 + (f - it.base);
+    return true;
+  }
+  __device__ void write(int rq, int pix, float v) const { L->reqs[rq].fb[pix] = v; }
+};
+
+// The paths of one warp: each lane runs its pixels' samples in order (camera
+// ray -> delta tracking -> NEE by ratio tracking -> isotropic scattering), the
+// tracking windows of all 32 lanes advancing together through warp_phase.
+template <class Work>
+__device__ __forceinline__ void render_paths(const Work& Wk, const float* env, WarpQ& Q,
+                                             float4* wch) {
+  const uint32_t lane = threadIdx.x & 31u;
   LaneRay& R = Q.r[lane];
-  float4* wch = chord_store + ((size_t)blockIdx.x * kWWarps + wid) * 32 * kSlotCh * 3;
   Counters cnt;
-  const int npix = P.cam.W * P.cam.H;
   const float inv4pi = 0.25f / 3.14159265358979f;
 
   PathState S;
+  S.rq = 0;
   S.pix = -1;
   S.kind = 0;
   S.acc = 0.f;
@@ -434,20 +520,28 @@ __global__ void __launch_bounds__(kWWarps * 32)
   auto begin_sample = [&]() {
     for (;;) {
       if (S.pix < 0) {
-        S.pix = atomicAdd(counter, 1);
-        if (S.pix >= npix) {
+        int rq = 0, pix = -1;
+        if (!Wk.next(rq, pix)) {
           S.pix = -1;
           S.kind = 0;
           return;
         }
+        const PathParams& P = Wk.params(rq);
+        S.rq = rq;
+        S.pix = pix;
         S.s = 0;
         S.acc = 0.f;
+        R.asset = Wk.asset(rq);
+        R.seed_lo = (uint32_t)P.seed;
+        R.seed_hi = (uint32_t)(P.seed >> 32);
       }
+      const PathParams& P = Wk.params(S.rq);
       if (S.s >= P.spp) {
-        out[S.pix] = S.acc / (float)P.spp;
+        Wk.write(S.rq, S.pix, S.acc / (float)P.spp);
         S.pix = -1;
         continue;
       }
+      const DevField& F = Wk.field(R.asset);
       const int px = S.pix % P.cam.W, py = S.pix / P.cam.W;
       float3 o, v;
       camera_ray(P.cam, P.seed, px, py, S.s, o, v);
@@ -465,6 +559,8 @@ __global__ void __launch_bounds__(kWWarps * 32)
   };
   // the lane's current ray is finished: move the path on
   auto finish_ray = [&](bool hit, float th) {
+    const PathParams& P = Wk.params(S.rq);
+    const DevField& F = Wk.field(R.asset);
     for (;;) {
       if (S.kind == 1) {
         if (!hit) {
@@ -520,8 +616,9 @@ __global__ void __launch_bounds__(kWWarps * 32)
     // ---- pass 1: tentative points of the window
     R.npts = 0;
     R.nch = 0;
+    R.hmax = 0;
     __syncwarp();
-    warp_phase(F, Q, want, lane, P.seed, env, wch, cnt);
+    warp_phase(Wk, Q, want, lane, env, wch, cnt);
     // owner: a window whose points overflowed the slots is halved and redone;
     // otherwise its points are sorted by t for the decisions
     int n = 0;
@@ -558,7 +655,7 @@ __global__ void __launch_bounds__(kWWarps * 32)
         const float w = R.te - R.ta;
         if (w <= 1e-6f * (1.0f + fabsf(R.ta))) {
           // more than kPK points at one t: give up on this ray
-          set_err(F, ERR_POINTS);
+          set_err(Wk.err_field(), ERR_POINTS);
           finish_ray(false, 0.f);
         } else {
           R.te = R.ta + 0.5f * w;
@@ -598,29 +695,72 @@ __global__ void __launch_bounds__(kWWarps * 32)
     __syncwarp();
     if (lane == 0) GF_TOC(cnt, 4, t_dec);
   }
-  flush_counters(F, cnt, lane);
+  flush_counters(Wk.err_field(), cnt, lane);
+}
+
+__device__ __forceinline__ WarpQ& setup_block(unsigned char* smraw, const float* env_src) {
+  float* env = reinterpret_cast<float*>(smraw);
+  WarpQ* Qs = reinterpret_cast<WarpQ*>(smraw + 64);
+  if (threadIdx.x < 8) env[threadIdx.x] = env_src[threadIdx.x];
+  __syncthreads();
+  return Qs[threadIdx.x >> 5];
+}
+
+__device__ __forceinline__ float4* warp_store(float4* chord_store) {
+  return chord_store + ((size_t)blockIdx.x * kWWarps + (threadIdx.x >> 5)) * 32 * kSlotCh * 3;
+}
+
+__global__ void __launch_bounds__(kWWarps * 32, 4)
+    k_render_scatter(const __grid_constant__ DevField F, const __grid_constant__ PathParams P,
+                     float* out, int* counter, float4* chord_store) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  WarpQ& Q = setup_block(smraw, F.env);
+  const ImageWork Wk{&F, &P, out, counter, P.cam.W * P.cam.H};
+  render_paths(Wk, reinterpret_cast<const float*>(smraw), Q, warp_store(chord_store));
+}
+
+__global__ void __launch_bounds__(kWWarps * 32, 4)
+    k_render_server(const __grid_constant__ ServerLaunch L, float4* chord_store) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  WarpQ& Q = setup_block(smraw, L.fields[0].env);
+  const ServerWork Wk{&L};
+  render_paths(Wk, reinterpret_cast<const float*>(smraw), Q, warp_store(chord_store));
 }
 
 size_t scatter_smem_bytes() { return 64 + sizeof(WarpQ) * kWWarps; }
+static_assert(64 + sizeof(WarpQ) * kWWarps <= 57344, "four blocks per SM (56 KB each)");
+
+size_t scatter_store_bytes(int64_t grid) {
+  return (size_t)grid * kWWarps * 32 * kSlotCh * 3 * sizeof(float4);
+}
+
+// persistent grid of the scattering kernels: every SM filled, never more
+// warps than work (4 warps x 32 lanes per block)
+template <class K>
+static cudaError_t scatter_grid(K kernel, int sm_count, int64_t pixels, int64_t& g) {
+  const size_t smem = scatter_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWWarps * 32, smem) != cudaSuccess)
+    (void)cudaGetLastError();
+  if (per_sm < 1) per_sm = 1;
+  const int64_t need = (pixels + kWWarps * 32 - 1) / (kWWarps * 32);
+  g = (int64_t)sm_count * per_sm;
+  if (need < g) g = need;
+  if (g < 1) g = 1;
+  return cudaSuccess;
+}
 
 cudaError_t launch_render_scatter(const Field& F, const PathParams& P, float* out, cudaStream_t s) {
   (void)cudaGetLastError();  // a stale error of an unrelated call is not ours
   cudaError_t e = cudaMemsetAsync(F.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  const size_t smem = scatter_smem_bytes();
-  e = cudaFuncSetAttribute(k_render_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_scatter, kWWarps * 32, smem) != cudaSuccess)
-    (void)cudaGetLastError();
-  if (per_sm < 1) per_sm = 1;
-  const int64_t npix = (int64_t)P.cam.W * P.cam.H;
-  const int64_t need = (npix + kWWarps * 32 - 1) / (kWWarps * 32);
-  int64_t g = (int64_t)F.ctx.sm_count * per_sm;
-  if (need < g) g = need;
-  if (g < 1) g = 1;
+  int64_t g = 1;
+  if ((e = scatter_grid(k_render_scatter, F.ctx.sm_count, (int64_t)P.cam.W * P.cam.H, g)) != cudaSuccess)
+    return e;
   // per-warp chord store: 32 slots x kSlotCh records of 3 float4
-  const size_t store = (size_t)g * kWWarps * 32 * kSlotCh * 3 * sizeof(float4);
+  const size_t store = scatter_store_bytes(g);
   if (F.wscratch_bytes < store) {
     if (F.wscratch) cudaFree(F.wscratch);
     F.wscratch = nullptr;
@@ -629,7 +769,20 @@ cudaError_t launch_render_scatter(const Field& F, const PathParams& P, float* ou
     if (e != cudaSuccess) return e;
     F.wscratch_bytes = store;
   }
-  k_render_scatter<<<(unsigned)g, kWWarps * 32, smem, s>>>(F.dev, P, out, F.counter, F.wscratch);
+  k_render_scatter<<<(unsigned)g, kWWarps * 32, scatter_smem_bytes(), s>>>(F.dev, P, out, F.counter,
+                                                                          F.wscratch);
+  return cudaGetLastError();
+}
+
+cudaError_t server_grid(int sm_count, int64_t& g) {
+  (void)cudaGetLastError();
+  return scatter_grid(k_render_server, sm_count, (int64_t)1 << 40, g);
+}
+
+cudaError_t launch_render_server(const ServerLaunch& L, int64_t grid, float4* chord_store,
+                                 cudaStream_t s) {
+  (void)cudaGetLastError();
+  k_render_server<<<(unsigned)grid, kWWarps * 32, scatter_smem_bytes(), s>>>(L, chord_store);
   return cudaGetLastError();
 }
 
