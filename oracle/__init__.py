@@ -101,6 +101,12 @@ def _load():
         lib.or_tomo_loss_grad.argtypes = [C.POINTER(FieldDesc), C.POINTER(Camera), i32, u64, vp,
                                           vp, i32]
         lib.or_tomo_image.argtypes = [C.POINTER(FieldDesc), C.POINTER(Camera), i32, u64, vp, i32]
+        lib.or_radiance_grad_rays.argtypes = [C.POINTER(FieldDesc), C.POINTER(Lod), C.POINTER(Lod),
+                                              C.POINTER(RenderOpts), vp, vp, i64, i32, u64, vp,
+                                              vp, vp, i32]
+        lib.or_radiance_grad_image.argtypes = [C.POINTER(FieldDesc), C.POINTER(Lod), C.POINTER(Lod),
+                                               C.POINTER(Camera), C.POINTER(RenderOpts), u64, vp,
+                                               vp, vp, i32]
         lib.or_rays_traced.restype = C.c_longlong
         lib.or_rays_traced.argtypes = [i32]
         _lib = lib
@@ -243,6 +249,35 @@ class Field:
         L = self.lib.or_tomo_loss_grad(C.byref(self.desc), C.byref(cam), int(spp), int(seed),
                                        _ptr(tgt), _ptr(g), int(threads))
         return L, g
+
+    def radiance_grad_rays(self, o, v, ropts, spp, seed, dLdI=None, lod=None, lod_nee=None,
+                           threads=0):
+        """Single-scattering radiance estimator and its adjoint along fixed rays:
+        returns (value per ray, gradient (15 N, SoA)); gradient is None without dLdI."""
+        o = _f64(o).reshape(-1)
+        v = _f64(v).reshape(-1)
+        n = o.size // 3
+        val = np.zeros(n)
+        g = np.zeros(15 * self.n) if dLdI is not None else None
+        lod = lod if lod is not None else Lod(0, 7, 0)
+        lod_nee = lod_nee if lod_nee is not None else lod
+        self.lib.or_radiance_grad_rays(C.byref(self.desc), C.byref(lod), C.byref(lod_nee),
+                                       C.byref(ropts), _ptr(o), _ptr(v), n, int(spp), int(seed),
+                                       _ptr(None if dLdI is None else _f64(dLdI).reshape(-1)),
+                                       _ptr(val), _ptr(g), int(threads))
+        return val, g
+
+    def radiance_grad(self, cam, ropts, seed, dLdI=None, lod=None, lod_nee=None, threads=0):
+        """Image version (jittered camera rays, spp from ropts): (image, gradient)."""
+        img = np.zeros(cam.width * cam.height)
+        g = np.zeros(15 * self.n) if dLdI is not None else None
+        lod = lod if lod is not None else Lod(0, 7, 0)
+        lod_nee = lod_nee if lod_nee is not None else lod
+        self.lib.or_radiance_grad_image(C.byref(self.desc), C.byref(lod), C.byref(lod_nee),
+                                        C.byref(cam), C.byref(ropts), int(seed),
+                                        _ptr(None if dLdI is None else _f64(dLdI).reshape(-1)),
+                                        _ptr(img), _ptr(g), int(threads))
+        return img.reshape(cam.height, cam.width), g
 
     def tomo_image(self, cam, spp, seed, threads=0):
         img = np.zeros(cam.width * cam.height)

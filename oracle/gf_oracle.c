@@ -1107,3 +1107,248 @@ double or_tomo_loss_grad(const or_field_desc* D, const or_camera* C, int spp, ui
   or_field_free(f);
   return L;
 }
+
+/* ------------------------------------------------------------------------ */
+/* single-scattering radiance adjoint                                        */
+/*                                                                            */
+/* Free flight by delta tracking has the same mean as the expected-value     */
+/* estimator over ALL tentative points t_j of the ray (rate kappa_bar):      */
+/*   I = sum_j W_j G(t_j),  W_j = prod_{i<j} (1 - p_i) p_j,                   */
+/*   p_j = max(kappa_j, 0) / kappa_bar_j,  G = albedo E/(4 pi) T_light,       */
+/* because the points before t form a Poisson process independent of the    */
+/* point at t (Campbell's formula gives int T kappa+ G dt).  One point js is */
+/* drawn with probability W_j / sum W and its NEE transmittance is ratio     */
+/* tracked, so a sample is sum W * G(t_js).  The derivative is taken with    */
+/* the tentative points, kappa_bar and the draw probabilities held fixed    */
+/* (each keeps the estimator's mean equal to I for nearby parameters), so   */
+/* only kappa_j and the NEE kappa_k vary:                                   */
+/*   d sample / d p_i  = (sum W / W_js) G dW_js/dp_i,                       */
+/*   d sample / d q_k  = sum W  albedo E/(4 pi) (-prod_{m != k} (1 - q_m)),  */
+/*   d p / d theta     = 1[kappa > 0] d kappa/d theta / kappa_bar,           */
+/* with d kappa/d theta summed over the kernels covering the point.  The    */
+/* k-sigma cut contributes no term (the derivative of the truncated field   */
+/* is taken where it is smooth).                                            */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  double t, kap, kb;
+} or_rpt;
+
+static int cmp_rpt(const void* A, const void* B) {
+  double a = ((const or_rpt*)A)->t, b = ((const or_rpt*)B)->t;
+  return (a > b) - (a < b);
+}
+
+/* all tentative points of a ray, sorted, with kappa and kappa_bar */
+static int ray_points(const or_field* f, const double o[3], const double v[3], uint64_t mask,
+                      const double* w64, uint64_t seed, uint32_t ray, uint32_t word,
+                      or_hit** hits, int* nhits, or_rpt** out) {
+  int nh = collect_hits(f, o, v, 0.0, INFINITY, mask, w64, hits);
+  or_pt* pts;
+  int np = gather_points(f, *hits, nh, seed, ray, word, &pts);
+  or_rpt* r = (or_rpt*)malloc(sizeof(or_rpt) * (size_t)(np > 0 ? np : 1));
+  for (int j = 0; j < np; ++j) {
+    r[j].t = pts[j].t;
+    eval_point(f, *hits, nh, o, v, pts[j].t, &r[j].kap, &r[j].kb);
+  }
+  free(pts);
+  qsort(r, (size_t)np, sizeof(or_rpt), cmp_rpt);
+  *nhits = nh;
+  *out = r;
+  return np;
+}
+
+/* add coef * d kappa(x(t)) / d theta to the 15 N gradient */
+static void add_dkappa(const or_field* f, const or_gprim* G, const or_hit* h, int nh,
+                       const double o[3], const double v[3], double t, double coef,
+                       double* g15) {
+  if (coef == 0.0) return;
+  for (int j = 0; j < nh; ++j) {
+    if (t < h[j].c.lo || t > h[j].c.hi) continue;
+    const or_gprim* Gi = &G[h[j].prim];
+    double y[3] = {o[0] + t * v[0] - Gi->mu[0], o[1] + t * v[1] - Gi->mu[1],
+                   o[2] + t * v[2] - Gi->mu[2]};
+    or_gpoint P;
+    gpoint(Gi, y, &P);
+    if (P.q > f->k * f->k) continue;
+    double cw = coef * h[j].w;
+    for (int r = 0; r < 15; ++r) {
+      double d = Gi->A * P.env * (-0.5 * P.dq[r] * P.c - P.sn * P.dth[r]) + P.dA[r] * P.env * P.c;
+      g15[h[j].prim * 15 + r] += cw * d;
+    }
+  }
+}
+
+/* one sample of the estimator along o + t v; adds dLdI * d sample/d theta
+   to g15 and returns the sample */
+static double radiance_grad_sample(const or_field* f, const or_gprim* G, const or_lod* lod,
+                                   const or_lod* lodn, const or_render_opts* ro,
+                                   const double o[3], const double v[3], uint64_t seed,
+                                   uint32_t ray, uint32_t s, double dLdI, double* g15) {
+  double l[3] = {ro->light_dir[0], ro->light_dir[1], ro->light_dir[2]};
+  normalise(l, l);
+  uint64_t mask;
+  double w64[OR_MAX_CELLS];
+  or_sample_mask(f, lod, v, seed, ray, s, 0, OR_TAG_MASK, &mask, w64);
+  or_hit* h;
+  int nh;
+  or_rpt* pt;
+  int np = ray_points(f, o, v, mask, w64, seed, ray, stream_word(s, 0, OR_TAG_TRACK), &h, &nh, &pt);
+  double* p = (double*)malloc(sizeof(double) * (size_t)(np > 0 ? np : 1));
+  double* W = (double*)malloc(sizeof(double) * (size_t)(np > 0 ? np : 1));
+  double P = 1.0, SW = 0.0;
+  for (int j = 0; j < np; ++j) {
+    double kp = pt[j].kap > 0 ? pt[j].kap : 0.0;
+    p[j] = pt[j].kb > 0 ? kp / pt[j].kb : 0.0;
+    W[j] = P * p[j];
+    SW += W[j];
+    P *= 1.0 - p[j];
+  }
+  double value = 0.0;
+  if (SW > 0.0) {
+    uint32_t y[4];
+    rng4(seed, 0, OR_NO_PRIM, ray, stream_word(s, 0, OR_TAG_SCATTER), y);
+    double target = u01(y[2]) * SW, acc = 0.0;
+    int js = np - 1;
+    for (int j = 0; j < np; ++j) {
+      acc += W[j];
+      if (target < acc && W[j] > 0.0) { js = j; break; }
+    }
+    while (js > 0 && !(W[js] > 0.0)) --js;
+    double x[3] = {o[0] + pt[js].t * v[0], o[1] + pt[js].t * v[1], o[2] + pt[js].t * v[2]};
+    /* NEE by ratio tracking from x_js */
+    uint64_t nmask;
+    double nw[OR_MAX_CELLS];
+    or_sample_mask(f, lodn, l, seed, ray, s, 0, OR_TAG_NEE_MASK, &nmask, nw);
+    or_hit* hl;
+    int nhl;
+    or_rpt* ql;
+    int nq = ray_points(f, x, l, nmask, nw, seed, ray, stream_word(s, 0, OR_TAG_NEE), &hl, &nhl, &ql);
+    double* q = (double*)malloc(sizeof(double) * (size_t)(nq > 0 ? nq : 1));
+    double Tl = 1.0;
+    for (int k = 0; k < nq; ++k) {
+      double kp = ql[k].kap > 0 ? ql[k].kap : 0.0;
+      q[k] = ql[k].kb > 0 ? kp / ql[k].kb : 0.0;
+      Tl *= 1.0 - q[k];
+    }
+    const double E = ro->albedo * ro->light_irradiance / (4.0 * OR_PI);
+    double Gv = E * Tl;
+    value = SW * Gv;
+    if (dLdI != 0.0) {
+      /* camera points i <= js: d sample/d p_i = (SW / W_js) G dW_js/dp_i */
+      for (int i = 0; i <= js; ++i) {
+        if (!(pt[i].kap > 0) || !(pt[i].kb > 0)) continue;
+        double dW;
+        if (i == js) {
+          dW = 1.0;
+          for (int m = 0; m < js; ++m) dW *= 1.0 - p[m];
+        } else {
+          dW = -p[js];
+          for (int m = 0; m < js; ++m)
+            if (m != i) dW *= 1.0 - p[m];
+        }
+        double coef = dLdI * SW / W[js] * Gv * dW / pt[i].kb;
+        add_dkappa(f, G, h, nh, o, v, pt[i].t, coef, g15);
+      }
+      /* NEE points: d sample/d q_k = -SW E prod_{m != k} (1 - q_m) */
+      for (int k = 0; k < nq; ++k) {
+        if (!(ql[k].kap > 0) || !(ql[k].kb > 0)) continue;
+        double pr = 1.0;
+        for (int m = 0; m < nq; ++m)
+          if (m != k) pr *= 1.0 - q[m];
+        double coef = -dLdI * SW * E * pr / ql[k].kb;
+        add_dkappa(f, G, hl, nhl, x, l, ql[k].t, coef, g15);
+      }
+    }
+    free(q);
+    free(ql);
+    free(hl);
+  }
+  free(p);
+  free(W);
+  free(pt);
+  free(h);
+  return value;
+}
+
+static void soa_grad(const double* g15, int64_t N, double* grad) {
+  for (int64_t i = 0; i < N; ++i) {
+    for (int j = 0; j < 3; ++j) grad[3 * i + j] = g15[i * 15 + j];
+    for (int j = 0; j < 4; ++j) grad[3 * N + 4 * i + j] = g15[i * 15 + 3 + j];
+    for (int j = 0; j < 3; ++j) grad[7 * N + 3 * i + j] = g15[i * 15 + 7 + j];
+    for (int j = 0; j < 3; ++j) grad[10 * N + 3 * i + j] = g15[i * 15 + 10 + j];
+    grad[13 * N + i] = g15[i * 15 + 13];
+    grad[14 * N + i] = g15[i * 15 + 14];
+  }
+}
+
+void or_radiance_grad_rays(const or_field_desc* D, const or_lod* lod, const or_lod* lodn,
+                           const or_render_opts* ro, const double* o, const double* v_in,
+                           int64_t n_rays, int spp, uint64_t seed, const double* dLdI,
+                           double* value, double* grad, int n_threads) {
+  gl_init();
+  or_field* f = field_of(D);
+  int64_t N = D->n;
+  or_gprim* G = (or_gprim*)malloc(sizeof(or_gprim) * (size_t)(N > 0 ? N : 1));
+  for (int64_t i = 0; i < N; ++i) gprim_init(&G[i], D, i);
+  int nt = nthreads_of(n_threads);
+  (void)nt;
+  double* g15 = (double*)calloc((size_t)N * 15, sizeof(double));
+#pragma omp parallel num_threads(nt)
+  {
+    double* loc = (double*)calloc((size_t)N * 15, sizeof(double));
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t r = 0; r < n_rays; ++r) {
+      double v[3];
+      normalise(v_in + 3 * r, v);
+      double acc = 0;
+      for (int s = 0; s < spp; ++s)
+        acc += radiance_grad_sample(f, G, lod, lodn, ro, o + 3 * r, v, seed, (uint32_t)r,
+                                    (uint32_t)s, dLdI ? dLdI[r] / spp : 0.0, loc);
+      if (value) value[r] = acc / spp;
+    }
+#pragma omp critical
+    for (int64_t k = 0; k < N * 15; ++k) g15[k] += loc[k];
+    free(loc);
+  }
+  if (grad) soa_grad(g15, N, grad);
+  free(g15);
+  free(G);
+  or_field_free(f);
+}
+
+void or_radiance_grad_image(const or_field_desc* D, const or_lod* lod, const or_lod* lodn,
+                            const or_camera* C, const or_render_opts* ro, uint64_t seed,
+                            const double* dLdI, double* image, double* grad, int n_threads) {
+  gl_init();
+  or_field* f = field_of(D);
+  int64_t N = D->n;
+  or_gprim* G = (or_gprim*)malloc(sizeof(or_gprim) * (size_t)(N > 0 ? N : 1));
+  for (int64_t i = 0; i < N; ++i) gprim_init(&G[i], D, i);
+  int nt = nthreads_of(n_threads);
+  (void)nt;
+  int64_t npix = (int64_t)C->width * C->height;
+  double* g15 = (double*)calloc((size_t)N * 15, sizeof(double));
+#pragma omp parallel num_threads(nt)
+  {
+    double* loc = (double*)calloc((size_t)N * 15, sizeof(double));
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t pix = 0; pix < npix; ++pix) {
+      int px = (int)(pix % C->width), py = (int)(pix / C->width);
+      double acc = 0;
+      for (int s = 0; s < ro->spp; ++s) {
+        double o[3], v[3];
+        or_camera_ray(C, seed, px, py, s, o, v);
+        acc += radiance_grad_sample(f, G, lod, lodn, ro, o, v, seed, (uint32_t)pix, (uint32_t)s,
+                                    dLdI ? dLdI[pix] / ro->spp : 0.0, loc);
+      }
+      if (image) image[pix] = acc / ro->spp;
+    }
+#pragma omp critical
+    for (int64_t k = 0; k < N * 15; ++k) g15[k] += loc[k];
+    free(loc);
+  }
+  if (grad) soa_grad(g15, N, grad);
+  free(g15);
+  free(G);
+  or_field_free(f);
+}

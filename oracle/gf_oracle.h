@@ -139,6 +139,21 @@ void or_camera_ray(const or_camera* cam, uint64_t seed, int px, int py, int s, d
 double or_tomo_loss_grad(const or_field_desc* desc, const or_camera* cam, int spp, uint64_t seed,
                          const float* target, double* grad, int n_threads);
 /* tomography image only (same estimator, deterministic quadrature, all cells) */
+/* single-scattering radiance adjoint: expected-value estimator over all
+   tentative points of the ray, one NEE point drawn in proportion to its
+   weight; derivatives with the points, the majorant and the draw
+   probabilities held fixed (see the .c file).  Per ray (or pixel) the mean
+   of spp samples goes to value/image; grad (15 N, SoA as the inputs)
+   receives sum dLdI[r] / spp * d sample / d theta.  ro->max_bounces must be
+   1.  Rays: o, v double[3 n]. */
+void or_radiance_grad_rays(const or_field_desc* desc, const or_lod* lod, const or_lod* lod_nee,
+                           const or_render_opts* ro, const double* o, const double* v,
+                           int64_t n_rays, int spp, uint64_t seed, const double* dLdI,
+                           double* value, double* grad, int n_threads);
+void or_radiance_grad_image(const or_field_desc* desc, const or_lod* lod, const or_lod* lod_nee,
+                            const or_camera* cam, const or_render_opts* ro, uint64_t seed,
+                            const double* dLdI, double* image, double* grad, int n_threads);
+
 void or_tomo_image(const or_field_desc* desc, const or_camera* cam, int spp, uint64_t seed,
                    double* image, int n_threads);
 

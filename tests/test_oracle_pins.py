@@ -523,3 +523,76 @@ def test_tomography_gradient_matches_central_differences():
             assert abs(fd - an) <= 2e-3 * abs(an) + 1e-5 * np.max(np.abs(g)), (key, j, fd, an)
             checked += 1
     assert checked == 45
+
+
+# --------------------------------------------------------------------------- radiance gradient
+def _positive_field():
+    """A wide Gaussian under three small Gabor kernels, k = 6 (the cut lies where
+    the kernels are ~1e-8 of their peak), with kappa > 0 wherever a kernel is."""
+    p = {"mu": np.array([[0.5, 0.5, 0.5], [0.45, 0.52, 0.5], [0.55, 0.46, 0.55],
+                         [0.5, 0.5, 0.42]], np.float32),
+         "quat": np.array([[1, 0, 0, 0], [0.9, 0.1, 0.3, 0.2], [0.7, 0.1, 0, 0.6],
+                           [1, 0.3, 0, 0.1]], np.float32),
+         "log_scale": np.log(np.array([[0.3, 0.3, 0.3], [0.06, 0.05, 0.08], [0.07, 0.07, 0.05],
+                                       [0.05, 0.08, 0.06]])).astype(np.float32),
+         "omega": np.array([[0, 0, 0], [1.1, 1.1, 1.1], [0.8, 0.8, 0.8], [1.3, 1.3, 1.3]],
+                           np.float32),
+         "phase": np.array([0.0, 0.7, 2.0, 4.1], np.float32),
+         "weight": np.array([2.0, 0.3, 0.25, 0.3], np.float32)}
+    return p
+
+
+def _nested_radiance(p, o, v, albedo=0.8):
+    """albedo E/(4 pi) int kappa(t) exp(-tau(0,t)) T_light(x(t)) dt by the
+    trapezoid rule on a fine grid, T_light from the deterministic quadrature."""
+    f = oracle.Field(p, omega_frame="local", k_sigma=6.0)
+    grid = np.linspace(0.0, 3.6, 3601)
+    kap = np.array([f.density(o + t * v) for t in grid])
+    cum = np.concatenate([[0.0], np.cumsum(0.5 * (kap[1:] + kap[:-1]) * np.diff(grid))])
+    light = np.array([1.0, 1.0, -1.0]) / math.sqrt(3.0)
+    xs = o[None] + grid[:, None] * v[None]
+    Tl, _ = f.transmittance(xs.astype(np.float32), np.tile(light, (len(grid), 1)).astype(np.float32),
+                            None, mode="det")
+    return albedo / (4 * math.pi) * np.trapezoid(kap * np.exp(-cum) * Tl, grid), kap
+
+
+def test_radiance_estimator_mean_and_gradient_match_nested_quadrature():
+    """The single-scattering radiance adjoint's expected-value estimator has the
+    mean of the nested-quadrature radiance, and its gradient (points, majorant
+    and draw probabilities held fixed) the central finite differences of it."""
+    p = _positive_field()
+    o = np.array([0.5, 0.5, -1.0])
+    v = np.array([0.0, 0.03, 1.0])
+    v /= np.linalg.norm(v)
+    I_ref, kap = _nested_radiance(p, o, v)
+    assert kap.min() >= 0.0 and I_ref > 1e-3
+    f = oracle.Field(p, omega_frame="local", k_sigma=6.0)
+    ro = oracle.render_opts("scatter", 1, 1, 0.8)
+    vals, grads = [], []
+    for seed in range(12):
+        val, g = f.radiance_grad_rays(o[None], v[None], ro, 2000, seed, dLdI=np.ones(1))
+        vals.append(val[0])
+        grads.append(g)
+    vals = np.array(vals)
+    grads = np.array(grads)
+    se = vals.std(ddof=1) / math.sqrt(len(vals))
+    assert abs(vals.mean() - I_ref) < 4.5 * se + 1e-6, (vals.mean(), I_ref, se)
+    gm = grads.mean(0)
+    gse = grads.std(0, ddof=1) / math.sqrt(len(grads))
+    N = 4
+    offs = {"mu": 0, "quat": 3 * N, "log_scale": 7 * N, "omega": 10 * N, "phase": 13 * N,
+            "weight": 14 * N}
+    checks = [("mu", 0), ("log_scale", 1), ("weight", 0), ("mu", 4), ("quat", 4),
+              ("log_scale", 5), ("omega", 3), ("phase", 1), ("weight", 1), ("mu", 8),
+              ("phase", 2)]
+    for key, j in checks:
+        base = float(p[key].reshape(-1)[j])
+        h = 1e-3 * max(abs(base), 0.5)
+        pp = {k: v_.copy() for k, v_ in p.items()}
+        pm = {k: v_.copy() for k, v_ in p.items()}
+        pp[key].reshape(-1)[j] = np.float32(base + h)
+        pm[key].reshape(-1)[j] = np.float32(base - h)
+        step = float(pp[key].reshape(-1)[j]) - float(pm[key].reshape(-1)[j])
+        fd = (_nested_radiance(pp, o, v)[0] - _nested_radiance(pm, o, v)[0]) / step
+        an, s_ = gm[offs[key] + j], gse[offs[key] + j]
+        assert abs(an - fd) < 4.5 * s_ + 2e-3 * abs(fd) + 1e-6, (key, j, an, fd, s_)
