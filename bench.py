@@ -373,7 +373,7 @@ def run_ours(args, rank, world):
         "e2e": {"value": st_e2e["rays"] / e2e_s / 1e6, "unit": "Mrays/s",
                 "h2d_bytes_per_step": 4 * (ctypes.sizeof(_abi.gf_camera) + ctypes.sizeof(_abi.gf_render_opts)),
                 "d2h_bytes_per_step": 4 * RES * RES * 4},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": 2 * 4 * args.steps,  # k_render_scatter + k_fix_to_image per render
         "storage_ms_per_step": prec_ms,
         "clocks": clk,
     }
@@ -381,8 +381,8 @@ def run_ours(args, rank, world):
                                 for k in ("chords", "evals", "nodes", "points", "windows", "steps", "leaves")}
     if any(st["cycles"]):
         tot = max(1, sum(st["cycles"]))
-        line["phase_cycles_share"] = dict(zip(("traversal_steps", "leaf_rounds_pass1", "chord_walks",
-                                               "leaf_rounds_pass2", "decisions"),
+        line["phase_cycles_share"] = dict(zip(("traversal_steps", "leaf_rounds", "chord_walks",
+                                               "point_evaluation", "decisions"),
                                               (c / tot for c in st["cycles"])))
     if world == 1 and args.server_requests > 0:
         line["server"] = server_leg(api, ctx, args.server_requests)

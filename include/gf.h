@@ -201,12 +201,22 @@ gf_status gf_transmittance(gf_field* field, const float* o, const float* d, cons
 gf_status gf_render(gf_field* field, const gf_camera* camera, const gf_render_opts* opts,
                     uint64_t seed, float* out_image, gf_stream stream);
 
-/* Adjoint of the TOMO integrator with all cells: given dL/dI (float[W*H]),
-   accumulate dL/dparam into grad (float[15 N], SoA like gf_params: mu[3N],
-   quat[4N], log_scale[3N], omega[3N] in the input frame, phase[N],
-   weight[N]); grad is overwritten.  Per ray the chords are recomputed
-   (no stored paths); dtau/dtheta = integral of d(integrand)/dtheta plus the
-   Leibniz terms of the chord ends on the ellipsoid. */
+/* Adjoint of a rendered image: given dL/dI (float[W*H]), write dL/dparam to
+   grad (float[15 N], SoA like gf_params: mu[3N], quat[4N], log_scale[3N],
+   omega[3N] in the input frame, phase[N], weight[N]); grad is overwritten.
+   Nothing per path is stored: every ray is re-traced.  FP32 records only.
+   TOMO (all cells): dtau/dtheta = integral of d(integrand)/dtheta plus the
+   Leibniz terms of the chord ends on the ellipsoid (Eq. 2-3).
+   SCATTER with max_bounces = 1 (LoD masks as set by gf_set_lod_mask): per
+   sample, the expected-value form of delta tracking over all tentative
+   points of the camera ray, I = sum_j W_j G(t_j), W_j = prod_{i<j}(1 - p_i)
+   p_j, p = max(kappa,0)/kappa_bar, G = albedo E/(4 pi) T_light, with one
+   point drawn in proportion to W (weighted reservoir sampling on the
+   points' own uniforms) for its NEE ray; differentiated with the tentative
+   points, kappa_bar and the draw probabilities held fixed, so the gradient
+   is unbiased for the derivative of the expected image (the derivative of
+   the k-sigma cut itself is not included).  Use a seed other than the
+   forward render's so that the two estimates are independent. */
 gf_status gf_render_backward(gf_field* field, const gf_camera* camera,
                              const gf_render_opts* opts, uint64_t seed,
                              const float* dL_dimage, float* grad, gf_stream stream);

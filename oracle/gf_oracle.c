@@ -1117,8 +1117,11 @@ double or_tomo_loss_grad(const or_field_desc* D, const or_camera* C, int spp, ui
 /*   p_j = max(kappa_j, 0) / kappa_bar_j,  G = albedo E/(4 pi) T_light,       */
 /* because the points before t form a Poisson process independent of the    */
 /* point at t (Campbell's formula gives int T kappa+ G dt).  One point js is */
-/* drawn with probability W_j / sum W and its NEE transmittance is ratio     */
-/* tracked, so a sample is sum W * G(t_js).  The derivative is taken with    */
+/* drawn with probability W_j / sum W by weighted reservoir sampling in t    */
+/* order (point j replaces the candidate when u_j S_j < W_j, S_j the running */
+/* sum of W and u_j the point's own second uniform), and its NEE             */
+/* transmittance is ratio tracked, so a sample is sum W * G(t_js).  The      */
+/* derivative is taken with                                                 */
 /* the tentative points, kappa_bar and the draw probabilities held fixed    */
 /* (each keeps the estimator's mean equal to I for nearby parameters), so   */
 /* only kappa_j and the NEE kappa_k vary:                                   */
@@ -1130,7 +1133,7 @@ double or_tomo_loss_grad(const or_field_desc* D, const or_camera* C, int spp, ui
 /* is taken where it is smooth).                                            */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-  double t, kap, kb;
+  double t, ua, kap, kb;
 } or_rpt;
 
 static int cmp_rpt(const void* A, const void* B) {
@@ -1148,6 +1151,7 @@ static int ray_points(const or_field* f, const double o[3], const double v[3], u
   or_rpt* r = (or_rpt*)malloc(sizeof(or_rpt) * (size_t)(np > 0 ? np : 1));
   for (int j = 0; j < np; ++j) {
     r[j].t = pts[j].t;
+    r[j].ua = pts[j].ua;
     eval_point(f, *hits, nh, o, v, pts[j].t, &r[j].kap, &r[j].kb);
   }
   free(pts);
@@ -1204,16 +1208,15 @@ static double radiance_grad_sample(const or_field* f, const or_gprim* G, const o
     P *= 1.0 - p[j];
   }
   double value = 0.0;
-  if (SW > 0.0) {
-    uint32_t y[4];
-    rng4(seed, 0, OR_NO_PRIM, ray, stream_word(s, 0, OR_TAG_SCATTER), y);
-    double target = u01(y[2]) * SW, acc = 0.0;
-    int js = np - 1;
+  int js = -1;
+  {
+    double S = 0.0;
     for (int j = 0; j < np; ++j) {
-      acc += W[j];
-      if (target < acc && W[j] > 0.0) { js = j; break; }
+      S += W[j];
+      if (W[j] > 0.0 && pt[j].ua * S < W[j]) js = j;
     }
-    while (js > 0 && !(W[js] > 0.0)) --js;
+  }
+  if (SW > 0.0 && js >= 0) {
     double x[3] = {o[0] + pt[js].t * v[0], o[1] + pt[js].t * v[1], o[2] + pt[js].t * v[2]};
     /* NEE by ratio tracking from x_js */
     uint64_t nmask;

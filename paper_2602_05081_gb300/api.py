@@ -177,6 +177,38 @@ class TomoRender(torch.autograd.Function):
                 parts["weight"], None, None, None, None, None, None, None)
 
 
+class RadianceRender(torch.autograd.Function):
+    """I = single-scattering image of the field given by the parameter tensors.
+
+    Forward packs the field and renders with delta tracking (seed); backward runs
+    the radiance adjoint kernel with its own seed (grad_seed), so the image and
+    the gradient estimate are independent Monte Carlo estimates.
+    """
+
+    @staticmethod
+    def forward(ctx_, mu, quat, log_scale, omega, phase, weight, gctx, cam, spp, seed, grad_seed,
+                lod_primary, lod_nee, omega_frame, weight_mode, k_sigma, albedo=0.8,
+                light_dir=(1.0, 1.0, -1.0)):
+        params = {"mu": mu, "quat": quat, "log_scale": log_scale, "omega": omega, "phase": phase,
+                  "weight": weight}
+        f = Field(gctx, params, omega_frame=omega_frame, weight_mode=weight_mode, k_sigma=k_sigma)
+        f.set_lod(lod_primary, lod_nee)
+        opts = render_opts("scatter", spp=spp, max_bounces=1, albedo=albedo, light_dir=light_dir)
+        img = f.render(cam, opts, seed)
+        ctx_.field = f
+        ctx_.cam, ctx_.opts, ctx_.grad_seed = cam, opts, grad_seed
+        return img
+
+    @staticmethod
+    def backward(ctx_, g_img):
+        f = ctx_.field
+        g = f.render_backward(ctx_.cam, ctx_.opts, ctx_.grad_seed, g_img.contiguous())
+        parts = split_grad(g, f.n)
+        f.free()
+        return (parts["mu"], parts["quat"], parts["log_scale"], parts["omega"], parts["phase"],
+                parts["weight"]) + (None,) * 12
+
+
 class Server:
     """Continuous-batching render server over resident fields (gf_server_*)."""
 

@@ -26,6 +26,113 @@ struct BackArgs {
   float* grad;
 };
 
+// Derivatives of one kernel g = A exp(-q/2) cos(theta) with respect to its 15
+// raw parameters (mu 3, quaternion 4 through qhat = q/|q|, log scale 3, omega 3
+// in the input frame, phase, weight), at offsets y = x - mu.
+struct PrimDeriv {
+  float R[3][3];
+  float dR[4][3][3];  // dR/dq_m of the raw quaternion
+  float s[3], is2[3], kin[3];
+  float A, dAdw;
+  float3 om;
+  float phi;
+  bool local, normalized;
+
+  __device__ void init(const BackArgs& B, const Prim& P, int64_t i) {
+    float q[4];
+    for (int k = 0; k < 4; ++k) q[k] = B.quat[4 * i + k];
+    const float qn = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    const float qh[4] = {q[0] / qn, q[1] / qn, q[2] / qn, q[3] / qn};
+    const float qw = qh[0], qx = qh[1], qy = qh[2], qz = qh[3];
+    const float Rm[3][3] = {{1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy)},
+                            {2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx)},
+                            {2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)}};
+    // dR/d(qhat_l), l = w, x, y, z
+    const float dRh[4][3][3] = {
+        {{0.f, -2.f * qz, 2.f * qy}, {2.f * qz, 0.f, -2.f * qx}, {-2.f * qy, 2.f * qx, 0.f}},
+        {{0.f, 2.f * qy, 2.f * qz}, {2.f * qy, -4.f * qx, -2.f * qw}, {2.f * qz, 2.f * qw, -4.f * qx}},
+        {{-4.f * qy, 2.f * qx, 2.f * qw}, {2.f * qx, 0.f, 2.f * qz}, {-2.f * qw, 2.f * qz, -4.f * qy}},
+        {{-4.f * qz, -2.f * qw, 2.f * qx}, {2.f * qw, -4.f * qz, 2.f * qy}, {2.f * qx, 2.f * qy, 0.f}}};
+    for (int a = 0; a < 3; ++a)
+      for (int k = 0; k < 3; ++k) R[a][k] = Rm[a][k];
+    // d qhat_l / d q_m = (delta_lm - qhat_l qhat_m) / |q|
+    for (int m = 0; m < 4; ++m)
+      for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 3; ++k) {
+          float acc = 0.f;
+          for (int l = 0; l < 4; ++l) acc += dRh[l][a][k] * ((l == m ? 1.f : 0.f) - qh[l] * qh[m]);
+          dR[m][a][k] = acc / qn;
+        }
+    for (int k = 0; k < 3; ++k) {
+      s[k] = expf(B.ls[3 * i + k]);
+      is2[k] = 1.f / (s[k] * s[k]);
+      kin[k] = B.om[3 * i + k];
+    }
+    local = B.frame == GF_OMEGA_LOCAL;
+    normalized = B.wmode == GF_WEIGHT_NORMALIZED;
+    A = P.A;
+    dAdw = normalized ? A / B.w[i] : 1.f;
+    om = P.om;
+    phi = P.phi;
+  }
+
+  // value g at y; d[15] = dg/dparam; dq[10] = dq/dparam (mu, quaternion, log scale)
+  __device__ float at(const float y[3], float d[15], float dq[10]) const {
+    float z[3];
+    for (int k = 0; k < 3; ++k) z[k] = R[0][k] * y[0] + R[1][k] * y[1] + R[2][k] * y[2];
+    const float qq = z[0] * z[0] * is2[0] + z[1] * z[1] * is2[1] + z[2] * z[2] * is2[2];
+    const float env = expf(-0.5f * qq);
+    const float th = om.x * y[0] + om.y * y[1] + om.z * y[2] + phi;
+    float sn, cs;
+    sincosf(th, &sn, &cs);
+    float dth[15], dA[15];
+    for (int r = 0; r < 15; ++r) {
+      dth[r] = 0.f;
+      dA[r] = 0.f;
+    }
+    for (int a = 0; a < 3; ++a)
+      dq[a] = -2.f * (R[a][0] * z[0] * is2[0] + R[a][1] * z[1] * is2[1] + R[a][2] * z[2] * is2[2]);
+    dth[0] = -om.x;
+    dth[1] = -om.y;
+    dth[2] = -om.z;
+    for (int m = 0; m < 4; ++m) {
+      float dqm = 0.f, dthm = 0.f;
+      for (int k = 0; k < 3; ++k) {
+        const float dz = dR[m][0][k] * y[0] + dR[m][1][k] * y[1] + dR[m][2][k] * y[2];
+        dqm += 2.f * z[k] * dz * is2[k];
+        if (local) dthm += kin[k] / s[k] * dz;
+      }
+      dq[3 + m] = dqm;
+      dth[3 + m] = dthm;
+    }
+    for (int k = 0; k < 3; ++k) {
+      dq[7 + k] = -2.f * z[k] * z[k] * is2[k];
+      if (local) dth[7 + k] = -kin[k] * z[k] / s[k];
+      if (normalized) dA[7 + k] = -A;
+    }
+    for (int k = 0; k < 3; ++k) dth[10 + k] = local ? z[k] / s[k] : y[k];
+    dth[13] = 1.f;
+    dA[14] = dAdw;
+    for (int r = 0; r < 15; ++r) {
+      const float dqr = r < 10 ? dq[r] : 0.f;
+      d[r] = A * env * (-0.5f * dqr * cs - sn * dth[r]) + dA[r] * env * cs;
+    }
+    return A * env * cs;
+  }
+};
+
+__device__ __forceinline__ void add_grad(const BackArgs& B, int64_t i, const float acc[15],
+                                         float scale) {
+  const int64_t N = B.n;
+  float* g = B.grad;
+  for (int k = 0; k < 3; ++k) atomicAdd(g + 3 * i + k, scale * acc[k]);
+  for (int k = 0; k < 4; ++k) atomicAdd(g + 3 * N + 4 * i + k, scale * acc[3 + k]);
+  for (int k = 0; k < 3; ++k) atomicAdd(g + 7 * N + 3 * i + k, scale * acc[7 + k]);
+  for (int k = 0; k < 3; ++k) atomicAdd(g + 10 * N + 3 * i + k, scale * acc[10 + k]);
+  atomicAdd(g + 13 * N + i, scale * acc[13]);
+  atomicAdd(g + 14 * N + i, scale * acc[14]);
+}
+
 struct BackLeaf {
   const DevField* F;
   const BackArgs* B;
@@ -40,114 +147,41 @@ struct BackLeaf {
     Chord ch;
     if (!chord_setup(P, o, v, tmin, tmax, F->k2, ch)) return;
     const int64_t i = ch.orig;
-    // raw parameters of primitive i
-    float q[4];
-    for (int k = 0; k < 4; ++k) q[k] = B->quat[4 * i + k];
-    float qn = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-    float qw = q[0] / qn, qx = q[1] / qn, qy = q[2] / qn, qz = q[3] / qn;
-    float R[3][3] = {{1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy)},
-                     {2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx)},
-                     {2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)}};
-    // dR/d(qhat_m), m = w, x, y, z
-    float dRh[4][3][3] = {
-        {{0.f, -2.f * qz, 2.f * qy}, {2.f * qz, 0.f, -2.f * qx}, {-2.f * qy, 2.f * qx, 0.f}},
-        {{0.f, 2.f * qy, 2.f * qz}, {2.f * qy, -4.f * qx, -2.f * qw}, {2.f * qz, 2.f * qw, -4.f * qx}},
-        {{-4.f * qy, 2.f * qx, 2.f * qw}, {2.f * qx, 0.f, 2.f * qz}, {-2.f * qw, 2.f * qz, -4.f * qy}},
-        {{-4.f * qz, -2.f * qw, 2.f * qx}, {2.f * qw, -4.f * qz, 2.f * qy}, {2.f * qx, 2.f * qy, 0.f}}};
-    float qh[4] = {qw, qx, qy, qz};
-    float s[3], is2[3], kin[3];
-    for (int k = 0; k < 3; ++k) {
-      s[k] = expf(B->ls[3 * i + k]);
-      is2[k] = 1.f / (s[k] * s[k]);
-      kin[k] = B->om[3 * i + k];
-    }
-    const bool local = B->frame == GF_OMEGA_LOCAL;
-    const float A = P.A, wgt = B->w[i];
-    // dA/dweight
-    const float dAdw = B->wmode == GF_WEIGHT_NORMALIZED ? A / wgt : 1.f;
+    PrimDeriv D;
+    D.init(*B, P, i);
     float acc[15];
     for (int r = 0; r < 15; ++r) acc[r] = 0.f;
-    // per-point derivatives at offset y = p + dt v
-    auto point = [&](float dt, float wq, bool endpoint, float sgn) {
-      float y[3] = {fmaf(dt, v.x, ch.p.x), fmaf(dt, v.y, ch.p.y), fmaf(dt, v.z, ch.p.z)};
-      float z[3];
-      for (int k = 0; k < 3; ++k) z[k] = R[0][k] * y[0] + R[1][k] * y[1] + R[2][k] * y[2];
-      float qq = z[0] * z[0] * is2[0] + z[1] * z[1] * is2[1] + z[2] * z[2] * is2[2];
-      float env = expf(-0.5f * qq);
-      float th = P.om.x * y[0] + P.om.y * y[1] + P.om.z * y[2] + P.phi;
-      float sn, cs;
-      sincosf(th, &sn, &cs);
-      float dq[10], dth[15], dA[15];
-      for (int r = 0; r < 15; ++r) {
-        dth[r] = 0.f;
-        dA[r] = 0.f;
-      }
-      // mu
-      for (int a = 0; a < 3; ++a) {
-        dq[a] = -2.f * (R[a][0] * z[0] * is2[0] + R[a][1] * z[1] * is2[1] + R[a][2] * z[2] * is2[2]);
-      }
-      dth[0] = -P.om.x;
-      dth[1] = -P.om.y;
-      dth[2] = -P.om.z;
-      // quaternion (through qhat = q/|q|)
-      for (int m = 0; m < 4; ++m) {
-        float dqm = 0.f, dthm = 0.f;
-        for (int k = 0; k < 3; ++k) {
-          float dz = 0.f;
-          for (int a = 0; a < 3; ++a) {
-            float dR = 0.f;
-            for (int l = 0; l < 4; ++l) dR += dRh[l][a][k] * ((l == m ? 1.f : 0.f) - qh[l] * qh[m]);
-            dz += dR / qn * y[a];
-          }
-          dqm += 2.f * z[k] * dz * is2[k];
-          if (local) dthm += kin[k] / s[k] * dz;
-        }
-        dq[3 + m] = dqm;
-        dth[3 + m] = dthm;
-      }
-      // log scale
-      for (int k = 0; k < 3; ++k) {
-        dq[7 + k] = -2.f * z[k] * z[k] * is2[k];
-        if (local) dth[7 + k] = -kin[k] * z[k] / s[k];
-        if (B->wmode == GF_WEIGHT_NORMALIZED) dA[7 + k] = -A;
-      }
-      for (int k = 0; k < 3; ++k) dth[10 + k] = local ? z[k] / s[k] : y[k];
-      dth[13] = 1.f;
-      dA[14] = dAdw;
-      if (!endpoint) {
-        for (int r = 0; r < 15; ++r) {
-          float dqr = r < 10 ? dq[r] : 0.f;
-          acc[r] = fmaf(wq, A * env * (-0.5f * dqr * cs - sn * dth[r]) + dA[r] * env * cs, acc[r]);
-        }
-      } else {
-        float g = A * env * cs;
-        float dqdt = -(v.x * dq[0] + v.y * dq[1] + v.z * dq[2]);
-        if (dqdt != 0.f)
-          for (int r = 0; r < 10; ++r) acc[r] += sgn * g * (-dq[r] / dqdt);
-      }
-    };
-    float len = ch.dtout - ch.dtin;
-    float m = sqrtf(ch.a) * len + 0.5f * fabsf(ch.B) * len;
-    int rule = gl_rule(m);
+    const float len = ch.dtout - ch.dtin;
+    const float m = sqrtf(ch.a) * len + 0.5f * fabsf(ch.B) * len;
+    const int rule = gl_rule(m);
     int n = gl_n(0), off = 0;
     for (int r = 0; r <= rule; ++r) {
       n = gl_n(r);
       off = gl_off(r);
     }
-    float mid = 0.5f * (ch.dtin + ch.dtout), hl = 0.5f * len;
-    for (int k = 0; k < n; ++k) point(fmaf(hl, glx[off + k], mid), hl * glw[off + k], false, 0.f);
+    const float mid = 0.5f * (ch.dtin + ch.dtout), hl = 0.5f * len;
+    for (int k = 0; k < n; ++k) {
+      const float dt = fmaf(hl, glx[off + k], mid), wq = hl * glw[off + k];
+      const float y[3] = {fmaf(dt, v.x, ch.p.x), fmaf(dt, v.y, ch.p.y), fmaf(dt, v.z, ch.p.z)};
+      float d[15], dq[10];
+      D.at(y, d, dq);
+      for (int r = 0; r < 15; ++r) acc[r] = fmaf(wq, d[r], acc[r]);
+    }
     nev += (unsigned long long)n;
-    // Leibniz terms where a chord end lies on the ellipsoid (not on tmin/tmax)
-    if (ch.dts - ch.hw > tmin - ch.tc) point(ch.dtin, 0.f, true, -1.f);
-    if (ch.dts + ch.hw < tmax - ch.tc) point(ch.dtout, 0.f, true, 1.f);
-    const int64_t N = B->n;
-    float* g = B->grad;
-    for (int k = 0; k < 3; ++k) atomicAdd(g + 3 * i + k, dLdtau * acc[k]);
-    for (int k = 0; k < 4; ++k) atomicAdd(g + 3 * N + 4 * i + k, dLdtau * acc[3 + k]);
-    for (int k = 0; k < 3; ++k) atomicAdd(g + 7 * N + 3 * i + k, dLdtau * acc[7 + k]);
-    for (int k = 0; k < 3; ++k) atomicAdd(g + 10 * N + 3 * i + k, dLdtau * acc[10 + k]);
-    atomicAdd(g + 13 * N + i, dLdtau * acc[13]);
-    atomicAdd(g + 14 * N + i, dLdtau * acc[14]);
+    // Leibniz terms where a chord end lies on the ellipsoid (not on tmin/tmax):
+    // the end moves as dt/dtheta = -(dq/dtheta)/(dq/dt)
+    const bool on_in = ch.dts - ch.hw > tmin - ch.tc, on_out = ch.dts + ch.hw < tmax - ch.tc;
+    for (int e = 0; e < 2; ++e) {
+      if (e == 0 ? !on_in : !on_out) continue;
+      const float dt = e == 0 ? ch.dtin : ch.dtout, sgn = e == 0 ? -1.f : 1.f;
+      const float y[3] = {fmaf(dt, v.x, ch.p.x), fmaf(dt, v.y, ch.p.y), fmaf(dt, v.z, ch.p.z)};
+      float d[15], dq[10];
+      const float g = D.at(y, d, dq);
+      const float dqdt = -(v.x * dq[0] + v.y * dq[1] + v.z * dq[2]);
+      if (dqdt != 0.f)
+        for (int r = 0; r < 10; ++r) acc[r] += sgn * g * (-dq[r] / dqdt);
+    }
+    add_grad(*B, i, acc, dLdtau);
   }
 };
 
@@ -232,6 +266,282 @@ cudaError_t launch_tomo_backward(const Field& F, const PathParams& P, const floa
   int64_t g = (int64_t)F.ctx.sm_count * per_sm;
   if (need < g) g = need;
   k_tomo_backward<<<(unsigned)(g < 1 ? 1 : g), kBackBlock, 0, s>>>(F.dev, P, B, dLdI, F.counter);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of the single-scattering radiance.
+//
+// Per camera sample, the expected-value form of delta tracking over all
+// tentative points t_j of the camera ray (Poisson process of rate kappa_bar):
+//   I = sum_j W_j G(t_j),   W_j = prod_{i<j} (1 - p_i) p_j,   p = kappa+/kappa_bar,
+// has the mean of the delta-tracking estimator (Sec. 3, Eq. 4 majorants; the
+// points before t form a Poisson process independent of the point at t).  One
+// point js is drawn with probability W_j / sum W by weighted reservoir
+// sampling in t order (point j replaces the candidate when u_j S_j < W_j, u_j
+// its own second uniform, S_j the running sum), and G(t_js) = albedo E/(4 pi)
+// T_light comes from ratio tracking of the NEE ray, so a sample is S G.  The
+// derivative holds the points, kappa_bar and the draw probabilities fixed:
+//   d/d p_i = S G / (1 - p_i) * (-1)  (i < js),   S G / p_js  (i = js),
+//   d/d q_k = -S albedo E/(4 pi) T_light / (1 - q_k)   (NEE points),
+// and d p / d theta = 1[kappa > 0] d kappa/d theta / kappa_bar, where
+// d kappa/d theta sums the mask-weighted derivatives of the kernels covering
+// the point.  Each ray is re-tracked (same Philox streams, same windows) for
+// the derivative passes: nothing per path is stored.
+// ---------------------------------------------------------------------------
+
+// Windows of kPts tentative points, in t order, with kappa and kappa_bar
+// (the windows of track()); win(B, n, kap, kb) returns false to stop.
+template <class Win>
+__device__ void for_windows(const DevField& F, const Mask& M, float3 o, float3 v, uint64_t seed,
+                            uint32_t ray, uint32_t word, const float* env, Counters& cnt,
+                            Win win) {
+  const unsigned am = __activemask();
+  const float3 inv = safe_inv(v);
+  float t0 = 0.f, t1 = 0.f;
+  bool more = M.bits != 0ull && scene_span(F, o, inv, 0.f, INFINITY, t0, t1);
+  float ta = t0;
+  bool first = true;
+  for (int guard = 0; guard < (1 << 16); ++guard) {
+    if (!__any_sync(am, more)) break;
+    if (!more) continue;
+    PointBuf B;
+#pragma unroll
+    for (int i = 0; i < kPts; ++i) {
+      B.t[i] = INFINITY;
+      B.u[i] = 0.f;
+    }
+    CollectLeaf cl;
+    cl.F = &F;
+    cl.M = &M;
+    cl.o = o;
+    cl.v = v;
+    cl.tmin = 0.f;
+    cl.tmax = INFINITY;
+    cl.ta = ta;
+    cl.first = first;
+    cl.bound = t1;
+    cl.B = &B;
+    cl.seed = seed;
+    cl.ray = ray;
+    cl.word = word;
+    cl.env = env;
+    CollectTest ctest{&cl.ta, &cl.bound};
+    traverse_ray(F, o, inv, M.bits, ctest, cl, cnt.nodes, cnt.leaves);
+    int n = 0;
+#pragma unroll
+    for (int i = 0; i < kPts; ++i) n += B.t[i] < INFINITY ? 1 : 0;
+    if (n == 0) {
+      more = false;
+      continue;
+    }
+    AccumLeaf al;
+    al.F = &F;
+    al.M = &M;
+    al.o = o;
+    al.v = v;
+    al.tmin = 0.f;
+    al.tmax = INFINITY;
+    al.B = &B;
+    al.n = n;
+    al.env = env;
+#pragma unroll
+    for (int i = 0; i < kPts; ++i) {
+      al.kap[i] = 0.f;
+      al.kb[i] = 0.f;
+    }
+    PointTest ptest{&B, n};
+    traverse_ray(F, o, inv, M.bits, ptest, al, cnt.nodes, cnt.leaves);
+    cnt.evals += al.nev;
+    if (!win(B, n, al.kap, al.kb) || n < kPts) {
+      more = false;
+      continue;
+    }
+    ta = B.t[kPts - 1];
+    first = false;
+  }
+}
+
+// coef_i * d kappa(x(t_i)) / d theta, scattered over the kernels at the points
+struct RadScatter {
+  const DevField* F;
+  const BackArgs* B;
+  const Mask* M;
+  float3 o, v;
+  const PointBuf* P;
+  const float* coef;
+  int n;
+  __device__ void operator()(int j) {
+    const Prim Pr = load_prim(*F, j);
+    Chord ch;
+    if (!chord_setup(Pr, o, v, 0.f, INFINITY, F->k2, ch)) return;
+    const float w = mask_weight(*M, ch.cell);
+    if (w == 0.f) return;
+    const float tin = ch.tc + ch.dtin, tout = ch.tc + ch.dtout;
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < kPts; ++i)
+      any |= i < n && coef[i] != 0.f && P->t[i] >= tin && P->t[i] <= tout;
+    if (!any) return;
+    PrimDeriv D;
+    D.init(*B, Pr, ch.orig);
+    float acc[15];
+    for (int r = 0; r < 15; ++r) acc[r] = 0.f;
+    for (int i = 0; i < n; ++i) {
+      const float t = P->t[i];
+      if (coef[i] == 0.f || t < tin || t > tout) continue;
+      const float dt = t - ch.tc;
+      const float y[3] = {fmaf(dt, v.x, ch.p.x), fmaf(dt, v.y, ch.p.y), fmaf(dt, v.z, ch.p.z)};
+      float d[15], dq[10];
+      D.at(y, d, dq);
+      for (int r = 0; r < 15; ++r) acc[r] = fmaf(coef[i], d[r], acc[r]);
+    }
+    add_grad(*B, ch.orig, acc, w);
+  }
+};
+
+__device__ __forceinline__ void scatter_window(const DevField& F, const BackArgs& Bk, const Mask& M,
+                                               float3 o, float3 v, const PointBuf& P,
+                                               const float* coef, int n, Counters& cnt) {
+  bool any = false;
+#pragma unroll
+  for (int i = 0; i < kPts; ++i) any |= i < n && coef[i] != 0.f;
+  if (!any) return;
+  RadScatter rs{&F, &Bk, &M, o, v, &P, coef, n};
+  PointTest ptest{&P, n};
+  traverse_ray(F, o, safe_inv(v), M.bits, ptest, rs, cnt.nodes, cnt.leaves);
+}
+
+struct RadSmem {
+  float env[8];
+};
+
+__global__ void __launch_bounds__(kBackBlock)
+    k_radiance_backward(const __grid_constant__ DevField F, const PathParams P, const BackArgs Bk,
+                        const float* dLdI, int* counter) {
+  __shared__ RadSmem sm;
+  if (threadIdx.x < 8) sm.env[threadIdx.x] = F.env[threadIdx.x];
+  __syncthreads();
+  const uint32_t lane = threadIdx.x & 31u;
+  Counters cnt;
+  const float E = P.albedo * P.irradiance * (0.25f / 3.14159265358979f);
+  const int tiles_x = (P.cam.W + 7) / 8, tiles_y = (P.cam.H + 3) / 4;
+  for (;;) {
+    int tile = 0;
+    if (lane == 0) tile = atomicAdd(counter, 1);
+    tile = __shfl_sync(kFull, tile, 0);
+    if (tile >= tiles_x * tiles_y) break;
+    const int px = (tile % tiles_x) * 8 + (int)(lane % 8);
+    const int py = (tile / tiles_x) * 4 + (int)(lane / 8);
+    if (px >= P.cam.W || py >= P.cam.H) continue;  // every lane returns to the tile fetch
+    const uint32_t pix = (uint32_t)(py * P.cam.W + px);
+    const float gI = dLdI[pix];
+    if (gI == 0.f) continue;
+    const float base = gI / (float)P.spp;
+    for (int s = 0; s < P.spp; ++s) {
+      float3 o, v;
+      camera_ray(P.cam, P.seed, px, py, s, o, v);
+      cnt.rays += 1;
+      const Mask M = sample_mask(F, P.lod, v, P.seed, pix, (uint32_t)s, 0, TAG_MASK);
+      const uint32_t wt = stream_word((uint32_t)s, 0, TAG_TRACK);
+      // pass 1: weights, their sum and the reservoir draw
+      float Pr = 1.f, S = 0.f, pjs = 0.f, tjs = 0.f;
+      int idx = 0, js = -1;
+      for_windows(F, M, o, v, P.seed, pix, wt, sm.env, cnt,
+                  [&](const PointBuf& B, int n, const float* kap, const float* kb) {
+                    for (int i = 0; i < n; ++i) {
+                      const float p = kb[i] > 0.f ? fmaxf(kap[i], 0.f) / kb[i] : 0.f;
+                      const float W = Pr * p;
+                      S += W;
+                      if (W > 0.f && B.u[i] * S < W) {
+                        js = idx + i;
+                        pjs = p;
+                        tjs = B.t[i];
+                      }
+                      Pr *= 1.f - p;
+                    }
+                    idx += n;
+                    return true;
+                  });
+      if (js < 0 || !(S > 0.f)) continue;
+      // NEE from the drawn point by ratio tracking
+      const float3 x = make_float3(fmaf(tjs, v.x, o.x), fmaf(tjs, v.y, o.y), fmaf(tjs, v.z, o.z));
+      const Mask Mn = sample_mask(F, P.lod_nee, P.light, P.seed, pix, (uint32_t)s, 0, TAG_NEE_MASK);
+      const uint32_t wn = stream_word((uint32_t)s, 0, TAG_NEE);
+      cnt.rays += 1;
+      const float Tl = track<false>(F, Mn, x, P.light, 0.f, INFINITY, true, P.seed, pix, wn,
+                                    sm.env, cnt, nullptr);
+      const float G = E * Tl;
+      // pass 2: camera points 0..js
+      idx = 0;
+      for_windows(F, M, o, v, P.seed, pix, wt, sm.env, cnt,
+                  [&](const PointBuf& B, int n, const float* kap, const float* kb) {
+                    float coef[kPts];
+#pragma unroll
+                    for (int i = 0; i < kPts; ++i) {
+                      coef[i] = 0.f;
+                      const int gi = idx + i;
+                      if (i < n && gi <= js && kap[i] > 0.f && kb[i] > 0.f) {
+                        const float p = kap[i] / kb[i];
+                        const float c = gi == js ? S * G / pjs : -S * G / (1.f - p);
+                        coef[i] = base * c / kb[i];
+                      }
+                    }
+                    scatter_window(F, Bk, M, o, v, B, coef, n, cnt);
+                    idx += n;
+                    return idx <= js;
+                  });
+      // pass 3: NEE points
+      if (Tl > 0.f) {
+        for_windows(F, Mn, x, P.light, P.seed, pix, wn, sm.env, cnt,
+                    [&](const PointBuf& B, int n, const float* kap, const float* kb) {
+                      float coef[kPts];
+#pragma unroll
+                      for (int i = 0; i < kPts; ++i) {
+                        coef[i] = 0.f;
+                        if (i < n && kap[i] > 0.f && kb[i] > 0.f) {
+                          const float q = kap[i] / kb[i];
+                          if (1.f - q > 0.f) coef[i] = -base * S * E * Tl / (1.f - q) / kb[i];
+                        }
+                      }
+                      scatter_window(F, Bk, Mn, x, P.light, B, coef, n, cnt);
+                      return true;
+                    });
+      }
+    }
+  }
+  flush_counters(F, cnt, lane);
+}
+
+static BackArgs back_args(const Field& F, float* grad) {
+  BackArgs B;
+  B.quat = F.p_quat;
+  B.ls = F.p_ls;
+  B.om = F.p_om;
+  B.w = F.p_w;
+  B.frame = F.opts.omega_frame;
+  B.wmode = F.opts.weight_mode;
+  B.n = F.n;
+  B.grad = grad;
+  return B;
+}
+
+cudaError_t launch_radiance_backward(const Field& F, const PathParams& P, const float* dLdI,
+                                     float* grad, cudaStream_t s) {
+  (void)cudaGetLastError();  // a stale error of an unrelated call is not ours
+  cudaError_t e = cudaMemsetAsync(F.counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  const BackArgs B = back_args(F, grad);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_radiance_backward, kBackBlock, 0) !=
+      cudaSuccess)
+    (void)cudaGetLastError();
+  if (per_sm < 1) per_sm = 1;
+  const int64_t tiles = (int64_t)((P.cam.W + 7) / 8) * ((P.cam.H + 3) / 4);
+  const int64_t need = (tiles + kBackBlock / 32 - 1) / (kBackBlock / 32);
+  int64_t g = (int64_t)F.ctx.sm_count * per_sm;
+  if (need < g) g = need;
+  k_radiance_backward<<<(unsigned)(g < 1 ? 1 : g), kBackBlock, 0, s>>>(F.dev, P, B, dLdI, F.counter);
   return cudaGetLastError();
 }
 

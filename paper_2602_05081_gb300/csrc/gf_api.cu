@@ -168,7 +168,7 @@ namespace {
 void free_field(Field& F) {
   void* ptrs[] = {F.p_mu, F.p_quat, F.p_ls, F.p_om, F.p_ph, F.p_w, F.rec_orig, F.box_orig,
                   F.kw_orig, F.rec, F.rec16, F.nodes, F.nodes4, F.sorted_orig, F.labels, F.err,
-                  F.stats, F.counter, F.cell_acc, F.stage, F.wscratch, F.gl};
+                  F.stats, F.counter, F.cell_acc, F.stage, F.wscratch, F.acc64, F.gl};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -462,8 +462,8 @@ gf_status gf_render_backward(gf_field* h, const gf_camera* camera, const gf_rend
   PathParams P;
   gf_status st = camera_params(camera, opts, seed, F, P);
   if (st) return st;
-  if (opts->integrator != GF_INTEG_TOMO)
-    return fail(GF_EINVAL, "the adjoint covers the tomography integrator");
+  if (opts->integrator == GF_INTEG_SCATTER && opts->max_bounces != 1)
+    return fail(GF_EINVAL, "the radiance adjoint covers single scattering (max_bounces 1)");
   if (F.opts.precision != GF_PREC_FP32)
     return fail(GF_EINVAL, "the adjoint needs FP32 records");
   GF_CUDA(cudaSetDevice(F.ctx.device), "cudaSetDevice");
@@ -477,7 +477,10 @@ gf_status gf_render_backward(gf_field* h, const gf_camera* camera, const gf_rend
       (st = stage(F, grad, gbytes, false, s, off, &gd)))
     return st;
   GF_CUDA(cudaMemsetAsync(gd, 0, gbytes, s), "zero grad");
-  GF_CUDA(launch_tomo_backward(F, P, (const float*)dl, (float*)gd, s), "backward launch");
+  if (opts->integrator == GF_INTEG_TOMO)
+    GF_CUDA(launch_tomo_backward(F, P, (const float*)dl, (float*)gd, s), "backward launch");
+  else
+    GF_CUDA(launch_radiance_backward(F, P, (const float*)dl, (float*)gd, s), "backward launch");
   if (gd != grad) {
     GF_CUDA(cudaMemcpyAsync(grad, gd, gbytes, cudaMemcpyDeviceToHost, s), "copy grad");
     GF_CUDA(cudaStreamSynchronize(s), "sync");

@@ -80,6 +80,9 @@ struct Field {
   // per-warp chord store of the scattering renderer (grows on demand)
   mutable float4* wscratch = nullptr;
   mutable size_t wscratch_bytes = 0;
+  // fixed-point pixel sums of the scattering renderer (grows on demand)
+  mutable unsigned long long* acc64 = nullptr;
+  mutable size_t acc_bytes = 0;
 };
 
 // Render server batch (one launch of k_render_server): items of many requests
@@ -118,6 +121,8 @@ size_t scatter_store_bytes(int64_t grid);
 cudaError_t server_grid(int sm_count, int64_t& grid);
 cudaError_t launch_render_server(const ServerLaunch& L, int64_t grid, float4* chord_store,
                                  cudaStream_t s);
+cudaError_t launch_radiance_backward(const Field& F, const PathParams& P, const float* dLdI,
+                                     float* grad, cudaStream_t s);
 cudaError_t launch_tomo_backward(const Field& F, const PathParams& P, const float* dLdI,
                                  float* grad, cudaStream_t s);
 

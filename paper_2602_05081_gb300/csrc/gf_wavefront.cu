@@ -84,6 +84,11 @@ __device__ __forceinline__ float ray_weight(const LaneRay& R, uint32_t cell) {
   return R.bw[b];
 }
 
+// byte k of x as a float, exactly: 0x4B0000xx is 2^23 + xx
+__device__ __forceinline__ float byte_float(uint32_t x, int k) {
+  return __int_as_float((int)__byte_perm(x, 0x4Bu, (uint32_t)k | 0x4550u)) - 8388608.0f;
+}
+
 __device__ __forceinline__ uint64_t slot_seed(const LaneRay& R) {
   return (uint64_t)R.seed_lo | ((uint64_t)R.seed_hi << 32);
 }
@@ -199,6 +204,9 @@ __device__ void warp_phase(const Work& Wk, WarpQ& Q, bool want, uint32_t lane, c
       const uint4 m01 = __ldg(&N->m01), m23 = __ldg(&N->m23);
       ++cnt.nodes;
       const uint32_t qlx = __float_as_uint(v1.z), qly = __float_as_uint(v1.w);
+      // slab distances straight from the codes: t = (lo + c s - o) inv = c (s inv) + (lo - o) inv
+      const float ax = v0.w * inv.x, ay = v1.x * inv.y, az = v1.y * inv.z;
+      const float bx = (v0.x - o.x) * inv.x, by = (v0.y - o.y) * inv.y, bz = (v0.z - o.z) * inv.z;
       const unsigned long long mk[4] = {
           (unsigned long long)m01.x | ((unsigned long long)m01.y << 32),
           (unsigned long long)m01.z | ((unsigned long long)m01.w << 32),
@@ -210,52 +218,37 @@ __device__ void warp_phase(const Work& Wk, WarpQ& Q, bool want, uint32_t lane, c
       ch[3] = c4.w;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const int sh = 8 * k;
-        const float x0 = fmaf((float)((qlx >> sh) & 255u), v0.w, v0.x);
-        const float y0 = fmaf((float)((qly >> sh) & 255u), v1.x, v0.y);
-        const float z0 = fmaf((float)((q.x >> sh) & 255u), v1.y, v0.z);
-        const float x1 = fmaf((float)((q.y >> sh) & 255u), v0.w, v0.x);
-        const float y1 = fmaf((float)((q.z >> sh) & 255u), v1.x, v0.y);
-        const float z1 = fmaf((float)((q.w >> sh) & 255u), v1.y, v0.z);
-        float tn, tf;
-        slab_interval(o, inv, x0, y0, z0, x1, y1, z1, tn, tf);
-        if ((mk[k] & mask) && fmaxf(tn, R.ta) <= fminf(tf, R.te)) hit |= 1u << k;
+        const float tx0 = fmaf(byte_float(qlx, k), ax, bx), tx1 = fmaf(byte_float(q.y, k), ax, bx);
+        const float ty0 = fmaf(byte_float(qly, k), ay, by), ty1 = fmaf(byte_float(q.z, k), ay, by);
+        const float tz0 = fmaf(byte_float(q.x, k), az, bz), tz1 = fmaf(byte_float(q.w, k), az, bz);
+        const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), R.ta));
+        const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), R.te));
+        if ((mk[k] & mask) && tn <= tf) hit |= 1u << k;
       }
     }
-    // ---------------- push internal children, queue leaves (one warp scan)
+    // ---------------- push internal children, queue leaves: per child slot k a
+    // ballot places the lanes' entries contiguously (no bank conflicts)
     {
       int np = 0, nl = 0;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        if (hit >> k & 1u) {
-          if (ch[k] >= 0) ++np;
-          else ++nl;
+        const bool h = (hit >> k & 1u) != 0u;
+        const unsigned bp = __ballot_sync(kFull, h && ch[k] >= 0);
+        const unsigned bl = __ballot_sync(kFull, h && ch[k] < 0);
+        if (h && ch[k] >= 0) {
+          const int pos = sp + np + __popc(bp & lt);
+          if (pos < kWStack) Q.stk[pos] = (ch[k] << 5) | slot;
         }
+        if (h && ch[k] < 0) Q.lq[lq_n + nl + __popc(bl & lt)] = (~ch[k] << 5) | slot;
+        np += __popc(bp);
+        nl += __popc(bl);
       }
-      int inc = np | (nl << 16);
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, inc, o);
-        if ((int)lane >= o) inc += y;
+      if (sp + np > kWStack) {
+        if (lane == 0) set_err(Wk.err_field(), ERR_STACK);
+        np = kWStack - sp;
       }
-      const int tot = __shfl_sync(kFull, inc, 31);
-      const int tp = tot & 0xFFFF, tl = tot >> 16;
-      int pp = sp + (inc & 0xFFFF) - np;
-      int pl = lq_n + (inc >> 16) - nl;
-      const bool room = sp + tp <= kWStack;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (hit >> k & 1u) {
-          if (ch[k] >= 0) {
-            if (room) Q.stk[pp++] = (ch[k] << 5) | slot;
-          } else {
-            Q.lq[pl++] = (~ch[k] << 5) | slot;
-          }
-        }
-      }
-      if (room) sp += tp;
-      else if (lane == 0) set_err(Wk.err_field(), ERR_STACK);
-      lq_n += tl;
+      sp += np;
+      lq_n += nl;
       __syncwarp();
     }
     const bool any_trav = sp > 0;
@@ -348,8 +341,10 @@ struct PathState {
   int rq;         // request of the pixel (0 for a single render)
   int pix;        // -1: no pixel
   int s, b;       // sample, bounce
+  int s_end;      // end of the lane's sample range of the pixel
   int kind;       // 0 idle, 1 delta tracking, 2 ratio tracking (NEE)
-  float acc, Lsum, thr, T;
+  long long acc;  // sum of the range's samples in fixed point (2^-32 units)
+  float Lsum, thr, T;
   float3 o, v;    // current ray
   float t0, t1;   // scene span of the current ray
   float step;     // window length for delta tracking
@@ -454,23 +449,40 @@ __device__ void eval_stored(WarpQ& Q, const float4* wch, const float* env, uint3
 // a field.  A single render is one request on one field; the render server
 // hands the kernel a batch of items from many requests on several fields.
 // ---------------------------------------------------------------------------
+// Radiance samples are summed in 64-bit fixed point (2^-32 units): a pixel's
+// value then does not depend on how its samples were split between lanes or
+// in which order the partial sums arrived.
+constexpr float kFixScale = 4294967296.0f;  // 2^32
+__device__ __forceinline__ long long fix_sample(float L) { return __float2ll_rn(L * kFixScale); }
+__device__ __forceinline__ float fix_mean(long long sum, int spp) {
+  return __ll2float_rn(sum) * (1.0f / kFixScale) / (float)spp;
+}
+
+// A single render: units of `chunk` consecutive samples of one pixel, so the
+// lanes stay busy to the end of the launch; partial sums meet in acc64.
 struct ImageWork {
   const DevField* F;
   const PathParams* P;
-  float* out;
+  unsigned long long* acc64;
   int* counter;
-  int npix;
+  int npix, chunk, nchunk;
   __device__ const DevField& field(int) const { return *F; }
   __device__ const DevField& err_field() const { return *F; }
   __device__ int64_t max_n() const { return F->n; }
   __device__ const PathParams& params(int) const { return *P; }
   __device__ int asset(int) const { return 0; }
-  __device__ bool next(int& rq, int& pix) const {
-    pix = atomicAdd(counter, 1);
+  __device__ bool next(int& rq, int& pix, int& s0, int& s1) const {
+    const int u = atomicAdd(counter, 1);
     rq = 0;
-    return pix < npix;
+    if (u >= npix * nchunk) return false;
+    pix = u / nchunk;
+    s0 = (u - pix * nchunk) * chunk;
+    s1 = min(s0 + chunk, P->spp);
+    return true;
   }
-  __device__ void write(int, int pix, float v) const { out[pix] = v; }
+  __device__ void finish(int, int pix, long long acc) const {
+    atomicAdd(acc64 + pix, (unsigned long long)acc);
+  }
 };
 
 struct ServerWork {
@@ -482,7 +494,7 @@ struct ServerWork {
   __device__ int asset(int rq) const { return L->reqs[rq].asset; }
   // the batch's pixels are numbered 0..total-1 item after item; a lane takes
   // the next number and finds its item by binary search over the item bases
-  __device__ bool next(int& rq, int& pix) const {
+  __device__ bool next(int& rq, int& pix, int& s0, int& s1) const {
     const int f = atomicAdd(L->counter, 1);
     if (f >= L->total) return false;
     int lo = 0, hi = L->n_items - 1;
@@ -494,9 +506,14 @@ struct ServerWork {
     const ServerItem it = L->items[lo];
     rq = it.req;
     pix = it.pix0 + (f - it.base);
+    s0 = 0;
+    s1 = L->reqs[rq].P.spp;
     return true;
   }
-  __device__ void write(int rq, int pix, float v) const { L->reqs[rq].fb[pix] = v; }
+  // a lane renders all samples of a pixel
+  __device__ void finish(int rq, int pix, long long acc) const {
+    L->reqs[rq].fb[pix] = fix_mean(acc, L->reqs[rq].P.spp);
+  }
 };
 
 // The paths of one warp: each lane runs its pixels' samples in order (camera
@@ -514,14 +531,14 @@ __device__ __forceinline__ void render_paths(const Work& Wk, const float* env, W
   S.rq = 0;
   S.pix = -1;
   S.kind = 0;
-  S.acc = 0.f;
+  S.acc = 0;
 
   // begin the next sample of the lane's pixel (or the next pixel); kind = 0 if none left
   auto begin_sample = [&]() {
     for (;;) {
       if (S.pix < 0) {
-        int rq = 0, pix = -1;
-        if (!Wk.next(rq, pix)) {
+        int rq = 0, pix = -1, s0 = 0, s1 = 0;
+        if (!Wk.next(rq, pix, s0, s1)) {
           S.pix = -1;
           S.kind = 0;
           return;
@@ -529,15 +546,16 @@ __device__ __forceinline__ void render_paths(const Work& Wk, const float* env, W
         const PathParams& P = Wk.params(rq);
         S.rq = rq;
         S.pix = pix;
-        S.s = 0;
-        S.acc = 0.f;
+        S.s = s0;
+        S.s_end = s1;
+        S.acc = 0;
         R.asset = Wk.asset(rq);
         R.seed_lo = (uint32_t)P.seed;
         R.seed_hi = (uint32_t)(P.seed >> 32);
       }
       const PathParams& P = Wk.params(S.rq);
-      if (S.s >= P.spp) {
-        Wk.write(S.rq, S.pix, S.acc / (float)P.spp);
+      if (S.s >= S.s_end) {
+        Wk.finish(S.rq, S.pix, S.acc);
         S.pix = -1;
         continue;
       }
@@ -564,7 +582,7 @@ __device__ __forceinline__ void render_paths(const Work& Wk, const float* env, W
     for (;;) {
       if (S.kind == 1) {
         if (!hit) {
-          S.acc += S.Lsum;
+          S.acc += fix_sample(S.Lsum);
           S.s += 1;
           begin_sample();
           return;
@@ -592,7 +610,7 @@ __device__ __forceinline__ void render_paths(const Work& Wk, const float* env, W
       const float3 nv = make_float3(rr * cs, rr * sn, z);
       S.b += 1;
       if (S.b >= P.max_bounces) {
-        S.acc += S.Lsum;
+        S.acc += fix_sample(S.Lsum);
         S.s += 1;
         begin_sample();
         return;
@@ -646,7 +664,9 @@ __device__ __forceinline__ void render_paths(const Work& Wk, const float* env, W
     cnt.windows += want ? 1ull : 0ull;
     __syncwarp();
     // ---- kappa and kappa_bar at the points, from the stored chords
+    GF_TIC(t_eval);
     if (__any_sync(kFull, want && n > 0)) eval_stored(Q, wch, env, lane, cnt);
+    if (lane == 0) GF_TOC(cnt, 3, t_eval);
     // ---- decisions
     GF_TIC(t_dec);
     if (want) {
@@ -712,11 +732,16 @@ __device__ __forceinline__ float4* warp_store(float4* chord_store) {
 
 __global__ void __launch_bounds__(kWWarps * 32, 4)
     k_render_scatter(const __grid_constant__ DevField F, const __grid_constant__ PathParams P,
-                     float* out, int* counter, float4* chord_store) {
+                     unsigned long long* acc64, int* counter, int chunk, float4* chord_store) {
   extern __shared__ __align__(16) unsigned char smraw[];
   WarpQ& Q = setup_block(smraw, F.env);
-  const ImageWork Wk{&F, &P, out, counter, P.cam.W * P.cam.H};
+  const ImageWork Wk{&F, &P, acc64, counter, P.cam.W * P.cam.H, chunk, (P.spp + chunk - 1) / chunk};
   render_paths(Wk, reinterpret_cast<const float*>(smraw), Q, warp_store(chord_store));
+}
+
+__global__ void k_fix_to_image(const unsigned long long* acc64, int64_t npix, int spp, float* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < npix) out[i] = fix_mean((long long)acc64[i], spp);
 }
 
 __global__ void __launch_bounds__(kWWarps * 32, 4)
@@ -756,9 +781,24 @@ cudaError_t launch_render_scatter(const Field& F, const PathParams& P, float* ou
   (void)cudaGetLastError();  // a stale error of an unrelated call is not ours
   cudaError_t e = cudaMemsetAsync(F.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
+  const int64_t npix = (int64_t)P.cam.W * P.cam.H;
   int64_t g = 1;
-  if ((e = scatter_grid(k_render_scatter, F.ctx.sm_count, (int64_t)P.cam.W * P.cam.H, g)) != cudaSuccess)
-    return e;
+  if ((e = scatter_grid(k_render_scatter, F.ctx.sm_count, npix * P.spp, g)) != cudaSuccess) return e;
+  // about 16 units per lane: chunk = ceil(npix spp / (16 lanes)), in [1, spp]
+  const int64_t lanes = g * kWWarps * 32;
+  int64_t chunk = (npix * P.spp + 16 * lanes - 1) / (16 * lanes);
+  chunk = chunk < 1 ? 1 : (chunk > P.spp ? P.spp : chunk);
+  const int64_t nchunk = (P.spp + chunk - 1) / chunk;
+  if (npix * nchunk >= (int64_t)INT_MAX) return cudaErrorInvalidValue;
+  // fixed-point pixel sums (8 bytes per pixel, grown on demand)
+  if (F.acc_bytes < (size_t)npix * 8) {
+    if (F.acc64) cudaFree(F.acc64);
+    F.acc64 = nullptr;
+    F.acc_bytes = 0;
+    if ((e = cudaMalloc((void**)&F.acc64, (size_t)npix * 8)) != cudaSuccess) return e;
+    F.acc_bytes = (size_t)npix * 8;
+  }
+  if ((e = cudaMemsetAsync(F.acc64, 0, (size_t)npix * 8, s)) != cudaSuccess) return e;
   // per-warp chord store: 32 slots x kSlotCh records of 3 float4
   const size_t store = scatter_store_bytes(g);
   if (F.wscratch_bytes < store) {
@@ -769,8 +809,10 @@ cudaError_t launch_render_scatter(const Field& F, const PathParams& P, float* ou
     if (e != cudaSuccess) return e;
     F.wscratch_bytes = store;
   }
-  k_render_scatter<<<(unsigned)g, kWWarps * 32, scatter_smem_bytes(), s>>>(F.dev, P, out, F.counter,
-                                                                          F.wscratch);
+  k_render_scatter<<<(unsigned)g, kWWarps * 32, scatter_smem_bytes(), s>>>(
+      F.dev, P, F.acc64, F.counter, (int)chunk, F.wscratch);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_fix_to_image<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(F.acc64, npix, P.spp, out);
   return cudaGetLastError();
 }
 
