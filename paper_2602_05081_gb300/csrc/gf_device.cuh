@@ -222,7 +222,8 @@ __device__ __forceinline__ bool chord_setup(const Prim& P, float3 o, float3 v, f
   float a = fmaf(v.x, ux, fmaf(v.y, uy, v.z * uz));
   // d0 = o - mu, error-free split; reference tc = -(d0 . u)/a
   float d0x = __fsub_rn(o.x, P.mu.x), d0y = __fsub_rn(o.y, P.mu.y), d0z = __fsub_rn(o.z, P.mu.z);
-  float tc = -fmaf(d0x, ux, fmaf(d0y, uy, d0z * uz)) / a;
+  const float ia = __frcp_rn(a);
+  float tc = -fmaf(d0x, ux, fmaf(d0y, uy, d0z * uz)) * ia;
   // p = (o - mu) + tc v with compensated arithmetic (positions ~1, offsets ~sigma)
   float ex, ey, ez;
   {
@@ -242,11 +243,11 @@ __device__ __forceinline__ bool chord_setup(const Prim& P, float3 o, float3 v, f
   float qy = fmaf(P.p01, px, fmaf(P.p11, py, P.p12 * pz));
   float qz = fmaf(P.p02, px, fmaf(P.p12, py, P.p22 * pz));
   float g = fmaf(px, qx, fmaf(py, qy, pz * qz));
-  float dts = -b / a;
+  float dts = -b * ia;
   float qmin = fmaf(b, dts, g);
   float disc = k2 - qmin;
   if (!(disc > 0.0f)) return false;
-  float hw = sqrtf(disc / a);
+  float hw = sqrtf(disc * ia);
   float lo = fmaxf(dts - hw, tmin - tc);
   float hi = fminf(dts + hw, tmax - tc);
   if (!(lo < hi)) return false;
@@ -323,7 +324,8 @@ __device__ __forceinline__ bool chord_setup16(const DevField& F, uint4 r0, uint4
   const float w0x = is0 * fmaf(R00, d0x, fmaf(R10, d0y, R20 * d0z));
   const float w0y = is1 * fmaf(R01, d0x, fmaf(R11, d0y, R21 * d0z));
   const float w0z = is2 * fmaf(R02, d0x, fmaf(R12, d0y, R22 * d0z));
-  const float tc = -fmaf(ux, w0x, fmaf(uy, w0y, uz * w0z)) / a;
+  const float ia = __frcp_rn(a);
+  const float tc = -fmaf(ux, w0x, fmaf(uy, w0y, uz * w0z)) * ia;
   // offset at tc in world space with compensated arithmetic, then whitened
   float ex, ey, ez;
   {
@@ -343,11 +345,11 @@ __device__ __forceinline__ bool chord_setup16(const DevField& F, uint4 r0, uint4
   const float pwz = is2 * fmaf(R02, px, fmaf(R12, py, R22 * pz));
   const float b = fmaf(ux, pwx, fmaf(uy, pwy, uz * pwz));
   const float g = fmaf(pwx, pwx, fmaf(pwy, pwy, pwz * pwz));
-  const float dts = -b / a;
+  const float dts = -b * ia;
   const float qmin = fmaf(b, dts, g);
   const float disc = F.k2 - qmin;
   if (!(disc > 0.0f)) return false;
-  const float hw = sqrtf(disc / a);
+  const float hw = sqrtf(disc * ia);
   const float lo = fmaxf(dts - hw, tmin - tc);
   const float hi = fminf(dts + hw, tmax - tc);
   if (!(lo < hi)) return false;

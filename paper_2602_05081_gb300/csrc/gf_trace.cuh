@@ -356,7 +356,7 @@ struct CollectLeaf {
     }
     for (uint32_t draw = 0; draw < (1u << 16); ++draw) {
       const uint4 x = rng4(seed, draw, ch.orig, ray, word);
-      float z = -logf(1.0f - u01(x.x));
+      float z = -__logf(1.0f - u01(x.x));
       bool emit = false;
       for (int q = 0; q < 2 * J + 2; ++q) {
         const float bp = p < J ? dts - (float)(J - p) * invs : dts + (float)(p - J + 1) * invs;

@@ -118,7 +118,7 @@ __device__ __forceinline__ void walk_chord(const DevField& F, WarpQ& Q, const Ch
   }
   for (uint32_t draw = 0; draw < (1u << 16); ++draw) {
     const uint4 x = rng4(seed, draw, c.orig, R.ray, R.word);
-    float z = -logf(1.0f - u01(x.x));
+    float z = -__logf(1.0f - u01(x.x));
     bool emit = false;
     for (int q = 0; q < 2 * J + 2; ++q) {
       const float bp = p < J ? c.dts - (float)(J - p) * invs : c.dts + (float)(p - J + 1) * invs;
@@ -187,6 +187,7 @@ __device__ void warp_phase(const Work& Wk, WarpQ& Q, bool want, uint32_t lane, c
     const int ent = (int)lane < take ? Q.stk[sp - take + (int)lane] : -1;
     __syncwarp();
     sp -= take;
+    if (lane == 0) ++cnt.steps;
     int slot = 0;
     int ch[4] = {0, 0, 0, 0};
     unsigned hit = 0u;  // bit k: child k overlaps the window and the ray's cells
