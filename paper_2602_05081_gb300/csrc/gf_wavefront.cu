@@ -217,13 +217,17 @@ __device__ void warp_phase(const Work& Wk, WarpQ& Q, bool want, uint32_t lane, c
       ch[1] = c4.y;
       ch[2] = c4.z;
       ch[3] = c4.w;
+      // near and far planes by the ray's direction signs, chosen once per node
+      const uint32_t nx = inv.x >= 0.f ? qlx : q.y, fx = inv.x >= 0.f ? q.y : qlx;
+      const uint32_t ny = inv.y >= 0.f ? qly : q.z, fy = inv.y >= 0.f ? q.z : qly;
+      const uint32_t nz = inv.z >= 0.f ? q.x : q.w, fz = inv.z >= 0.f ? q.w : q.x;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const float tx0 = fmaf(byte_float(qlx, k), ax, bx), tx1 = fmaf(byte_float(q.y, k), ax, bx);
-        const float ty0 = fmaf(byte_float(qly, k), ay, by), ty1 = fmaf(byte_float(q.z, k), ay, by);
-        const float tz0 = fmaf(byte_float(q.x, k), az, bz), tz1 = fmaf(byte_float(q.w, k), az, bz);
-        const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), R.ta));
-        const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), R.te));
+        const float txn = fmaf(byte_float(nx, k), ax, bx), txf = fmaf(byte_float(fx, k), ax, bx);
+        const float tyn = fmaf(byte_float(ny, k), ay, by), tyf = fmaf(byte_float(fy, k), ay, by);
+        const float tzn = fmaf(byte_float(nz, k), az, bz), tzf = fmaf(byte_float(fz, k), az, bz);
+        const float tn = fmaxf(fmaxf(txn, tyn), fmaxf(tzn, R.ta));
+        const float tf = fminf(fminf(txf, tyf), fminf(tzf, R.te));
         if ((mk[k] & mask) && tn <= tf) hit |= 1u << k;
       }
     }
@@ -385,6 +389,48 @@ __device__ __forceinline__ bool start_ray(const DevField& F, LaneRay& R, PathSta
   return true;
 }
 
+// the points of slot R (ns <= NP of them) against its stored chords
+template <int NP>
+__device__ __forceinline__ void eval_slot(LaneRay& R, const float4* base, int ns, float S,
+                                          float invS, const float* env, uint32_t lane,
+                                          Counters& cnt) {
+  const int mc = R.nch;
+  float pt[NP];
+  long long kap[NP], kb[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    pt[i] = i < ns ? R.pt[i] : INFINITY;
+    kap[i] = 0;
+    kb[i] = 0;
+  }
+  for (int c = (int)lane; c < mc; c += 32) {
+    const float4 a = base[3 * c], b = base[3 * c + 1], e = base[3 * c + 2];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      const float t = pt[i];
+      if (t >= a.y && t <= a.z) {
+        const float dt = t - a.x;
+        const float y = fmaf(fmaf(b.x, dt, b.y), dt, b.z);
+        kap[i] += __float2ll_rn(ex2f(y) * cosf_fast(fmaf(a.w, dt, b.w)) * S);
+        int m = (int)(fabsf(dt - e.z) * e.y);
+        m = m > 7 ? 7 : m;
+        kb[i] += __float2ll_rn(e.x * env[m] * S);
+        ++cnt.evals;
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    if (i < ns) {
+      const long long k1 = warp_sum_ll(kap[i]), k2 = warp_sum_ll(kb[i]);
+      if (lane == 0) {
+        R.kap[i] = __ll2float_rn(k1) * invS;
+        R.kb[i] = __ll2float_rn(k2) * invS;
+      }
+    }
+  }
+}
+
 // kappa and kappa_bar at the points of every slot, from the chords pass 1
 // stored: the warp scans each slot's list (lanes over chords), then reduces.
 // The sums are exact in 64-bit fixed point: a term is at most the peak h of
@@ -400,46 +446,15 @@ __device__ void eval_stored(WarpQ& Q, const float4* wch, const float* env, uint3
     LaneRay& R = Q.r[s];
     const int ns = R.npts;
     if (ns <= 0) continue;  // uniform: every lane reads the same slot
-    const int mc = R.nch;
     int ex = ((R.hmax >> 23) & 0xFF) - 126;  // H < 2^ex
     ex = ex < -70 ? -70 : ex;
     const float S = __int_as_float((127 + 54 - ex) << 23);     // 2^(54 - ex)
     const float invS = __int_as_float((127 - 54 + ex) << 23);  // 2^(ex - 54)
-    float pt[kPK];
-    long long kap[kPK], kb[kPK];
-#pragma unroll
-    for (int i = 0; i < kPK; ++i) {
-      pt[i] = i < ns ? R.pt[i] : INFINITY;
-      kap[i] = 0;
-      kb[i] = 0;
-    }
     const float4* base = wch + (size_t)s * kSlotCh * 3;
-    for (int c = (int)lane; c < mc; c += 32) {
-      const float4 a = base[3 * c], b = base[3 * c + 1], e = base[3 * c + 2];
-#pragma unroll
-      for (int i = 0; i < kPK; ++i) {
-        const float t = pt[i];
-        if (t >= a.y && t <= a.z) {
-          const float dt = t - a.x;
-          const float y = fmaf(fmaf(b.x, dt, b.y), dt, b.z);
-          kap[i] += __float2ll_rn(ex2f(y) * cosf_fast(fmaf(a.w, dt, b.w)) * S);
-          int m = (int)(fabsf(dt - e.z) * e.y);
-          m = m > 7 ? 7 : m;
-          kb[i] += __float2ll_rn(e.x * env[m] * S);
-          ++cnt.evals;
-        }
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < kPK; ++i) {
-      if (i < ns) {
-        const long long k1 = warp_sum_ll(kap[i]), k2 = warp_sum_ll(kb[i]);
-        if (lane == 0) {
-          R.kap[i] = __ll2float_rn(k1) * invS;
-          R.kb[i] = __ll2float_rn(k2) * invS;
-        }
-      }
-    }
+    // the point count is the same for every lane: size the unrolled loops to it
+    if (ns <= 2) eval_slot<2>(R, base, ns, S, invS, env, lane, cnt);
+    else if (ns <= 4) eval_slot<4>(R, base, ns, S, invS, env, lane, cnt);
+    else eval_slot<kPK>(R, base, ns, S, invS, env, lane, cnt);
   }
   __syncwarp();
 }
