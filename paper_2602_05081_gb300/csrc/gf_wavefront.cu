@@ -33,6 +33,7 @@ constexpr int kLeafQ = 160;     // queued leaves per warp (<= 31 left + 128 new)
 constexpr int kChordQ = 64;     // queued chords per warp (<= 31 left + 32 new)
 constexpr int kPK = 8;          // tentative points per lane and window
 constexpr int kSlotCh = 256;    // stored chords per lane and window (global scratch)
+constexpr int kRecF4 = 2;       // float4s per stored chord record
 
 // One slot per lane, 61 words: an odd stride keeps same-field accesses of the
 // 32 slots in distinct shared-memory banks.
@@ -288,11 +289,12 @@ __device__ void warp_phase(const Work& Wk, WarpQ& Q, bool want, uint32_t lane, c
             atomicMax(&Q.r[own].hmax, __float_as_int(h));
             const int k = atomicAdd(&Q.r[own].nch, 1);
             if (k < kSlotCh) {
-              float4* dst = wch + ((size_t)own * kSlotCh + k) * 3;
-              dst[0] = make_float4(ch.tc, tin, tout, ch.B);
-              dst[1] = make_float4(-0.5f * kLog2e * ch.a, -kLog2e * ch.b,
-                                   fmaf(-0.5f * kLog2e, ch.g, log2f(wa)), ch.delta);
-              dst[2] = make_float4(h, sa, ch.dts, 0.f);
+              // centred on the envelope peak t* = tc + dts: exponent y2 dt^2 + log2 h,
+              // phase B dt + delta*, majorant piece floor(|dt| sqrt(a))
+              float4* dst = wch + ((size_t)own * kSlotCh + k) * kRecF4;
+              dst[0] = make_float4(ch.tc + ch.dts, tin, tout, ch.B);
+              dst[1] = make_float4(-0.5f * kLog2e * ch.a, __log2f(h),
+                                   reduce_2pi(fmaf(ch.B, ch.dts, ch.delta)), sa);
             }
             ci.tc = ch.tc;
             ci.dtin = ch.dtin;
@@ -404,17 +406,16 @@ __device__ __forceinline__ void eval_slot(LaneRay& R, const float4* base, int ns
     kb[i] = 0;
   }
   for (int c = (int)lane; c < mc; c += 32) {
-    const float4 a = base[3 * c], b = base[3 * c + 1], e = base[3 * c + 2];
+    const float4 a = base[kRecF4 * c], b = base[kRecF4 * c + 1];
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
       const float t = pt[i];
       if (t >= a.y && t <= a.z) {
         const float dt = t - a.x;
-        const float y = fmaf(fmaf(b.x, dt, b.y), dt, b.z);
-        kap[i] += __float2ll_rn(ex2f(y) * cosf_fast(fmaf(a.w, dt, b.w)) * S);
-        int m = (int)(fabsf(dt - e.z) * e.y);
+        kap[i] += __float2ll_rn(ex2f(fmaf(b.x, dt * dt, b.y)) * cosf_fast(fmaf(a.w, dt, b.z)) * S);
+        int m = (int)(fabsf(dt) * b.w);
         m = m > 7 ? 7 : m;
-        kb[i] += __float2ll_rn(e.x * env[m] * S);
+        kb[i] += __float2ll_rn(ex2f(b.y + env[8 + m]) * S);  // h exp(-m^2/2)
         ++cnt.evals;
       }
     }
@@ -450,7 +451,7 @@ __device__ void eval_stored(WarpQ& Q, const float4* wch, const float* env, uint3
     ex = ex < -70 ? -70 : ex;
     const float S = __int_as_float((127 + 54 - ex) << 23);     // 2^(54 - ex)
     const float invS = __int_as_float((127 - 54 + ex) << 23);  // 2^(ex - 54)
-    const float4* base = wch + (size_t)s * kSlotCh * 3;
+    const float4* base = wch + (size_t)s * kSlotCh * kRecF4;
     // the point count is the same for every lane: size the unrolled loops to it
     if (ns <= 2) eval_slot<2>(R, base, ns, S, invS, env, lane, cnt);
     else if (ns <= 4) eval_slot<4>(R, base, ns, S, invS, env, lane, cnt);
@@ -735,15 +736,19 @@ __device__ __forceinline__ void render_paths(const Work& Wk, const float* env, W
 }
 
 __device__ __forceinline__ WarpQ& setup_block(unsigned char* smraw, const float* env_src) {
+  // env[0..7] = exp(-n^2/2), env[8..15] = its log2 (-n^2 log2(e) / 2)
   float* env = reinterpret_cast<float*>(smraw);
   WarpQ* Qs = reinterpret_cast<WarpQ*>(smraw + 64);
-  if (threadIdx.x < 8) env[threadIdx.x] = env_src[threadIdx.x];
+  if (threadIdx.x < 8) {
+    env[threadIdx.x] = env_src[threadIdx.x];
+    env[8 + threadIdx.x] = -0.5f * kLog2e * (float)(threadIdx.x * threadIdx.x);
+  }
   __syncthreads();
   return Qs[threadIdx.x >> 5];
 }
 
 __device__ __forceinline__ float4* warp_store(float4* chord_store) {
-  return chord_store + ((size_t)blockIdx.x * kWWarps + (threadIdx.x >> 5)) * 32 * kSlotCh * 3;
+  return chord_store + ((size_t)blockIdx.x * kWWarps + (threadIdx.x >> 5)) * 32 * kSlotCh * kRecF4;
 }
 
 __global__ void __launch_bounds__(kWWarps * 32, 4)
@@ -772,7 +777,7 @@ size_t scatter_smem_bytes() { return 64 + sizeof(WarpQ) * kWWarps; }
 static_assert(64 + sizeof(WarpQ) * kWWarps <= 57344, "four blocks per SM (56 KB each)");
 
 size_t scatter_store_bytes(int64_t grid) {
-  return (size_t)grid * kWWarps * 32 * kSlotCh * 3 * sizeof(float4);
+  return (size_t)grid * kWWarps * 32 * kSlotCh * kRecF4 * sizeof(float4);
 }
 
 // persistent grid of the scattering kernels: every SM filled, never more
