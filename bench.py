@@ -217,6 +217,124 @@ def server_leg(api, ctx, n_requests, load=0.7):
     }
 
 
+# ---------------------------------------------------------------------------
+# Other workloads of the method, one JSON line each (bench.py --workload NAME);
+# the default line is the single-scattering workload above.
+# ---------------------------------------------------------------------------
+def _timed(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for a, b in ev:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def workload_line(name, value, unit, ms, args, extra, higher=True):
+    line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": higher,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": name}}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def run_workload(args):
+    """Transmittance, multiple scattering with stochastic masks, and the adjoints."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2602_05081_gb300 import _abi, api
+    ctx = api.Context(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    c = synth.DEFAULT_CAMERA
+    if args.workload == "transmittance":
+        # 256 absorption-only kernels, 64x64 orthographic rays: deterministic optical
+        # depth and 1-spp ratio tracking, all bands
+        p = synth.absorption_field(256, seed=0)
+        f = api.Field(ctx, p)
+        o, d, tr = (torch.from_numpy(a).to(dev) for a in synth.orthographic_rays(64))
+        n = o.shape[0]
+        T = torch.empty(n, device=dev)
+        tau = torch.empty(n, device=dev)
+        out = {}
+        for mode in ("det", "rt"):
+            m = _abi.GF_TR_DETERMINISTIC if mode == "det" else _abi.GF_TR_RATIO_TRACKING
+            ms = _timed(lambda: _abi.gf_transmittance(f.h, o, d, tr, n, m, 1, 0, T, tau, stream),
+                        args.steps * 50, args.warmup, stream)
+            out[mode] = statistics.median(ms)
+        f.sync()
+        workload_line("absorption transmittance, 256 kernels, 64x64 orthographic rays",
+                      n / (out["det"] * 1e-3) / 1e6, "Mrays/s", out["det"], args,
+                      {"us_per_call": {k: v * 1e3 for k, v in out.items()},
+                       "ratio_tracking_mrays_per_s": n / (out["rt"] * 1e-3) / 1e6,
+                       "gpu_launches": 1})
+    elif args.workload == "multiscatter":
+        # 1M kernels in 6 octaves, up to 8 bounces, per-bounce Uniform+CV band and
+        # importance-sampled cone masks, FP32 and FP16 records
+        res, spp = args.res if args.res != RES else 1024, args.spp if args.spp != SPP else 64
+        p = synth.octave_field(1_000_000, 6, seed=0)
+        cam = api.camera(c["eye"], c["look_at"], c["up"], c["vfov_deg"], res, res)
+        ro = api.render_opts("scatter", spp, 8, 0.8, synth.LIGHT_DIR, 1.0)
+        out = torch.empty(res, res, device=dev)
+        lo = api.lod("unif_cv", 7, "is")
+        res_ms, rays = {}, {}
+        for prec in ("fp32", "fp16"):
+            f = api.Field(ctx, p, precision=prec)
+            f.set_lod(lo, lo)
+            f.stats(reset=True)
+            ms = _timed(lambda: f.render(cam, ro, seed=3, out=out), args.steps, 1, stream)
+            f.sync()
+            st = f.stats(reset=True)
+            rays[prec] = st["rays"] / (1 + args.steps)
+            res_ms[prec] = statistics.mean(ms)
+            f.free()
+        workload_line("multiple scattering, 1M-kernel 6-octave field, %dx%d, %d spp, <= 8 bounces, "
+                      "per-bounce stochastic LoD masks" % (res, res, spp),
+                      rays["fp32"] / (res_ms["fp32"] * 1e-3) / 1e6, "Mrays/s", res_ms["fp32"], args,
+                      {"ms_per_render": res_ms,
+                       "mrays_per_s": {k: rays[k] / (res_ms[k] * 1e-3) / 1e6 for k in rays},
+                       "gpu_launches": 2})
+    elif args.workload == "adjoint":
+        # 200k kernels, 256x256 at 8 spp: forward render plus hand-written adjoint of an
+        # L2 loss against a target rendered from perturbed parameters
+        res, spp = 256, 8
+        p = synth.octave_field(200_000, 4, seed=0)
+        rng = np.random.default_rng(1)
+        tgt = dict(p)
+        for k in ("mu", "log_scale", "weight"):
+            tgt[k] = (p[k] * (1 + 0.01 * rng.standard_normal(p[k].shape))).astype(np.float32)
+        cam = api.camera(c["eye"], c["look_at"], c["up"], c["vfov_deg"], res, res)
+        out = {}
+        for integ in ("tomo", "scatter"):
+            ro = api.render_opts(integ, spp, 1, 0.8, synth.LIGHT_DIR, 1.0)
+            ft = api.Field(ctx, tgt)
+            target = ft.render(cam, ro, seed=11)
+            ft.free()
+            f = api.Field(ctx, p)
+            grad = torch.empty(15 * f.n, device=dev)
+
+            def step():
+                img = f.render(cam, ro, seed=12)
+                g = 2.0 * (img - target)
+                f.render_backward(cam, ro, 13, g, grad=grad)
+            ms = _timed(step, args.steps, args.warmup, stream)
+            f.sync()
+            out[integ] = statistics.mean(ms)
+            f.free()
+        workload_line("differentiable rendering, 200k kernels, 256x256, 8 spp, forward + adjoint",
+                      res * res * spp / (out["scatter"] * 1e-3) / 1e6, "Msamples/s", out["scatter"],
+                      args, {"ms_per_forward_backward": out, "gpu_launches": 3})
+    ctx.close()
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -400,6 +518,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--server-requests", type=int, default=16,
                     help="requests of the render-server leg (0: skip)")
+    ap.add_argument("--workload", choices=["scatter", "transmittance", "multiscatter", "adjoint"],
+                    default="scatter", help="workload of the JSON line (default: the single-"
+                    "scattering benchmark)")
     ap.add_argument("--res", type=int, default=RES, help="profiling only: image size")
     ap.add_argument("--spp", type=int, default=SPP, help="profiling only: samples per pixel")
     args = ap.parse_args()
@@ -408,6 +529,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload != "scatter":
+        if rank == 0:
+            run_workload(args)
         return
     if world > 1:
         import torch

@@ -111,10 +111,15 @@ __global__ void k_pack(const __grid_constant__ PackArgs A) {
     float sjj = R[a][0] * R[a][0] * s[0] * s[0] + R[a][1] * R[a][1] * s[1] * s[1] +
                 R[a][2] * R[a][2] * s[2] * s[2];
     float hw = A.ksig * sqrtf(sjj);
-    // reduced-precision records move the decoded ellipsoid by up to ~5e-4 (FP16)
-    // or ~4e-3 (BF16) of its size and the mean by half a u16 step: pad for it
-    const float rel = A.precision == GF_PREC_BF16 ? 1e-2f : (A.precision == GF_PREC_FP16 ? 2e-3f : 1e-5f);
-    float pad = rel * hw + (A.precision == GF_PREC_FP32 ? 1e-6f : 1e-4f) * (1.f + fabsf(mu[a]));
+    // reduced-precision records change the decoded ellipsoid: inverse scales by
+    // 2^-11 (FP16) or 2^-8 (BF16) of themselves, the rotation by an angle of at
+    // most 6.1e-5 (snorm16 quaternion), which moves an extent by that angle
+    // times the longest semi-axis; pad for both with a 1.5x margin (the mean's
+    // u16 step is added once the means' box is known, in build_bvh)
+    const float aniso = fmaxf(fmaxf(s[0], s[1]), s[2]) / fminf(fminf(s[0], s[1]), s[2]);
+    const float rel = A.precision == GF_PREC_BF16 ? 5.9e-3f + 9.2e-5f * aniso
+                    : A.precision == GF_PREC_FP16 ? 7.4e-4f + 9.2e-5f * aniso : 1e-5f;
+    float pad = rel * hw + 1e-6f * (1.f + fabsf(mu[a]));
     A.box[6 * i + a] = mu[a] - hw - pad;
     A.box[6 * i + 3 + a] = mu[a] + hw + pad;
   }
@@ -399,6 +404,19 @@ __global__ void k_collapse4(const Node* nodes, int64_t m, const int* even, const
   out[map[i]] = o;
 }
 
+// reduced-precision records: the decoded mean moves by up to half a u16 step of
+// the means' box on each axis; grow every box by that (with 2 % margin)
+__global__ void k_pad_mean_step(float* box, int64_t n, const unsigned int* bounds) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int a = 0; a < 3; ++a) {
+    const float ext = ord_dec(bounds[9 + a]) - ord_dec(bounds[6 + a]);
+    const float pad = ext > 0.f ? 0.51f * ext / 65535.f : 0.f;
+    box[6 * i + a] -= pad;
+    box[6 * i + 3 + a] += pad;
+  }
+}
+
 static cudaError_t dalloc(void** p, size_t bytes) { return cudaMalloc(p, bytes ? bytes : 16); }
 
 cudaError_t build_bvh(Field& F, cudaStream_t s) {
@@ -434,6 +452,16 @@ cudaError_t build_bvh(Field& F, cudaStream_t s) {
     if (blocks > 4096) blocks = 4096;
     k_bounds<<<blocks, 256, 0, s>>>(F.box_orig, F.rec_orig, n, bounds);
     GF_TRY(cudaGetLastError());
+    if (F.opts.precision != GF_PREC_FP32) {
+      // grow the boxes by the mean's quantisation step, then take the bounds again
+      k_pad_mean_step<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(F.box_orig, n, bounds);
+      GF_TRY(cudaGetLastError());
+      unsigned int init[12];
+      for (int j = 0; j < 12; ++j) init[j] = ((j < 3) || (j >= 6 && j < 9)) ? 0xFFFFFFFFu : 0u;
+      GF_TRY(cudaMemcpyAsync(bounds, init, sizeof(init), cudaMemcpyHostToDevice, s));
+      k_bounds<<<blocks, 256, 0, s>>>(F.box_orig, F.rec_orig, n, bounds);
+      GF_TRY(cudaGetLastError());
+    }
     k_morton<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(F.rec_orig, n, bounds, keys, idx);
     GF_TRY(cudaGetLastError());
   }

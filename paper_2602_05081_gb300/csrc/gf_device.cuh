@@ -284,6 +284,13 @@ __device__ __forceinline__ bool chord_setup(const Prim& P, float3 o, float3 v, f
 // Decoded to FP32; the chord is set up in the whitened frame W = S^-1 R^T
 // (Sec. 4.4): u = W v, p_W = W (o + tc v - mu), phase k_W . p_W + phi.
 // ---------------------------------------------------------------------------
+// exact integer-to-float conversions by exponent insertion (0x4B000000 is 2^23)
+__device__ __forceinline__ float u16_float(uint32_t x) {
+  return __int_as_float((int)(0x4B000000u | x)) - 8388608.0f;
+}
+__device__ __forceinline__ float s16_float(uint32_t x) {  // two's complement 16-bit value
+  return __int_as_float((int)(0x4B000000u | (x ^ 0x8000u))) - 8421376.0f;
+}
 __device__ __forceinline__ float half_bits_to_float(uint32_t h, int prec) {
   return prec == 2 ? __uint_as_float(h << 16) : __half2float(__ushort_as_half((unsigned short)h));
 }
@@ -292,29 +299,29 @@ __device__ __forceinline__ bool chord_setup16(const DevField& F, uint4 r0, uint4
                                               float3 o, float3 v, float tmin, float tmax,
                                               Chord& c) {
   const int prec = F.precision;
-  const float3 mu = make_float3(fmaf((float)(r0.x & 0xFFFFu), F.qscale.x, F.qlo.x),
-                                fmaf((float)(r0.x >> 16), F.qscale.y, F.qlo.y),
-                                fmaf((float)(r0.y & 0xFFFFu), F.qscale.z, F.qlo.z));
-  const float qw = (float)(short)(r0.y >> 16), qx = (float)(short)(r0.z & 0xFFFFu);
-  const float qy = (float)(short)(r0.z >> 16), qz = (float)(short)(r0.w & 0xFFFFu);
-  const float is0 = half_bits_to_float(r0.w >> 16, prec);
-  const float is1 = half_bits_to_float(r1.x & 0xFFFFu, prec);
-  const float is2 = half_bits_to_float(r1.x >> 16, prec);
+  const float3 mu = make_float3(fmaf(u16_float(r0.x & 0xFFFFu), F.qscale.x, F.qlo.x),
+                                fmaf(u16_float(r0.x >> 16), F.qscale.y, F.qlo.y),
+                                fmaf(u16_float(r0.y & 0xFFFFu), F.qscale.z, F.qlo.z));
+  const float qw = s16_float(r0.y >> 16), qx = s16_float(r0.z & 0xFFFFu);
+  const float qy = s16_float(r0.z >> 16), qz = s16_float(r0.w & 0xFFFFu);
   const float k0 = half_bits_to_float(r1.y & 0xFFFFu, prec);
   const float k1 = half_bits_to_float(r1.y >> 16, prec);
   const float k2 = half_bits_to_float(r1.z & 0xFFFFu, prec);
   const float A = half_bits_to_float(r1.z >> 16, prec);
-  const float phi = (float)(r1.w & 0xFFFFu) * (6.28318530717958647692f / 65536.0f);
-  // rotation of the unnormalised quaternion: R = M(q) / |q|^2
-  const float n2 = qw * qw + qx * qx + qy * qy + qz * qz;
-  const float in2 = 1.0f / n2;
-  const float R00 = (qw * qw + qx * qx - qy * qy - qz * qz) * in2;
-  const float R01 = 2.f * (qx * qy - qw * qz) * in2, R02 = 2.f * (qx * qz + qw * qy) * in2;
-  const float R10 = 2.f * (qx * qy + qw * qz) * in2;
-  const float R11 = (qw * qw - qx * qx + qy * qy - qz * qz) * in2;
-  const float R12 = 2.f * (qy * qz - qw * qx) * in2, R20 = 2.f * (qx * qz - qw * qy) * in2;
-  const float R21 = 2.f * (qy * qz + qw * qx) * in2;
-  const float R22 = (qw * qw - qx * qx - qy * qy + qz * qz) * in2;
+  const float phi = u16_float(r1.w & 0xFFFFu) * (6.28318530717958647692f / 65536.0f);
+  // rotation of the unnormalised quaternion, R = M(q) / |q|^2: the 1/|q|^2
+  // is folded into the inverse scales
+  const float in2 = __frcp_rn(qw * qw + qx * qx + qy * qy + qz * qz);
+  const float is0 = half_bits_to_float(r0.w >> 16, prec) * in2;
+  const float is1 = half_bits_to_float(r1.x & 0xFFFFu, prec) * in2;
+  const float is2 = half_bits_to_float(r1.x >> 16, prec) * in2;
+  const float R00 = qw * qw + qx * qx - qy * qy - qz * qz;
+  const float R01 = 2.f * (qx * qy - qw * qz), R02 = 2.f * (qx * qz + qw * qy);
+  const float R10 = 2.f * (qx * qy + qw * qz);
+  const float R11 = qw * qw - qx * qx + qy * qy - qz * qz;
+  const float R12 = 2.f * (qy * qz - qw * qx), R20 = 2.f * (qx * qz - qw * qy);
+  const float R21 = 2.f * (qy * qz + qw * qx);
+  const float R22 = qw * qw - qx * qx - qy * qy + qz * qz;
   // whitened direction and offset
   const float ux = is0 * fmaf(R00, v.x, fmaf(R10, v.y, R20 * v.z));
   const float uy = is1 * fmaf(R01, v.x, fmaf(R11, v.y, R21 * v.z));
