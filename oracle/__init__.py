@@ -50,7 +50,8 @@ class FieldDesc(C.Structure):
 
 
 class Lod(C.Structure):
-    _fields_ = [("freq_policy", C.c_int), ("max_band", C.c_int), ("cone_policy", C.c_int)]
+    _fields_ = [("freq_policy", C.c_int), ("max_band", C.c_int), ("cone_policy", C.c_int),
+                ("beta", C.c_float), ("delta", C.c_float)]
 
 
 class Camera(C.Structure):

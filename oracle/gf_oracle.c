@@ -244,6 +244,21 @@ static uint64_t band_cells(const or_field* f, int b) {
   return m & f->occupied;
 }
 
+/* power-law level choice over n levels (App. B frequency table): the level is
+   floor(n x^(1/(1-beta))), x uniform, i.e. level j when
+   (j/n)^(1-beta) <= x < ((j+1)/n)^(1-beta); the thresholds are compared in
+   FP32, as the kernel does */
+static int power_level(double x, int n, double beta) {
+  float e = (float)(1.0 - beta);
+  int j = 0;
+  while (j + 1 < n && (float)x >= powf((float)(j + 1) / (float)n, e)) ++j;
+  return j;
+}
+/* probability of power-law level j out of n: ((j+1)/n)^(1-beta) - (j/n)^(1-beta) */
+static double power_prob(int j, int n, double beta) {
+  return pow((double)(j + 1) / n, 1.0 - beta) - pow((double)j / n, 1.0 - beta);
+}
+
 void or_sample_mask(const or_field* f, const or_lod* L, const double v[3], uint64_t seed,
                     uint32_t ray, uint32_t sample, uint32_t bounce, uint32_t tag,
                     uint64_t* mask_out, double* w64) {
@@ -260,6 +275,7 @@ void or_sample_mask(const or_field* f, const or_lod* L, const double v[3], uint6
   uint32_t x[4];
   rng4(seed, 0, OR_NO_PRIM, ray, word, x);
   uint32_t x24 = x[0] >> 8;
+  const double beta = L->beta;
   if (L->freq_policy == 0 || L->freq_policy == 1) {
     for (int j = 0; j < nocc; ++j) { sel[occ[j]] = 1; bw[occ[j]] = 1.0; }
   } else if (L->freq_policy == 2) {
@@ -271,12 +287,36 @@ void or_sample_mask(const or_field* f, const or_lod* L, const double v[3], uint6
       sel[gab[j]] = 1;
       bw[gab[j]] = (double)ngab;
     }
-  } else {
+  } else if (L->freq_policy == 3) {
     /* Uniform: one level out of P with weight P */
     if (nocc > 0) {
       int j = (int)(((uint64_t)x24 * (uint64_t)nocc) >> 24);
       sel[occ[j]] = 1;
       bw[occ[j]] = (double)nocc;
+    }
+  } else if (L->freq_policy == 4) {
+    /* Power law over all P levels, weight 1 / P(level) */
+    if (nocc > 0) {
+      int j = power_level(u01(x[0]), nocc, beta);
+      sel[occ[j]] = 1;
+      bw[occ[j]] = 1.0 / power_prob(j, nocc, beta);
+    }
+  } else {
+    /* control variate: Gaussians always, weight 1; power law over the G Gabor
+       levels: one level (5), or every level up to the drawn one (6, level j
+       kept with probability 1 - (j/G)^(1-beta)) */
+    if (band_cells(f, 0)) { sel[0] = 1; bw[0] = 1.0; }
+    if (ngab > 0) {
+      int k = power_level(u01(x[0]), ngab, beta);
+      if (L->freq_policy == 5) {
+        sel[gab[k]] = 1;
+        bw[gab[k]] = 1.0 / power_prob(k, ngab, beta);
+      } else {
+        for (int j = 0; j <= k; ++j) {
+          sel[gab[j]] = 1;
+          bw[gab[j]] = 1.0 / (1.0 - pow((double)j / ngab, 1.0 - beta));
+        }
+      }
     }
   }
   uint64_t mask = 0;
@@ -302,6 +342,35 @@ void or_sample_mask(const or_field* f, const or_lod* L, const double v[3], uint6
       int j = (int)(((uint64_t)(y[0] >> 8) * (uint64_t)nc) >> 24);
       mask |= 1ull << cc[j];
       w64[cc[j]] = bw[b] * nc;
+    } else if (L->cone_policy == 3 || L->cone_policy == 4) {
+      /* alignment a = |v . o| decided in FP32 against delta: threshold culling
+         keeps the bins with a <= delta (weight 1; if none, the least aligned
+         bin, the one of largest contribution); threshold + uniform keeps them
+         and draws one of the N_above others uniformly, weight N_above */
+      int above[OR_N_CONES], na = 0, best = -1;
+      float abest = 2.0f;
+      for (int j = 0; j < nc; ++j) {
+        int k = (cc[j] - 1) % OR_N_CONES;
+        float a = fabsf((float)v[0] * (float)f->axes[k][0] + (float)v[1] * (float)f->axes[k][1] +
+                        (float)v[2] * (float)f->axes[k][2]);
+        if (a < abest) { abest = a; best = cc[j]; }
+        if (a <= L->delta) {
+          mask |= 1ull << cc[j];
+          w64[cc[j]] = bw[b];
+        } else {
+          above[na++] = cc[j];
+        }
+      }
+      if (L->cone_policy == 3) {
+        if (na == nc && best >= 0) {
+          mask |= 1ull << best;
+          w64[best] = bw[b];
+        }
+      } else if (na > 0) {
+        int j = (int)(((uint64_t)(y[0] >> 8) * (uint64_t)na) >> 24);
+        mask |= 1ull << above[j];
+        w64[above[j]] = bw[b] * na;
+      }
     } else {
       /* Importance sampling: p_i = w_i / W, weight W / w_i with
          w(a) = exp(-kbar^2 a^2 / 2), a = |v . o_i| (Eq. 17, App. B) */

@@ -16,6 +16,13 @@
  *   weight / sqrt(8 pi^3 |Sigma|) (normalised mode, Eq. 6).
  *   kernel: A exp(-q/2) cos(omega.(x-mu) + phi) 1[q <= k^2],
  *   q = (x-mu)^T Sigma^-1 (x-mu)  (Eq. 6 with the k-sigma support of Sec. 3).
+ *
+ * Parity unpinned: the composition of two or more scattering bounces in
+ * or_render / or_render_samples (max_bounces >= 2) has no closed form or
+ * independent reference; its parts are pinned (delta-tracking collision CDF,
+ * ratio-tracking expectation, single-scatter nested quadrature, mask weights),
+ * the multi-bounce loop itself only by agreement with the CUDA path under
+ * shared random streams.
  */
 #ifndef GF_ORACLE_H
 #define GF_ORACLE_H
@@ -43,9 +50,14 @@ typedef struct {
 } or_field_desc;
 
 typedef struct {
-  int freq_policy; /* 0 all, 1 cutoff, 2 uniform + control variate, 3 uniform */
+  int freq_policy; /* 0 all, 1 cutoff, 2 uniform + control variate, 3 uniform,
+                      4 power law, 5 power law + control variate,
+                      6 power law + control variate, accumulating */
   int max_band;    /* bands above this are never used (cutoff / sampled modes) */
-  int cone_policy; /* 0 all, 1 importance w(a)=exp(-kbar^2 a^2/2), 2 uniform */
+  int cone_policy; /* 0 all, 1 importance w(a)=exp(-kbar^2 a^2/2), 2 uniform,
+                      3 threshold culling, 4 threshold + uniform */
+  float beta;      /* power-law shape, [0, 1) */
+  float delta;     /* alignment threshold on a = |v . o|, [0, 1] */
 } or_lod;
 
 typedef struct {

@@ -596,3 +596,92 @@ def test_radiance_estimator_mean_and_gradient_match_nested_quadrature():
         fd = (_nested_radiance(pp, o, v)[0] - _nested_radiance(pm, o, v)[0]) / step
         an, s_ = gm[offs[key] + j], gse[offs[key] + j]
         assert abs(an - fd) < 4.5 * s_ + 2e-3 * abs(fd) + 1e-6, (key, j, an, fd, s_)
+
+
+@pytest.mark.parametrize("freq,cone,beta,delta", [(4, 0, 0.3, 0.0), (5, 2, 0.5, 0.0),
+                                                  (6, 1, 0.2, 0.0), (2, 4, 0.0, 0.5),
+                                                  (3, 4, 0.0, 0.3), (6, 4, 0.6, 0.4)])
+def test_strategy_weights_are_reciprocal_probabilities(freq, cone, beta, delta):
+    """Power-law (with and without control variate, accumulating) and threshold +
+    uniform strategies of the App. B tables: every occupied cell's mean of
+    w * 1[selected] is 1, and power-law levels occur with probability
+    ((j+1)/n)^(1-beta) - (j/n)^(1-beta)."""
+    f, p = _small_octave(n=5460, octaves=6)
+    occ, _ = f.cells()
+    lod = oracle.Lod(freq, 7, cone, beta, delta)
+    v = np.array([0.3, -0.5, 0.81]); v /= np.linalg.norm(v)
+    n = 30000
+    acc = np.zeros(64)
+    sq = np.zeros(64)
+    levels = np.zeros(8)
+    for r in range(n):
+        m, w = f.sample_mask(lod, v, seed=5, ray=r, sample=0, bounce=0, tag=oracle.TAG_MASK)
+        bits = np.array([(m >> c) & 1 for c in range(64)], bool)
+        x = np.where(bits, w, 0.0)
+        acc += x
+        sq += x * x
+        gab = [b for b in range(1, 8) if any((m >> c) & 1 for c in range(1 + 8 * (b - 1), 9 + 8 * (b - 1)))]
+        if freq in (4, 5):
+            if freq == 4 and m & 1 and not gab:
+                levels[0] += 1
+            for b in gab:
+                levels[b] += 1
+        # the stated weights, exactly: 1/P(level) for a single level, 1/P(level kept)
+        # when accumulating (the weight of a band, before the cone factor)
+        nb = 6 if freq in (3, 4) else 5
+        b32 = float(np.float32(beta))  # the descriptor holds beta as a float
+        for b in gab:
+            c = next(c for c in range(1 + 8 * (b - 1), 9 + 8 * (b - 1)) if (m >> c) & 1)
+            j = b if freq in (3, 4) else b - 1
+            if freq in (4, 5):
+                wb = 1.0 / (((j + 1) / nb) ** (1 - b32) - (j / nb) ** (1 - b32))
+            elif freq == 6:
+                wb = 1.0 / (1.0 - (j / nb) ** (1 - b32))
+            else:
+                wb = float(nb)
+            ratio = w[c] / wb
+            if cone == 0:
+                assert ratio == pytest.approx(1.0, rel=1e-12)
+            elif cone in (2, 4):
+                assert ratio == pytest.approx(round(ratio), rel=1e-12) or ratio == pytest.approx(1.0)
+    cells = [c for c in range(64) if (occ >> c) & 1]
+    for c in cells:
+        mean = acc[c] / n
+        se = math.sqrt(max(sq[c] / n - mean * mean, 0.0) / n)
+        assert abs(mean - 1.0) < 5 * se + 1e-9, (c, mean, se)
+    if freq in (4, 5):
+        nb = 6 if freq == 4 else 5
+        first = 0 if freq == 4 else 1
+        for j in range(nb):
+            pj = ((j + 1) / nb) ** (1 - beta) - (j / nb) ** (1 - beta)
+            sd = math.sqrt(pj * (1 - pj) / n)
+            assert abs(levels[first + j] / n - pj) < 5 * sd, (j, levels[first + j] / n, pj)
+
+
+def test_threshold_culling_keeps_perpendicular_bins():
+    """Threshold culling (App. B orientation table): a Gabor band keeps exactly the
+    bins with |v . o| <= delta, weight 1; with none below the threshold, the
+    least aligned bin (largest contribution weight)."""
+    f, p = _small_octave(n=5460, octaves=6)
+    occ, _ = f.cells()
+    axes = []
+    for k in range(8):
+        z = 1 - (k + 0.5) / 8; r_ = math.sqrt(1 - z * z); ph = k * math.pi * (3 - math.sqrt(5))
+        axes.append((r_ * math.cos(ph), r_ * math.sin(ph), z))
+    rng = np.random.default_rng(4)
+    for t in range(20):
+        v = rng.standard_normal(3); v /= np.linalg.norm(v)
+        delta = float(rng.uniform(0.0, 0.8))
+        m, w = f.sample_mask(oracle.Lod(0, 7, 3, 0.0, delta), v, seed=1, ray=t, sample=0,
+                             bounce=0, tag=oracle.TAG_MASK)
+        a = [abs(np.float32(v[0]) * np.float32(ax[0]) + np.float32(v[1]) * np.float32(ax[1])
+                 + np.float32(v[2]) * np.float32(ax[2])) for ax in axes]
+        for b in range(1, 6):
+            cells = [1 + 8 * (b - 1) + k for k in range(8) if (occ >> (1 + 8 * (b - 1) + k)) & 1]
+            keep = {c for c in cells if a[(c - 1) % 8] <= np.float32(delta)}
+            if not keep:
+                keep = {min(cells, key=lambda c: a[(c - 1) % 8])}
+            got = {c for c in cells if (m >> c) & 1}
+            assert got == keep, (t, b, got, keep)
+            assert all(w[c] == 1.0 for c in got)
+        assert m & 1 and w[0] == 1.0
