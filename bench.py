@@ -36,6 +36,7 @@ N_PRIMS = 100_000
 OCTAVES = 4
 RES = 512
 SPP = 16
+DEFAULT_RES, DEFAULT_SPP = RES, SPP
 CUTOFFS = (3, 2, 1, 0)
 # smaller launches of the same kernel for profiling captures (--res / --spp)
 SEED = 1
@@ -279,7 +280,8 @@ def run_workload(args):
     elif args.workload == "multiscatter":
         # 1M kernels in 6 octaves, up to 8 bounces, per-bounce Uniform+CV band and
         # importance-sampled cone masks, FP32 and FP16 records
-        res, spp = args.res if args.res != RES else 1024, args.spp if args.spp != SPP else 64
+        res = args.res if args.res != DEFAULT_RES else 1024
+        spp = args.spp if args.spp != DEFAULT_SPP else 64
         p = synth.octave_field(1_000_000, 6, seed=0)
         cam = api.camera(c["eye"], c["look_at"], c["up"], c["vfov_deg"], res, res)
         ro = api.render_opts("scatter", spp, 8, 0.8, synth.LIGHT_DIR, 1.0)

@@ -93,19 +93,45 @@ typedef struct gf_field_opts {
 /* Level-of-detail mask (Sec. 4.5.1-4.5.2, 4.6; strategy tables of App. B).
    Cells: cell 0 = Gaussian band; cell 1 + 8 (band-1) + cone for Gabor bands,
    cone = the nearest of 8 fixed orientation axes to the carrier direction.
-   freq_policy: ALL every band weight 1; CUTOFF bands <= max_band weight 1;
-   UNIF_CV Gaussians weight 1 plus one Gabor band (<= max_band) chosen
-   uniformly, weight P-1; UNIFORM one band (<= max_band) uniformly, weight P.
-   cone_policy (applied inside every selected Gabor band): ALL; IS one cone
-   with probability w(a)/W, w(a) = exp(-kbar^2 a^2/2), a = |v.o_c|, weight
-   W/w(a) (Eq. 17); UNIFORM one cone, weight K.  A new mask is drawn for
-   every path segment (per bounce) and every NEE ray. */
-enum { GF_FREQ_ALL = 0, GF_FREQ_CUTOFF = 1, GF_FREQ_UNIF_CV = 2, GF_FREQ_UNIFORM = 3 };
-enum { GF_CONE_ALL = 0, GF_CONE_IS = 1, GF_CONE_UNIFORM = 2 };
+   Bands above max_band are never used.  P = occupied bands, G = occupied
+   Gabor bands (band >= 1), both counted up to max_band.
+   freq_policy:
+     ALL         every band, weight 1 (max_band ignored);
+     CUTOFF      bands <= max_band, weight 1;
+     UNIF_CV     Gaussians weight 1 plus one Gabor band uniformly, weight G;
+     UNIFORM     one band uniformly, weight P;
+     POWER       one band, level floor(P x^(1/(1-beta))) of the P in order,
+                 weight 1/(((j+1)/P)^(1-beta) - (j/P)^(1-beta));
+     POW_CV      Gaussians weight 1 plus one Gabor band by the power law over G;
+     POW_CV_ACC  Gaussians weight 1 plus every Gabor band up to the level k
+                 drawn by the power law over G; Gabor level j has weight
+                 1/(1 - (j/G)^(1-beta)).
+   cone_policy (inside every selected Gabor band; a = |v.o_c|):
+     ALL             every cone;
+     IS              one cone with probability w(a)/W, w(a) = exp(-kbar^2 a^2/2),
+                     weight W/w(a) (Eq. 17);
+     UNIFORM         one cone, weight K;
+     THRESH          the cones with a <= delta, weight 1 (none: the least
+                     aligned cone); deterministic and biased;
+     THRESH_UNIFORM  the cones with a <= delta, weight 1, plus one of the
+                     N_above others uniformly, weight N_above.
+   beta in [0, 1) shapes the power law; delta in [0, 1] is the alignment
+   threshold.  A new mask is drawn for every path segment (per bounce) and
+   every NEE ray. */
+enum {
+  GF_FREQ_ALL = 0, GF_FREQ_CUTOFF = 1, GF_FREQ_UNIF_CV = 2, GF_FREQ_UNIFORM = 3,
+  GF_FREQ_POWER = 4, GF_FREQ_POW_CV = 5, GF_FREQ_POW_CV_ACC = 6
+};
+enum {
+  GF_CONE_ALL = 0, GF_CONE_IS = 1, GF_CONE_UNIFORM = 2, GF_CONE_THRESH = 3,
+  GF_CONE_THRESH_UNIFORM = 4
+};
 typedef struct gf_lod_desc {
   int freq_policy;
   int max_band;
   int cone_policy;
+  float beta;
+  float delta;
 } gf_lod_desc;
 
 enum { GF_TR_DETERMINISTIC = 0, GF_TR_RATIO_TRACKING = 1 };

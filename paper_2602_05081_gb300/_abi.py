@@ -22,8 +22,9 @@ STATUS_NAMES = {0: "GF_OK", 1: "GF_EINVAL", 2: "GF_ENOMEM", 3: "GF_ECUDA", 4: "G
 GF_PREC_FP32, GF_PREC_FP16, GF_PREC_BF16 = 0, 1, 2
 GF_WEIGHT_PEAK, GF_WEIGHT_NORMALIZED = 0, 1
 GF_OMEGA_WORLD, GF_OMEGA_LOCAL = 0, 1
-GF_FREQ_ALL, GF_FREQ_CUTOFF, GF_FREQ_UNIF_CV, GF_FREQ_UNIFORM = 0, 1, 2, 3
-GF_CONE_ALL, GF_CONE_IS, GF_CONE_UNIFORM = 0, 1, 2
+(GF_FREQ_ALL, GF_FREQ_CUTOFF, GF_FREQ_UNIF_CV, GF_FREQ_UNIFORM, GF_FREQ_POWER, GF_FREQ_POW_CV,
+ GF_FREQ_POW_CV_ACC) = range(7)
+GF_CONE_ALL, GF_CONE_IS, GF_CONE_UNIFORM, GF_CONE_THRESH, GF_CONE_THRESH_UNIFORM = range(5)
 GF_TR_DETERMINISTIC, GF_TR_RATIO_TRACKING = 0, 1
 GF_INTEG_TOMO, GF_INTEG_SCATTER = 0, 1
 
@@ -46,7 +47,8 @@ class gf_field_opts(C.Structure):
 
 
 class gf_lod_desc(C.Structure):
-    _fields_ = [("freq_policy", C.c_int), ("max_band", C.c_int), ("cone_policy", C.c_int)]
+    _fields_ = [("freq_policy", C.c_int), ("max_band", C.c_int), ("cone_policy", C.c_int),
+                ("beta", C.c_float), ("delta", C.c_float)]
 
 
 class gf_camera(C.Structure):

@@ -37,11 +37,17 @@ def _as_tensor(x, device, dtype=torch.float32):
     return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device=device).contiguous()
 
 
-def lod(freq="all", max_band=7, cone="all"):
+def lod(freq="all", max_band=7, cone="all", beta=0.0, delta=0.5):
+    """LoD mask descriptor (strategy tables of App. B): freq in all, cutoff,
+    unif_cv, uniform, power, pow_cv, pow_cv_acc; cone in all, is, uniform,
+    thresh, thresh_uniform; beta the power-law shape, delta the alignment
+    threshold."""
     f = {"all": A.GF_FREQ_ALL, "cutoff": A.GF_FREQ_CUTOFF, "unif_cv": A.GF_FREQ_UNIF_CV,
-         "uniform": A.GF_FREQ_UNIFORM}[freq]
-    c = {"all": A.GF_CONE_ALL, "is": A.GF_CONE_IS, "uniform": A.GF_CONE_UNIFORM}[cone]
-    return A.gf_lod_desc(f, int(max_band), c)
+         "uniform": A.GF_FREQ_UNIFORM, "power": A.GF_FREQ_POWER, "pow_cv": A.GF_FREQ_POW_CV,
+         "pow_cv_acc": A.GF_FREQ_POW_CV_ACC}[freq]
+    c = {"all": A.GF_CONE_ALL, "is": A.GF_CONE_IS, "uniform": A.GF_CONE_UNIFORM,
+         "thresh": A.GF_CONE_THRESH, "thresh_uniform": A.GF_CONE_THRESH_UNIFORM}[cone]
+    return A.gf_lod_desc(f, int(max_band), c, float(beta), float(delta))
 
 
 def camera(eye, look_at, up, vfov_deg, width, height):

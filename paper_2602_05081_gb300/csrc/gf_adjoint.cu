@@ -31,7 +31,7 @@ struct BackArgs {
 // in the input frame, phase, weight), at offsets y = x - mu.
 struct PrimDeriv {
   float R[3][3];
-  float dR[4][3][3];  // dR/dq_m of the raw quaternion
+  float qh[4], iqn;    // unit quaternion (w, x, y, z) and 1/|q| of the raw one
   float s[3], is2[3], kin[3];
   float A, dAdw;
   float3 om;
@@ -40,29 +40,20 @@ struct PrimDeriv {
 
   __device__ void init(const BackArgs& B, const Prim& P, int64_t i) {
     float q[4];
+#pragma unroll
     for (int k = 0; k < 4; ++k) q[k] = B.quat[4 * i + k];
     const float qn = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-    const float qh[4] = {q[0] / qn, q[1] / qn, q[2] / qn, q[3] / qn};
+    iqn = 1.f / qn;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) qh[k] = q[k] * iqn;
     const float qw = qh[0], qx = qh[1], qy = qh[2], qz = qh[3];
-    const float Rm[3][3] = {{1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy)},
-                            {2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx)},
-                            {2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)}};
-    // dR/d(qhat_l), l = w, x, y, z
-    const float dRh[4][3][3] = {
-        {{0.f, -2.f * qz, 2.f * qy}, {2.f * qz, 0.f, -2.f * qx}, {-2.f * qy, 2.f * qx, 0.f}},
-        {{0.f, 2.f * qy, 2.f * qz}, {2.f * qy, -4.f * qx, -2.f * qw}, {2.f * qz, 2.f * qw, -4.f * qx}},
-        {{-4.f * qy, 2.f * qx, 2.f * qw}, {2.f * qx, 0.f, 2.f * qz}, {-2.f * qw, 2.f * qz, -4.f * qy}},
-        {{-4.f * qz, -2.f * qw, 2.f * qx}, {2.f * qw, -4.f * qz, 2.f * qy}, {2.f * qx, 2.f * qy, 0.f}}};
-    for (int a = 0; a < 3; ++a)
-      for (int k = 0; k < 3; ++k) R[a][k] = Rm[a][k];
-    // d qhat_l / d q_m = (delta_lm - qhat_l qhat_m) / |q|
-    for (int m = 0; m < 4; ++m)
-      for (int a = 0; a < 3; ++a)
-        for (int k = 0; k < 3; ++k) {
-          float acc = 0.f;
-          for (int l = 0; l < 4; ++l) acc += dRh[l][a][k] * ((l == m ? 1.f : 0.f) - qh[l] * qh[m]);
-          dR[m][a][k] = acc / qn;
-        }
+    R[0][0] = 1.f - 2.f * (qy * qy + qz * qz); R[0][1] = 2.f * (qx * qy - qw * qz);
+    R[0][2] = 2.f * (qx * qz + qw * qy);
+    R[1][0] = 2.f * (qx * qy + qw * qz); R[1][1] = 1.f - 2.f * (qx * qx + qz * qz);
+    R[1][2] = 2.f * (qy * qz - qw * qx);
+    R[2][0] = 2.f * (qx * qz - qw * qy); R[2][1] = 2.f * (qy * qz + qw * qx);
+    R[2][2] = 1.f - 2.f * (qx * qx + qy * qy);
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
       s[k] = expf(B.ls[3 * i + k]);
       is2[k] = 1.f / (s[k] * s[k]);
@@ -79,6 +70,7 @@ struct PrimDeriv {
   // value g at y; d[15] = dg/dparam; dq[10] = dq/dparam (mu, quaternion, log scale)
   __device__ float at(const float y[3], float d[15], float dq[10]) const {
     float z[3];
+#pragma unroll
     for (int k = 0; k < 3; ++k) z[k] = R[0][k] * y[0] + R[1][k] * y[1] + R[2][k] * y[2];
     const float qq = z[0] * z[0] * is2[0] + z[1] * z[1] * is2[1] + z[2] * z[2] * is2[2];
     const float env = expf(-0.5f * qq);
@@ -86,33 +78,60 @@ struct PrimDeriv {
     float sn, cs;
     sincosf(th, &sn, &cs);
     float dth[15], dA[15];
+#pragma unroll
     for (int r = 0; r < 15; ++r) {
       dth[r] = 0.f;
       dA[r] = 0.f;
     }
+#pragma unroll
     for (int a = 0; a < 3; ++a)
       dq[a] = -2.f * (R[a][0] * z[0] * is2[0] + R[a][1] * z[1] * is2[1] + R[a][2] * z[2] * is2[2]);
     dth[0] = -om.x;
     dth[1] = -om.y;
     dth[2] = -om.z;
+    // dz/d(qhat_l) = (dR/d qhat_l)^T y, written out from R(qhat); then through
+    // qhat = q/|q|: dz/dq_m = (g_m - qhat_m sum_l qhat_l g_l) / |q|
+    const float w = qh[0], x = qh[1], yq = qh[2], zq = qh[3];
+    const float y0 = y[0], y1 = y[1], y2 = y[2];
+    float g[4][3];
+    g[0][0] = 2.f * (zq * y1 - yq * y2);
+    g[0][1] = 2.f * (-zq * y0 + x * y2);
+    g[0][2] = 2.f * (yq * y0 - x * y1);
+    g[1][0] = 2.f * (yq * y1 + zq * y2);
+    g[1][1] = 2.f * (yq * y0 - 2.f * x * y1 + w * y2);
+    g[1][2] = 2.f * (zq * y0 - w * y1 - 2.f * x * y2);
+    g[2][0] = 2.f * (-2.f * yq * y0 + x * y1 - w * y2);
+    g[2][1] = 2.f * (x * y0 + zq * y2);
+    g[2][2] = 2.f * (w * y0 + zq * y1 - 2.f * yq * y2);
+    g[3][0] = 2.f * (-2.f * zq * y0 + w * y1 + x * y2);
+    g[3][1] = 2.f * (-w * y0 - 2.f * zq * y1 + yq * y2);
+    g[3][2] = 2.f * (x * y0 + yq * y1);
+    float sg[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sg[k] = w * g[0][k] + x * g[1][k] + yq * g[2][k] + zq * g[3][k];
+#pragma unroll
     for (int m = 0; m < 4; ++m) {
       float dqm = 0.f, dthm = 0.f;
+#pragma unroll
       for (int k = 0; k < 3; ++k) {
-        const float dz = dR[m][0][k] * y[0] + dR[m][1][k] * y[1] + dR[m][2][k] * y[2];
+        const float dz = (g[m][k] - qh[m] * sg[k]) * iqn;
         dqm += 2.f * z[k] * dz * is2[k];
         if (local) dthm += kin[k] / s[k] * dz;
       }
       dq[3 + m] = dqm;
       dth[3 + m] = dthm;
     }
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
       dq[7 + k] = -2.f * z[k] * z[k] * is2[k];
       if (local) dth[7 + k] = -kin[k] * z[k] / s[k];
       if (normalized) dA[7 + k] = -A;
     }
+#pragma unroll
     for (int k = 0; k < 3; ++k) dth[10 + k] = local ? z[k] / s[k] : y[k];
     dth[13] = 1.f;
     dA[14] = dAdw;
+#pragma unroll
     for (int r = 0; r < 15; ++r) {
       const float dqr = r < 10 ? dq[r] : 0.f;
       d[r] = A * env * (-0.5f * dqr * cs - sn * dth[r]) + dA[r] * env * cs;
@@ -290,12 +309,61 @@ cudaError_t launch_tomo_backward(const Field& F, const PathParams& P, const floa
 // the derivative passes: nothing per path is stored.
 // ---------------------------------------------------------------------------
 
+// The primitives whose chords cross a ray under its mask, gathered by one
+// traversal; the replay passes then visit the list instead of the tree.
+constexpr int kRayList = 512;
+struct RayList {
+  int* idx;  // this thread's slice, kRayList entries
+  int n;     // listed primitives; > kRayList: overflow, traverse instead
+  __device__ bool ok() const { return n <= kRayList; }
+};
+
+struct ListLeaf {
+  const DevField* F;
+  const Mask* M;
+  float3 o, v;
+  RayList* L;
+  __device__ void operator()(int j) {
+    const Mask& Mk = *M;
+    Chord ch;
+    float w;
+    if (!prim_chord(*F, j, o, v, 0.f, INFINITY, [&](uint32_t c) { return mask_weight(Mk, c); }, w, ch))
+      return;
+    if (L->n < kRayList) L->idx[L->n] = j;
+    ++L->n;
+  }
+};
+
+__device__ __forceinline__ void gather_list(const DevField& F, const Mask& M, float3 o, float3 v,
+                                            RayList& L, Counters& cnt) {
+  L.n = 0;
+  const float3 inv = safe_inv(v);
+  float t0, t1;
+  if (M.bits == 0ull || !scene_span(F, o, inv, 0.f, INFINITY, t0, t1)) return;
+  ListLeaf leaf{&F, &M, o, v, &L};
+  SpanTest test{t0, t1};
+  traverse_ray(F, o, inv, M.bits, test, leaf, cnt.nodes, cnt.leaves);
+}
+
+// every primitive of the list, or a traversal with `test` when it overflowed
+template <class Test, class Leaf>
+__device__ __forceinline__ void visit(const DevField& F, const RayList* L, float3 o, float3 inv,
+                                      unsigned long long mask, Test& test, Leaf& leaf,
+                                      Counters& cnt) {
+  if (L && L->ok()) {
+    for (int k = 0; k < L->n; ++k) leaf(L->idx[k]);
+    cnt.leaves += (unsigned long long)L->n;
+  } else {
+    traverse_ray(F, o, inv, mask, test, leaf, cnt.nodes, cnt.leaves);
+  }
+}
+
 // Windows of kPts tentative points, in t order, with kappa and kappa_bar
 // (the windows of track()); win(B, n, kap, kb) returns false to stop.
 template <class Win>
 __device__ void for_windows(const DevField& F, const Mask& M, float3 o, float3 v, uint64_t seed,
                             uint32_t ray, uint32_t word, const float* env, Counters& cnt,
-                            Win win) {
+                            const RayList* L, Win win) {
   const unsigned am = __activemask();
   const float3 inv = safe_inv(v);
   float t0 = 0.f, t1 = 0.f;
@@ -327,7 +395,7 @@ __device__ void for_windows(const DevField& F, const Mask& M, float3 o, float3 v
     cl.word = word;
     cl.env = env;
     CollectTest ctest{&cl.ta, &cl.bound};
-    traverse_ray(F, o, inv, M.bits, ctest, cl, cnt.nodes, cnt.leaves);
+    visit(F, L, o, inv, M.bits, ctest, cl, cnt);
     int n = 0;
 #pragma unroll
     for (int i = 0; i < kPts; ++i) n += B.t[i] < INFINITY ? 1 : 0;
@@ -351,7 +419,7 @@ __device__ void for_windows(const DevField& F, const Mask& M, float3 o, float3 v
       al.kb[i] = 0.f;
     }
     PointTest ptest{&B, n};
-    traverse_ray(F, o, inv, M.bits, ptest, al, cnt.nodes, cnt.leaves);
+    visit(F, L, o, inv, M.bits, ptest, al, cnt);
     cnt.evals += al.nev;
     if (!win(B, n, al.kap, al.kb) || n < kPts) {
       more = false;
@@ -402,14 +470,15 @@ struct RadScatter {
 
 __device__ __forceinline__ void scatter_window(const DevField& F, const BackArgs& Bk, const Mask& M,
                                                float3 o, float3 v, const PointBuf& P,
-                                               const float* coef, int n, Counters& cnt) {
+                                               const float* coef, int n, const RayList* L,
+                                               Counters& cnt) {
   bool any = false;
 #pragma unroll
   for (int i = 0; i < kPts; ++i) any |= i < n && coef[i] != 0.f;
   if (!any) return;
   RadScatter rs{&F, &Bk, &M, o, v, &P, coef, n};
   PointTest ptest{&P, n};
-  traverse_ray(F, o, safe_inv(v), M.bits, ptest, rs, cnt.nodes, cnt.leaves);
+  visit(F, L, o, safe_inv(v), M.bits, ptest, rs, cnt);
 }
 
 struct RadSmem {
@@ -418,7 +487,9 @@ struct RadSmem {
 
 __global__ void __launch_bounds__(kBackBlock)
     k_radiance_backward(const __grid_constant__ DevField F, const PathParams P, const BackArgs Bk,
-                        const float* dLdI, int* counter) {
+                        const float* dLdI, int* counter, int* lists) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  RayList Lc{lists + tid * 2 * kRayList, 0}, Ln{lists + tid * 2 * kRayList + kRayList, 0};
   __shared__ RadSmem sm;
   if (threadIdx.x < 8) sm.env[threadIdx.x] = F.env[threadIdx.x];
   __syncthreads();
@@ -444,10 +515,11 @@ __global__ void __launch_bounds__(kBackBlock)
       cnt.rays += 1;
       const Mask M = sample_mask(F, P.lod, v, P.seed, pix, (uint32_t)s, 0, TAG_MASK);
       const uint32_t wt = stream_word((uint32_t)s, 0, TAG_TRACK);
+      gather_list(F, M, o, v, Lc, cnt);
       // pass 1: weights, their sum and the reservoir draw
       float Pr = 1.f, S = 0.f, pjs = 0.f, tjs = 0.f;
       int idx = 0, js = -1;
-      for_windows(F, M, o, v, P.seed, pix, wt, sm.env, cnt,
+      for_windows(F, M, o, v, P.seed, pix, wt, sm.env, cnt, &Lc,
                   [&](const PointBuf& B, int n, const float* kap, const float* kb) {
                     for (int i = 0; i < n; ++i) {
                       const float p = kb[i] > 0.f ? fmaxf(kap[i], 0.f) / kb[i] : 0.f;
@@ -469,12 +541,19 @@ __global__ void __launch_bounds__(kBackBlock)
       const Mask Mn = sample_mask(F, P.lod_nee, P.light, P.seed, pix, (uint32_t)s, 0, TAG_NEE_MASK);
       const uint32_t wn = stream_word((uint32_t)s, 0, TAG_NEE);
       cnt.rays += 1;
-      const float Tl = track<false>(F, Mn, x, P.light, 0.f, INFINITY, true, P.seed, pix, wn,
-                                    sm.env, cnt, nullptr);
+      gather_list(F, Mn, x, P.light, Ln, cnt);
+      // ratio tracking of the NEE ray, T = prod (1 - kappa+/kappa_bar)
+      float Tl = 1.f;
+      for_windows(F, Mn, x, P.light, P.seed, pix, wn, sm.env, cnt, &Ln,
+                  [&](const PointBuf& B, int n, const float* kap, const float* kb) {
+                    for (int i = 0; i < n; ++i)
+                      if (kb[i] > 0.f) Tl *= 1.f - fmaxf(kap[i], 0.f) / kb[i];
+                    return true;
+                  });
       const float G = E * Tl;
       // pass 2: camera points 0..js
       idx = 0;
-      for_windows(F, M, o, v, P.seed, pix, wt, sm.env, cnt,
+      for_windows(F, M, o, v, P.seed, pix, wt, sm.env, cnt, &Lc,
                   [&](const PointBuf& B, int n, const float* kap, const float* kb) {
                     float coef[kPts];
 #pragma unroll
@@ -487,13 +566,13 @@ __global__ void __launch_bounds__(kBackBlock)
                         coef[i] = base * c / kb[i];
                       }
                     }
-                    scatter_window(F, Bk, M, o, v, B, coef, n, cnt);
+                    scatter_window(F, Bk, M, o, v, B, coef, n, &Lc, cnt);
                     idx += n;
                     return idx <= js;
                   });
       // pass 3: NEE points
       if (Tl > 0.f) {
-        for_windows(F, Mn, x, P.light, P.seed, pix, wn, sm.env, cnt,
+        for_windows(F, Mn, x, P.light, P.seed, pix, wn, sm.env, cnt, &Ln,
                     [&](const PointBuf& B, int n, const float* kap, const float* kb) {
                       float coef[kPts];
 #pragma unroll
@@ -504,7 +583,7 @@ __global__ void __launch_bounds__(kBackBlock)
                           if (1.f - q > 0.f) coef[i] = -base * S * E * Tl / (1.f - q) / kb[i];
                         }
                       }
-                      scatter_window(F, Bk, Mn, x, P.light, B, coef, n, cnt);
+                      scatter_window(F, Bk, Mn, x, P.light, B, coef, n, &Ln, cnt);
                       return true;
                     });
       }
@@ -541,7 +620,17 @@ cudaError_t launch_radiance_backward(const Field& F, const PathParams& P, const 
   const int64_t need = (tiles + kBackBlock / 32 - 1) / (kBackBlock / 32);
   int64_t g = (int64_t)F.ctx.sm_count * per_sm;
   if (need < g) g = need;
-  k_radiance_backward<<<(unsigned)(g < 1 ? 1 : g), kBackBlock, 0, s>>>(F.dev, P, B, dLdI, F.counter);
+  if (g < 1) g = 1;
+  // per-thread primitive lists of the camera and NEE rays (grown on demand)
+  const size_t lbytes = (size_t)g * kBackBlock * 2 * kRayList * sizeof(int);
+  if (F.rlist_bytes < lbytes) {
+    if (F.rlist) cudaFree(F.rlist);
+    F.rlist = nullptr;
+    F.rlist_bytes = 0;
+    if ((e = cudaMalloc((void**)&F.rlist, lbytes)) != cudaSuccess) return e;
+    F.rlist_bytes = lbytes;
+  }
+  k_radiance_backward<<<(unsigned)g, kBackBlock, 0, s>>>(F.dev, P, B, dLdI, F.counter, F.rlist);
   return cudaGetLastError();
 }
 

@@ -112,8 +112,13 @@ gf_status ensure_stage(Field& F, size_t bytes) {
 namespace gf {
 
 bool lod_ok(const gf_lod_desc* l) {
-  return l && l->freq_policy >= 0 && l->freq_policy <= 3 && l->cone_policy >= 0 &&
-         l->cone_policy <= 2 && l->max_band >= 0 && l->max_band <= 7;
+  return l && l->freq_policy >= 0 && l->freq_policy <= 6 && l->cone_policy >= 0 &&
+         l->cone_policy <= 4 && l->max_band >= 0 && l->max_band <= 7 && l->beta >= 0.f &&
+         l->beta < 1.f && l->delta >= 0.f && l->delta <= 1.f;
+}
+
+LodDev lod_dev(const gf_lod_desc& l) {
+  return LodDev{l.freq_policy, l.max_band, l.cone_policy, l.beta, l.delta};
 }
 
 gf_status camera_params(const gf_camera* c, const gf_render_opts* o, uint64_t seed,
@@ -168,7 +173,7 @@ namespace {
 void free_field(Field& F) {
   void* ptrs[] = {F.p_mu, F.p_quat, F.p_ls, F.p_om, F.p_ph, F.p_w, F.rec_orig, F.box_orig,
                   F.kw_orig, F.rec, F.rec16, F.nodes, F.nodes4, F.sorted_orig, F.labels, F.err,
-                  F.stats, F.counter, F.cell_acc, F.stage, F.wscratch, F.acc64, F.gl};
+                  F.stats, F.counter, F.cell_acc, F.stage, F.wscratch, F.acc64, F.rlist, F.gl};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -375,9 +380,9 @@ gf_status gf_build_bvh(gf_field* h, gf_stream stream) {
 
 gf_status gf_set_lod_mask(gf_field* h, const gf_lod_desc* primary, const gf_lod_desc* nee) {
   if (!h || !lod_ok(primary) || (nee && !lod_ok(nee))) return fail(GF_EINVAL, "bad lod descriptor");
-  h->f.lod = LodDev{primary->freq_policy, primary->max_band, primary->cone_policy};
+  h->f.lod = lod_dev(*primary);
   const gf_lod_desc* n2 = nee ? nee : primary;
-  h->f.lod_nee = LodDev{n2->freq_policy, n2->max_band, n2->cone_policy};
+  h->f.lod_nee = lod_dev(*n2);
   return GF_OK;
 }
 

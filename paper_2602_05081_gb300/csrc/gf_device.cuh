@@ -54,6 +54,8 @@ struct __align__(16) Node4 {
 
 struct LodDev {
   int freq_policy, max_band, cone_policy;
+  float beta;   // power-law shape of the band choice, [0, 1)
+  float delta;  // alignment threshold of the cone choice, [0, 1]
 };
 
 // Everything a kernel needs to read a packed field; passed by value.

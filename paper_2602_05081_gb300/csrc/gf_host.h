@@ -73,7 +73,7 @@ struct Field {
   bool built = false;
   float mu_lo[3] = {0, 0, 0}, mu_hi[3] = {0, 0, 0};  // box of the means (from the build)
   DevField dev{};
-  LodDev lod{0, 7, 0}, lod_nee{0, 7, 0};
+  LodDev lod{0, 7, 0, 0.f, 0.f}, lod_nee{0, 7, 0, 0.f, 0.f};
   // staging for host buffers
   void* stage = nullptr;
   size_t stage_bytes = 0;
@@ -83,6 +83,9 @@ struct Field {
   // fixed-point pixel sums of the scattering renderer (grows on demand)
   mutable unsigned long long* acc64 = nullptr;
   mutable size_t acc_bytes = 0;
+  // per-thread primitive lists of the radiance adjoint (grows on demand)
+  mutable int* rlist = nullptr;
+  mutable size_t rlist_bytes = 0;
 };
 
 // Render server batch (one launch of k_render_server): items of many requests
@@ -132,6 +135,7 @@ gf_status report(gf_status s, const std::string& msg);
 gf_status camera_params(const gf_camera* c, const gf_render_opts* o, uint64_t seed, const Field& F,
                         PathParams& P);
 bool lod_ok(const gf_lod_desc* l);
+LodDev lod_dev(const gf_lod_desc& l);
 
 }  // namespace gf
 

@@ -492,8 +492,8 @@ gf_status gf_server_submit(gf_server* S, const gf_request* rq, uint64_t* ticket)
   auto r = std::make_unique<Req>();
   gf_status s = camera_params(&rq->camera, &rq->opts, rq->seed, *S->fields[rq->asset], r->dev.P);
   if (s != GF_OK) return s;
-  r->dev.P.lod = LodDev{rq->lod.freq_policy, rq->lod.max_band, rq->lod.cone_policy};
-  r->dev.P.lod_nee = LodDev{rq->lod_nee.freq_policy, rq->lod_nee.max_band, rq->lod_nee.cone_policy};
+  r->dev.P.lod = lod_dev(rq->lod);
+  r->dev.P.lod_nee = lod_dev(rq->lod_nee);
   r->dev.asset = rq->asset;
   r->r = *rq;
   r->npix = (int64_t)rq->camera.width * rq->camera.height;

@@ -78,10 +78,20 @@ __device__ __forceinline__ void flush_counters(const DevField& F, Counters& c, u
 // either every occupied cone is selected with one weight or exactly one cone
 // is, so a mask is its cell bits plus one weight per band.
 // ---------------------------------------------------------------------------
+// A drawn mask: cell bits, the weight of each band, and per band one cone
+// whose weight is the band's times a factor (threshold + uniform draws one
+// bin above the threshold with weight N_above): byte b of cx is
+// cone | factor << 3, 0 for none.
 struct Mask {
   unsigned long long bits;
   float bw[8];
+  uint32_t cx[2] = {0u, 0u};  // no cone with an extra factor unless a draw sets one
 };
+
+__device__ __forceinline__ float cone_factor(const uint32_t cx[2], uint32_t cell, int b) {
+  const uint32_t e = (cx[b >> 2] >> (8 * (b & 3))) & 0xFFu;
+  return (e != 0u && ((cell - 1u) & 7u) == (e & 7u)) ? (float)(e >> 3) : 1.f;
+}
 
 __device__ __forceinline__ float mask_weight(const Mask& m, uint32_t cell) {
   if (!(m.bits >> cell & 1ull)) return 0.f;
@@ -89,7 +99,7 @@ __device__ __forceinline__ float mask_weight(const Mask& m, uint32_t cell) {
   float w = m.bw[0];
 #pragma unroll
   for (int k = 1; k < 8; ++k) w = (b == k) ? m.bw[k] : w;
-  return w;
+  return b == 0 ? w : w * cone_factor(m.cx, cell, b);
 }
 
 __device__ __forceinline__ unsigned band_cells8(unsigned long long occ, int b) {
@@ -99,13 +109,27 @@ __device__ __forceinline__ unsigned band_cells8(unsigned long long occ, int b) {
 __device__ __forceinline__ int nth_bit(unsigned m, int j) { return (int)__fns(m, 0, j + 1); }
 
 __host__ __device__ __forceinline__ bool lod_is_deterministic(const LodDev& L) {
-  return (L.freq_policy == 0 || L.freq_policy == 1) && L.cone_policy == 0;
+  return (L.freq_policy == 0 || L.freq_policy == 1) && (L.cone_policy == 0 || L.cone_policy == 3);
+}
+
+// power-law level out of n (App. B): level j when (j/n)^(1-beta) <= x < ((j+1)/n)^(1-beta)
+__device__ __forceinline__ int power_level(float x, int n, float beta) {
+  const float e = 1.0f - beta;
+  int j = 0;
+  for (int k = 1; k < n; ++k) j += x >= powf((float)k / (float)n, e) ? 1 : 0;
+  return j;
+}
+__device__ __forceinline__ float power_prob(int j, int n, float beta) {
+  const float e = 1.0f - beta;
+  return powf((float)(j + 1) / (float)n, e) - powf((float)j / (float)n, e);
 }
 
 static __device__ Mask sample_mask(const DevField& F, const LodDev& L, float3 v, uint64_t seed,
                                    uint32_t ray, uint32_t sample, uint32_t bounce, uint32_t tag) {
   Mask M;
   M.bits = 0;
+  M.cx[0] = 0u;
+  M.cx[1] = 0u;
   const int maxb = L.freq_policy == 0 ? 7 : L.max_band;
   unsigned occ = 0;
 #pragma unroll
@@ -136,12 +160,44 @@ static __device__ Mask sample_mask(const DevField& F, const LodDev& L, float3 v,
         pickb = nth_bit(gab, (int)(((unsigned long long)x24 * (unsigned)G) >> 24));
         wb = (float)G;
       }
-    } else {
+    } else if (L.freq_policy == 3) {
       // one band out of P uniformly (weight P)
       const int Q = __popc(occ);
       if (Q > 0) {
         pickb = nth_bit(occ, (int)(((unsigned long long)x24 * (unsigned)Q) >> 24));
         wb = (float)Q;
+      }
+    } else if (L.freq_policy == 4) {
+      // power law over the P levels, weight 1/P(level)
+      const int Q = __popc(occ);
+      if (Q > 0) {
+        const int j = power_level(u01(x24 << 8), Q, L.beta);
+        pickb = nth_bit(occ, j);
+        wb = 1.0f / power_prob(j, Q, L.beta);
+      }
+    } else {
+      // Gaussians always (weight 1); power law over the G Gabor levels: one (5),
+      // or every level up to the drawn one, level j with weight 1/(1 - (j/G)^(1-beta)) (6)
+      if (occ & 1u) {
+        sel |= 1u;
+        bw[0] = 1.f;
+      }
+      const unsigned gab = occ & ~1u;
+      const int G = __popc(gab);
+      if (G > 0) {
+        const int k = power_level(u01(x24 << 8), G, L.beta);
+        if (L.freq_policy == 5) {
+          pickb = nth_bit(gab, k);
+          wb = 1.0f / power_prob(k, G, L.beta);
+        } else {
+          for (int j = 0; j <= k; ++j) {
+            const int b = nth_bit(gab, j);
+            sel |= 1u << b;
+            const float wj = 1.0f / (1.0f - powf((float)j / (float)G, 1.0f - L.beta));
+#pragma unroll
+            for (int q = 0; q < 8; ++q) bw[q] = (q == b) ? wj : bw[q];
+          }
+        }
       }
     }
     if (pickb >= 0) {
@@ -167,6 +223,39 @@ static __device__ Mask sample_mask(const DevField& F, const LodDev& L, float3 v,
     const int nc = __popc(cells);
     int k;
     float cf;
+    if (L.cone_policy == 3 || L.cone_policy == 4) {
+      // alignment a = |v . o| against delta (FP32): threshold culling keeps the
+      // bins with a <= delta, weight 1 (none: the least aligned bin);
+      // threshold + uniform keeps them and draws one of the N_above others,
+      // weight N_above
+      unsigned below = 0u, above = 0u;
+      int best = 0;
+      float abest = 2.f;
+#pragma unroll
+      for (int c = 0; c < kCones; ++c) {
+        if (!(cells >> c & 1u)) continue;
+        // no contraction: the same float operations as the oracle's decision
+        const float a = fabsf(__fadd_rn(__fadd_rn(__fmul_rn(v.x, F.axes[c][0]), __fmul_rn(v.y, F.axes[c][1])),
+                                        __fmul_rn(v.z, F.axes[c][2])));
+        if (a < abest) {
+          abest = a;
+          best = c;
+        }
+        if (a <= L.delta) below |= 1u << c;
+        else above |= 1u << c;
+      }
+      if (L.cone_policy == 3) {
+        if (below == 0u) below = 1u << best;
+      } else if (above != 0u) {
+        const int na = __popc(above);
+        const int c = nth_bit(above, (int)(((unsigned long long)(y >> 8) * (unsigned)na) >> 24));
+        below |= 1u << c;
+        M.cx[b >> 2] |= ((uint32_t)c | ((uint32_t)na << 3)) << (8 * (b & 3));
+      }
+      M.bw[b] = bw[b];
+      M.bits |= (unsigned long long)below << (1 + kCones * (b - 1));
+      continue;
+    }
     if (L.cone_policy == 2) {
       // one cone uniformly, weight K
       k = nth_bit(cells, (int)(((unsigned long long)(y >> 8) * (unsigned)nc) >> 24));

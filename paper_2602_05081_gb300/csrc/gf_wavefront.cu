@@ -35,7 +35,7 @@ constexpr int kPK = 8;          // tentative points per lane and window
 constexpr int kSlotCh = 256;    // stored chords per lane and window (global scratch)
 constexpr int kRecF4 = 2;       // float4s per stored chord record
 
-// One slot per lane, 61 words: an odd stride keeps same-field accesses of the
+// One slot per lane, 63 words: an odd stride keeps same-field accesses of the
 // 32 slots in distinct shared-memory banks.
 struct LaneRay {
   float o[3], v[3], inv[3];
@@ -44,6 +44,7 @@ struct LaneRay {
   uint32_t seed_lo, seed_hi;    // Philox key of the path's render
   int asset;                    // field of the path
   float bw[8];                  // LoD band weights
+  uint32_t cx[2];               // per band: one cone with an extra weight factor (Mask::cx)
   uint32_t mask_lo, mask_hi;    // LoD cell bits
   int npts;                     // points emitted in the window (may exceed kPK)
   int nch;                      // chords stored for the window (may exceed kSlotCh)
@@ -61,7 +62,7 @@ struct ChordItem {
 // depth first (one entry per step, net growth <= 3 per tree level), so the
 // stack holds a full step plus 40 levels of descent.  Four blocks of four
 // warps fit one SM.
-constexpr int kWStack = 848;
+constexpr int kWStack = 768;
 constexpr int kStackMargin = 248;
 struct WarpQ {
   LaneRay r[32];
@@ -82,7 +83,7 @@ __device__ __forceinline__ unsigned long long slot_mask(const LaneRay& R) {
 __device__ __forceinline__ float ray_weight(const LaneRay& R, uint32_t cell) {
   if (!(slot_mask(R) >> cell & 1ull)) return 0.f;
   const int b = cell == 0 ? 0 : (int)((cell - 1u) >> 3) + 1;
-  return R.bw[b];
+  return b == 0 ? R.bw[0] : R.bw[b] * cone_factor(R.cx, cell, b);
 }
 
 // byte k of x as a float, exactly: 0x4B0000xx is 2^23 + xx
@@ -369,6 +370,8 @@ __device__ __forceinline__ void set_slot(LaneRay& R, float3 o, float3 v, const M
   R.mask_hi = (uint32_t)(m.bits >> 32);
 #pragma unroll
   for (int k = 0; k < 8; ++k) R.bw[k] = m.bw[k];
+  R.cx[0] = m.cx[0];
+  R.cx[1] = m.cx[1];
 }
 
 // Start a tracking ray: returns false if it misses the scene (nothing to do).

@@ -166,6 +166,46 @@ def test_deterministic_transmittance_lod_masks(api, ctx):
     assert np.abs(tau.cpu().numpy() - tau_ref).max() <= 2e-5 * max(1.0, np.abs(tau_ref).max())
 
 
+@pytest.mark.parametrize("freq,cone,beta,delta", [("power", "all", 0.3, 0.5),
+                                                  ("pow_cv", "uniform", 0.5, 0.5),
+                                                  ("pow_cv_acc", "is", 0.2, 0.5),
+                                                  ("unif_cv", "thresh", 0.0, 0.45),
+                                                  ("pow_cv_acc", "thresh_uniform", 0.6, 0.4)])
+def test_deterministic_transmittance_strategy_tables(api, ctx, freq, cone, beta, delta):
+    """Power-law band choices and threshold cone choices (App. B tables): optical
+    depth averaged over spp mask draws equals the oracle's under the same Philox
+    draws; masks decided in FP32 on both sides."""
+    codes_f = {"power": 4, "pow_cv": 5, "pow_cv_acc": 6, "unif_cv": 2}
+    codes_c = {"all": 0, "is": 1, "uniform": 2, "thresh": 3, "thresh_uniform": 4}
+    p = synth.octave_field(21000, 5, seed=4)
+    f = api.Field(ctx, p)
+    orc = oracle.Field(p, omega_frame="local")
+    o, d, tr = synth.random_rays(96, seed=6)
+    f.set_lod(api.lod(freq, 7, cone, beta, delta))
+    T, tau = f.transmittance(_t(o), _t(d), _t(tr), mode="det", spp=16, seed=13)
+    f.sync()
+    lo = oracle.Lod(codes_f[freq], 7, codes_c[cone], beta, delta)
+    _, tau_ref = orc.transmittance(o, d, tr, mode="det", spp=16, seed=13, lod=lo)
+    assert np.abs(tau.cpu().numpy() - tau_ref).max() <= 2e-5 * max(1.0, np.abs(tau_ref).max())
+
+
+def test_single_scatter_strategy_tables_parity(api, ctx):
+    """Scattering renderer under power-law accumulating bands and threshold +
+    uniform cones (per-cone weights inside a band) against the oracle."""
+    p = synth.octave_field(3000, 4, seed=8)
+    f = api.Field(ctx, p)
+    orc = oracle.Field(p, omega_frame="local")
+    cg, co = _cam_pair(api, 24, 24)
+    f.set_lod(api.lod("pow_cv_acc", 7, "thresh_uniform", 0.4, 0.45),
+              api.lod("cutoff", 1, "thresh", 0.0, 0.5))
+    lo = oracle.Lod(6, 7, 4, 0.4, 0.45)
+    ln = oracle.Lod(1, 1, 3, 0.0, 0.5)
+    diff, noise, ref = _mc_parity(api, f, orc, cg, co, api.render_opts("scatter", 8, 1),
+                                  oracle.render_opts("scatter", 8, 1), 2, lo, ln)
+    assert ref.max() > 1e-3
+    assert diff <= 0.01 * noise, (diff, noise)
+
+
 def test_ratio_tracking_same_streams(api, ctx):
     """1 spp ratio tracking: each ray's estimate equals the oracle's under the
     shared Philox streams, except for rare FP32 decision flips."""
@@ -311,8 +351,11 @@ def test_autograd_function_uses_the_adjoint(api, ctx):
     f = api.Field(ctx, p)
     g = f.render_backward(cg, api.render_opts("tomo", 1), 3, (2 * img).detach().contiguous())
     parts = api.split_grad(g, 64)
+    # float atomics add the per-ray contributions in a varying order: compare to
+    # the gradient's own scale
     for k in ts:
-        assert torch.allclose(ts[k].grad, parts[k].view_as(ts[k].grad), rtol=1e-5, atol=1e-6)
+        ref = parts[k].view_as(ts[k].grad)
+        assert torch.allclose(ts[k].grad, ref, rtol=1e-4, atol=1e-5 * float(ref.abs().max())), k
 
 
 def test_radiance_gradient_matches_oracle(api, ctx):
@@ -362,7 +405,8 @@ def test_radiance_autograd_function_uses_the_adjoint(api, ctx):
     g = f.render_backward(cg, api.render_opts("scatter", 4, 1), 4, (2 * img).detach().contiguous())
     parts = api.split_grad(g, 600)
     for k in ts:
-        assert torch.allclose(ts[k].grad, parts[k].view_as(ts[k].grad), rtol=1e-4, atol=1e-6)
+        ref = parts[k].view_as(ts[k].grad)
+        assert torch.allclose(ts[k].grad, ref, rtol=1e-4, atol=1e-5 * float(ref.abs().max())), k
     from paper_2602_05081_gb300 import _abi
     with pytest.raises(_abi.GfError) as e:
         f.render_backward(cg, api.render_opts("scatter", 4, 2), 4, (2 * img).detach().contiguous())
