@@ -204,6 +204,57 @@ struct BackLeaf {
   }
 };
 
+// The primitives whose chords cross a ray under its mask, gathered by one
+// traversal; the replay passes then visit the list instead of the tree.
+constexpr int kRayList = 1024;
+struct RayList {
+  int* idx;    // this thread's first entry; entry k at idx[k * stride] (a warp's
+  int stride;  // lanes hold neighbouring words: coalesced)
+  int n;       // listed primitives; > kRayList: overflow, traverse instead
+  __device__ bool ok() const { return n <= kRayList; }
+  __device__ int at(int k) const { return idx[(int64_t)k * stride]; }
+};
+
+struct ListLeaf {
+  const DevField* F;
+  const Mask* M;
+  float3 o, v;
+  RayList* L;
+  __device__ void operator()(int j) {
+    const Mask& Mk = *M;
+    Chord ch;
+    float w;
+    if (!prim_chord(*F, j, o, v, 0.f, INFINITY, [&](uint32_t c) { return mask_weight(Mk, c); }, w, ch))
+      return;
+    if (L->n < kRayList) L->idx[(int64_t)L->n * L->stride] = j;
+    ++L->n;
+  }
+};
+
+__device__ __forceinline__ void gather_list(const DevField& F, const Mask& M, float3 o, float3 v,
+                                            RayList& L, Counters& cnt) {
+  L.n = 0;
+  const float3 inv = safe_inv(v);
+  float t0, t1;
+  if (M.bits == 0ull || !scene_span(F, o, inv, 0.f, INFINITY, t0, t1)) return;
+  ListLeaf leaf{&F, &M, o, v, &L};
+  SpanTest test{t0, t1};
+  traverse_ray(F, o, inv, M.bits, test, leaf, cnt.nodes, cnt.leaves);
+}
+
+// every primitive of the list, or a traversal with `test` when it overflowed
+template <class Test, class Leaf>
+__device__ __forceinline__ void visit(const DevField& F, const RayList* L, float3 o, float3 inv,
+                                      unsigned long long mask, Test& test, Leaf& leaf,
+                                      Counters& cnt) {
+  if (L && L->ok()) {
+    for (int k = 0; k < L->n; ++k) leaf(L->at(k));
+    cnt.leaves += (unsigned long long)L->n;
+  } else {
+    traverse_ray(F, o, inv, mask, test, leaf, cnt.nodes, cnt.leaves);
+  }
+}
+
 constexpr int kBackBlock = 128;
 struct BackSmem {
   float glx[kGLTotal], glw[kGLTotal];
@@ -240,10 +291,13 @@ __global__ void __launch_bounds__(kBackBlock)
       float3 o, v;
       camera_ray(P.cam, P.seed, px, py, s, o, v);
       cnt.rays += 1;
-      const float tau = det_tau(F, all, o, v, 0.f, INFINITY, sm.glx, sm.glw, cnt);
       const float3 inv = safe_inv(v);
       float t0, t1;
       if (!scene_span(F, o, inv, 0.f, INFINITY, t0, t1)) continue;
+      // forward optical depth, then the adjoint pass (two traversals: a primitive
+      // list measured slower here, the Gauss-Legendre work dominating)
+      const float tau = det_tau(F, all, o, v, 0.f, INFINITY, sm.glx, sm.glw, cnt);
+      SpanTest test{t0, t1};
       BackLeaf leaf;
       leaf.F = &F;
       leaf.B = &Bk;
@@ -254,12 +308,23 @@ __global__ void __launch_bounds__(kBackBlock)
       leaf.dLdtau = -gI * expf(-tau) / (float)P.spp;
       leaf.glx = sm.glx;
       leaf.glw = sm.glw;
-      SpanTest test{t0, t1};
       traverse_ray(F, o, inv, F.occupied, test, leaf, cnt.nodes, cnt.leaves);
       cnt.evals += leaf.nev;
     }
   }
   flush_counters(F, cnt, lane);
+}
+
+// per-thread primitive lists of the adjoint kernels (2 per thread, grown on demand)
+static cudaError_t ensure_lists(const Field& F, int64_t threads) {
+  const size_t lbytes = (size_t)threads * 2 * kRayList * sizeof(int);
+  if (F.rlist_bytes >= lbytes) return cudaSuccess;
+  if (F.rlist) cudaFree(F.rlist);
+  F.rlist = nullptr;
+  F.rlist_bytes = 0;
+  const cudaError_t e = cudaMalloc((void**)&F.rlist, lbytes);
+  if (e == cudaSuccess) F.rlist_bytes = lbytes;
+  return e;
 }
 
 cudaError_t launch_tomo_backward(const Field& F, const PathParams& P, const float* dLdI,
@@ -284,7 +349,8 @@ cudaError_t launch_tomo_backward(const Field& F, const PathParams& P, const floa
   const int64_t need = (tiles + kBackBlock / 32 - 1) / (kBackBlock / 32);
   int64_t g = (int64_t)F.ctx.sm_count * per_sm;
   if (need < g) g = need;
-  k_tomo_backward<<<(unsigned)(g < 1 ? 1 : g), kBackBlock, 0, s>>>(F.dev, P, B, dLdI, F.counter);
+  if (g < 1) g = 1;
+  k_tomo_backward<<<(unsigned)g, kBackBlock, 0, s>>>(F.dev, P, B, dLdI, F.counter);
   return cudaGetLastError();
 }
 
@@ -308,55 +374,6 @@ cudaError_t launch_tomo_backward(const Field& F, const PathParams& P, const floa
 // the point.  Each ray is re-tracked (same Philox streams, same windows) for
 // the derivative passes: nothing per path is stored.
 // ---------------------------------------------------------------------------
-
-// The primitives whose chords cross a ray under its mask, gathered by one
-// traversal; the replay passes then visit the list instead of the tree.
-constexpr int kRayList = 512;
-struct RayList {
-  int* idx;  // this thread's slice, kRayList entries
-  int n;     // listed primitives; > kRayList: overflow, traverse instead
-  __device__ bool ok() const { return n <= kRayList; }
-};
-
-struct ListLeaf {
-  const DevField* F;
-  const Mask* M;
-  float3 o, v;
-  RayList* L;
-  __device__ void operator()(int j) {
-    const Mask& Mk = *M;
-    Chord ch;
-    float w;
-    if (!prim_chord(*F, j, o, v, 0.f, INFINITY, [&](uint32_t c) { return mask_weight(Mk, c); }, w, ch))
-      return;
-    if (L->n < kRayList) L->idx[L->n] = j;
-    ++L->n;
-  }
-};
-
-__device__ __forceinline__ void gather_list(const DevField& F, const Mask& M, float3 o, float3 v,
-                                            RayList& L, Counters& cnt) {
-  L.n = 0;
-  const float3 inv = safe_inv(v);
-  float t0, t1;
-  if (M.bits == 0ull || !scene_span(F, o, inv, 0.f, INFINITY, t0, t1)) return;
-  ListLeaf leaf{&F, &M, o, v, &L};
-  SpanTest test{t0, t1};
-  traverse_ray(F, o, inv, M.bits, test, leaf, cnt.nodes, cnt.leaves);
-}
-
-// every primitive of the list, or a traversal with `test` when it overflowed
-template <class Test, class Leaf>
-__device__ __forceinline__ void visit(const DevField& F, const RayList* L, float3 o, float3 inv,
-                                      unsigned long long mask, Test& test, Leaf& leaf,
-                                      Counters& cnt) {
-  if (L && L->ok()) {
-    for (int k = 0; k < L->n; ++k) leaf(L->idx[k]);
-    cnt.leaves += (unsigned long long)L->n;
-  } else {
-    traverse_ray(F, o, inv, mask, test, leaf, cnt.nodes, cnt.leaves);
-  }
-}
 
 // Windows of kPts tentative points, in t order, with kappa and kappa_bar
 // (the windows of track()); win(B, n, kap, kb) returns false to stop.
@@ -489,7 +506,8 @@ __global__ void __launch_bounds__(kBackBlock)
     k_radiance_backward(const __grid_constant__ DevField F, const PathParams P, const BackArgs Bk,
                         const float* dLdI, int* counter, int* lists) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  RayList Lc{lists + tid * 2 * kRayList, 0}, Ln{lists + tid * 2 * kRayList + kRayList, 0};
+  const int nth = gridDim.x * blockDim.x;
+  RayList Lc{lists + tid, nth, 0}, Ln{lists + (int64_t)kRayList * nth + tid, nth, 0};
   __shared__ RadSmem sm;
   if (threadIdx.x < 8) sm.env[threadIdx.x] = F.env[threadIdx.x];
   __syncthreads();
@@ -513,7 +531,7 @@ __global__ void __launch_bounds__(kBackBlock)
       float3 o, v;
       camera_ray(P.cam, P.seed, px, py, s, o, v);
       cnt.rays += 1;
-      const Mask M = sample_mask(F, P.lod, v, P.seed, pix, (uint32_t)s, 0, TAG_MASK);
+      const Mask M = sample_mask_impl<true>(F, P.lod, v, P.seed, pix, (uint32_t)s, 0, TAG_MASK);
       const uint32_t wt = stream_word((uint32_t)s, 0, TAG_TRACK);
       gather_list(F, M, o, v, Lc, cnt);
       // pass 1: weights, their sum and the reservoir draw
@@ -538,7 +556,7 @@ __global__ void __launch_bounds__(kBackBlock)
       if (js < 0 || !(S > 0.f)) continue;
       // NEE from the drawn point by ratio tracking
       const float3 x = make_float3(fmaf(tjs, v.x, o.x), fmaf(tjs, v.y, o.y), fmaf(tjs, v.z, o.z));
-      const Mask Mn = sample_mask(F, P.lod_nee, P.light, P.seed, pix, (uint32_t)s, 0, TAG_NEE_MASK);
+      const Mask Mn = sample_mask_impl<true>(F, P.lod_nee, P.light, P.seed, pix, (uint32_t)s, 0, TAG_NEE_MASK);
       const uint32_t wn = stream_word((uint32_t)s, 0, TAG_NEE);
       cnt.rays += 1;
       gather_list(F, Mn, x, P.light, Ln, cnt);
@@ -621,15 +639,7 @@ cudaError_t launch_radiance_backward(const Field& F, const PathParams& P, const 
   int64_t g = (int64_t)F.ctx.sm_count * per_sm;
   if (need < g) g = need;
   if (g < 1) g = 1;
-  // per-thread primitive lists of the camera and NEE rays (grown on demand)
-  const size_t lbytes = (size_t)g * kBackBlock * 2 * kRayList * sizeof(int);
-  if (F.rlist_bytes < lbytes) {
-    if (F.rlist) cudaFree(F.rlist);
-    F.rlist = nullptr;
-    F.rlist_bytes = 0;
-    if ((e = cudaMalloc((void**)&F.rlist, lbytes)) != cudaSuccess) return e;
-    F.rlist_bytes = lbytes;
-  }
+  if ((e = ensure_lists(F, g * kBackBlock)) != cudaSuccess) return e;
   k_radiance_backward<<<(unsigned)g, kBackBlock, 0, s>>>(F.dev, P, B, dLdI, F.counter, F.rlist);
   return cudaGetLastError();
 }

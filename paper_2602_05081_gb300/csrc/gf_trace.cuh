@@ -124,8 +124,12 @@ __device__ __forceinline__ float power_prob(int j, int n, float beta) {
   return powf((float)(j + 1) / (float)n, e) - powf((float)j / (float)n, e);
 }
 
-static __device__ Mask sample_mask(const DevField& F, const LodDev& L, float3 v, uint64_t seed,
-                                   uint32_t ray, uint32_t sample, uint32_t bounce, uint32_t tag) {
+// EXT = false compiles the ALL / CUTOFF / UNIF_CV / UNIFORM bands and ALL / IS /
+// UNIFORM cones only; EXT = true adds the power-law and threshold strategies
+template <bool EXT>
+__device__ __forceinline__ Mask sample_mask_impl(const DevField& F, const LodDev& L, float3 v,
+                                                 uint64_t seed, uint32_t ray, uint32_t sample,
+                                                 uint32_t bounce, uint32_t tag) {
   Mask M;
   M.bits = 0;
   M.cx[0] = 0u;
@@ -167,7 +171,7 @@ static __device__ Mask sample_mask(const DevField& F, const LodDev& L, float3 v,
         pickb = nth_bit(occ, (int)(((unsigned long long)x24 * (unsigned)Q) >> 24));
         wb = (float)Q;
       }
-    } else if (L.freq_policy == 4) {
+    } else if (EXT && L.freq_policy == 4) {
       // power law over the P levels, weight 1/P(level)
       const int Q = __popc(occ);
       if (Q > 0) {
@@ -175,7 +179,7 @@ static __device__ Mask sample_mask(const DevField& F, const LodDev& L, float3 v,
         pickb = nth_bit(occ, j);
         wb = 1.0f / power_prob(j, Q, L.beta);
       }
-    } else {
+    } else if (EXT) {
       // Gaussians always (weight 1); power law over the G Gabor levels: one (5),
       // or every level up to the drawn one, level j with weight 1/(1 - (j/G)^(1-beta)) (6)
       if (occ & 1u) {
@@ -223,7 +227,7 @@ static __device__ Mask sample_mask(const DevField& F, const LodDev& L, float3 v,
     const int nc = __popc(cells);
     int k;
     float cf;
-    if (L.cone_policy == 3 || L.cone_policy == 4) {
+    if (EXT && (L.cone_policy == 3 || L.cone_policy == 4)) {
       // alignment a = |v . o| against delta (FP32): threshold culling keeps the
       // bins with a <= delta, weight 1 (none: the least aligned bin);
       // threshold + uniform keeps them and draws one of the N_above others,
@@ -300,6 +304,22 @@ static __device__ Mask sample_mask(const DevField& F, const LodDev& L, float3 v,
     M.bits |= 1ull << (1 + kCones * (b - 1) + k);
   }
   return M;
+}
+
+// the extended strategies in a call of their own: the common ones stay inline
+// without the extended code's registers
+static __device__ __noinline__ Mask sample_mask_ext(const DevField& F, const LodDev& L, float3 v,
+                                                    uint64_t seed, uint32_t ray, uint32_t sample,
+                                                    uint32_t bounce, uint32_t tag) {
+  return sample_mask_impl<true>(F, L, v, seed, ray, sample, bounce, tag);
+}
+
+__device__ __forceinline__ Mask sample_mask(const DevField& F, const LodDev& L, float3 v,
+                                            uint64_t seed, uint32_t ray, uint32_t sample,
+                                            uint32_t bounce, uint32_t tag) {
+  if (L.freq_policy >= 4 || L.cone_policy >= 3)
+    return sample_mask_ext(F, L, v, seed, ray, sample, bounce, tag);
+  return sample_mask_impl<false>(F, L, v, seed, ray, sample, bounce, tag);
 }
 
 // ---------------------------------------------------------------------------

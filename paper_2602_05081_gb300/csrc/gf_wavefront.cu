@@ -83,7 +83,8 @@ __device__ __forceinline__ unsigned long long slot_mask(const LaneRay& R) {
 __device__ __forceinline__ float ray_weight(const LaneRay& R, uint32_t cell) {
   if (!(slot_mask(R) >> cell & 1ull)) return 0.f;
   const int b = cell == 0 ? 0 : (int)((cell - 1u) >> 3) + 1;
-  return b == 0 ? R.bw[0] : R.bw[b] * cone_factor(R.cx, cell, b);
+  if (b == 0 || (R.cx[0] | R.cx[1]) == 0u) return R.bw[b];
+  return R.bw[b] * cone_factor(R.cx, cell, b);
 }
 
 // byte k of x as a float, exactly: 0x4B0000xx is 2^23 + xx
