@@ -45,6 +45,13 @@ WORKLOAD = ("single scattering, 100k-primitive 4-octave Gabor field, 512x512, 16
             "4 LoD band cutoffs (all, <=1/2, <=1/4, <=1/8)")
 MUFU_PER_SM_CLK = 16  # SFU results per SM per clock
 MUFU_PER_EVAL = 2     # ex2 + cos per Gabor evaluation
+# DRAM bytes (read + write) per k_render_scatter launch of this workload, from
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+#       --clock-control none -k regex:k_render_scatter -s 4 -c 4 --csv
+#       python bench.py --res 512 --spp 2 --steps 1 --warmup 2 --cpu-seconds 0 --server-requests 0
+# (the 4 cutoffs: 7.32, 5.15, 3.02, 0.78 GB at 2 spp), scaled by the traced rays to 16 spp
+# (x 8.0; the traffic is the chord store's, proportional to the rays)
+TRAFFIC_BYTES_PER_LAUNCH = 4.07e9 * 8.0
 
 
 def config(extra=None):
@@ -286,8 +293,8 @@ def run_workload(args):
     elif args.workload == "multiscatter":
         # 1M kernels in 6 octaves, up to 8 bounces, per-bounce Uniform+CV band and
         # importance-sampled cone masks, FP32 and FP16 records
-        res = args.res if args.res != DEFAULT_RES else 1024
-        spp = args.spp if args.spp != DEFAULT_SPP else 64
+        res = args.res or 1024
+        spp = args.spp or 64
         p = synth.octave_field(1_000_000, 6, seed=0)
         cam = api.camera(c["eye"], c["look_at"], c["up"], c["vfov_deg"], res, res)
         ro = api.render_opts("scatter", spp, 8, 0.8, synth.LIGHT_DIR, 1.0)
@@ -476,7 +483,7 @@ def run_ours(args, rank, world):
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_geval = sm_count * MUFU_PER_SM_CLK / MUFU_PER_EVAL * peaks.get("sm_max_mhz", 2070.0) * 1e-3
     achieved = (st["evals"] / (4 * args.steps)) / (statistics.mean(flat) * 1e-3) * 1e-9
-    traffic = None
+    traffic = TRAFFIC_BYTES_PER_LAUNCH if (RES, SPP) == (DEFAULT_RES, DEFAULT_SPP) else None
     value = rays_all / (total_ms_max * 1e-3) / 1e6
     line = {
         "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world,
@@ -529,10 +536,12 @@ def main():
     ap.add_argument("--workload", choices=["scatter", "transmittance", "multiscatter", "adjoint"],
                     default="scatter", help="workload of the JSON line (default: the single-"
                     "scattering benchmark)")
-    ap.add_argument("--res", type=int, default=RES, help="profiling only: image size")
-    ap.add_argument("--spp", type=int, default=SPP, help="profiling only: samples per pixel")
+    ap.add_argument("--res", type=int, default=None, help="profiling only: image size")
+    ap.add_argument("--spp", type=int, default=None, help="profiling only: samples per pixel")
     args = ap.parse_args()
-    globals()["RES"], globals()["SPP"] = args.res, args.spp
+    if args.workload == "scatter":
+        globals()["RES"] = args.res or RES
+        globals()["SPP"] = args.spp or SPP
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
