@@ -43,27 +43,47 @@ __global__ void __launch_bounds__(kBlock)
   const uint32_t lane = threadIdx.x & 31u;
   Counters cnt;
   const bool det_mask = lod_is_deterministic(P.lod);
+  // deterministic mode: G = P.group lanes per ray, 32/G rays per tile
+  const int G = TRACK ? 1 : P.group;
+  const int rpt = 32 / G;
+  const int sub = (int)lane % G;
   for (;;) {
     const int tile = next_tile(P.counter, lane);
-    if ((int64_t)tile * 32 >= P.n) break;
-    const int64_t r = (int64_t)tile * 32 + lane;
-    if (r < P.n) {
+    if ((int64_t)tile * rpt >= P.n) break;
+    const int64_t r = (int64_t)tile * rpt + (int)lane / G;
+    if (!TRACK) {
+      float s_acc = 0.f, c_acc = 0.f;
+      const int spp = det_mask ? 1 : P.spp;
+      if (r < P.n) {
+        const float3 o = make_float3(P.o[3 * r], P.o[3 * r + 1], P.o[3 * r + 2]);
+        const float3 v = normalize3(make_float3(P.d[3 * r], P.d[3 * r + 1], P.d[3 * r + 2]));
+        const float tmin = P.trange ? P.trange[2 * r] : 0.f;
+        const float tmax = P.trange ? P.trange[2 * r + 1] : INFINITY;
+        for (int s = 0; s < spp; ++s) {
+          const Mask m = sample_mask(F, P.lod, v, P.seed, (uint32_t)r, (uint32_t)s, 0, TAG_MASK);
+          if (sub == 0) cnt.rays += 1;
+          neumaier_add(s_acc, c_acc, det_tau(F, m, o, v, tmin, tmax, sm.glx, sm.glw, cnt, sub, G));
+        }
+      }
+      // compensated sum over the ray's G lanes (fixed butterfly order)
+      for (int off = 1; off < G; off <<= 1) {
+        const float so = __shfl_xor_sync(kFull, s_acc, off), co = __shfl_xor_sync(kFull, c_acc, off);
+        float t, e;
+        two_sum(s_acc, so, t, e);
+        s_acc = t;
+        c_acc = __fadd_rn(__fadd_rn(c_acc, co), e);
+      }
+      if (r < P.n && sub == 0) {
+        const float tau = __fadd_rn(s_acc, c_acc) / (float)spp;
+        P.out_T[r] = expf(-tau);
+        if (P.out_tau) P.out_tau[r] = tau;
+      }
+    } else if (r < P.n) {
       const float3 o = make_float3(P.o[3 * r], P.o[3 * r + 1], P.o[3 * r + 2]);
       const float3 v = normalize3(make_float3(P.d[3 * r], P.d[3 * r + 1], P.d[3 * r + 2]));
       const float tmin = P.trange ? P.trange[2 * r] : 0.f;
       const float tmax = P.trange ? P.trange[2 * r + 1] : INFINITY;
-      if (!TRACK) {
-        const int spp = det_mask ? 1 : P.spp;
-        float s_acc = 0.f, c_acc = 0.f;
-        for (int s = 0; s < spp; ++s) {
-          const Mask m = sample_mask(F, P.lod, v, P.seed, (uint32_t)r, (uint32_t)s, 0, TAG_MASK);
-          cnt.rays += 1;
-          neumaier_add(s_acc, c_acc, det_tau(F, m, o, v, tmin, tmax, sm.glx, sm.glw, cnt));
-        }
-        const float tau = __fadd_rn(s_acc, c_acc) / (float)spp;
-        P.out_T[r] = expf(-tau);
-        if (P.out_tau) P.out_tau[r] = tau;
-      } else {
+      {
         float acc = 0.f;
         for (int s = 0; s < P.spp; ++s) {
           const Mask m = sample_mask(F, P.lod, v, P.seed, (uint32_t)r, (uint32_t)s, 0, TAG_MASK);
@@ -197,10 +217,17 @@ cudaError_t launch_transmittance(const Field& F, const TrParams& P, cudaStream_t
   (void)cudaGetLastError();  // a stale error of an unrelated call is not ours
   cudaError_t e = cudaMemsetAsync(P.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  const int64_t tiles = (P.n + 31) / 32;
   if (P.mode == GF_TR_DETERMINISTIC) {
-    k_transmittance<false><<<persistent_grid(F, k_transmittance<false>, tiles), kBlock, 0, s>>>(F.dev, P);
+    // few rays: several lanes per ray so that enough warps hide the latency
+    // (about 16 resident warps of 32 lanes per SM as the target)
+    TrParams Q = P;
+    const int64_t lanes = (int64_t)F.ctx.sm_count * 16 * 32;
+    Q.group = 1;
+    while (Q.group < 8 && P.n * Q.group * 2 <= lanes) Q.group *= 2;
+    const int64_t tiles_g = (P.n + 32 / Q.group - 1) / (32 / Q.group);
+    k_transmittance<false><<<persistent_grid(F, k_transmittance<false>, tiles_g), kBlock, 0, s>>>(F.dev, Q);
   } else {
+    const int64_t tiles = (P.n + 31) / 32;
     k_transmittance<true><<<persistent_grid(F, k_transmittance<true>, tiles), kBlock, 0, s>>>(F.dev, P);
   }
   return cudaGetLastError();

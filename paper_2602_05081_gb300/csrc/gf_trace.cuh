@@ -354,7 +354,11 @@ struct DetLeaf {
   const float* glw;
   float s = 0.f, c = 0.f;
   unsigned long long nch = 0, nev = 0;
+  // a group of `group` lanes traverses the same ray; lane `sub` integrates every
+  // group-th leaf reached (the leaf order is the same for all of them)
+  int sub = 0, group = 1, seen = 0;
   __device__ __forceinline__ void operator()(int j) {
+    if (group > 1 && (seen++ % group) != sub) return;
     const Mask& Mk = *M;
     Chord ch;
     float w;
@@ -379,11 +383,14 @@ struct DetLeaf {
 
 __device__ __forceinline__ float det_tau(const DevField& F, const Mask& M, float3 o, float3 v,
                                          float tmin, float tmax, const float* glx,
-                                         const float* glw, Counters& cnt) {
+                                         const float* glw, Counters& cnt, int sub = 0,
+                                         int group = 1) {
   const float3 inv = safe_inv(v);
   float t0, t1;
   if (M.bits == 0ull || !scene_span(F, o, inv, tmin, tmax, t0, t1)) return 0.f;
   DetLeaf leaf;
+  leaf.sub = sub;
+  leaf.group = group;
   leaf.F = &F;
   leaf.M = &M;
   leaf.o = o;

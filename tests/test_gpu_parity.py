@@ -112,6 +112,22 @@ def test_deterministic_transmittance_absorption_64x64(api, ctx):
     assert np.abs(tau_ref).max() > 0.2  # non-trivial optical depths
 
 
+def test_deterministic_transmittance_lane_groups_agree(api, ctx):
+    """Small batches integrate each ray with several lanes (each lane every G-th
+    leaf), large ones with one lane per ray: the same rays give the same optical
+    depth up to FP32 summation order, and match the oracle."""
+    p = synth.octave_field(6000, 4, seed=5)
+    f = api.Field(ctx, p)
+    o, d, tr = synth.random_rays(200000, seed=9)
+    _, tau_all = f.transmittance(_t(o), _t(d), _t(tr), mode="det")   # one lane per ray
+    _, tau_few = f.transmittance(_t(o[:500]), _t(d[:500]), _t(tr[:500]), mode="det")  # 8 lanes
+    f.sync()
+    a, b = tau_all.cpu().numpy()[:500], tau_few.cpu().numpy()
+    assert np.abs(a - b).max() <= 2e-6 * max(1.0, np.abs(a).max())
+    _, tau_ref = oracle.Field(p, omega_frame="local").transmittance(o[:64], d[:64], tr[:64], mode="det")
+    assert np.abs(np.exp(-b[:64]) - np.exp(-tau_ref)).max() <= 1e-5
+
+
 def test_deterministic_transmittance_edges(api, ctx):
     """Clipped ranges, rays that miss, one- and two-primitive fields, host buffers."""
     p = synth.absorption_field(256, seed=1)
