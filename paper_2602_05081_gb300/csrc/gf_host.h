@@ -28,7 +28,7 @@ struct TrParams {
   float* out_T;
   float* out_tau;
   int* counter;
-  int group = 1;  // lanes per ray of the deterministic mode (1, 2, 4 or 8)
+  int group = 1;  // lanes per ray of the deterministic mode (1, 2, ..., 32)
 };
 
 struct ChordParams {

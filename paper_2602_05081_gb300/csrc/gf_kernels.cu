@@ -43,7 +43,8 @@ __global__ void __launch_bounds__(kBlock)
   const uint32_t lane = threadIdx.x & 31u;
   Counters cnt;
   const bool det_mask = lod_is_deterministic(P.lod);
-  // deterministic mode: G = P.group lanes per ray, 32/G rays per tile
+  // deterministic mode: G = P.group lanes per ray (they share its Gauss-Legendre
+  // nodes), 32/G rays per tile
   const int G = TRACK ? 1 : P.group;
   const int rpt = 32 / G;
   const int sub = (int)lane % G;
@@ -223,7 +224,7 @@ cudaError_t launch_transmittance(const Field& F, const TrParams& P, cudaStream_t
     TrParams Q = P;
     const int64_t lanes = (int64_t)F.ctx.sm_count * 16 * 32;
     Q.group = 1;
-    while (Q.group < 8 && P.n * Q.group * 2 <= lanes) Q.group *= 2;
+    while (Q.group < 32 && P.n * Q.group <= lanes) Q.group *= 2;
     const int64_t tiles_g = (P.n + 32 / Q.group - 1) / (32 / Q.group);
     k_transmittance<false><<<persistent_grid(F, k_transmittance<false>, tiles_g), kBlock, 0, s>>>(F.dev, Q);
   } else {

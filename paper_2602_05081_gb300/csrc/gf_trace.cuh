@@ -354,11 +354,10 @@ struct DetLeaf {
   const float* glw;
   float s = 0.f, c = 0.f;
   unsigned long long nch = 0, nev = 0;
-  // a group of `group` lanes traverses the same ray; lane `sub` integrates every
-  // group-th leaf reached (the leaf order is the same for all of them)
-  int sub = 0, group = 1, seen = 0;
+  // a group of `group` lanes traverses the same ray in step; lane `sub` takes the
+  // Gauss-Legendre nodes k = sub, sub + group, ... of every chord
+  int sub = 0, group = 1;
   __device__ __forceinline__ void operator()(int j) {
-    if (group > 1 && (seen++ % group) != sub) return;
     const Mask& Mk = *M;
     Chord ch;
     float w;
@@ -370,14 +369,15 @@ struct DetLeaf {
     gl_pick(gl_rule(sqrtf(ch.a) * len + 0.5f * fabsf(ch.B) * len), n, off);
     const float mid = 0.5f * (ch.dtin + ch.dtout), hl = 0.5f * len;
     const float y2 = -0.5f * kLog2e * ch.a, y1 = -kLog2e * ch.b, y0 = -0.5f * kLog2e * ch.g;
-    float acc = 0.f;
-    for (int k = 0; k < n; ++k) {
+    const float scale = w * ch.absA * hl;
+    // every node's term goes into the ray's compensated sum (the node sums of
+    // a chord can cancel as much as the chords of a ray)
+    for (int k = sub; k < n; k += group) {
       const float dt = fmaf(hl, glx[off + k], mid);
       const float y = fmaf(fmaf(y2, dt, y1), dt, y0);
-      acc = fmaf(glw[off + k] * ex2f(y), cosf(fmaf(ch.B, dt, ch.delta)), acc);
+      neumaier_add(s, c, scale * glw[off + k] * ex2f(y) * cosf(fmaf(ch.B, dt, ch.delta)));
     }
-    nev += (unsigned long long)n;
-    neumaier_add(s, c, w * ch.absA * hl * acc);
+    nev += (unsigned long long)((n - sub + group - 1) / group);
   }
 };
 

@@ -113,14 +113,14 @@ def test_deterministic_transmittance_absorption_64x64(api, ctx):
 
 
 def test_deterministic_transmittance_lane_groups_agree(api, ctx):
-    """Small batches integrate each ray with several lanes (each lane every G-th
-    leaf), large ones with one lane per ray: the same rays give the same optical
-    depth up to FP32 summation order, and match the oracle."""
+    """Small batches integrate each ray with several lanes (sharing each chord's
+    Gauss-Legendre nodes), large ones with one lane per ray: the same rays give
+    the same optical depth up to FP32 summation order, and match the oracle."""
     p = synth.octave_field(6000, 4, seed=5)
     f = api.Field(ctx, p)
     o, d, tr = synth.random_rays(200000, seed=9)
     _, tau_all = f.transmittance(_t(o), _t(d), _t(tr), mode="det")   # one lane per ray
-    _, tau_few = f.transmittance(_t(o[:500]), _t(d[:500]), _t(tr[:500]), mode="det")  # 8 lanes
+    _, tau_few = f.transmittance(_t(o[:500]), _t(d[:500]), _t(tr[:500]), mode="det")  # 32 lanes
     f.sync()
     a, b = tau_all.cpu().numpy()[:500], tau_few.cpu().numpy()
     assert np.abs(a - b).max() <= 2e-6 * max(1.0, np.abs(a).max())
@@ -286,7 +286,7 @@ def test_multiple_scatter_stochastic_mask_parity(api, ctx):
 
 
 def test_tomography_render_parity(api, ctx):
-    """Tomography image: per camera ray |dT| <= 1e-5 on identical float rays, and
+    """Tomography image: per camera ray |dT| <= 1e-5 max(1, |T|) on identical float rays, and
     the rendered image within 1% of the MC noise of its jittered samples.  The
     image's own rays are built in FP32 on the GPU: a position rounding of
     ~1e-7 times carriers of ~1e3 rad/unit moves phases by ~1e-4, which is why
@@ -299,10 +299,13 @@ def test_tomography_render_parity(api, ctx):
             for s in range(2)]
     o = np.array([r[0] for r in rays], np.float32)
     d = np.array([r[1] for r in rays], np.float32)
-    T, _ = f.transmittance(_t(o), _t(d), None, mode="det")
+    T, tau = f.transmittance(_t(o), _t(d), None, mode="det")
     f.sync()
-    T_ref, _ = orc.transmittance(o, d, None, mode="det")
-    assert np.abs(T.cpu().numpy() - T_ref).max() <= 1e-5
+    T_ref, tau_ref = orc.transmittance(o, d, None, mode="det")
+    # signed densities give T = exp(-tau) above 1 (up to ~11 here): an FP32 error
+    # in tau scales by |T|, so T is held per ray relative to max(1, |T|)
+    assert np.abs(tau.cpu().numpy() - tau_ref).max() <= 1e-5 * max(1.0, np.abs(tau_ref).max())
+    assert (np.abs(T.cpu().numpy() - T_ref) / np.maximum(1.0, np.abs(T_ref))).max() <= 1e-5
     diff, noise, ref = _mc_parity(api, f, orc, cg, co, api.render_opts("tomo", 4),
                                   oracle.render_opts("tomo", 4), 4)
     assert diff <= 0.01 * noise, (diff, noise)
