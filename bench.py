@@ -273,8 +273,9 @@ def run_workload(args):
         T = torch.empty(n, device=dev)
         tau = torch.empty(n, device=dev)
         out, batch = {}, {}
-        for mode in ("det", "rt"):
-            m = _abi.GF_TR_DETERMINISTIC if mode == "det" else _abi.GF_TR_RATIO_TRACKING
+        modes = {"det": _abi.GF_TR_DETERMINISTIC, "closed": _abi.GF_TR_CLOSED_FORM,
+                 "rt": _abi.GF_TR_RATIO_TRACKING}
+        for mode, m in modes.items():
             call = lambda: _abi.gf_transmittance(f.h, o, d, tr, n, m, 1, 0, T, tau, stream)  # noqa: E731
             # one call between two events (latency, host enqueue included) ...
             out[mode] = statistics.median(_timed(call, args.steps * 50, args.warmup, stream))
@@ -284,11 +285,32 @@ def run_workload(args):
                     call()
             batch[mode] = statistics.median(_timed(hundred, args.steps, 1, stream)) / 100
         f.sync()
+        # throughput: 1M random rays through the 100k-kernel 4-octave field,
+        # Gauss-Legendre quadrature against the closed form
+        q = synth.octave_field(100_000, 4, seed=0)
+        g = api.Field(ctx, q)
+        nb = 1 << 20
+        ob, db, trb = (torch.from_numpy(a).to(dev) for a in synth.random_rays(nb, seed=3))
+        Tb = torch.empty(nb, device=dev)
+        taub = {k: torch.empty(nb, device=dev) for k in ("det", "closed")}
+        big = {}
+        for mode in ("det", "closed"):
+            m = modes[mode]
+            call = lambda: _abi.gf_transmittance(g.h, ob, db, trb, nb, m, 1, 0, Tb,  # noqa: E731
+                                                 taub[mode], stream)
+            big[mode] = statistics.median(_timed(call, args.steps * 2, args.warmup, stream))
+        g.sync()
+        dtau = (taub["det"] - taub["closed"]).abs().max().item()
+        scale = max(1.0, taub["det"].abs().max().item())
         workload_line("absorption transmittance, 256 kernels, 64x64 orthographic rays",
                       n / (batch["det"] * 1e-3) / 1e6, "Mrays/s", batch["det"], args,
                       {"us_per_call_latency": {k: v * 1e3 for k, v in out.items()},
                        "us_per_call_back_to_back": {k: v * 1e3 for k, v in batch.items()},
                        "ratio_tracking_mrays_per_s": n / (batch["rt"] * 1e-3) / 1e6,
+                       "closed_form_mrays_per_s": n / (batch["closed"] * 1e-3) / 1e6,
+                       "octave_100k_1m_rays_mrays_per_s": {k: nb / (v * 1e-3) / 1e6
+                                                           for k, v in big.items()},
+                       "octave_100k_max_dtau_det_vs_closed_rel": dtau / scale,
                        "gpu_launches": 1})
     elif args.workload == "multiscatter":
         # 1M kernels in 6 octaves, up to 8 bounces, per-bounce Uniform+CV band and

@@ -134,7 +134,7 @@ typedef struct gf_lod_desc {
   float delta;
 } gf_lod_desc;
 
-enum { GF_TR_DETERMINISTIC = 0, GF_TR_RATIO_TRACKING = 1 };
+enum { GF_TR_DETERMINISTIC = 0, GF_TR_RATIO_TRACKING = 1, GF_TR_CLOSED_FORM = 2 };
 
 /* Pinhole camera: pixel (px,py) of a width x height image (py = 0 at the top)
    looks along normalize(f + sx r + sy u) with f = normalize(look_at - eye),
@@ -208,6 +208,11 @@ gf_status gf_set_lod_mask(gf_field* field, const gf_lod_desc* primary, const gf_
    length and carrier phase span, FP32 with compensated summation; with a
    stochastic mask tau is averaged over spp mask draws (Sec. 4.6 tomography);
    out_T = exp(-tau), out_tau = tau (nullable).
+   CLOSED_FORM: as DETERMINISTIC, but each chord integral is the finite-segment
+   closed form of Sec. 4.4 / App. A.3 (complex error function), evaluated
+   through the Faddeeva function w (Weideman's rational expansion, see
+   gf_faddeeva) so that no term grows with the carrier frequency; chords
+   shorter than 1e-4 in whitened length take the midpoint rule (Sec. 4.4).
    RATIO_TRACKING: out_T = mean over spp samples of prod (1 - kappa/kappa_bar)
    over the tentative points (per-segment majorants, see gf_render);
    out_tau is not written.  Signed kappa (absorption only).
@@ -265,6 +270,14 @@ gf_status gf_ray_chords(gf_field* field, const float* o, const float* d, const f
    (uint32, host or device). */
 gf_status gf_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n,
                     gf_stream stream);
+
+/* The Faddeeva function w(z) = exp(-z^2) erfc(-iz) that the CLOSED_FORM
+   transmittance uses (Sec. 4.4 complex error function), for testing: FP32,
+   Weideman's rational expansion with 20 terms (SIAM J. Numer. Anal. 31 (1994)
+   1497).  z and w are float[2n] as (re, im) pairs, host or device memory;
+   valid for im z >= 0 (w is NaN where im z < 0).  Host buffers make the call
+   synchronise the stream. */
+gf_status gf_faddeeva(const float* z, float* w, int64_t n, gf_stream stream);
 
 /* gf_transmittance for callers that cannot allocate device memory at call time
    (an external memory manager forbids it, the device budget is spent, or only

@@ -25,7 +25,7 @@ GF_OMEGA_WORLD, GF_OMEGA_LOCAL = 0, 1
 (GF_FREQ_ALL, GF_FREQ_CUTOFF, GF_FREQ_UNIF_CV, GF_FREQ_UNIFORM, GF_FREQ_POWER, GF_FREQ_POW_CV,
  GF_FREQ_POW_CV_ACC) = range(7)
 GF_CONE_ALL, GF_CONE_IS, GF_CONE_UNIFORM, GF_CONE_THRESH, GF_CONE_THRESH_UNIFORM = range(5)
-GF_TR_DETERMINISTIC, GF_TR_RATIO_TRACKING = 0, 1
+GF_TR_DETERMINISTIC, GF_TR_RATIO_TRACKING, GF_TR_CLOSED_FORM = 0, 1, 2
 GF_INTEG_TOMO, GF_INTEG_SCATTER = 0, 1
 
 
@@ -114,6 +114,7 @@ _SIGS = {
     "gf_field_labels": [_vp, _vp, _vp, _vp, _vp],
     "gf_ray_chords": [_vp, _vp, _vp, _vp, _i64, _int, _vp, _vp, _vp, _vp, _vp],
     "gf_philox": [_vp, _vp, _vp, _i64, _vp],
+    "gf_faddeeva": [_vp, _vp, _i64, _vp],
     "gf_get_stats": [_vp, C.POINTER(gf_stats), _int],
     "gf_sync": [_vp, _vp],
     "gf_field_info": [_vp, C.POINTER(_i64), C.POINTER(_int), C.POINTER(_u64)],
@@ -233,6 +234,10 @@ def gf_ray_chords(field, o, d, trange, n_rays, cap, counts, prims, t_in=None, t_
 
 def gf_philox(ctr, key, out, n, stream=None):
     _check(lib.gf_philox(ptr(ctr), ptr(key), ptr(out), int(n), stream_handle(stream)))
+
+
+def gf_faddeeva(z, w, n, stream=None):
+    _check(lib.gf_faddeeva(ptr(z), ptr(w), int(n), stream_handle(stream)))
 
 
 def gf_get_stats(field, reset=False) -> dict:

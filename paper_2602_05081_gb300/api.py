@@ -103,9 +103,10 @@ class Field:
         if out_T is None:
             dev = o.device if isinstance(o, torch.Tensor) else torch.device("cpu")
             out_T = torch.empty(n, dtype=torch.float32, device=dev)
-            if mode == "det" and out_tau is None:
+            if mode != "rt" and out_tau is None:
                 out_tau = torch.empty(n, dtype=torch.float32, device=dev)
-        m = A.GF_TR_DETERMINISTIC if mode == "det" else A.GF_TR_RATIO_TRACKING
+        m = {"det": A.GF_TR_DETERMINISTIC, "rt": A.GF_TR_RATIO_TRACKING,
+             "closed": A.GF_TR_CLOSED_FORM}[mode]
         A.gf_transmittance(self.h, o, d, trange, n, m, spp, seed, out_T, out_tau, stream)
         return out_T, out_tau
 

@@ -166,6 +166,27 @@ gf_status camera_params(const gf_camera* c, const gf_render_opts* o, uint64_t se
   return GF_OK;
 }
 
+
+// Weideman's coefficients a_n, n = 1..N, of the Faddeeva expansion: the
+// Fourier cosine coefficients of f(theta) = (L^2 + t^2) exp(-t^2),
+// t = L tan(theta/2), by the trapezoidal rule on theta_k = k pi / M,
+// |k| < M = 2N (f vanishes at theta = pi), with L = sqrt(N / sqrt(2))
+// (SIAM J. Numer. Anal. 31 (1994) 1497-1518).
+void weideman_coefficients(Weideman& W) {
+  const double pi = 3.14159265358979323846;
+  const int N = kWeidN, M = 2 * N;
+  const double L = std::sqrt(N / std::sqrt(2.0));
+  for (int n = 1; n <= N; ++n) {
+    double acc = 0.0;
+    for (int k = -M + 1; k < M; ++k) {
+      const double th = k * pi / M, t = L * std::tan(0.5 * th);
+      acc += (L * L + t * t) * std::exp(-t * t) * std::cos(n * th);
+    }
+    W.a[n - 1] = (float)(acc / (2.0 * M));
+  }
+  W.L = (float)L;
+}
+
 }  // namespace gf
 
 namespace {
@@ -329,6 +350,7 @@ gf_status gf_load_field(gf_ctx* ctx, const gf_params* p, const gf_field_opts* op
   F.dev.err = F.err;
   F.dev.stats = F.stats;
   F.dev.gl = F.gl;
+  weideman_coefficients(F.dev.wd);
   F.dev.root = -1;
   *out = h;
   return GF_OK;
@@ -393,7 +415,8 @@ gf_status gf_transmittance(gf_field* h, const float* o, const float* d, const fl
   Field& F = h->f;
   if (!F.built) return fail(GF_ESTATE, "gf_build_bvh has not run");
   if (n_rays < 0 || n_rays > (1ll << 31) - 1) return fail(GF_EINVAL, "n_rays out of range");
-  if (mode != GF_TR_DETERMINISTIC && mode != GF_TR_RATIO_TRACKING) return fail(GF_EINVAL, "bad mode");
+  if (mode != GF_TR_DETERMINISTIC && mode != GF_TR_RATIO_TRACKING && mode != GF_TR_CLOSED_FORM)
+    return fail(GF_EINVAL, "bad mode");
   if (spp < 1 || spp > (1 << 20)) return fail(GF_EINVAL, "spp in [1, 2^20]");
   if (n_rays == 0) return GF_OK;
   GF_CUDA(cudaSetDevice(F.ctx.device), "cudaSetDevice");
@@ -406,7 +429,7 @@ gf_status gf_transmittance(gf_field* h, const float* o, const float* d, const fl
   if ((st = stage(F, o, 12 * n, true, s, off, &od)) || (st = stage(F, d, 12 * n, true, s, off, &dd)) ||
       (st = stage(F, trange, 8 * n, true, s, off, &td)) ||
       (st = stage(F, out_T, 4 * n, false, s, off, &Td)) ||
-      (st = stage(F, mode == GF_TR_DETERMINISTIC ? out_tau : nullptr, 4 * n, false, s, off, &taud)))
+      (st = stage(F, mode != GF_TR_RATIO_TRACKING ? out_tau : nullptr, 4 * n, false, s, off, &taud)))
     return st;
   TrParams P;
   P.o = (const float*)od;
@@ -573,6 +596,29 @@ gf_status gf_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int
   cudaFree(k);
   cudaFree(r);
   if (e) return cuda_fail(e, "gf_philox");
+  return GF_OK;
+}
+
+gf_status gf_faddeeva(const float* z, float* w, int64_t n, gf_stream stream) {
+  if (!z || !w || n < 0) return fail(GF_EINVAL, "bad argument");
+  if (n == 0) return GF_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  Weideman W;
+  weideman_coefficients(W);
+  if (is_device_ptr(z) && is_device_ptr(w)) {
+    GF_CUDA(launch_faddeeva(W, z, w, n, s), "faddeeva launch");
+    return GF_OK;
+  }
+  float *zd = nullptr, *wd = nullptr;
+  GF_CUDA(cudaMalloc((void**)&zd, 8 * n), "alloc");
+  cudaError_t e = cudaMalloc((void**)&wd, 8 * n);
+  if (!e) e = cudaMemcpyAsync(zd, z, 8 * n, cudaMemcpyDefault, s);
+  if (!e) e = launch_faddeeva(W, zd, wd, n, s);
+  if (!e) e = cudaMemcpyAsync(w, wd, 8 * n, cudaMemcpyDefault, s);
+  if (!e) e = cudaStreamSynchronize(s);
+  cudaFree(zd);
+  cudaFree(wd);
+  if (e) return cuda_fail(e, "gf_faddeeva");
   return GF_OK;
 }
 

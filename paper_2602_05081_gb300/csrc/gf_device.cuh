@@ -59,6 +59,16 @@ struct LodDev {
 };
 
 // Everything a kernel needs to read a packed field; passed by value.
+// Coefficients of Weideman's rational expansion of the Faddeeva function
+// (J. A. C. Weideman, "Computation of the complex error function", SIAM J.
+// Numer. Anal. 31 (1994) 1497-1518): a[n-1] = a_n, n = 1..N, and the scale L.
+// N = 20 reaches FP32 rounding over the closed upper half plane.
+constexpr int kWeidN = 20;
+struct Weideman {
+  float a[kWeidN];
+  float L;
+};
+
 struct DevField {
   const float4* rec;       // FP32 records: 4 x float4 per primitive, BVH order
   const uint4* rec16;      // FP16/BF16 records: 2 x uint4 per primitive, BVH order
@@ -76,6 +86,7 @@ struct DevField {
   const int* orig16;       // reduced-precision records: BVH position -> original index
   float3 qlo, qscale;      // reduced-precision records: mean = qlo + code * qscale
   const float* gl;         // Gauss-Legendre nodes then weights (2 x kGLTotal)
+  Weideman wd;             // Faddeeva expansion (closed-form chord integrals)
   int* err;
   unsigned long long* stats;  // rays, chords, evals, nodes, points
 };
@@ -129,6 +140,32 @@ __device__ __forceinline__ float reduce_2pi(float x) {
 }
 
 constexpr float kLog2e = 1.4426950408889634f;
+
+// ---------------------------------------------------------------------------
+// Faddeeva function w(z) = exp(-z^2) erfc(-iz) for z = x + iy, y >= 0, by
+// Weideman's expansion: with Z = (L + iz)/(L - iz), which stays in the unit
+// disc for y >= 0,
+//   w(z) = 2 sum_{n=1..N} a_n Z^(n-1) / (L - iz)^2 + 1 / (sqrt(pi) (L - iz)).
+// Here L - iz = (L + y) - ix, so 1/(L - iz) = ((L + y) + ix)/D and
+// Z = ((L^2 - y^2 - x^2) + 2iLx)/D with D = (L + y)^2 + x^2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 faddeeva_w(const Weideman& W, float x, float y) {
+  const float kRsqrtPi = 0.56418958354775628f;
+  const float lp = W.L + y, lm = W.L - y;
+  const float iD = 1.0f / fmaf(lp, lp, x * x);
+  const float zr = fmaf(lm, lp, -x * x) * iD, zi = 2.0f * W.L * x * iD;
+  float pr = W.a[kWeidN - 1], pim = 0.0f;
+#pragma unroll
+  for (int n = kWeidN - 2; n >= 0; --n) {
+    const float t = fmaf(pr, zr, fmaf(-pim, zi, W.a[n]));
+    pim = fmaf(pr, zi, pim * zr);
+    pr = t;
+  }
+  const float ir = lp * iD, ii = x * iD;                    // 1/(L - iz)
+  const float sr = fmaf(ir, ir, -ii * ii), si = 2.0f * ir * ii;  // 1/(L - iz)^2
+  return make_float2(fmaf(2.0f, fmaf(pr, sr, -pim * si), kRsqrtPi * ir),
+                     fmaf(2.0f, fmaf(pr, si, pim * sr), kRsqrtPi * ii));
+}
 
 // ---------------------------------------------------------------------------
 // warp helpers

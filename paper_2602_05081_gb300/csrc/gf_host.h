@@ -118,6 +118,9 @@ cudaError_t launch_render_scatter(const Field& F, const PathParams& P, float* ou
 cudaError_t launch_ray_chords(const Field& F, const ChordParams& P, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n,
                           cudaStream_t s);
+cudaError_t launch_faddeeva(const Weideman& W, const float* z, float* w, int64_t n,
+                           cudaStream_t s);
+void weideman_coefficients(Weideman& W);
 cudaError_t launch_pack(Field& F, const gf_params& P, cudaStream_t s);
 cudaError_t build_bvh(Field& F, cudaStream_t s);
 cudaError_t launch_pack16(Field& F, cudaStream_t s);

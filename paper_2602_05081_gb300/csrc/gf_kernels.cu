@@ -33,18 +33,20 @@ __device__ __forceinline__ int next_tile(int* counter, uint32_t lane) {
 }
 
 // ---------------------------------------------------------------------------
-// transmittance: deterministic quadrature or ratio tracking, one ray per lane
+// transmittance: deterministic optical depth (Gauss-Legendre quadrature or
+// closed-form chord integrals) or ratio tracking, one ray per lane
 // ---------------------------------------------------------------------------
-template <bool TRACK>
+template <int MODE>  // GF_TR_DETERMINISTIC, GF_TR_RATIO_TRACKING or GF_TR_CLOSED_FORM
 __global__ void __launch_bounds__(kBlock)
     k_transmittance(const __grid_constant__ DevField F, const TrParams P) {
+  constexpr bool TRACK = MODE == GF_TR_RATIO_TRACKING;
   __shared__ BlockTables sm;
   init_tables(sm, F);
   const uint32_t lane = threadIdx.x & 31u;
   Counters cnt;
   const bool det_mask = lod_is_deterministic(P.lod);
-  // deterministic mode: G = P.group lanes per ray (they share its Gauss-Legendre
-  // nodes), 32/G rays per tile
+  // deterministic modes: G = P.group lanes per ray (they share its Gauss-Legendre
+  // nodes, or take its chords round robin), 32/G rays per tile
   const int G = TRACK ? 1 : P.group;
   const int rpt = 32 / G;
   const int sub = (int)lane % G;
@@ -63,7 +65,10 @@ __global__ void __launch_bounds__(kBlock)
         for (int s = 0; s < spp; ++s) {
           const Mask m = sample_mask(F, P.lod, v, P.seed, (uint32_t)r, (uint32_t)s, 0, TAG_MASK);
           if (sub == 0) cnt.rays += 1;
-          neumaier_add(s_acc, c_acc, det_tau(F, m, o, v, tmin, tmax, sm.glx, sm.glw, cnt, sub, G));
+          neumaier_add(s_acc, c_acc,
+                       MODE == GF_TR_CLOSED_FORM
+                           ? closed_tau(F, m, o, v, tmin, tmax, cnt, sub, G)
+                           : det_tau(F, m, o, v, tmin, tmax, sm.glx, sm.glw, cnt, sub, G));
         }
       }
       // compensated sum over the ray's G lanes (fixed butterfly order)
@@ -123,6 +128,16 @@ __global__ void __launch_bounds__(kBlock)
     if (active) out[(int64_t)py * P.cam.W + px] = acc / (float)P.spp;
   }
   flush_counters(F, cnt, lane);
+}
+
+__global__ void k_faddeeva(const Weideman W, const float* z, float* w, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float x = z[2 * i], y = z[2 * i + 1];
+  float2 r = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+  if (y >= 0.0f) r = faddeeva_w(W, x, y);
+  w[2 * i] = r.x;
+  w[2 * i + 1] = r.y;
 }
 
 // ---------------------------------------------------------------------------
@@ -218,7 +233,7 @@ cudaError_t launch_transmittance(const Field& F, const TrParams& P, cudaStream_t
   (void)cudaGetLastError();  // a stale error of an unrelated call is not ours
   cudaError_t e = cudaMemsetAsync(P.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  if (P.mode == GF_TR_DETERMINISTIC) {
+  if (P.mode == GF_TR_DETERMINISTIC || P.mode == GF_TR_CLOSED_FORM) {
     // few rays: several lanes per ray so that enough warps hide the latency
     // (about 16 resident warps of 32 lanes per SM as the target)
     TrParams Q = P;
@@ -226,10 +241,17 @@ cudaError_t launch_transmittance(const Field& F, const TrParams& P, cudaStream_t
     Q.group = 1;
     while (Q.group < 32 && P.n * Q.group <= lanes) Q.group *= 2;
     const int64_t tiles_g = (P.n + 32 / Q.group - 1) / (32 / Q.group);
-    k_transmittance<false><<<persistent_grid(F, k_transmittance<false>, tiles_g), kBlock, 0, s>>>(F.dev, Q);
+    if (P.mode == GF_TR_DETERMINISTIC) {
+      auto k = k_transmittance<GF_TR_DETERMINISTIC>;
+      k<<<persistent_grid(F, k, tiles_g), kBlock, 0, s>>>(F.dev, Q);
+    } else {
+      auto k = k_transmittance<GF_TR_CLOSED_FORM>;
+      k<<<persistent_grid(F, k, tiles_g), kBlock, 0, s>>>(F.dev, Q);
+    }
   } else {
     const int64_t tiles = (P.n + 31) / 32;
-    k_transmittance<true><<<persistent_grid(F, k_transmittance<true>, tiles), kBlock, 0, s>>>(F.dev, P);
+    auto k = k_transmittance<GF_TR_RATIO_TRACKING>;
+    k<<<persistent_grid(F, k, tiles), kBlock, 0, s>>>(F.dev, P);
   }
   return cudaGetLastError();
 }
@@ -249,6 +271,15 @@ cudaError_t launch_ray_chords(const Field& F, const ChordParams& P, cudaStream_t
   cudaError_t e = cudaMemsetAsync(P.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   k_ray_chords<<<persistent_grid(F, k_ray_chords, (P.n + 31) / 32), kBlock, 0, s>>>(F.dev, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_faddeeva(const Weideman& W, const float* z, float* w, int64_t n,
+                           cudaStream_t s) {
+  (void)cudaGetLastError();  // a stale error of an unrelated call is not ours
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = (n + 255) / 256;
+  k_faddeeva<<<(unsigned)blocks, 256, 0, s>>>(W, z, w, n);
   return cudaGetLastError();
 }
 

@@ -57,7 +57,8 @@ extern "C" gf_status gf_transmittance_static(gf_field* h, const float* o, const 
   if (n_rays > kStaticMaxRays)
     return report(GF_EINVAL, "n_rays exceeds the static scratch capacity of " +
                                  std::to_string(kStaticMaxRays) + " rays; split the call");
-  if (mode != GF_TR_DETERMINISTIC && mode != GF_TR_RATIO_TRACKING) return report(GF_EINVAL, "bad mode");
+  if (mode != GF_TR_DETERMINISTIC && mode != GF_TR_RATIO_TRACKING && mode != GF_TR_CLOSED_FORM)
+    return report(GF_EINVAL, "bad mode");
   if (spp < 1 || spp > (1 << 20)) return report(GF_EINVAL, "spp in [1, 2^20]");
   if (n_rays == 0) return GF_OK;
   const int dev = F.ctx.device;
@@ -93,7 +94,7 @@ extern "C" gf_status gf_transmittance_static(gf_field* h, const float* o, const 
     cur += align256(bytes);
     return in ? cudaMemcpyAsync(*out, p, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
   };
-  float* tau_arg = mode == GF_TR_DETERMINISTIC ? out_tau : nullptr;
+  float* tau_arg = mode != GF_TR_RATIO_TRACKING ? out_tau : nullptr;
   void *od, *dd, *td, *Td, *taud;
   if ((e = view(o, 12 * n, true, &od)) || (e = view(d, 12 * n, true, &dd)) ||
       (e = view(trange, 8 * n, true, &td)) || (e = view(out_T, 4 * n, false, &Td)) ||

@@ -400,10 +400,110 @@ __device__ __forceinline__ float det_tau(const DevField& F, const Mask& M, float
   leaf.glx = glx;
   leaf.glw = glw;
   SpanTest test{t0, t1};
-  traverse_ray(F, o, inv, M.bits, test, leaf, cnt.nodes, cnt.leaves);
-  cnt.windows += 1;
-  cnt.chords += leaf.nch;
+  // the lanes of a group walk the same tree: lane 0 of the group counts it
+  unsigned long long nodes = 0, leaves = 0;
+  traverse_ray(F, o, inv, M.bits, test, leaf, nodes, leaves);
+  if (sub == 0) {
+    cnt.nodes += nodes;
+    cnt.leaves += leaves;
+    cnt.windows += 1;
+    cnt.chords += leaf.nch;
+  }
   cnt.evals += leaf.nev;
+  return __fadd_rn(leaf.s, leaf.c);
+}
+
+// ---------------------------------------------------------------------------
+// closed-form chord integrals (Sec. 4.4, App. A.3)
+//
+// The integral of |A| exp(-q/2) cos(theta) over a chord, written with the
+// Faddeeva function w so that no term grows with the carrier frequency.  With
+// u = dt - dts (envelope peak at dts), s = sqrt(a/2), x = s u, beta = B/(2s)
+// and delta' = B dts + delta the carrier phase at the peak:
+//   int = |A| e^(-qmin/2) sqrt(pi)/(2s) Re{e^(i delta') [F(x0) - F(x1)]},
+//   F(x) = e^(-beta^2) erfc(x - i beta).
+// From erfc(y) = e^(-y^2) w(iy), erfc(y) = 2 - erfc(-y) and w(-conj z) = conj w(z):
+//   e^(-qmin/2) Re{e^(i delta') F(x)}
+//     = e^(-q/2) Re{e^(i theta) w(beta + i|x|)}                         x >= 0
+//     = 2 e^(-qmin/2 - beta^2) cos(delta')
+//       - e^(-q/2) Re{e^(i theta) conj w(beta + i|x|)}                   x < 0
+// where q = qmin + 2 x^2 and theta = B dt + delta belong to the end point, so
+// w is only taken in the upper half plane.  A chord shorter than 1e-4 in
+// whitened length takes the midpoint rule (Sec. 4.4).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float closed_end(const Weideman& W, float x, float beta, float qmin,
+                                            float theta) {
+  const float2 w = faddeeva_w(W, beta, fabsf(x));
+  float sn, cs;
+  sincosf(theta, &sn, &cs);
+  const float e = ex2f(-0.5f * kLog2e * fmaf(2.0f * x, x, qmin));
+  return x >= 0.0f ? e * fmaf(cs, w.x, -sn * w.y) : -e * fmaf(cs, w.x, sn * w.y);
+}
+
+__device__ __forceinline__ float chord_closed(const Weideman& W, const Chord& ch) {
+  const float len = ch.dtout - ch.dtin;
+  const float ra = sqrtf(ch.a);
+  if (ra * len < 1e-4f) {
+    const float m = 0.5f * (ch.dtin + ch.dtout);
+    const float q = fmaf(fmaf(ch.a, m, 2.0f * ch.b), m, ch.g);
+    return ch.absA * len * ex2f(-0.5f * kLog2e * q) * cosf(fmaf(ch.B, m, ch.delta));
+  }
+  const float s = 0.70710678118654752f * ra;
+  const float beta = ch.B / (2.0f * s);
+  const float x0 = s * (ch.dtin - ch.dts), x1 = s * (ch.dtout - ch.dts);
+  float acc = closed_end(W, x0, beta, ch.qmin, fmaf(ch.B, ch.dtin, ch.delta)) -
+              closed_end(W, x1, beta, ch.qmin, fmaf(ch.B, ch.dtout, ch.delta));
+  if (x0 < 0.0f && x1 >= 0.0f)  // the chord holds the peak: the full-line term
+    acc += 2.0f * ex2f(-kLog2e * fmaf(beta, beta, 0.5f * ch.qmin)) *
+           cosf(fmaf(ch.B, ch.dts, ch.delta));
+  return ch.absA * (0.88622692545275801f / s) * acc;  // sqrt(pi)/2 / s
+}
+
+// the lanes of a group walk the same tree and take the chords round robin
+struct ClosedLeaf {
+  const DevField* F;
+  const Mask* M;
+  float3 o, v;
+  float tmin, tmax;
+  float s = 0.f, c = 0.f;
+  unsigned long long nch = 0;
+  int sub = 0, group = 1;  // group is a power of two
+  __device__ __forceinline__ void operator()(int j) {
+    const Mask& Mk = *M;
+    Chord ch;
+    float w;
+    if (!prim_chord(*F, j, o, v, tmin, tmax, [&](uint32_t c) { return mask_weight(Mk, c); }, w, ch))
+      return;
+    const bool mine = (int)(nch & (unsigned long long)(group - 1)) == sub;
+    ++nch;
+    if (mine) neumaier_add(s, c, w * chord_closed(F->wd, ch));
+  }
+};
+
+__device__ __forceinline__ float closed_tau(const DevField& F, const Mask& M, float3 o, float3 v,
+                                            float tmin, float tmax, Counters& cnt, int sub = 0,
+                                            int group = 1) {
+  const float3 inv = safe_inv(v);
+  float t0, t1;
+  if (M.bits == 0ull || !scene_span(F, o, inv, tmin, tmax, t0, t1)) return 0.f;
+  ClosedLeaf leaf;
+  leaf.sub = sub;
+  leaf.group = group;
+  leaf.F = &F;
+  leaf.M = &M;
+  leaf.o = o;
+  leaf.v = v;
+  leaf.tmin = tmin;
+  leaf.tmax = tmax;
+  SpanTest test{t0, t1};
+  unsigned long long nodes = 0, leaves = 0;
+  traverse_ray(F, o, inv, M.bits, test, leaf, nodes, leaves);
+  if (sub == 0) {
+    cnt.nodes += nodes;
+    cnt.leaves += leaves;
+    cnt.windows += 1;
+    cnt.chords += leaf.nch;
+  }
   return __fadd_rn(leaf.s, leaf.c);
 }
 

@@ -128,6 +128,86 @@ def test_deterministic_transmittance_lane_groups_agree(api, ctx):
     assert np.abs(np.exp(-b[:64]) - np.exp(-tau_ref)).max() <= 1e-5
 
 
+def test_faddeeva_matches_library(api):
+    """The Faddeeva function behind the closed-form chord integrals (Sec. 4.4
+    complex error function) against scipy's FP64 wofz over the arguments the
+    chords reach (real part beta = B / sqrt(2a), imaginary part |x| <= k/sqrt(2))
+    and far beyond; NaN below the real axis, where the expansion does not hold."""
+    from scipy.special import wofz
+    from paper_2602_05081_gb300 import _abi
+    x = np.concatenate([np.linspace(-80, 80, 1601), [-1e4, -300.0, 1e-6, 300.0, 1e4]])
+    y = np.concatenate([np.linspace(0, 3, 61), [5.0, 20.0, 1e3]])
+    X, Y = np.meshgrid(x.astype(np.float32), y.astype(np.float32))
+    z = np.stack([X.ravel(), Y.ravel()], 1).astype(np.float32)
+    w = np.zeros_like(z)
+    _abi.gf_faddeeva(z, w, len(z))
+    ref = wofz(z[:, 0].astype(np.float64) + 1j * z[:, 1].astype(np.float64))
+    err = np.abs((w[:, 0] + 1j * w[:, 1]) - ref)
+    # FP32 Horner over |Z| <= 1: |dw| <= gamma_2N sum|a_n| 2/L^2 + a few ulp, with
+    # N = 20, L = sqrt(N/sqrt 2) = 3.76 and sum|a_n| = 6.02 from the coefficients' definition
+    N, L, u = 20, math.sqrt(20 / math.sqrt(2.0)), 2.0 ** -24
+    th = np.arange(-2 * N + 1, 2 * N) * np.pi / (2 * N)
+    t = L * np.tan(th / 2)
+    a = np.array([np.sum((L * L + t * t) * np.exp(-t * t) * np.cos(n * th)) / (4 * N)
+                  for n in range(1, N + 1)])
+    bound = 2 * N * u / (1 - 2 * N * u) * np.abs(a).sum() * 2 / L ** 2 + 8 * u
+    assert err.max() <= bound, (err.max(), bound)
+    big = np.abs(ref) >= 0.05
+    assert (err[big] / np.abs(ref[big])).max() <= 2e-5
+    zb = np.array([[0.5, -0.1], [3.0, -2.0]], np.float32)
+    wb = torch.zeros(2, 2, dtype=torch.float32, device=DEV)
+    _abi.gf_faddeeva(_t(zb), wb, 2)
+    torch.cuda.synchronize()
+    assert torch.isnan(wb).all()
+
+
+@pytest.mark.parametrize("field", ["absorption", "octave", "high_frequency"])
+def test_closed_form_transmittance_matches_oracle(api, ctx, field):
+    """Closed-form chord integrals (Faddeeva form of App. A.3) against the
+    oracle's optical depth, whose composite quadrature is exact to rounding:
+    |dtau| <= 1e-5 max(1, max|tau|), |dT| <= 1e-5 max(1, |T|) per ray.  Ranges
+    clip chords to pieces down to 1e-7 (the midpoint branch) and to empty."""
+    if field == "absorption":
+        p = synth.absorption_field(256, seed=0)
+    elif field == "octave":
+        p = synth.octave_field(6000, 4, seed=5)
+    else:  # carriers 8x faster: beta = B / sqrt(2a) up to ~30
+        p = synth.absorption_field(256, seed=4)
+        p = dict(p, omega=(p["omega"] * 8.0).astype(np.float32))
+    omega_frame = "local" if field == "octave" else "world"
+    f = api.Field(ctx, p)
+    orc = oracle.Field(p, omega_frame=omega_frame)
+    o, d, tr = synth.random_rays(600, seed=21)
+    tr = tr.copy()
+    rng = np.random.default_rng(22)
+    tr[:200, 0] = rng.uniform(0.8, 2.2, 200).astype(np.float32)
+    tr[:200, 1] = tr[:200, 0] + (10.0 ** rng.uniform(-7, -1, 200)).astype(np.float32)
+    tr[200:210, 1] = tr[200:210, 0]
+    T, tau = f.transmittance(_t(o), _t(d), _t(tr), mode="closed")
+    f.sync()
+    T_ref, tau_ref = orc.transmittance(o, d, tr, mode="det")
+    tau_g = tau.cpu().numpy()
+    assert np.abs(tau_g - tau_ref).max() <= 1e-5 * max(1.0, np.abs(tau_ref).max())
+    assert (np.abs(T.cpu().numpy() - T_ref) / np.maximum(1.0, np.abs(T_ref))).max() <= 1e-5
+    assert np.all(tau_g[200:210] == 0.0)
+    assert np.abs(tau_ref[210:]).max() > 0.1  # non-trivial optical depths
+
+
+def test_closed_form_lane_groups_agree(api, ctx):
+    """Closed form with one lane per ray (large batch) and with 32 lanes taking
+    a ray's chords round robin (small batch): equal up to FP32 summation order."""
+    p = synth.octave_field(6000, 4, seed=5)
+    f = api.Field(ctx, p)
+    o, d, tr = synth.random_rays(200000, seed=9)
+    _, tau_all = f.transmittance(_t(o), _t(d), _t(tr), mode="closed")
+    _, tau_few = f.transmittance(_t(o[:500]), _t(d[:500]), _t(tr[:500]), mode="closed")
+    _, tau_gl = f.transmittance(_t(o[:500]), _t(d[:500]), _t(tr[:500]), mode="det")
+    f.sync()
+    a, b, c = tau_all.cpu().numpy()[:500], tau_few.cpu().numpy(), tau_gl.cpu().numpy()
+    assert np.abs(a - b).max() <= 2e-6 * max(1.0, np.abs(a).max())
+    assert np.abs(b - c).max() <= 1e-5 * max(1.0, np.abs(c).max())
+
+
 def test_deterministic_transmittance_edges(api, ctx):
     """Clipped ranges, rays that miss, one- and two-primitive fields, host buffers."""
     p = synth.absorption_field(256, seed=1)
