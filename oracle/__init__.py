@@ -46,7 +46,7 @@ class FieldDesc(C.Structure):
     _fields_ = [("n", C.c_int64), ("mu", C.c_void_p), ("quat", C.c_void_p),
                 ("log_scale", C.c_void_p), ("omega", C.c_void_p), ("phase", C.c_void_p),
                 ("weight", C.c_void_p), ("band", C.c_void_p), ("weight_mode", C.c_int),
-                ("omega_frame", C.c_int), ("k_sigma", C.c_double)]
+                ("omega_frame", C.c_int), ("k_sigma", C.c_double), ("clamp_eps", C.c_double)]
 
 
 class Lod(C.Structure):
@@ -78,6 +78,8 @@ def _load():
         lib.or_field_labels.argtypes = [vp, vp, vp, vp]
         lib.or_field_cells.argtypes = [vp, vp, vp]
         lib.or_field_prim.argtypes = [vp, i64, vp, vp, vp]
+        lib.or_field_extent.restype = dbl
+        lib.or_field_extent.argtypes = [vp, i64]
         lib.or_philox4x32_10.argtypes = [vp, vp, vp]
         lib.or_sample_mask.argtypes = [vp, C.POINTER(Lod), vp, u64, u32, u32, u32, u32, vp, vp]
         lib.or_density.restype = dbl
@@ -137,7 +139,7 @@ class Field:
     log_scale (N,3), omega (N,3), phase (N,), weight (N,), optional band (N,) u8.
     """
 
-    def __init__(self, params, weight_mode="peak", omega_frame="world", k_sigma=3.0):
+    def __init__(self, params, weight_mode="peak", omega_frame="world", k_sigma=3.0, clamp_eps=0.0):
         self.lib = _load()
         self._arrs = {k: _f32(params[k]).reshape(-1) for k in
                       ("mu", "quat", "log_scale", "omega", "phase", "weight")}
@@ -148,7 +150,7 @@ class Field:
                               _ptr(self._arrs["log_scale"]), _ptr(self._arrs["omega"]),
                               _ptr(self._arrs["phase"]), _ptr(self._arrs["weight"]),
                               _ptr(self._band), WEIGHT_MODES[weight_mode],
-                              OMEGA_FRAMES[omega_frame], float(k_sigma))
+                              OMEGA_FRAMES[omega_frame], float(k_sigma), float(clamp_eps))
         self.h = self.lib.or_field_create(C.byref(self.desc))
         self.k_sigma = float(k_sigma)
 
@@ -169,6 +171,11 @@ class Field:
         occ = np.zeros(1, np.uint64); kb = np.zeros(64, np.float64)
         self.lib.or_field_cells(self.h, _ptr(occ), _ptr(kb))
         return int(occ[0]), kb
+
+    def extents(self):
+        """Support radius of every primitive in sigma units (Sec. 4.4 adaptive
+        clamping when clamp_eps > 0; 0 = dropped)."""
+        return np.array([self.lib.or_field_extent(self.h, i) for i in range(self.n)])
 
     def prim(self, i):
         s = np.zeros(9); w = np.zeros(3); a = np.zeros(1)

@@ -74,6 +74,7 @@ typedef struct {
   double omega[3];   /* world-space carrier, rad per unit length */
   double kw[3];      /* whitened-frame carrier k_W = S R^T omega */
   double phi, A;
+  double k;          /* support radius in whitened units (k_sigma or adaptive) */
   int band, cone, cell;
 } or_prim;
 
@@ -87,6 +88,8 @@ struct or_field {
 };
 
 int64_t or_field_size(const or_field* f) { return f->n; }
+
+double or_field_extent(const or_field* f, int64_t i) { return f->p[i].k; }
 
 /* cone axes on the upper hemisphere, Fibonacci spiral (reading of the
    unspecified orientation bins of Sec. 4.5.2) */
@@ -194,8 +197,20 @@ or_field* or_field_create(const or_field_desc* D) {
     P->cone = P->band == 0 ? 0 : cone_from_omega(P->omega, f->axes);
     P->cell = P->band == 0 ? 0 : 1 + OR_N_CONES * (P->band - 1) + P->cone;
     f->occupied |= 1ull << P->cell;
-    ksum[P->cell] += sqrt(P->kw[0] * P->kw[0] + P->kw[1] * P->kw[1] + P->kw[2] * P->kw[2]);
+    double kw2 = P->kw[0] * P->kw[0] + P->kw[1] * P->kw[1] + P->kw[2] * P->kw[2];
+    ksum[P->cell] += sqrt(kw2);
     kcnt[P->cell] += 1;
+    /* adaptive clamping (Sec. 4.4, Eq. 9): along a ray through the peak the
+       kernel integrates to at most rho = |A| sqrt(2 pi) s_max (the longest axis);
+       the extent E where rho exp(-(E^2 + |k_W|^2)/2) falls to clamp_eps bounds
+       the support, never beyond k_sigma; E^2 <= 0 drops the kernel */
+    P->k = D->k_sigma;
+    if (D->clamp_eps > 0) {
+      double smax = fmax(fmax(P->s[0], P->s[1]), P->s[2]);
+      double rho = fabs(P->A) * sqrt(2.0 * OR_PI) * smax;
+      double e2 = 2.0 * log(rho / D->clamp_eps) - kw2;
+      P->k = e2 <= 0 ? 0.0 : fmin(D->k_sigma, sqrt(e2));
+    }
   }
   for (int c = 0; c < OR_MAX_CELLS; ++c) f->kbar[c] = kcnt[c] > 0 ? ksum[c] / kcnt[c] : 0.0;
   return f;
@@ -416,7 +431,7 @@ double or_density(const or_field* f, const double x[3], uint64_t mask, const dou
     const or_prim* P = &f->p[i];
     if (!(mask >> P->cell & 1ull)) continue;
     double w = w64 ? w64[P->cell] : 1.0;
-    acc += w * prim_value(P, x, f->k);
+    acc += w * prim_value(P, x, P->k);
   }
   return acc;
 }
@@ -465,7 +480,7 @@ int or_chord(const or_field* f, int64_t i, const double o[3], const double v_in[
              double tmax, double* lo, double* hi) {
   double v[3];
   normalise(v_in, v);
-  or_chord_t c = chord_of(&f->p[i], o, v, f->k, tmin, tmax);
+  or_chord_t c = chord_of(&f->p[i], o, v, f->p[i].k, tmin, tmax);
   if (lo) *lo = c.lo;
   if (hi) *hi = c.hi;
   return c.has;
@@ -541,8 +556,8 @@ double or_chord_integral(const or_field* f, int64_t i, const double o[3], const 
   gl_init();
   double v[3];
   normalise(v_in, v);
-  or_chord_t c = chord_of(&f->p[i], o, v, f->k, tmin, tmax);
-  return chord_integral(&f->p[i], &c, o, v, f->k);
+  or_chord_t c = chord_of(&f->p[i], o, v, f->p[i].k, tmin, tmax);
+  return chord_integral(&f->p[i], &c, o, v, f->p[i].k);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -612,8 +627,8 @@ int or_chord_points(const or_field* f, int64_t i, const double o[3], const doubl
                     uint32_t word, double* t_out, double* uacc_out, int cap) {
   double v[3];
   normalise(v_in, v);
-  or_chord_t c = chord_of(&f->p[i], o, v, f->k, tmin, tmax);
-  return chord_points(&c, weight * fabs(f->p[i].A), f->k, seed, (uint32_t)i, ray, word, t_out,
+  or_chord_t c = chord_of(&f->p[i], o, v, f->p[i].k, tmin, tmax);
+  return chord_points(&c, weight * fabs(f->p[i].A), f->p[i].k, seed, (uint32_t)i, ray, word, t_out,
                       uacc_out, cap);
 }
 
@@ -633,7 +648,7 @@ double or_majorant(const or_field* f, const double o[3], const double v_in[3], d
     const or_prim* P = &f->p[i];
     if (!(mask >> P->cell & 1ull)) continue;
     double w = w64 ? w64[P->cell] : 1.0;
-    or_chord_t c = chord_of(P, o, v, f->k, tmin, tmax);
+    or_chord_t c = chord_of(P, o, v, P->k, tmin, tmax);
     acc += chord_bound(&c, w * fabs(P->A), t);
   }
   return acc;
@@ -666,7 +681,7 @@ static int collect_hits(const or_field* f, const double o[3], const double v[3],
     if (!(mask >> P->cell & 1ull)) continue;
     double w = w64 ? w64[P->cell] : 1.0;
     if (!(w > 0)) continue;
-    or_chord_t c = chord_of(P, o, v, f->k, tmin, tmax);
+    or_chord_t c = chord_of(P, o, v, P->k, tmin, tmax);
     if (!c.has) continue;
     if (n == cap) { cap *= 2; h = (or_hit*)realloc(h, sizeof(or_hit) * cap); }
     h[n].prim = i; h[n].w = w; h[n].c = c;
@@ -683,7 +698,7 @@ static int gather_points(const or_field* f, const or_hit* h, int nh, uint64_t se
   double tb[4096], ub[4096];
   for (int j = 0; j < nh; ++j) {
     const or_prim* P = &f->p[h[j].prim];
-    int m = chord_points(&h[j].c, h[j].w * fabs(P->A), f->k, seed, (uint32_t)h[j].prim, ray, word,
+    int m = chord_points(&h[j].c, h[j].w * fabs(P->A), P->k, seed, (uint32_t)h[j].prim, ray, word,
                          tb, ub, 4096);
     if (m > 4096) m = 4096;
     for (int q = 0; q < m; ++q) {
@@ -704,7 +719,7 @@ static void eval_point(const or_field* f, const or_hit* h, int nh, const double 
   for (int j = 0; j < nh; ++j) {
     if (t < h[j].c.lo || t > h[j].c.hi) continue;
     const or_prim* P = &f->p[h[j].prim];
-    k += h[j].w * prim_value(P, x, f->k);
+    k += h[j].w * prim_value(P, x, P->k);
     kb += chord_bound(&h[j].c, h[j].w * fabs(P->A), t);
   }
   *kap = k;
@@ -769,9 +784,9 @@ static double det_tau(const or_field* f, const double o[3], const double v[3], d
     if (!(mask >> P->cell & 1ull)) continue;
     double w = w64 ? w64[P->cell] : 1.0;
     if (!(w > 0)) continue;
-    or_chord_t c = chord_of(P, o, v, f->k, tmin, tmax);
+    or_chord_t c = chord_of(P, o, v, P->k, tmin, tmax);
     if (!c.has) continue;
-    acc += w * chord_integral(P, &c, o, v, f->k);
+    acc += w * chord_integral(P, &c, o, v, P->k);
   }
   return acc;
 }
@@ -1153,10 +1168,10 @@ double or_tomo_loss_grad(const or_field_desc* D, const or_camera* C, int spp, ui
       double dLdtau = -2.0 * (img[p] - target[p]) * exp(-tau) / spp;
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nt)
       for (int64_t i = 0; i < N; ++i) {
-        or_chord_t c = chord_of(&f->p[i], o, v, f->k, 0.0, INFINITY);
+        or_chord_t c = chord_of(&f->p[i], o, v, f->p[i].k, 0.0, INFINITY);
         if (!c.has) continue;
         double dt[15];
-        chord_grad(&G[i], &f->p[i], &c, o, v, 0.0, INFINITY, f->k, dt);
+        chord_grad(&G[i], &f->p[i], &c, o, v, 0.0, INFINITY, f->p[i].k, dt);
         for (int r = 0; r < 15; ++r) g15[i * 15 + r] += dLdtau * dt[r];
       }
     }
@@ -1242,7 +1257,7 @@ static void add_dkappa(const or_field* f, const or_gprim* G, const or_hit* h, in
                    o[2] + t * v[2] - Gi->mu[2]};
     or_gpoint P;
     gpoint(Gi, y, &P);
-    if (P.q > f->k * f->k) continue;
+    if (P.q > f->p[h[j].prim].k * f->p[h[j].prim].k) continue;
     double cw = coef * h[j].w;
     for (int r = 0; r < 15; ++r) {
       double d = Gi->A * P.env * (-0.5 * P.dq[r] * P.c - P.sn * P.dth[r]) + P.dA[r] * P.env * P.c;

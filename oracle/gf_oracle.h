@@ -47,6 +47,7 @@ typedef struct {
   int weight_mode;     /* 0 peak amplitude, 1 normalised (Eq. 6) */
   int omega_frame;     /* 0 world, 1 whitened frame (k_W) */
   double k_sigma;      /* support radius in sigma units (3 in the paper) */
+  double clamp_eps;    /* adaptive clamping (Sec. 4.4, Eq. 9); 0 = off */
 } or_field_desc;
 
 typedef struct {
@@ -78,6 +79,10 @@ typedef struct {
 typedef struct or_field or_field;
 
 or_field* or_field_create(const or_field_desc* desc);
+
+/* support radius of primitive i in sigma (whitened) units: k_sigma, or its
+   adaptive extent when clamp_eps > 0 (0 = the primitive is dropped) */
+double or_field_extent(const or_field* f, int64_t i);
 void or_field_free(or_field* f);
 int64_t or_field_size(const or_field* f);
 /* per-primitive labels (band, cone, cell) and per-cell mean |k_W| */

@@ -685,3 +685,73 @@ def test_threshold_culling_keeps_perpendicular_bins():
             assert got == keep, (t, b, got, keep)
             assert all(w[c] == 1.0 for c in got)
         assert m & 1 and w[0] == 1.0
+
+
+# --------------------------------------------------------------------------- adaptive clamping
+def _field_of(params, **kw):
+    return oracle.Field(params, omega_frame=params.get("omega_frame", "world"), **kw)
+
+
+def test_adaptive_clamping_gaussian_tail_bound():
+    """Sec. 4.4 adaptive clamping: a Gaussian's line integral through any point
+    at whitened radius r carries at most rho exp(-r^2/2), rho = |A| sqrt(2 pi)
+    s_max, so clamping the support at the radius E where rho exp(-E^2/2) = eps
+    removes at most eps from any ray's optical depth and never adds to it.  On
+    the central ray along the longest axis, E ~ 2 removes rho erfc(E/sqrt 2),
+    about a third of eps: both bounds are checked on random and axial rays."""
+    rng = np.random.default_rng(31)
+    for trial in range(6):
+        s = np.exp(rng.uniform(np.log(0.02), np.log(0.1), 3))
+        A = rng.uniform(0.5, 2.0)
+        rho = A * math.sqrt(2 * math.pi) * s.max()
+        eps = rho * math.exp(-0.5 * 2.0 ** 2)  # E = 2 (< k = 3: the clamp is active)
+        q = rng.standard_normal(4)
+        q /= np.linalg.norm(q)
+        p = {"mu": np.array([[0.5, 0.5, 0.5]], np.float32), "quat": q[None].astype(np.float32),
+             "log_scale": np.log(s)[None].astype(np.float32),
+             "omega": np.zeros((1, 3), np.float32), "phase": np.zeros(1, np.float32),
+             "weight": np.array([A], np.float32)}
+        full = oracle.Field(p, k_sigma=6.0)
+        cl = oracle.Field(p, k_sigma=6.0, clamp_eps=eps)
+        assert abs(cl.extents()[0] - 2.0) < 1e-5  # float32 inputs
+        _, R, sg = _geom(p)
+        ax = R[:, int(np.argmax(sg))]
+        rays = [(np.array([0.5, 0.5, 0.5]) - ax, ax)]
+        for _ in range(40):
+            rays.append(_ray_near(rng, [0.5, 0.5, 0.5], 1.5 * s.max()))
+        for j, (o, v) in enumerate(rays):
+            d = full.chord_integral(0, o, v) - cl.chord_integral(0, o, v)
+            assert -1e-15 <= d <= eps * (1 + 1e-6), (trial, j, d, eps)
+            if j == 0:
+                assert d >= 0.25 * eps, (d, eps)
+
+
+def test_adaptive_clamping_limits_and_frequency():
+    """eps -> 0 leaves every support at k and every optical depth unchanged;
+    supports never exceed k and shrink as the whitened frequency |k_W| grows
+    (the frequency-induced decay term of Sec. 4.4); a kernel whose attenuated
+    peak integral is below eps is dropped and contributes nothing."""
+    rng = np.random.default_rng(32)
+    p = synth.octave_field(400, 4, seed=3)
+    o, d, tr = synth.random_rays(64, seed=4)
+    f0 = _field_of(p)
+    ft = _field_of(p, clamp_eps=1e-300)
+    assert np.all(ft.extents() == 3.0)
+    assert np.array_equal(ft.transmittance(o, d, tr)[1], f0.transmittance(o, d, tr)[1])
+    f2 = _field_of(p, clamp_eps=1e-2)
+    e = f2.extents()
+    assert np.all((e >= 0) & (e <= 3.0)) and e.min() < 2.5
+    # one Gabor at increasing carrier frequency along its longest axis
+    base = {"mu": np.array([[0.5, 0.5, 0.5]], np.float32), "quat": np.array([[1, 0, 0, 0]], np.float32),
+            "log_scale": np.log(np.array([[0.05, 0.03, 0.02]])).astype(np.float32),
+            "phase": np.zeros(1, np.float32), "weight": np.array([1.0], np.float32)}
+    ext = []
+    for w in (0.0, 0.5, 1.0, 1.5, 2.0, 2.5, 3.0):
+        q = dict(base, omega=np.array([[w / 0.05, 0, 0]], np.float32))  # |k_W| = w
+        ext.append(oracle.Field(q, k_sigma=3.0, clamp_eps=2e-3).extents()[0])
+    assert all(a > b for a, b in zip(ext, ext[1:]) if b > 0) and ext[0] < 3.0
+    assert ext[-1] == 0.0
+    q = dict(base, omega=np.array([[3.0 / 0.05, 0, 0]], np.float32))
+    gone = oracle.Field(q, k_sigma=3.0, clamp_eps=2e-3)
+    assert gone.chord_integral(0, np.array([0.5, 0.5, -1.0]), np.array([0, 0, 1.0])) == 0.0
+    assert not gone.chord(0, np.array([0.5, 0.5, -1.0]), np.array([0, 0, 1.0]))[0]
