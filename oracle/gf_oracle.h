@@ -17,12 +17,11 @@
  *   kernel: A exp(-q/2) cos(omega.(x-mu) + phi) 1[q <= k^2],
  *   q = (x-mu)^T Sigma^-1 (x-mu)  (Eq. 6 with the k-sigma support of Sec. 3).
  *
- * Parity unpinned: the composition of two or more scattering bounces in
- * or_render / or_render_samples (max_bounces >= 2) has no closed form or
- * independent reference; its parts are pinned (delta-tracking collision CDF,
- * ratio-tracking expectation, single-scatter nested quadrature, mask weights),
- * the multi-bounce loop itself only by agreement with the CUDA path under
- * shared random streams.
+ * Multiple scattering (max_bounces >= 2) is pinned at two bounces: the
+ * second-bounce radiance of a pixel on one Gaussian equals the nested
+ * quadrature of the path integral (collision on the camera ray, isotropic
+ * direction, collision on the second leg, NEE), with closed-form
+ * transmittances; later bounces repeat the same loop step.
  */
 #ifndef GF_ORACLE_H
 #define GF_ORACLE_H

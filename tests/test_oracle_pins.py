@@ -755,3 +755,75 @@ def test_adaptive_clamping_limits_and_frequency():
     gone = oracle.Field(q, k_sigma=3.0, clamp_eps=2e-3)
     assert gone.chord_integral(0, np.array([0.5, 0.5, -1.0]), np.array([0, 0, 1.0])) == 0.0
     assert not gone.chord(0, np.array([0.5, 0.5, -1.0]), np.array([0, 0, 1.0]))[0]
+
+
+# --------------------------------------------------------------------------- multiple scattering
+def test_second_bounce_matches_nested_quadrature():
+    """Multiple scattering (Sec. 3 path integral with delta tracking, isotropic
+    phase, NEE at every collision): on one Gaussian (tau ~ 2 through its
+    centre, k = 6 so the cut is negligible) the second-bounce radiance of a
+    pixel, the oracle's 2-bounce minus 1-bounce render under shared streams,
+    equals the nested quadrature
+      a^2 E/(4 pi) int dt1 kappa(x1) T(o,x1) int dw/(4 pi) int dt2 kappa(x2) T(x1,x2) T_l(x2)
+    with every transmittance in closed form (scipy erf), within 4.5 standard errors."""
+    mu = np.array([0.5, 0.5, 0.5])
+    s = np.array([0.2, 0.15, 0.12])
+    q = np.array([0.9, 0.2, 0.3, 0.1])
+    q /= np.linalg.norm(q)
+    p = {"mu": mu[None].astype(np.float32), "quat": q[None].astype(np.float32),
+         "log_scale": np.log(s)[None].astype(np.float32), "omega": np.zeros((1, 3), np.float32),
+         "phase": np.zeros(1, np.float32), "weight": np.array([6.0], np.float32)}
+    f = oracle.Field(p, k_sigma=6.0)
+    Si, _, _ = _geom(p)
+    muf, A = p["mu"][0].astype(np.float64), float(p["weight"][0])
+
+    def depth(x, w, t0, t1):  # int_t0^t1 A exp(-q(x + s w)/2) ds, broadcast over leading axes
+        d = x - muf
+        a = np.einsum("...i,ij,...j->...", w, Si, w)
+        b = np.einsum("...i,ij,...j->...", w, Si, d)
+        g = np.einsum("...i,ij,...j->...", d, Si, d)
+        c = np.sqrt(a / 2)
+        return A * np.exp(-(g - b * b / a) / 2) * np.sqrt(np.pi / (2 * a)) * (
+            special.erf(c * (t1 + b / a)) - special.erf(c * (t0 + b / a)))
+
+    def kappa(x):
+        d = x - muf
+        return A * np.exp(-0.5 * np.einsum("...i,ij,...j->...", d, Si, d))
+
+    light = np.array([1.0, 1.0, -1.0]) / math.sqrt(3.0)
+    # an oblique camera ray that misses the centre: no symmetry hides a wrong direction law
+    cam = oracle.camera((1.4, 0.3, -0.5), (0.58, 0.44, 0.5), (0, 1, 0), 1.0, 64, 64)
+    px, py, albedo = 32, 31, 0.8
+    o, v = oracle.camera_ray(cam, 5, px, py, 0)  # the pixel spans 3e-4 rad: jitter is negligible
+    _, lo, hi = f.chord(0, o, v)
+    xn, wn = np.polynomial.legendre.leggauss(40)
+    t1 = 0.5 * (hi - lo) * xn + 0.5 * (hi + lo)
+    w1 = 0.5 * (hi - lo) * wn
+    X1 = o[None] + t1[:, None] * v[None]
+    first = w1 * kappa(X1) * np.exp(-depth(np.broadcast_to(o, X1.shape), np.broadcast_to(v, X1.shape), 0.0, t1))
+    mn, mw = np.polynomial.legendre.leggauss(32)
+    ph = (np.arange(64) + 0.5) * 2 * np.pi / 64
+    M, P = np.meshgrid(mn, ph, indexing="ij")
+    W = np.stack([np.sqrt(1 - M ** 2) * np.cos(P), np.sqrt(1 - M ** 2) * np.sin(P), M], -1).reshape(-1, 3)
+    Ww = (mw[:, None] * np.full(64, 2 * np.pi / 64)[None]).reshape(-1)  # sums to 4 pi
+    un, uw = np.polynomial.legendre.leggauss(48)
+    L2 = 0.0
+    for i in range(len(t1)):
+        d = X1[i] - muf
+        a = np.einsum("ki,ij,kj->k", W, Si, W)
+        b = np.einsum("ki,ij,j->k", W, Si, d)
+        texit = (-b + np.sqrt(b * b - a * (d @ Si @ d - 36.0))) / a  # leave the 6-sigma support
+        T2 = 0.5 * texit[:, None] * (un[None] + 1)
+        X2 = X1[i][None, None] + T2[..., None] * W[:, None, :]
+        inner = np.sum(0.5 * texit[:, None] * uw[None] * kappa(X2)
+                       * np.exp(-depth(np.broadcast_to(X1[i], X2.shape), np.broadcast_to(W[:, None, :], X2.shape), 0.0, T2))
+                       * np.exp(-depth(X2, np.broadcast_to(light, X2.shape), 0.0, np.inf)), axis=1)
+        L2 += first[i] * np.sum(Ww * inner) / (4 * np.pi)
+    L2 *= albedo * albedo / (4 * np.pi)
+    spp = 40000
+    r1 = f.render(cam, oracle.render_opts("scatter", spp, 1, albedo), seed=5, crop=(px, py, 1, 1), samples=True).ravel()
+    r2 = f.render(cam, oracle.render_opts("scatter", spp, 2, albedo), seed=5, crop=(px, py, 1, 1), samples=True).ravel()
+    d2 = r2 - r1
+    se = d2.std(ddof=1) / math.sqrt(spp)
+    assert abs(d2.mean() - L2) < 4.5 * se, (d2.mean(), L2, se)
+    assert L2 > 50 * se  # a resolved second bounce
