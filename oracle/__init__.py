@@ -80,6 +80,7 @@ def _load():
         lib.or_field_prim.argtypes = [vp, i64, vp, vp, vp]
         lib.or_field_extent.restype = dbl
         lib.or_field_extent.argtypes = [vp, i64]
+        lib.or_field_set_camera_lod.argtypes = [vp, vp]
         lib.or_philox4x32_10.argtypes = [vp, vp, vp]
         lib.or_sample_mask.argtypes = [vp, C.POINTER(Lod), vp, u64, u32, u32, u32, u32, vp, vp]
         lib.or_density.restype = dbl
@@ -176,6 +177,11 @@ class Field:
         """Support radius of every primitive in sigma units (Sec. 4.4 adaptive
         clamping when clamp_eps > 0; 0 = dropped)."""
         return np.array([self.lib.or_field_extent(self.h, i) for i in range(self.n)])
+
+    def set_camera_lod(self, cam):
+        """Camera-Nyquist LoD selection (Supp. A) for ``cam`` (None: every kernel)."""
+        self._lod_cam = cam
+        self.lib.or_field_set_camera_lod(self.h, None if cam is None else C.byref(cam))
 
     def prim(self, i):
         s = np.zeros(9); w = np.zeros(3); a = np.zeros(1)

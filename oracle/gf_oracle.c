@@ -74,7 +74,8 @@ typedef struct {
   double omega[3];   /* world-space carrier, rad per unit length */
   double kw[3];      /* whitened-frame carrier k_W = S R^T omega */
   double phi, A;
-  double k;          /* support radius in whitened units (k_sigma or adaptive) */
+  double k;          /* support radius in whitened units (k_sigma or adaptive; 0 = removed) */
+  double k_own;      /* the radius before any camera selection */
   int band, cone, cell;
 } or_prim;
 
@@ -90,6 +91,24 @@ struct or_field {
 int64_t or_field_size(const or_field* f) { return f->n; }
 
 double or_field_extent(const or_field* f, int64_t i) { return f->p[i].k; }
+
+void or_field_set_camera_lod(or_field* f, const or_camera* cam) {
+  if (!cam) {
+    for (int64_t i = 0; i < f->n; ++i) f->p[i].k = f->p[i].k_own;
+    return;
+  }
+  const double th = tan(0.5 * (double)cam->vfov_deg * OR_PI / 180.0);
+  const float c = (float)(OR_PI * (double)cam->height / (2.0 * th));
+  for (int64_t i = 0; i < f->n; ++i) {
+    or_prim* P = &f->p[i];
+    float ox = (float)P->omega[0], oy = (float)P->omega[1], oz = (float)P->omega[2];
+    float wn = sqrtf((ox * ox + oy * oy) + oz * oz);
+    float dx = (float)P->mu[0] - cam->eye[0], dy = (float)P->mu[1] - cam->eye[1],
+          dz = (float)P->mu[2] - cam->eye[2];
+    float d = sqrtf((dx * dx + dy * dy) + dz * dz);
+    P->k = (wn * d <= c) ? P->k_own : 0.0;
+  }
+}
 
 /* cone axes on the upper hemisphere, Fibonacci spiral (reading of the
    unspecified orientation bins of Sec. 4.5.2) */
@@ -211,6 +230,7 @@ or_field* or_field_create(const or_field_desc* D) {
       double e2 = 2.0 * log(rho / D->clamp_eps) - kw2;
       P->k = e2 <= 0 ? 0.0 : fmin(D->k_sigma, sqrt(e2));
     }
+    P->k_own = P->k;
   }
   for (int c = 0; c < OR_MAX_CELLS; ++c) f->kbar[c] = kcnt[c] > 0 ? ksum[c] / kcnt[c] : 0.0;
   return f;

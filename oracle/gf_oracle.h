@@ -80,8 +80,19 @@ typedef struct or_field or_field;
 or_field* or_field_create(const or_field_desc* desc);
 
 /* support radius of primitive i in sigma (whitened) units: k_sigma, or its
-   adaptive extent when clamp_eps > 0 (0 = the primitive is dropped) */
+   adaptive extent when clamp_eps > 0 (0 = the primitive is dropped, by the
+   clamp or by the camera selection below) */
 double or_field_extent(const or_field* f, int64_t i);
+
+/* camera-Nyquist LoD selection (Supp. A, LOD Selection): a pinhole camera
+   with H rows and vertical field of view phi spans 2 d tan(phi/2) / H per
+   pixel at distance d (the same along both image axes: square pixels), so
+   the finest carrier it resolves there is f_limit(d) = pi H / (2 d tan(phi/2))
+   rad per unit.  Every kernel whose |omega| exceeds f_limit at the distance d
+   from the eye to its mean is removed from the mixture until the next call.
+   The decision is taken in FP32 without contraction:
+   |omega| d <= (float)(pi H / (2 tan(phi/2))).  cam == NULL keeps all. */
+void or_field_set_camera_lod(or_field* f, const or_camera* cam);
 void or_field_free(or_field* f);
 int64_t or_field_size(const or_field* f);
 /* per-primitive labels (band, cone, cell) and per-cell mean |k_W| */

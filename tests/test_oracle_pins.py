@@ -827,3 +827,62 @@ def test_second_bounce_matches_nested_quadrature():
     se = d2.std(ddof=1) / math.sqrt(spp)
     assert abs(d2.mean() - L2) < 4.5 * se, (d2.mean(), L2, se)
     assert L2 > 50 * se  # a resolved second bounce
+
+
+# --------------------------------------------------------------------------- camera-Nyquist LoD
+def test_camera_lod_selection_against_measured_pixel_pitch():
+    """Supp. A (LOD Selection): a kernel stays iff its carrier is resolved at
+    its depth, |omega| <= pi / (pitch d), with the pixel pitch measured here on
+    the camera's own jittered rays (horizontally and vertically, non-square
+    image); kernels within 2% of the threshold are not judged."""
+    p = synth.absorption_field(400, seed=6)
+    p = dict(p, omega=(p["omega"] * 6.0).astype(np.float32))
+    f = oracle.Field(p)
+    eye, look = np.array([0.3, 0.6, -1.2]), np.array([0.5, 0.5, 0.5])
+    W, H, fov = 96, 64, 40.0
+    cam = oracle.camera(tuple(eye), tuple(look), (0, 1, 0), fov, W, H)
+    fw = (look - eye) / np.linalg.norm(look - eye)
+    rt = np.cross([0, 1, 0], fw); rt /= np.linalg.norm(rt)
+    up = np.cross(fw, rt)
+    pitches = []
+    for axis, n, pix in (("x", W, lambda k, s: (k, H // 2)), ("y", H, lambda k, s: (W // 2, k))):
+        lo, hi = [], []
+        for s in range(400):
+            for k, acc in ((0, lo), (n - 1, hi)):
+                _, v = oracle.camera_ray(cam, 3, *pix(k, s), s)
+                e = rt if axis == "x" else up
+                acc.append((v @ e) / (v @ fw))  # image-plane coordinate at unit depth
+        span = (max(max(lo), max(hi)) - min(min(lo), min(hi)))  # ~ n pitches
+        pitches.append(span / n)
+    assert abs(pitches[0] / pitches[1] - 1) < 0.01  # square pixels
+    pitch = np.mean(pitches)
+    for H2 in (64, 24, 8):
+        cam2 = oracle.camera(tuple(eye), tuple(look), (0, 1, 0), fov, W * H2 // H, H2)
+        f.set_camera_lod(cam2)
+        kept = f.extents() > 0
+        pit = pitch * H / H2
+        d = np.linalg.norm(p["mu"].astype(np.float64) - eye, axis=1)
+        lim = np.pi / (pit * d)
+        wn = np.linalg.norm(p["omega"].astype(np.float64), axis=1)
+        sure = np.abs(wn / lim - 1) > 0.02
+        assert np.array_equal(kept[sure], (wn <= lim)[sure]), H2
+        assert 0 < kept.sum() < len(kept) or H2 == 64
+    f.set_camera_lod(None)
+    assert np.all(f.extents() == 3.0)
+
+
+def test_camera_lod_selection_limits():
+    """A camera that resolves everything leaves every optical depth bit-equal;
+    one that resolves no carrier keeps exactly the Gaussian band (the band-0
+    cutoff of Sec. 4.5.1), again bit-equal."""
+    p = synth.octave_field(500, 4, seed=7)
+    o, d, tr = synth.random_rays(48, seed=8)
+    f = oracle.Field(p, omega_frame="local")
+    base = f.transmittance(o, d, tr)[1]
+    g0 = f.transmittance(o, d, tr, lod=oracle.Lod(1, 0, 0))[1]
+    c = synth.DEFAULT_CAMERA
+    f.set_camera_lod(oracle.camera(c["eye"], c["look_at"], c["up"], c["vfov_deg"], 1 << 20, 1 << 20))
+    assert np.array_equal(f.transmittance(o, d, tr)[1], base)
+    f.set_camera_lod(oracle.camera(c["eye"], c["look_at"], c["up"], c["vfov_deg"], 1, 1))
+    assert np.array_equal(f.extents() > 0, f.labels()[0] == 0)
+    assert np.array_equal(f.transmittance(o, d, tr)[1], g0)
