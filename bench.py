@@ -339,6 +339,60 @@ def run_workload(args):
                       {"ms_per_render": res_ms,
                        "mrays_per_s": {k: rays[k] / (res_ms[k] * 1e-3) / 1e6 for k in rays},
                        "gpu_launches": 2})
+    elif args.workload == "clamping":
+        # adaptive clamping (Sec. 4.4) on the single-scattering benchmark field and
+        # camera, all bands, at several thresholds; camera-Nyquist LoD selection
+        # (Supp. A) on 128x128 thumbnails of the same field.  Image differences are
+        # set beside the Monte Carlo noise: the RMSE between two renders of the
+        # unmodified field that differ only in the seed.
+        res = args.res or 512
+        spp = args.spp or 16
+        p = synth.octave_field(100_000, 4, seed=0)
+        ro = api.render_opts("scatter", spp, 1, 0.8, synth.LIGHT_DIR, 1.0)
+
+        def measure(f, cam, seed=2):
+            out = torch.empty(cam.height, cam.width, device=dev)
+            f.stats(reset=True)
+            ms = _timed(lambda: f.render(cam, ro, seed=seed, out=out), args.steps, args.warmup, stream)
+            f.sync()
+            st = f.stats(reset=True)
+            rays = st["rays"] / (args.steps + args.warmup)
+            return out.clone(), {"ms_per_render": statistics.mean(ms),
+                                 "mrays_per_s": rays / (statistics.mean(ms) * 1e-3) / 1e6,
+                                 "chords_per_ray": st["chords"] / max(1, st["rays"]),
+                                 "nodes_per_ray": st["nodes"] / max(1, st["rays"])}
+
+        def rmse(a, b):
+            return (a - b).pow(2).mean().sqrt().item()
+
+        cam = api.camera(c["eye"], c["look_at"], c["up"], c["vfov_deg"], res, res)
+        rows, ref = {}, None
+        for eps in (0.0, 1e-3, 3e-3, 1e-2):
+            f = api.Field(ctx, p, clamp_eps=eps)
+            img, row = measure(f, cam)
+            if ref is None:
+                ref = img
+                other, _ = measure(f, cam, seed=3)
+                noise = rmse(img, other)
+            row["image_rmse_vs_unclamped"] = rmse(img, ref)
+            rows[str(eps)] = row
+            f.free()
+        thumb = api.camera(c["eye"], c["look_at"], c["up"], c["vfov_deg"], 128, 128)
+        f = api.Field(ctx, p)
+        full, row_full = measure(f, thumb)
+        other, _ = measure(f, thumb, seed=3)
+        f.set_lod_camera(thumb)
+        sel, row_sel = measure(f, thumb)
+        f.free()
+        row_sel["image_rmse_vs_unfiltered"] = rmse(sel, full)
+        workload_line("adaptive clamping, 100k-primitive 4-octave field, %dx%d, %d spp, all bands"
+                      % (res, res, spp), rows["0.01"]["mrays_per_s"], "Mrays/s",
+                      rows["0.01"]["ms_per_render"], args,
+                      {"by_clamp_eps": rows, "image_rms": ref.pow(2).mean().sqrt().item(),
+                       "seed_to_seed_rmse": noise,
+                       "camera_lod_128x128": {"unfiltered": row_full, "nyquist": row_sel,
+                                              "seed_to_seed_rmse": rmse(full, other)},
+                       "gpu_launches": 2})
     elif args.workload == "adjoint":
         # 200k kernels, 256x256 at 8 spp: forward render plus hand-written adjoint of an
         # L2 loss against a target rendered from perturbed parameters
@@ -555,7 +609,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--server-requests", type=int, default=16,
                     help="requests of the render-server leg (0: skip)")
-    ap.add_argument("--workload", choices=["scatter", "transmittance", "multiscatter", "adjoint"],
+    ap.add_argument("--workload", choices=["scatter", "transmittance", "multiscatter", "adjoint",
+                                           "clamping"],
                     default="scatter", help="workload of the JSON line (default: the single-"
                     "scattering benchmark)")
     ap.add_argument("--res", type=int, default=None, help="profiling only: image size")

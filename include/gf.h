@@ -88,6 +88,12 @@ typedef struct gf_field_opts {
   int weight_mode; /* GF_WEIGHT_* */
   int omega_frame; /* GF_OMEGA_* */
   float k_sigma;   /* support radius in sigma units, (0, 6]; the paper uses 3 */
+  /* adaptive clamping (Sec. 4.4, Eq. 9): 0 = off; else each kernel's support
+     radius becomes k_i = min(k_sigma, E_i) in whitened units with
+     E_i^2 = 2 ln(rho_i / clamp_eps) - |k_W,i|^2, rho_i = |A_i| sqrt(2 pi) s_max,i
+     (the kernel's largest line integral through its peak, the paper's alpha K
+     at the longest axis); a kernel with E_i^2 <= 0 is dropped.  Finite, >= 0. */
+  float clamp_eps;
 } gf_field_opts;
 
 /* Level-of-detail mask (Sec. 4.5.1-4.5.2, 4.6; strategy tables of App. B).
@@ -200,6 +206,18 @@ gf_status gf_build_bvh(gf_field* field, gf_stream stream);
 /* Set the LoD mask used by subsequent calls: primary rays (camera and bounce
    segments, transmittance API) and NEE rays (nee may be NULL = same as primary). */
 gf_status gf_set_lod_mask(gf_field* field, const gf_lod_desc* primary, const gf_lod_desc* nee);
+
+/* Camera-Nyquist LoD selection (Supp. A, LOD Selection) for subsequent calls:
+   a pinhole camera with H = camera->height rows and vertical field of view
+   phi spans 2 d tan(phi/2) / H per pixel at distance d (square pixels), so it
+   resolves carriers up to f_limit(d) = pi H / (2 d tan(phi/2)) rad per unit;
+   every kernel with |omega| > f_limit(d) at the distance d from camera->eye
+   to its mean leaves the mixture (all rays: camera, bounce, NEE, API), and
+   cells left empty are skipped by the traversal.  Decided in FP32 without
+   contraction: |omega| d <= (float)(pi H / (2 tan(phi/2))).  Composes with
+   gf_set_lod_mask and with adaptive clamping.  camera NULL restores every
+   kernel.  Synchronises the stream. */
+gf_status gf_set_lod_camera(gf_field* field, const gf_camera* camera, gf_stream stream);
 
 /* Transmittance of n_rays rays x(t) = o + t d, t in [trange[2r], trange[2r+1]]
    (trange NULL: [0, inf)); d is normalised by the library.

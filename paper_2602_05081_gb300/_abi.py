@@ -43,7 +43,7 @@ class gf_params(C.Structure):
 
 class gf_field_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("weight_mode", C.c_int), ("omega_frame", C.c_int),
-                ("k_sigma", C.c_float)]
+                ("k_sigma", C.c_float), ("clamp_eps", C.c_float)]
 
 
 class gf_lod_desc(C.Structure):
@@ -106,6 +106,7 @@ _SIGS = {
     "gf_field_free": [_vp],
     "gf_build_bvh": [_vp, _vp],
     "gf_set_lod_mask": [_vp, C.POINTER(gf_lod_desc), C.POINTER(gf_lod_desc)],
+    "gf_set_lod_camera": [_vp, C.POINTER(gf_camera), _vp],
     "gf_transmittance": [_vp, _vp, _vp, _vp, _i64, _int, _int, _u64, _vp, _vp, _vp],
     "gf_transmittance_static": [_vp, _vp, _vp, _vp, _i64, _int, _int, _u64, _vp, _vp, _vp],
     "gf_render": [_vp, C.POINTER(gf_camera), C.POINTER(gf_render_opts), _u64, _vp, _vp],
@@ -194,6 +195,11 @@ def gf_build_bvh(field, stream=None):
 
 def gf_set_lod_mask(field, primary: gf_lod_desc, nee: gf_lod_desc | None = None):
     _check(lib.gf_set_lod_mask(field, C.byref(primary), None if nee is None else C.byref(nee)))
+
+
+def gf_set_lod_camera(field, camera: "gf_camera | None", stream=None):
+    _check(lib.gf_set_lod_camera(field, None if camera is None else C.byref(camera),
+                                 stream_handle(stream)))
 
 
 def gf_transmittance(field, o, d, trange, n_rays, mode, spp, seed, out_T, out_tau=None,

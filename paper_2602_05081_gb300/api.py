@@ -66,7 +66,7 @@ class Field:
     """A packed primitive set with its BVH on one GPU."""
 
     def __init__(self, ctx: Context, params: dict, precision="fp32", weight_mode=None,
-                 omega_frame=None, k_sigma=3.0, stream=None, device_inputs=True):
+                 omega_frame=None, k_sigma=3.0, stream=None, device_inputs=True, clamp_eps=0.0):
         self.ctx = ctx
         dev = torch.device("cuda", ctx.device) if device_inputs else torch.device("cpu")
         self._keep = {k: _as_tensor(params[k], dev) for k in _KEYS}
@@ -77,7 +77,8 @@ class Field:
                         A.ptr(self._keep["band"]))
         wm = weight_mode or params.get("weight_mode", "peak")
         fr = omega_frame or params.get("omega_frame", "world")
-        opts = A.gf_field_opts(_PRECS[precision], _WMODES[wm], _FRAMES[fr], float(k_sigma))
+        opts = A.gf_field_opts(_PRECS[precision], _WMODES[wm], _FRAMES[fr], float(k_sigma),
+                               float(clamp_eps))
         self.h = A.gf_load_field(ctx.h, p, opts, stream)
         A.gf_build_bvh(self.h, stream)
         if not device_inputs:
@@ -96,6 +97,10 @@ class Field:
 
     def set_lod(self, primary=None, nee=None):
         A.gf_set_lod_mask(self.h, primary if primary is not None else lod(), nee)
+
+    def set_lod_camera(self, cam=None, stream=None):
+        """Camera-Nyquist LoD selection (Supp. A) for ``cam``; None restores all kernels."""
+        A.gf_set_lod_camera(self.h, cam, stream)
 
     def transmittance(self, o, d, trange=None, mode="det", spp=1, seed=0, out_T=None,
                       out_tau=None, stream=None):

@@ -164,7 +164,8 @@ struct BackLeaf {
   __device__ void operator()(int j) {
     Prim P = load_prim(*F, j);
     Chord ch;
-    if (!chord_setup(P, o, v, tmin, tmax, F->k2, ch)) return;
+    // the support radius is a constant of the differentiation (adaptive extents too)
+    if (!chord_setup(P, o, v, tmin, tmax, P.k2, ch)) return;
     const int64_t i = ch.orig;
     PrimDeriv D;
     D.init(*B, P, i);
@@ -459,7 +460,7 @@ struct RadScatter {
   __device__ void operator()(int j) {
     const Prim Pr = load_prim(*F, j);
     Chord ch;
-    if (!chord_setup(Pr, o, v, 0.f, INFINITY, F->k2, ch)) return;
+    if (!chord_setup(Pr, o, v, 0.f, INFINITY, Pr.k2, ch)) return;
     const float w = mask_weight(*M, ch.cell);
     if (w == 0.f) return;
     const float tin = ch.tc + ch.dtin, tout = ch.tc + ch.dtout;

@@ -194,7 +194,8 @@ namespace {
 void free_field(Field& F) {
   void* ptrs[] = {F.p_mu, F.p_quat, F.p_ls, F.p_om, F.p_ph, F.p_w, F.rec_orig, F.box_orig,
                   F.kw_orig, F.rec, F.rec16, F.nodes, F.nodes4, F.sorted_orig, F.labels, F.err,
-                  F.stats, F.counter, F.cell_acc, F.stage, F.wscratch, F.acc64, F.rlist, F.gl};
+                  F.stats, F.counter, F.cell_acc, F.stage, F.wscratch, F.acc64, F.rlist, F.gl,
+                  F.ext2_orig, F.ext2, F.keff2, F.muw, F.cells_dev};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -267,6 +268,8 @@ gf_status gf_load_field(gf_ctx* ctx, const gf_params* p, const gf_field_opts* op
   if (opts->precision < 0 || opts->precision > 2) return fail(GF_EINVAL, "bad precision");
   if (opts->weight_mode < 0 || opts->weight_mode > 1) return fail(GF_EINVAL, "bad weight_mode");
   if (opts->omega_frame < 0 || opts->omega_frame > 1) return fail(GF_EINVAL, "bad omega_frame");
+  if (!(opts->clamp_eps >= 0.f && opts->clamp_eps < INFINITY))
+    return fail(GF_EINVAL, "clamp_eps must be finite and >= 0");
   GF_CUDA(cudaSetDevice(ctx->c.device), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
   gf_field* h = new gf_field;
@@ -288,6 +291,7 @@ gf_status gf_load_field(gf_ctx* ctx, const gf_params* p, const gf_field_opts* op
         (e = A((void**)&F.counter, 16)) || (e = A((void**)&F.cell_acc, 128 * 4)) ||
         (e = A((void**)&F.gl, 2 * kGLTotal * sizeof(float))))
       break;
+    if ((e = A((void**)&F.ext2_orig, 4 * n)) || (e = A((void**)&F.ext2, 4 * n))) break;
     if ((e = cudaMemcpyAsync(F.gl, ctx->c.gl, 2 * kGLTotal * sizeof(float),
                              cudaMemcpyDeviceToDevice, s)))
       break;
@@ -351,6 +355,7 @@ gf_status gf_load_field(gf_ctx* ctx, const gf_params* p, const gf_field_opts* op
   F.dev.stats = F.stats;
   F.dev.gl = F.gl;
   weideman_coefficients(F.dev.wd);
+  F.dev.cells_on = ~0ull;
   F.dev.root = -1;
   *out = h;
   return GF_OK;
@@ -373,11 +378,14 @@ gf_status gf_build_bvh(gf_field* h, gf_stream stream) {
   GF_CUDA(cudaMalloc((void**)&F.rec, 64 * n), "alloc records");
   GF_CUDA(cudaMalloc((void**)&F.nodes, n > 1 ? (n - 1) * sizeof(Node) : 16), "alloc nodes");
   GF_CUDA(cudaMalloc((void**)&F.sorted_orig, 4 * n), "alloc order");
+  GF_CUDA(cudaMalloc((void**)&F.muw, 16 * n), "alloc means");
   GF_CUDA(build_bvh(F, (cudaStream_t)stream), "build_bvh");
   cudaFree(F.rec_orig);
   F.rec_orig = nullptr;
   cudaFree(F.box_orig);
   F.box_orig = nullptr;
+  cudaFree(F.ext2_orig);
+  F.ext2_orig = nullptr;
   if (F.opts.precision != GF_PREC_FP32) {
     // 32-byte records replace the 64-byte ones on the rendering path
     GF_CUDA(cudaMalloc((void**)&F.rec16, 32 * n), "alloc reduced records");
@@ -397,6 +405,35 @@ gf_status gf_build_bvh(gf_field* h, gf_stream stream) {
     F.dev.rec = nullptr;
   }
   F.built = true;
+  return GF_OK;
+}
+
+gf_status gf_set_lod_camera(gf_field* h, const gf_camera* cam, gf_stream stream) {
+  if (!h) return fail(GF_EINVAL, "field null");
+  Field& F = h->f;
+  if (!F.built) return fail(GF_ESTATE, "gf_build_bvh has not run");
+  if (cam && (cam->width < 1 || cam->height < 1 || !(cam->vfov_deg > 0.f && cam->vfov_deg < 180.f)))
+    return fail(GF_EINVAL, "bad camera");
+  GF_CUDA(cudaSetDevice(F.ctx.device), "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool reduced = F.opts.precision != GF_PREC_FP32;
+  if (!F.cells_dev) GF_CUDA(cudaMalloc((void**)&F.cells_dev, sizeof(unsigned long long)), "alloc");
+  if (reduced && !F.keff2) GF_CUDA(cudaMalloc((void**)&F.keff2, 4 * F.n), "alloc");
+  // the finest resolved carrier at distance d is c / d (pixel pitch 2 d tan(phi/2) / H)
+  const double pi = 3.14159265358979323846;
+  float3 eye = make_float3(0.f, 0.f, 0.f);
+  float c = INFINITY;
+  if (cam) {
+    const double th = std::tan(0.5 * (double)cam->vfov_deg * pi / 180.0);
+    c = (float)(pi * (double)cam->height / (2.0 * th));
+    eye = make_float3(cam->eye[0], cam->eye[1], cam->eye[2]);
+  }
+  GF_CUDA(launch_camera_lod(F, eye, c, s), "camera lod launch");
+  unsigned long long cells = 0;
+  GF_CUDA(cudaMemcpyAsync(&cells, F.cells_dev, sizeof(cells), cudaMemcpyDeviceToHost, s), "cells");
+  GF_CUDA(cudaStreamSynchronize(s), "sync");
+  F.dev.cells_on = cam ? cells : ~0ull;
+  if (reduced) F.dev.ext2 = cam ? F.keff2 : F.ext2;
   return GF_OK;
 }
 

@@ -22,10 +22,12 @@ struct PackArgs {
   gf_params p;
   int weight_mode, omega_frame, precision;
   float ksig;
+  float clamp_eps;  // adaptive clamping threshold (0: off)
   float axes[kCones][3];
   float4* rec;
   float* box;
   float* kw;
+  float* ext2;      // support radius squared per primitive (k^2 or adaptive)
   uint8_t* labels;  // band[N], cone[N], cell[N]
   float* cell_acc;  // sum |k_W| [64], count [64]
   int* err;
@@ -101,16 +103,28 @@ __global__ void k_pack(const __grid_constant__ PackArgs A) {
     }
   }
   int cell = band == 0 ? 0 : 1 + kCones * (band - 1) + cone;
+  float kn = sqrtf(kw[0] * kw[0] + kw[1] * kw[1] + kw[2] * kw[2]);
+  // support radius: k, or the adaptive extent of Sec. 4.4 (Eq. 9) where the
+  // kernel's largest line integral rho = |A| sqrt(2 pi) s_max, attenuated by
+  // exp(-(E^2 + |k_W|^2)/2), falls to clamp_eps
+  float k2i = A.ksig * A.ksig;
+  if (A.clamp_eps > 0.0f) {
+    const float rho = fabsf(amp) * 2.5066282746310002f * fmaxf(fmaxf(s[0], s[1]), s[2]);
+    const float e2 = 2.0f * logf(rho / A.clamp_eps) - kn * kn;
+    k2i = fminf(k2i, fmaxf(e2, 0.0f));
+  }
+  A.ext2[i] = k2i;
+  const float kext = sqrtf(k2i);
   float4* r = A.rec + 4 * i;
   r[0] = make_float4(mu[0], mu[1], mu[2], amp);
   r[1] = make_float4(P[0][0], P[0][1], P[0][2], P[1][1]);
-  r[2] = make_float4(P[1][2], P[2][2], phi, __uint_as_float((uint32_t)cell));
-  r[3] = make_float4(om[0], om[1], om[2], __uint_as_float((uint32_t)i));
+  r[2] = make_float4(P[1][2], P[2][2], phi, k2i);
+  r[3] = make_float4(om[0], om[1], om[2], __uint_as_float((uint32_t)i | ((uint32_t)cell << 26)));
   // box of the k-sigma ellipsoid: half-extent k sqrt(Sigma_jj), padded
   for (int a = 0; a < 3; ++a) {
     float sjj = R[a][0] * R[a][0] * s[0] * s[0] + R[a][1] * R[a][1] * s[1] * s[1] +
                 R[a][2] * R[a][2] * s[2] * s[2];
-    float hw = A.ksig * sqrtf(sjj);
+    float hw = kext * sqrtf(sjj);
     // reduced-precision records change the decoded ellipsoid: inverse scales by
     // 2^-11 (FP16) or 2^-8 (BF16) of themselves, the rotation by an angle of at
     // most 6.1e-5 (snorm16 quaternion), which moves an extent by that angle
@@ -123,7 +137,6 @@ __global__ void k_pack(const __grid_constant__ PackArgs A) {
     A.box[6 * i + a] = mu[a] - hw - pad;
     A.box[6 * i + 3 + a] = mu[a] + hw + pad;
   }
-  float kn = sqrtf(kw[0] * kw[0] + kw[1] * kw[1] + kw[2] * kw[2]);
   A.kw[i] = kn;
   A.labels[i] = (uint8_t)band;
   A.labels[A.p.n + i] = (uint8_t)cone;
@@ -140,6 +153,8 @@ cudaError_t launch_pack(Field& F, const gf_params& P, cudaStream_t s) {
   A.omega_frame = F.opts.omega_frame;
   A.precision = F.opts.precision;
   A.ksig = F.opts.k_sigma;
+  A.clamp_eps = F.opts.clamp_eps;
+  A.ext2 = F.ext2_orig;
   for (int k = 0; k < kCones; ++k)
     for (int j = 0; j < 3; ++j) A.axes[k][j] = F.dev.axes[k][j];
   A.rec = F.rec_orig;
@@ -213,7 +228,7 @@ __global__ void k_morton(const float4* rec, int64_t n, const unsigned int* bound
     hi[j] = ord_dec(bounds[9 + j]);
   }
   float4 r0 = rec[4 * i];
-  uint32_t cell = __float_as_uint(rec[4 * i + 2].w);
+  uint32_t cell = __float_as_uint(rec[4 * i + 3].w) >> 26;
   float m[3] = {r0.x, r0.y, r0.z};
   unsigned int c[3];
   for (int j = 0; j < 3; ++j) {
@@ -227,14 +242,56 @@ __global__ void k_morton(const float4* rec, int64_t n, const unsigned int* bound
   idx[i] = (int)i;
 }
 
-__global__ void k_gather(const float4* rec_in, const float* box_in, const int* idx, int64_t n,
-                         float4* rec_out, float* box_out, int* sorted_orig) {
+__global__ void k_gather(const float4* rec_in, const float* box_in, const float* ext2_in,
+                         const int* idx, int64_t n, float4* rec_out, float* box_out,
+                         float* ext2_out, float4* muw_out, int* sorted_orig) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   int i = idx[j];
   for (int k = 0; k < 4; ++k) rec_out[4 * j + k] = rec_in[4 * (int64_t)i + k];
   for (int k = 0; k < 6; ++k) box_out[6 * j + k] = box_in[6 * (int64_t)i + k];
+  ext2_out[j] = ext2_in[i];
+  // mean and |omega| (FP32, no contraction) for the camera LoD selection
+  const float4 r0 = rec_in[4 * (int64_t)i], r3 = rec_in[4 * (int64_t)i + 3];
+  const float wn = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(r3.x, r3.x), __fmul_rn(r3.y, r3.y)),
+                                        __fmul_rn(r3.z, r3.z)));
+  muw_out[j] = make_float4(r0.x, r0.y, r0.z, wn);
   sorted_orig[j] = i;
+}
+
+// camera LoD selection (Supp. A): primitive j stays in the mixture iff
+// |omega| d <= c, d the distance from the eye to its mean, c = pi H / (2 tan(phi/2))
+// (c = +inf restores every primitive).  A removed primitive gets the support
+// radius squared -1, so no ray finds a chord of it; the cells still holding a
+// primitive are OR-ed into *cells.
+__global__ void k_camera_lod(const float4* muw, const float* k2own, const uint8_t* cell_of_orig,
+                             const int* sorted_orig, int64_t n, float3 eye, float c, float4* rec,
+                             float* k2eff, unsigned long long* cells) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long cb = 0ull;
+  if (j < n) {
+    const float4 m = muw[j];
+    const float dx = __fsub_rn(m.x, eye.x), dy = __fsub_rn(m.y, eye.y), dz = __fsub_rn(m.z, eye.z);
+    const float d = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)),
+                                         __fmul_rn(dz, dz)));
+    const bool k = __fmul_rn(m.w, d) <= c;
+    const float v = k ? k2own[j] : -1.0f;
+    if (rec) rec[4 * j + 2].w = v;
+    if (k2eff) k2eff[j] = v;
+    if (k) cb = 1ull << (cell_of_orig[sorted_orig[j]] & 63u);
+  }
+  const unsigned lo = __reduce_or_sync(kFull, (unsigned)cb);
+  const unsigned hi = __reduce_or_sync(kFull, (unsigned)(cb >> 32));
+  if ((threadIdx.x & 31u) == 0 && (lo | hi)) atomicOr(cells, ((unsigned long long)hi << 32) | lo);
+}
+
+cudaError_t launch_camera_lod(Field& F, float3 eye, float c, cudaStream_t s) {
+  (void)cudaGetLastError();  // a stale error of an unrelated call is not ours
+  cudaError_t e = cudaMemsetAsync(F.cells_dev, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k_camera_lod<<<(unsigned)((F.n + 255) / 256), 256, 0, s>>>(
+      F.muw, F.ext2, F.labels + 2 * F.n, F.sorted_orig, F.n, eye, c, F.rec, F.keff2, F.cells_dev);
+  return cudaGetLastError();
 }
 
 __device__ __forceinline__ int delta_key(const unsigned long long* k, int64_t n, int64_t i, int64_t j) {
@@ -293,7 +350,7 @@ __global__ void k_refit(const float* box, const float4* rec, int64_t n, Node* no
   if (j >= n) return;
   float b[6];
   for (int k = 0; k < 6; ++k) b[k] = box[6 * j + k];
-  unsigned long long m = 1ull << (__float_as_uint(rec[4 * j + 2].w) & 63u);
+  unsigned long long m = 1ull << (__float_as_uint(rec[4 * j + 3].w) >> 26);
   int child = ~(int)j;
   int node = leaf_parent[j];
   for (int guard = 0; node >= 0 && guard < 4096; ++guard) {
@@ -468,8 +525,9 @@ cudaError_t build_bvh(Field& F, cudaStream_t s) {
   GF_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys, keys2, idx, idx2, (int)n, 0, 36, s));
   GF_TRY(dalloc(&tmp, tmp_bytes));
   GF_TRY(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys, keys2, idx, idx2, (int)n, 0, 36, s));
-  k_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(F.rec_orig, F.box_orig, idx2, n, F.rec,
-                                                      box_sorted, F.sorted_orig);
+  k_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(F.rec_orig, F.box_orig, F.ext2_orig, idx2,
+                                                      n, F.rec, box_sorted, F.ext2, F.muw,
+                                                      F.sorted_orig);
   GF_TRY(cudaGetLastError());
   if (n >= 2) {
     GF_TRY(cudaMemsetAsync(F.nodes, 0, (n - 1) * sizeof(Node), s));
@@ -519,6 +577,7 @@ cudaError_t build_bvh(Field& F, cudaStream_t s) {
     }
   }
   F.dev.rec = F.rec;
+  F.dev.ext2 = F.ext2;  // read by the reduced-precision path (FP32 records carry their own)
   F.dev.nodes = F.nodes;
   F.dev.nodes4 = F.nodes4;
   F.dev.root = n >= 2 ? 0 : -1;

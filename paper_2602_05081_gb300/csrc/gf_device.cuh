@@ -87,6 +87,9 @@ struct DevField {
   float3 qlo, qscale;      // reduced-precision records: mean = qlo + code * qscale
   const float* gl;         // Gauss-Legendre nodes then weights (2 x kGLTotal)
   Weideman wd;             // Faddeeva expansion (closed-form chord integrals)
+  const float* ext2;       // reduced-precision records: support radius squared per primitive,
+                           // BVH order, -1 = not in the mixture (FP32 records carry their own)
+  unsigned long long cells_on;  // cells holding a primitive of the mixture (all ones by default)
   int* err;
   unsigned long long* stats;  // rays, chords, evals, nodes, points
 };
@@ -212,11 +215,15 @@ __device__ __forceinline__ float warp_sum_comp(float s, float c) {
 // FP32 record (64 B): {mu.xyz, A}, {P00, P01, P02, P11}, {P12, P22, phi, cell},
 // {omega.xyz, orig index}, P = Sigma^-1.
 // ---------------------------------------------------------------------------
+// FP32 record word 15: original index (26 bits) | cell << 26
+constexpr uint32_t kOrigMask = (1u << 26) - 1u;
+
 struct Prim {
   float3 mu;
   float A;
   float p00, p01, p02, p11, p12, p22;
   float phi;
+  float k2;  // support radius squared: k^2, the adaptive extent, or -1 (not in the mixture)
   uint32_t cell;
   float3 om;
   uint32_t orig;
@@ -229,9 +236,10 @@ __device__ __forceinline__ Prim load_prim(const DevField& F, int j) {
   P.mu = make_float3(r0.x, r0.y, r0.z);
   P.A = r0.w;
   P.p00 = r1.x; P.p01 = r1.y; P.p02 = r1.z; P.p11 = r1.w;
-  P.p12 = r2.x; P.p22 = r2.y; P.phi = r2.z; P.cell = __float_as_uint(r2.w);
+  P.p12 = r2.x; P.p22 = r2.y; P.phi = r2.z; P.k2 = r2.w;
   P.om = make_float3(r3.x, r3.y, r3.z);
-  P.orig = __float_as_uint(r3.w);
+  P.orig = __float_as_uint(r3.w) & kOrigMask;
+  P.cell = __float_as_uint(r3.w) >> 26;
   return P;
 }
 
@@ -393,7 +401,7 @@ __device__ __forceinline__ bool chord_setup16(const DevField& F, uint4 r0, uint4
   const float g = fmaf(pwx, pwx, fmaf(pwy, pwy, pwz * pwz));
   const float dts = -b * ia;
   const float qmin = fmaf(b, dts, g);
-  const float disc = F.k2 - qmin;
+  const float disc = __ldg(F.ext2 + j) - qmin;
   if (!(disc > 0.0f)) return false;
   const float hw = sqrtf(disc * ia);
   const float lo = fmaxf(dts - hw, tmin - tc);
@@ -429,7 +437,7 @@ __device__ __forceinline__ bool prim_chord(const DevField& F, int j, float3 o, f
     const Prim P = load_prim(F, j);
     w = weight(P.cell & 63u);
     if (!(w > 0.f)) return false;
-    return chord_setup(P, o, v, tmin, tmax, F.k2, ch);
+    return chord_setup(P, o, v, tmin, tmax, P.k2, ch);
   }
   const uint4* r = F.rec16 + 2 * (int64_t)j;
   const uint4 r0 = __ldg(r), r1 = __ldg(r + 1);

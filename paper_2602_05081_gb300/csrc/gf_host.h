@@ -61,6 +61,11 @@ struct Field {
   float4* rec_orig = nullptr;   // FP32 records in original order (until the build)
   float* box_orig = nullptr;    // 6 floats per primitive
   float* kw_orig = nullptr;     // |k_W| per primitive
+  float* ext2_orig = nullptr;   // own support radius squared per primitive (until the build)
+  float* ext2 = nullptr;        // own support radius squared, BVH order (k^2 or adaptive)
+  float* keff2 = nullptr;       // reduced precision + camera LoD: effective k_i^2, BVH order
+  float4* muw = nullptr;        // BVH order: mean and |omega| (camera LoD selection)
+  unsigned long long* cells_dev = nullptr;  // camera LoD selection: cells still occupied
   float4* rec = nullptr;        // FP32 records in BVH order
   uint4* rec16 = nullptr;       // reduced-precision records in BVH order
   Node* nodes = nullptr;
@@ -120,6 +125,7 @@ cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* ou
                           cudaStream_t s);
 cudaError_t launch_faddeeva(const Weideman& W, const float* z, float* w, int64_t n,
                            cudaStream_t s);
+cudaError_t launch_camera_lod(Field& F, float3 eye, float c, cudaStream_t s);
 void weideman_coefficients(Weideman& W);
 cudaError_t launch_pack(Field& F, const gf_params& P, cudaStream_t s);
 cudaError_t build_bvh(Field& F, cudaStream_t s);

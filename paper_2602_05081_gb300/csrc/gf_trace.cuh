@@ -303,6 +303,7 @@ __device__ __forceinline__ Mask sample_mask_impl(const DevField& F, const LodDev
     M.bw[b] = bw[b] * cf;
     M.bits |= 1ull << (1 + kCones * (b - 1) + k);
   }
+  M.bits &= F.cells_on;  // cells the camera selection emptied are not traversed
   return M;
 }
 
