@@ -62,7 +62,7 @@ class Camera(C.Structure):
 class RenderOpts(C.Structure):
     _fields_ = [("integrator", C.c_int), ("spp", C.c_int), ("max_bounces", C.c_int),
                 ("albedo", C.c_float), ("light_dir", C.c_float * 3),
-                ("light_irradiance", C.c_float)]
+                ("light_irradiance", C.c_float), ("free_flight", C.c_int)]
 
 
 def _load():
@@ -95,6 +95,8 @@ def _load():
         lib.or_majorant.argtypes = [vp, vp, vp, dbl, dbl, dbl, u64, vp]
         lib.or_transmittance.argtypes = [vp, C.POINTER(Lod), vp, vp, vp, i64, i32, i32, u64, vp,
                                          vp, i32]
+        lib.or_cdf_flight.restype = i32
+        lib.or_cdf_flight.argtypes = [vp, vp, vp, dbl, dbl, u64, vp, u64, u32, u32, vp]
         lib.or_delta_track.restype = i32
         lib.or_delta_track.argtypes = [vp, vp, vp, dbl, dbl, u64, vp, u64, u32, u32, vp]
         lib.or_render.argtypes = [vp, C.POINTER(Lod), C.POINTER(Lod), C.POINTER(Camera),
@@ -232,6 +234,15 @@ class Field:
                                   int(threads))
         return T, tau
 
+    def cdf_flight(self, o, v, seed, ray, word, tmin=0.0, tmax=np.inf, mask=(1 << 64) - 1,
+                   w64=None):
+        """Free flight by inversion of the optical-depth CDF (bisection)."""
+        t = np.zeros(1)
+        hit = self.lib.or_cdf_flight(self.h, _ptr(_f64(o)), _ptr(_f64(v)), float(tmin), float(tmax),
+                                     int(mask), None if w64 is None else _ptr(_f64(w64)),
+                                     int(seed), int(ray), int(word), _ptr(t))
+        return bool(hit), float(t[0])
+
     def delta_track(self, o, v, seed, ray, word, tmin=0.0, tmax=np.inf, mask=(1 << 64) - 1,
                     w64=None):
         t = np.zeros(1)
@@ -321,9 +332,10 @@ def camera_ray(cam, seed, px, py, s):
 
 
 def render_opts(integrator="scatter", spp=1, max_bounces=1, albedo=0.8,
-                light_dir=(1.0, 1.0, -1.0), light_irradiance=1.0):
+                light_dir=(1.0, 1.0, -1.0), light_irradiance=1.0, free_flight="delta"):
     return RenderOpts(0 if integrator == "tomo" else 1, int(spp), int(max_bounces), float(albedo),
-                      (C.c_float * 3)(*light_dir), float(light_irradiance))
+                      (C.c_float * 3)(*light_dir), float(light_irradiance),
+                      {"delta": 0, "cdf": 1}[free_flight])
 
 
 def rays_traced(reset=False):

@@ -811,6 +811,35 @@ static double det_tau(const or_field* f, const double o[3], const double v[3], d
   return acc;
 }
 
+int or_cdf_flight(const or_field* f, const double o[3], const double v_in[3], double tmin,
+                  double tmax, uint64_t mask, const double* w64, uint64_t seed, uint32_t ray,
+                  uint32_t word, double* t_hit) {
+  gl_init();
+  double v[3];
+  normalise(v_in, v);
+  uint32_t x[4];
+  rng4(seed, 0, OR_NO_PRIM, ray, word, x);
+  const double target = -log(1.0 - u01(x[0]));
+  /* the optical depth stops growing at the last chord exit */
+  double tend = tmin;
+  for (int64_t i = 0; i < f->n; ++i) {
+    const or_prim* P = &f->p[i];
+    if (!(mask >> P->cell & 1ull)) continue;
+    if (w64 && !(w64[P->cell] > 0)) continue;
+    or_chord_t c = chord_of(P, o, v, P->k, tmin, tmax);
+    if (c.has && c.hi > tend) tend = c.hi;
+  }
+  if (!(tend > tmin) || det_tau(f, o, v, tmin, tend, mask, w64) < target) return 0;
+  double lo = tmin, hi = tend;
+  for (int it = 0; it < 60; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (det_tau(f, o, v, tmin, mid, mask, w64) < target) lo = mid;
+    else hi = mid;
+  }
+  *t_hit = 0.5 * (lo + hi);
+  return 1;
+}
+
 static int nthreads_of(int n) {
 #ifdef _OPENMP
   return n > 0 ? n : omp_get_max_threads();
@@ -928,8 +957,9 @@ static double path_sample(const or_field* f, const or_lod* lod, const or_lod* lo
     or_sample_mask(f, lod, v, seed, pix, (uint32_t)s, (uint32_t)b, OR_TAG_MASK, &mask, w64);
     double th;
     count_ray();
-    if (!or_delta_track(f, o, v, 0.0, INFINITY, mask, w64, seed, pix,
-                        stream_word((uint32_t)s, (uint32_t)b, OR_TAG_TRACK), &th))
+    const uint32_t tw = stream_word((uint32_t)s, (uint32_t)b, OR_TAG_TRACK);
+    if (ro->free_flight ? !or_cdf_flight(f, o, v, 0.0, INFINITY, mask, w64, seed, pix, tw, &th)
+                        : !or_delta_track(f, o, v, 0.0, INFINITY, mask, w64, seed, pix, tw, &th))
       break;
     double x[3] = {o[0] + th * v[0], o[1] + th * v[1], o[2] + th * v[2]};
     thr *= ro->albedo;
@@ -937,8 +967,10 @@ static double path_sample(const or_field* f, const or_lod* lod, const or_lod* lo
     double nw[OR_MAX_CELLS];
     or_sample_mask(f, lodn, l, seed, pix, (uint32_t)s, (uint32_t)b, OR_TAG_NEE_MASK, &nmask, nw);
     count_ray();
-    double Tl = ratio_track(f, x, l, 0.0, INFINITY, nmask, nw, seed, pix,
-                            stream_word((uint32_t)s, (uint32_t)b, OR_TAG_NEE), 1);
+    double Tl = ro->free_flight
+                    ? exp(-det_tau(f, x, l, 0.0, INFINITY, nmask, nw))
+                    : ratio_track(f, x, l, 0.0, INFINITY, nmask, nw, seed, pix,
+                                  stream_word((uint32_t)s, (uint32_t)b, OR_TAG_NEE), 1);
     L += thr * ro->light_irradiance * Tl / (4.0 * OR_PI);
     uint32_t y[4];
     rng4(seed, 0, OR_NO_PRIM, pix, stream_word((uint32_t)s, (uint32_t)b, OR_TAG_SCATTER), y);

@@ -73,6 +73,8 @@ typedef struct {
   float albedo;
   float light_dir[3]; /* direction towards the light */
   float light_irradiance;
+  int free_flight;    /* 0 delta tracking (NEE by ratio tracking); 1 inversion of the
+                         optical-depth CDF by bisection (NEE transmittance exp(-tau)) */
 } or_render_opts;
 
 typedef struct or_field or_field;
@@ -136,6 +138,16 @@ double or_majorant(const or_field* f, const double o[3], const double v[3], doub
 void or_transmittance(const or_field* f, const or_lod* lod, const float* o, const float* d,
                       const float* trange, int64_t n_rays, int mode, int spp, uint64_t seed,
                       double* T, double* tau, int n_threads);
+
+/* free flight by inversion of the optical-depth CDF (Sec. 3 segment-based
+   transfer, Sec. 4.4 distance sampling): with xi the first uniform of the
+   (seed, ray, word) stream, the distance t solves tau(tmin, t) = -ln(1 - xi),
+   found by 60 bisections of [tmin, last chord exit]; returns 0 (escape) when
+   the whole ray's tau does not reach the target.  The density must be
+   non-negative along the ray for t to be the first crossing. */
+int or_cdf_flight(const or_field* f, const double o[3], const double v[3], double tmin,
+                  double tmax, uint64_t mask, const double* w64, uint64_t seed, uint32_t ray,
+                  uint32_t word, double* t_hit);
 
 /* delta tracking along one ray: returns 1 and the collision t, or 0 if the ray escapes */
 int or_delta_track(const or_field* f, const double o[3], const double v[3], double tmin,

@@ -886,3 +886,40 @@ def test_camera_lod_selection_limits():
     f.set_camera_lod(oracle.camera(c["eye"], c["look_at"], c["up"], c["vfov_deg"], 1, 1))
     assert np.array_equal(f.extents() > 0, f.labels()[0] == 0)
     assert np.array_equal(f.transmittance(o, d, tr)[1], g0)
+
+
+# --------------------------------------------------------------------------- CDF-inversion free flight
+def test_cdf_inversion_free_flight_distribution():
+    """Free flight by inversion of the optical-depth CDF (Sec. 3, Sec. 4.4): on a
+    non-negative field the sampled distance has CDF 1 - exp(-tau(0, t)) (chi^2
+    against a trapezoid integral of the density), each sample solves
+    tau(0, t) = -ln(1 - xi) with xi its own stream's first uniform, and a ray
+    whose whole optical depth is below the target escapes."""
+    p = _gauss_only()
+    f = oracle.Field(p)
+    o = np.array([0.5, 0.5, -0.5]); v = np.array([0.0, 0.0, 1.0])
+    grid = np.linspace(0.0, 2.0, 40001)
+    kap = np.array([f.density(o + t * v) for t in grid])
+    cum = np.concatenate([[0.0], np.cumsum(0.5 * (kap[1:] + kap[:-1]) * np.diff(grid))])
+    edges = np.linspace(0.6, 1.4, 17)
+    Fe = 1 - np.exp(-np.interp(edges, grid, cum))
+    probs = np.concatenate([[Fe[0]], np.diff(Fe), [1 - Fe[-1]]])
+    n = 4000
+    word = oracle.stream_word(0, 0, oracle.TAG_TRACK)
+    hits = []
+    for r in range(n):
+        h, t = f.cdf_flight(o, v, seed=2, ray=r, word=word)
+        hits.append(t if h else np.inf)
+        if r < 40:
+            xi = (oracle.philox4x32_10([0, 0xFFFFFFFF, r, word], [2, 0])[0] >> 8) / 2.0 ** 24
+            if h:
+                tau_t = np.interp(t, grid, cum)
+                assert abs(tau_t + math.log1p(-xi)) < 1e-4, (r, tau_t, xi)
+            else:
+                assert cum[-1] < -math.log1p(-xi) + 1e-4
+    hits = np.array(hits)
+    counts = np.concatenate([[np.sum(hits < edges[0])], np.histogram(hits, edges)[0],
+                             [np.sum(hits >= edges[-1])]])
+    keep = probs * n > 5
+    chi2 = np.sum((counts[keep] - n * probs[keep]) ** 2 / (n * probs[keep]))
+    assert chi2 < stats.chi2.ppf(0.9999, keep.sum() - 1)
