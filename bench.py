@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -393,6 +394,41 @@ def run_workload(args):
                        "camera_lod_128x128": {"unfiltered": row_full, "nyquist": row_sel,
                                               "seed_to_seed_rmse": rmse(full, other)},
                        "gpu_launches": 2})
+    elif args.workload == "free_flight":
+        # free flight by delta tracking against inversion of the optical-depth CDF
+        # (bisection on the closed-form tau, closed-form NEE transmittance): the
+        # benchmark field's Gaussian band (a non-negative density), single
+        # scattering, at equal samples per pixel; the noise of each is the RMSE
+        # between two renders that differ only in the seed
+        res = args.res or 256
+        spp = args.spp or 4
+        p = synth.octave_field(100_000, 4, seed=0)
+        cam = api.camera(c["eye"], c["look_at"], c["up"], c["vfov_deg"], res, res)
+        f = api.Field(ctx, p)
+        f.set_lod(api.lod("cutoff", 0))
+        rows, imgs = {}, {}
+        for mode in ("delta", "cdf"):
+            ro = api.render_opts("scatter", spp, 1, 0.8, synth.LIGHT_DIR, 1.0, free_flight=mode)
+            a = torch.empty(res, res, device=dev)
+            b = torch.empty(res, res, device=dev)
+            f.stats(reset=True)
+            ms = _timed(lambda: f.render(cam, ro, seed=2, out=a), args.steps, args.warmup, stream)
+            f.sync()
+            st = f.stats(reset=True)
+            f.render(cam, ro, seed=3, out=b)
+            f.sync()
+            imgs[mode] = a.clone()
+            noise = (a - b).pow(2).mean().sqrt().item() / math.sqrt(2.0)
+            t = statistics.mean(ms)
+            rows[mode] = {"ms_per_render": t,
+                          "mrays_per_s": st["rays"] / (args.steps + args.warmup) / (t * 1e-3) / 1e6,
+                          "nodes_per_ray": st["nodes"] / max(1, st["rays"]),
+                          "pixel_noise_rms": noise, "time_x_variance": t * noise * noise}
+        f.free()
+        rows["image_mean"] = {k: v.mean().item() for k, v in imgs.items()}
+        workload_line("free flight, Gaussian band of the 100k-primitive 4-octave field, %dx%d, %d spp"
+                      % (res, res, spp), rows["cdf"]["mrays_per_s"], "Mrays/s",
+                      rows["cdf"]["ms_per_render"], args, {"by_free_flight": rows, "gpu_launches": 1})
     elif args.workload == "adjoint":
         # 200k kernels, 256x256 at 8 spp: forward render plus hand-written adjoint of an
         # L2 loss against a target rendered from perturbed parameters
@@ -610,7 +646,7 @@ def main():
     ap.add_argument("--server-requests", type=int, default=16,
                     help="requests of the render-server leg (0: skip)")
     ap.add_argument("--workload", choices=["scatter", "transmittance", "multiscatter", "adjoint",
-                                           "clamping"],
+                                           "clamping", "free_flight"],
                     default="scatter", help="workload of the JSON line (default: the single-"
                     "scattering benchmark)")
     ap.add_argument("--res", type=int, default=None, help="profiling only: image size")

@@ -158,6 +158,15 @@ typedef struct gf_camera {
    isotropic phase 1/(4 pi), isotropic re-emission, up to max_bounces
    collisions (1 = single scattering). */
 enum { GF_INTEG_TOMO = 0, GF_INTEG_SCATTER = 1 };
+/* Free flight of the scattering integrator.  DELTA: delta tracking on the
+   per-segment majorants, NEE transmittance by ratio tracking (see gf_render).
+   CDF: the collision distance solves tau(0, t) = -ln(1 - xi) (Sec. 3
+   segment-based transfer, Sec. 4.4 distance sampling), by 32 bisections on the
+   closed-form optical depth (see GF_TR_CLOSED_FORM), and the NEE transmittance
+   is exp(-tau) in closed form; it assumes a non-negative mixture along each
+   ray (the first crossing) and is rendered per thread. */
+enum { GF_FLIGHT_DELTA = 0, GF_FLIGHT_CDF = 1 };
+
 typedef struct gf_render_opts {
   int integrator;
   int spp;
@@ -165,6 +174,7 @@ typedef struct gf_render_opts {
   float albedo;
   float light_dir[3]; /* direction towards the light, normalised by the library */
   float light_irradiance;
+  int free_flight;    /* GF_FLIGHT_*: scattering only (the server and the adjoint: DELTA) */
 } gf_render_opts;
 
 /* Work counters accumulated by the kernels since the last reset. */

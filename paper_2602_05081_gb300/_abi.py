@@ -26,6 +26,7 @@ GF_OMEGA_WORLD, GF_OMEGA_LOCAL = 0, 1
  GF_FREQ_POW_CV_ACC) = range(7)
 GF_CONE_ALL, GF_CONE_IS, GF_CONE_UNIFORM, GF_CONE_THRESH, GF_CONE_THRESH_UNIFORM = range(5)
 GF_TR_DETERMINISTIC, GF_TR_RATIO_TRACKING, GF_TR_CLOSED_FORM = 0, 1, 2
+GF_FLIGHT_DELTA, GF_FLIGHT_CDF = 0, 1
 GF_INTEG_TOMO, GF_INTEG_SCATTER = 0, 1
 
 
@@ -59,7 +60,7 @@ class gf_camera(C.Structure):
 class gf_render_opts(C.Structure):
     _fields_ = [("integrator", C.c_int), ("spp", C.c_int), ("max_bounces", C.c_int),
                 ("albedo", C.c_float), ("light_dir", C.c_float * 3),
-                ("light_irradiance", C.c_float)]
+                ("light_irradiance", C.c_float), ("free_flight", C.c_int)]
 
 
 class gf_stats(C.Structure):

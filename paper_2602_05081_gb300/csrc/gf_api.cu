@@ -150,7 +150,10 @@ gf_status camera_params(const gf_camera* c, const gf_render_opts* o, uint64_t se
   P.cam.aspect = (float)((double)c->width / (double)c->height);
   P.cam.W = c->width;
   P.cam.H = c->height;
+  if (o->free_flight != GF_FLIGHT_DELTA && o->free_flight != GF_FLIGHT_CDF)
+    return fail(GF_EINVAL, "bad free_flight");
   P.integrator = o->integrator;
+  P.free_flight = o->free_flight;
   P.spp = o->spp;
   P.max_bounces = o->max_bounces;
   P.albedo = o->albedo;
@@ -219,6 +222,9 @@ gf_status gf_create(int device, gf_ctx** out) {
   GF_CUDA(cudaSetDevice(device), "cudaSetDevice");
   cudaDeviceProp prop;
   GF_CUDA(cudaGetDeviceProperties(&prop, device), "cudaGetDeviceProperties");
+  // the per-thread stack of this context (a limit of the process, not of the GPU):
+  // explicit, so that every kernel's local frame is covered (launchers check it)
+  GF_CUDA(cudaDeviceSetLimit(cudaLimitStackSize, kStackLimit), "cudaDeviceSetLimit");
   if (!(prop.major == 10 && prop.minor == 3))
     return fail(GF_ECUDA, "libgf is built for sm_103a (GB300); device is sm_" +
                               std::to_string(prop.major) + std::to_string(prop.minor));
@@ -527,6 +533,7 @@ gf_status gf_render_backward(gf_field* h, const gf_camera* camera, const gf_rend
   PathParams P;
   gf_status st = camera_params(camera, opts, seed, F, P);
   if (st) return st;
+  if (P.free_flight != GF_FLIGHT_DELTA) return fail(GF_EINVAL, "the adjoint differentiates GF_FLIGHT_DELTA");
   if (opts->integrator == GF_INTEG_SCATTER && opts->max_bounces != 1)
     return fail(GF_EINVAL, "the radiance adjoint covers single scattering (max_bounces 1)");
   if (F.opts.precision != GF_PREC_FP32)

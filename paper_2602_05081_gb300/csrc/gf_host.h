@@ -117,6 +117,9 @@ struct ServerLaunch {
 };
 
 // launchers (return cudaError_t of the launch)
+// per-thread stack limit set on every context (bytes); kernels above it are not launched
+constexpr int kStackLimit = 2048;
+
 cudaError_t launch_transmittance(const Field& F, const TrParams& P, cudaStream_t s);
 cudaError_t launch_render(const Field& F, const PathParams& P, float* out, cudaStream_t s);
 cudaError_t launch_render_scatter(const Field& F, const PathParams& P, float* out, cudaStream_t s);

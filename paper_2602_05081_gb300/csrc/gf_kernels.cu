@@ -106,8 +106,9 @@ __global__ void __launch_bounds__(kBlock)
 
 // ---------------------------------------------------------------------------
 // render: each lane owns one pixel of an 8x4 tile and runs its samples in
-// order (deterministic per pixel)
+// order (deterministic per pixel); CDF: scattering with CDF-inversion free flight
 // ---------------------------------------------------------------------------
+template <bool CDF>
 __global__ void __launch_bounds__(kBlock)
     k_render(const __grid_constant__ DevField F, const PathParams P, float* out, int* counter) {
   __shared__ BlockTables sm;
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(kBlock)
     const bool active = px < P.cam.W && py < P.cam.H;
     float acc = 0.f;
     for (int s = 0; s < P.spp; ++s)
-      acc += path_sample(F, P, active, px, py, s, sm.glx, sm.glw, sm.env, cnt);
+      acc += path_sample<CDF>(F, P, active, px, py, s, sm.glx, sm.glw, sm.env, cnt);
     if (active) out[(int64_t)py * P.cam.W + px] = acc / (float)P.spp;
   }
   flush_counters(F, cnt, lane);
@@ -217,6 +218,15 @@ __global__ void k_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out
 // ---------------------------------------------------------------------------
 // launchers: persistent grids of (resident blocks per SM) x SMs
 // ---------------------------------------------------------------------------
+// every kernel's per-thread stack (its local memory frame, callees included)
+// must fit the context's stack limit, which gf_create sets to kStackLimit
+template <class K>
+static bool stack_fits(K kernel) {
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, kernel) != cudaSuccess) return false;
+  return a.localSizeBytes <= (size_t)kStackLimit;
+}
+
 template <class K>
 static int persistent_grid(const Field& F, K kernel, int64_t warps_of_work) {
   int per_sm = 0;
@@ -260,9 +270,18 @@ cudaError_t launch_render(const Field& F, const PathParams& P, float* out, cudaS
   (void)cudaGetLastError();  // a stale error of an unrelated call is not ours
   cudaError_t e = cudaMemsetAsync(F.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  if (P.integrator == GF_INTEG_SCATTER) return launch_render_scatter(F, P, out, s);
+  if (P.integrator == GF_INTEG_SCATTER && P.free_flight == GF_FLIGHT_DELTA)
+    return launch_render_scatter(F, P, out, s);
   const int64_t tiles = (int64_t)((P.cam.W + kTileW - 1) / kTileW) * ((P.cam.H + kTileH - 1) / kTileH);
-  k_render<<<persistent_grid(F, k_render, tiles), kBlock, 0, s>>>(F.dev, P, out, F.counter);
+  if (P.integrator == GF_INTEG_SCATTER) {
+    auto k = k_render<true>;
+    if (!stack_fits(k)) return cudaErrorLaunchOutOfResources;
+    k<<<persistent_grid(F, k, tiles), kBlock, 0, s>>>(F.dev, P, out, F.counter);
+  } else {
+    auto k = k_render<false>;
+    if (!stack_fits(k)) return cudaErrorLaunchOutOfResources;
+    k<<<persistent_grid(F, k, tiles), kBlock, 0, s>>>(F.dev, P, out, F.counter);
+  }
   return cudaGetLastError();
 }
 

@@ -488,6 +488,7 @@ gf_status gf_server_submit(gf_server* S, const gf_request* rq, uint64_t* ticket)
   if (rq->asset < 0 || rq->asset >= (int)S->fields.size()) return report(GF_EINVAL, "bad asset index");
   if (!rq->out) return report(GF_EINVAL, "out null");
   if (rq->opts.integrator != GF_INTEG_SCATTER) return report(GF_EINVAL, "the server renders GF_INTEG_SCATTER");
+  if (rq->opts.free_flight != GF_FLIGHT_DELTA) return report(GF_EINVAL, "the server renders GF_FLIGHT_DELTA");
   if (!lod_ok(&rq->lod) || !lod_ok(&rq->lod_nee)) return report(GF_EINVAL, "bad lod descriptor");
   auto r = std::make_unique<Req>();
   gf_status s = camera_params(&rq->camera, &rq->opts, rq->seed, *S->fields[rq->asset], r->dev.P);

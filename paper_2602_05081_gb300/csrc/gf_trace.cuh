@@ -467,6 +467,7 @@ struct ClosedLeaf {
   float3 o, v;
   float tmin, tmax;
   float s = 0.f, c = 0.f;
+  float tend = -INFINITY;  // the last chord exit
   unsigned long long nch = 0;
   int sub = 0, group = 1;  // group is a power of two
   __device__ __forceinline__ void operator()(int j) {
@@ -477,15 +478,17 @@ struct ClosedLeaf {
       return;
     const bool mine = (int)(nch & (unsigned long long)(group - 1)) == sub;
     ++nch;
+    tend = fmaxf(tend, ch.tc + ch.dtout);
     if (mine) neumaier_add(s, c, w * chord_closed(F->wd, ch));
   }
 };
 
 __device__ __forceinline__ float closed_tau(const DevField& F, const Mask& M, float3 o, float3 v,
                                             float tmin, float tmax, Counters& cnt, int sub = 0,
-                                            int group = 1) {
+                                            int group = 1, float* tend = nullptr) {
   const float3 inv = safe_inv(v);
   float t0, t1;
+  if (tend) *tend = -INFINITY;
   if (M.bits == 0ull || !scene_span(F, o, inv, tmin, tmax, t0, t1)) return 0.f;
   ClosedLeaf leaf;
   leaf.sub = sub;
@@ -505,7 +508,33 @@ __device__ __forceinline__ float closed_tau(const DevField& F, const Mask& M, fl
     cnt.windows += 1;
     cnt.chords += leaf.nch;
   }
+  if (tend) *tend = leaf.tend;
   return __fadd_rn(leaf.s, leaf.c);
+}
+
+// Free flight by inversion of the optical-depth CDF (Sec. 3 segment-based
+// transfer, Sec. 4.4 distance sampling): with xi the first uniform of the
+// segment's tracking stream, the distance solves tau(0, t) = -ln(1 - xi),
+// found by 32 bisections of [0, last chord exit] on the closed-form optical
+// depth (one windowed traversal each).  Returns false when the whole ray's
+// optical depth does not reach the target.  The first crossing needs a
+// non-negative density along the ray.
+__device__ __forceinline__ bool cdf_flight(const DevField& F, const Mask& M, float3 o, float3 v,
+                                           uint64_t seed, uint32_t ray, uint32_t word, float& th,
+                                           Counters& cnt) {
+  const uint4 y = rng4(seed, 0, kNoPrim, ray, word);
+  const float target = -log1pf(-u01(y.x));
+  float tend;
+  const float total = closed_tau(F, M, o, v, 0.f, INFINITY, cnt, 0, 1, &tend);
+  if (!(tend > 0.f) || total < target) return false;
+  float lo = 0.f, hi = tend;
+  for (int it = 0; it < 32; ++it) {
+    const float mid = 0.5f * (lo + hi);
+    if (closed_tau(F, M, o, v, 0.f, mid, cnt) < target) lo = mid;
+    else hi = mid;
+  }
+  th = 0.5f * (lo + hi);
+  return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -795,6 +824,7 @@ __device__ __forceinline__ void camera_ray(const CamDev& C, uint64_t seed, int p
 struct PathParams {
   CamDev cam;
   int integrator, spp, max_bounces;
+  int free_flight;  // GF_FLIGHT_DELTA or GF_FLIGHT_CDF
   float albedo, irradiance;
   float3 light;
   uint64_t seed;
@@ -805,6 +835,9 @@ struct PathParams {
 // Called by all lanes of a warp together (inactive lanes with active = false):
 // every phase (camera tracking, NEE, scattering) runs with the lanes that need
 // it converged, and the lanes regroup after each phase.
+// CDF selects the free flight at compile time (GF_FLIGHT_CDF; else delta
+// tracking), so that each kernel carries only the stack of the path it runs.
+template <bool CDF>
 static __device__ float path_sample(const DevField& F, const PathParams& P, bool active, int px,
                                     int py, int s, const float* glx, const float* glw,
                                     const float* env, Counters& cnt) {
@@ -831,8 +864,11 @@ static __device__ float path_sample(const DevField& F, const PathParams& P, bool
       const Mask m = sample_mask(F, P.lod, v, P.seed, pix, (uint32_t)s, (uint32_t)b, TAG_MASK);
       GF_TOC(cnt, 3, cm);
       cnt.rays += 1;
-      hit = track<true>(F, m, o, v, 0.f, INFINITY, true, P.seed, pix,
-                        stream_word((uint32_t)s, (uint32_t)b, TAG_TRACK), env, cnt, &th);
+      const uint32_t tw = stream_word((uint32_t)s, (uint32_t)b, TAG_TRACK);
+      if constexpr (CDF)
+        hit = cdf_flight(F, m, o, v, P.seed, pix, tw, th, cnt) ? 1.f : 0.f;
+      else
+        hit = track<true>(F, m, o, v, 0.f, INFINITY, true, P.seed, pix, tw, env, cnt, &th);
     }
     __syncwarp();
     alive = alive && hit != 0.f;
@@ -842,8 +878,12 @@ static __device__ float path_sample(const DevField& F, const PathParams& P, bool
       const Mask mn = sample_mask(F, P.lod_nee, P.light, P.seed, pix, (uint32_t)s, (uint32_t)b,
                                   TAG_NEE_MASK);
       cnt.rays += 1;
-      const float Tl = track<false>(F, mn, x, P.light, 0.f, INFINITY, true, P.seed, pix,
-                                    stream_word((uint32_t)s, (uint32_t)b, TAG_NEE), env, cnt, nullptr);
+      float Tl;
+      if constexpr (CDF)
+        Tl = expf(-closed_tau(F, mn, x, P.light, 0.f, INFINITY, cnt));
+      else
+        Tl = track<false>(F, mn, x, P.light, 0.f, INFINITY, true, P.seed, pix,
+                          stream_word((uint32_t)s, (uint32_t)b, TAG_NEE), env, cnt, nullptr);
       Lsum += thr * P.irradiance * Tl * (0.25f / 3.14159265358979f);
       const uint4 y = rng4(P.seed, 0, kNoPrim, pix, stream_word((uint32_t)s, (uint32_t)b, TAG_SCATTER));
       const float z = 1.0f - 2.0f * u01(y.x);
