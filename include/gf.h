@@ -226,7 +226,8 @@ gf_status gf_set_lod_mask(gf_field* field, const gf_lod_desc* primary, const gf_
    cells left empty are skipped by the traversal.  Decided in FP32 without
    contraction: |omega| d <= (float)(pi H / (2 tan(phi/2))).  Composes with
    gf_set_lod_mask and with adaptive clamping.  camera NULL restores every
-   kernel.  Synchronises the stream. */
+   kernel.  GF_ESTATE while a render server holds the field.  Synchronises
+   the stream. */
 gf_status gf_set_lod_camera(gf_field* field, const gf_camera* camera, gf_stream stream);
 
 /* Transmittance of n_rays rays x(t) = o + t d, t in [trange[2r], trange[2r+1]]
@@ -384,8 +385,11 @@ typedef struct gf_server_stats {
 /* Create a server over n_fields built fields of one context (the fields stay
    owned by the caller).  Allocates the framebuffer pool, per-launch scratch
    for two launches in flight and the batch buffers, then starts the
-   scheduler thread.  GF_EINVAL for bad options, GF_ESTATE for an unbuilt
-   field, GF_ENOMEM if the pool does not fit. */
+   scheduler thread.  Every request carries its own camera, so a field with a
+   camera LoD selection (gf_set_lod_camera) cannot be served, and a field
+   cannot get one while a server holds it.  GF_EINVAL for bad options,
+   GF_ESTATE for an unbuilt field or one with a camera selection, GF_ENOMEM if
+   the pool does not fit. */
 gf_status gf_server_create(gf_ctx* ctx, gf_field* const* fields, int n_fields,
                            const gf_server_opts* opts, gf_server** out);
 /* Queue a request; *ticket identifies it.  Validated here: asset index,

@@ -420,6 +420,7 @@ gf_status gf_set_lod_camera(gf_field* h, const gf_camera* cam, gf_stream stream)
   if (!F.built) return fail(GF_ESTATE, "gf_build_bvh has not run");
   if (cam && (cam->width < 1 || cam->height < 1 || !(cam->vfov_deg > 0.f && cam->vfov_deg < 180.f)))
     return fail(GF_EINVAL, "bad camera");
+  if (F.server_refs > 0) return fail(GF_ESTATE, "a render server holds this field");
   GF_CUDA(cudaSetDevice(F.ctx.device), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
   const bool reduced = F.opts.precision != GF_PREC_FP32;
@@ -439,6 +440,7 @@ gf_status gf_set_lod_camera(gf_field* h, const gf_camera* cam, gf_stream stream)
   GF_CUDA(cudaMemcpyAsync(&cells, F.cells_dev, sizeof(cells), cudaMemcpyDeviceToHost, s), "cells");
   GF_CUDA(cudaStreamSynchronize(s), "sync");
   F.dev.cells_on = cam ? cells : ~0ull;
+  F.camera_lod = cam != nullptr;
   if (reduced) F.dev.ext2 = cam ? F.keff2 : F.ext2;
   return GF_OK;
 }

@@ -77,6 +77,8 @@ struct Field {
   int* counter = nullptr;
   float* cell_acc = nullptr;    // per-cell |k_W| sums (64) and counts (64)
   bool built = false;
+  bool camera_lod = false;  // a camera LoD selection is active
+  int server_refs = 0;      // render servers holding this field
   float mu_lo[3] = {0, 0, 0}, mu_hi[3] = {0, 0, 0};  // box of the means (from the build)
   DevField dev{};
   LodDev lod{0, 7, 0, 0.f, 0.f}, lod_nee{0, 7, 0, 0.f, 0.f};

@@ -424,6 +424,8 @@ gf_status gf_server_create(gf_ctx* ctx, gf_field* const* fields, int n_fields,
   for (int i = 0; i < n_fields; ++i) {
     if (!fields[i]) return report(GF_EINVAL, "null field");
     if (!fields[i]->f.built) return report(GF_ESTATE, "field not built");
+    if (fields[i]->f.camera_lod)
+      return report(GF_ESTATE, "field has a camera LoD selection (requests carry their cameras)");
     if (fields[i]->f.ctx.device != ctx->c.device) return report(GF_EINVAL, "field of another device");
   }
   cudaError_t e = cudaSetDevice(ctx->c.device);
@@ -479,6 +481,7 @@ gf_status gf_server_create(gf_ctx* ctx, gf_field* const* fields, int n_fields,
   }
   S->t0 = std::chrono::steady_clock::now();
   S->worker = std::thread([S] { S->run(); });
+  for (const Field* f : S->fields) ++const_cast<Field*>(f)->server_refs;
   *out = S;
   return GF_OK;
 }
@@ -572,6 +575,7 @@ gf_status gf_server_destroy(gf_server* S) {
     S->cv_work.notify_all();
   }
   if (S->worker.joinable()) S->worker.join();
+  for (const Field* f : S->fields) --const_cast<Field*>(f)->server_refs;
   cudaSetDevice(S->ctx.device);
   free_server(S);
   return GF_OK;

@@ -145,6 +145,13 @@ def test_server_admission_queue_and_errors(api, ctx, assets):
         with pytest.raises(_abi.GfError) as e:
             srv.submit(0, _cam(api, 8, 8), api.render_opts("tomo", 1))
         assert e.value.status == _abi.GF_EINVAL
+        with pytest.raises(_abi.GfError) as e:
+            srv.submit(0, _cam(api, 8, 8), api.render_opts("scatter", 1, 1, free_flight="cdf"))
+        assert e.value.status == _abi.GF_EINVAL
+        # a camera LoD selection belongs to one camera: not on a served field
+        with pytest.raises(_abi.GfError) as e:
+            fields[0].set_lod_camera(_cam(api, 8, 8))
+        assert e.value.status == _abi.GF_ESTATE
         # one full-pool request at a time; the queue bound is enforced at submit
         tk = []
         refused = 0
@@ -160,6 +167,13 @@ def test_server_admission_queue_and_errors(api, ctx, assets):
         srv.close()
     assert all(r["state"] == 2 for r in res)
     assert st["max_inflight_seen"] == 1
+    # a field with a selection cannot be served; without it, again it can
+    fields[0].set_lod_camera(_cam(api, 8, 8))
+    with pytest.raises(_abi.GfError) as e:
+        api.Server(ctx, fields[:1], mem_budget=64 * 64 * 4)
+    assert e.value.status == _abi.GF_ESTATE
+    fields[0].set_lod_camera(None)
+    api.Server(ctx, fields[:1], mem_budget=64 * 64 * 4).close()
     # admissions are in arrival order: each admitted after the previous finished
     for a, b in zip(res, res[1:]):
         assert b["t_admit_ms"] >= a["t_done_ms"] - 1e-3
