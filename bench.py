@@ -429,6 +429,42 @@ def run_workload(args):
         workload_line("free flight, Gaussian band of the 100k-primitive 4-octave field, %dx%d, %d spp"
                       % (res, res, spp), rows["cdf"]["mrays_per_s"], "Mrays/s",
                       rows["cdf"]["ms_per_render"], args, {"by_free_flight": rows, "gpu_launches": 1})
+    elif args.workload == "precision":
+        # FP32 against FP16/BF16 records as the field outgrows the 129 MB L2: 6-octave
+        # fields of 1M, 2M and 4M kernels, single scattering, 512x512, 4 spp, all bands;
+        # the image difference between storages beside the seed-to-seed noise
+        res = args.res or 512
+        spp = args.spp or 4
+        cam = api.camera(c["eye"], c["look_at"], c["up"], c["vfov_deg"], res, res)
+        ro = api.render_opts("scatter", spp, 1, 0.8, synth.LIGHT_DIR, 1.0)
+        rows = {}
+        for n in (1_000_000, 2_000_000, 4_000_000):
+            p = synth.octave_field(n, 6, seed=0)
+            row, ref = {}, None
+            for prec in ("fp32", "fp16", "bf16"):
+                f = api.Field(ctx, p, precision=prec)
+                out = torch.empty(res, res, device=dev)
+                ms = _timed(lambda: f.render(cam, ro, seed=2, out=out), args.steps, args.warmup, stream)
+                f.sync()
+                img = out.clone()
+                entry = {"ms_per_render": statistics.mean(ms)}
+                if ref is None:
+                    ref = img
+                    f.render(cam, ro, seed=3, out=out)
+                    f.sync()
+                    row["seed_to_seed_rmse"] = (img - out).pow(2).mean().sqrt().item()
+                else:
+                    entry["image_rmse_vs_fp32"] = (img - ref).pow(2).mean().sqrt().item()
+                row[prec] = entry
+                f.free()
+                torch.cuda.empty_cache()
+            row["record_mb"] = {"fp32": 64 * n / 2 ** 20, "reduced": 32 * n / 2 ** 20}
+            rows[str(n)] = row
+        big = rows[str(4_000_000)]
+        workload_line("record precision vs field size, 6-octave fields of 1M/2M/4M kernels, %dx%d, "
+                      "%d spp, all bands" % (res, res, spp), big["fp32"]["ms_per_render"] /
+                      big["fp16"]["ms_per_render"], "x (FP16 speed-up at 4M)",
+                      big["fp16"]["ms_per_render"], args, {"by_kernels": rows, "gpu_launches": 2})
     elif args.workload == "adjoint":
         # 200k kernels, 256x256 at 8 spp: forward render plus hand-written adjoint of an
         # L2 loss against a target rendered from perturbed parameters
@@ -646,7 +682,7 @@ def main():
     ap.add_argument("--server-requests", type=int, default=16,
                     help="requests of the render-server leg (0: skip)")
     ap.add_argument("--workload", choices=["scatter", "transmittance", "multiscatter", "adjoint",
-                                           "clamping", "free_flight"],
+                                           "clamping", "free_flight", "precision"],
                     default="scatter", help="workload of the JSON line (default: the single-"
                     "scattering benchmark)")
     ap.add_argument("--res", type=int, default=None, help="profiling only: image size")
