@@ -498,14 +498,32 @@ __device__ __forceinline__ void slab_interval(float3 o, float3 inv, float lx, fl
   tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
 }
 
+// the subtree that lane `sub` of a group of `group` lanes (a power of two)
+// walks: log2(group) levels down from the root along the bits of sub, most
+// significant first, so the group's lanes cover the tree without overlap.  A
+// leaf met on the way belongs to the lane whose remaining bits are all zero.
+// Returns an internal node (>= 0), a leaf ~j (< 0), or kNoStart.
+constexpr int kNoStart = -2147483647 - 1;
+__device__ __forceinline__ int group_start(const DevField& F, int sub, int group) {
+  int node = F.root < 0 ? ~0 : F.root;
+  for (int l = 31 - __clz(group) - 1; l >= 0; --l) {
+    if (node < 0) return (sub & ((2 << l) - 1)) == 0 ? node : kNoStart;
+    const int4 d = __ldg(&F.nodes[node].d);
+    node = (sub >> l & 1) ? d.y : d.x;
+  }
+  return node;
+}
+
+// traversal of the subtree `start` (group_start's result)
 template <class TestFn, class LeafFn>
-__device__ __forceinline__ void traverse_ray(const DevField& F, float3 o, float3 inv,
-                                             unsigned long long mask, TestFn& test, LeafFn& leaf,
-                                             unsigned long long& nvis,
-                                             unsigned long long& nleaves) {
-  if (F.root < 0) {
+__device__ __forceinline__ void traverse_from(const DevField& F, int start, float3 o, float3 inv,
+                                              unsigned long long mask, TestFn& test, LeafFn& leaf,
+                                              unsigned long long& nvis,
+                                              unsigned long long& nleaves) {
+  if (start == kNoStart) return;
+  if (start < 0) {
     ++nleaves;
-    leaf(0);
+    leaf(~start);
     return;
   }
   // lanes that entered together stay together: they reconverge after every
@@ -514,7 +532,7 @@ __device__ __forceinline__ void traverse_ray(const DevField& F, float3 o, float3
   int st_node[kStack];
   float st_tn[kStack];
   int sp = 0;
-  int node = F.root;           // next internal node, -1 once the tree is exhausted
+  int node = start;            // next internal node, -1 once the tree is exhausted
   int pend0 = -1, pend1 = -1;  // queued leaves
   // each internal node is fetched at most once per traversal
   const long long max_steps = F.n + 64;
@@ -582,6 +600,15 @@ __device__ __forceinline__ void traverse_ray(const DevField& F, float3 o, float3
     }
     if (!__any_sync(am, node >= 0 || pend0 >= 0)) return;
   }
+}
+
+// traversal of the whole tree
+template <class TestFn, class LeafFn>
+__device__ __forceinline__ void traverse_ray(const DevField& F, float3 o, float3 inv,
+                                             unsigned long long mask, TestFn& test, LeafFn& leaf,
+                                             unsigned long long& nvis,
+                                             unsigned long long& nleaves) {
+  traverse_from(F, F.root < 0 ? ~0 : F.root, o, inv, mask, test, leaf, nvis, nleaves);
 }
 
 }  // namespace gf

@@ -37,7 +37,7 @@ __device__ __forceinline__ int next_tile(int* counter, uint32_t lane) {
 // closed-form chord integrals) or ratio tracking, one ray per lane
 // ---------------------------------------------------------------------------
 template <int MODE>  // GF_TR_DETERMINISTIC, GF_TR_RATIO_TRACKING or GF_TR_CLOSED_FORM
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, 3)  // at most 168 registers: 12 warps per SM
     k_transmittance(const __grid_constant__ DevField F, const TrParams P) {
   constexpr bool TRACK = MODE == GF_TR_RATIO_TRACKING;
   __shared__ BlockTables sm;
@@ -45,8 +45,8 @@ __global__ void __launch_bounds__(kBlock)
   const uint32_t lane = threadIdx.x & 31u;
   Counters cnt;
   const bool det_mask = lod_is_deterministic(P.lod);
-  // deterministic modes: G = P.group lanes per ray (they share its Gauss-Legendre
-  // nodes, or take its chords round robin), 32/G rays per tile
+  // deterministic modes: G = P.group lanes per ray, each walking its own part of
+  // the tree (group_start), 32/G rays per tile
   const int G = TRACK ? 1 : P.group;
   const int rpt = 32 / G;
   const int sub = (int)lane % G;

@@ -355,8 +355,8 @@ struct DetLeaf {
   const float* glw;
   float s = 0.f, c = 0.f;
   unsigned long long nch = 0, nev = 0;
-  // a group of `group` lanes traverses the same ray in step; lane `sub` takes the
-  // Gauss-Legendre nodes k = sub, sub + group, ... of every chord
+  // lane `sub` of `group` lanes takes the Gauss-Legendre nodes sub, sub + group, ...
+  // (the transmittance kernel splits a ray's tree instead and passes 0 and 1)
   int sub = 0, group = 1;
   __device__ __forceinline__ void operator()(int j) {
     const Mask& Mk = *M;
@@ -390,8 +390,8 @@ __device__ __forceinline__ float det_tau(const DevField& F, const Mask& M, float
   float t0, t1;
   if (M.bits == 0ull || !scene_span(F, o, inv, tmin, tmax, t0, t1)) return 0.f;
   DetLeaf leaf;
-  leaf.sub = sub;
-  leaf.group = group;
+  leaf.sub = 0;
+  leaf.group = 1;
   leaf.F = &F;
   leaf.M = &M;
   leaf.o = o;
@@ -401,15 +401,13 @@ __device__ __forceinline__ float det_tau(const DevField& F, const Mask& M, float
   leaf.glx = glx;
   leaf.glw = glw;
   SpanTest test{t0, t1};
-  // the lanes of a group walk the same tree: lane 0 of the group counts it
+  // the lanes of a group walk disjoint subtrees of the same ray
   unsigned long long nodes = 0, leaves = 0;
-  traverse_ray(F, o, inv, M.bits, test, leaf, nodes, leaves);
-  if (sub == 0) {
-    cnt.nodes += nodes;
-    cnt.leaves += leaves;
-    cnt.windows += 1;
-    cnt.chords += leaf.nch;
-  }
+  traverse_from(F, group_start(F, sub, group), o, inv, M.bits, test, leaf, nodes, leaves);
+  cnt.nodes += nodes;
+  cnt.leaves += leaves;
+  if (sub == 0) cnt.windows += 1;
+  cnt.chords += leaf.nch;
   cnt.evals += leaf.nev;
   return __fadd_rn(leaf.s, leaf.c);
 }
@@ -460,7 +458,6 @@ __device__ __forceinline__ float chord_closed(const Weideman& W, const Chord& ch
   return ch.absA * (0.88622692545275801f / s) * acc;  // sqrt(pi)/2 / s
 }
 
-// the lanes of a group walk the same tree and take the chords round robin
 struct ClosedLeaf {
   const DevField* F;
   const Mask* M;
@@ -469,17 +466,15 @@ struct ClosedLeaf {
   float s = 0.f, c = 0.f;
   float tend = -INFINITY;  // the last chord exit
   unsigned long long nch = 0;
-  int sub = 0, group = 1;  // group is a power of two
   __device__ __forceinline__ void operator()(int j) {
     const Mask& Mk = *M;
     Chord ch;
     float w;
     if (!prim_chord(*F, j, o, v, tmin, tmax, [&](uint32_t c) { return mask_weight(Mk, c); }, w, ch))
       return;
-    const bool mine = (int)(nch & (unsigned long long)(group - 1)) == sub;
     ++nch;
     tend = fmaxf(tend, ch.tc + ch.dtout);
-    if (mine) neumaier_add(s, c, w * chord_closed(F->wd, ch));
+    neumaier_add(s, c, w * chord_closed(F->wd, ch));
   }
 };
 
@@ -491,8 +486,6 @@ __device__ __forceinline__ float closed_tau(const DevField& F, const Mask& M, fl
   if (tend) *tend = -INFINITY;
   if (M.bits == 0ull || !scene_span(F, o, inv, tmin, tmax, t0, t1)) return 0.f;
   ClosedLeaf leaf;
-  leaf.sub = sub;
-  leaf.group = group;
   leaf.F = &F;
   leaf.M = &M;
   leaf.o = o;
@@ -500,14 +493,13 @@ __device__ __forceinline__ float closed_tau(const DevField& F, const Mask& M, fl
   leaf.tmin = tmin;
   leaf.tmax = tmax;
   SpanTest test{t0, t1};
+  // the lanes of a group walk disjoint subtrees of the same ray
   unsigned long long nodes = 0, leaves = 0;
-  traverse_ray(F, o, inv, M.bits, test, leaf, nodes, leaves);
-  if (sub == 0) {
-    cnt.nodes += nodes;
-    cnt.leaves += leaves;
-    cnt.windows += 1;
-    cnt.chords += leaf.nch;
-  }
+  traverse_from(F, group_start(F, sub, group), o, inv, M.bits, test, leaf, nodes, leaves);
+  cnt.nodes += nodes;
+  cnt.leaves += leaves;
+  if (sub == 0) cnt.windows += 1;
+  cnt.chords += leaf.nch;
   if (tend) *tend = leaf.tend;
   return __fadd_rn(leaf.s, leaf.c);
 }

@@ -113,9 +113,9 @@ def test_deterministic_transmittance_absorption_64x64(api, ctx):
 
 
 def test_deterministic_transmittance_lane_groups_agree(api, ctx):
-    """Small batches integrate each ray with several lanes (sharing each chord's
-    Gauss-Legendre nodes), large ones with one lane per ray: the same rays give
-    the same optical depth up to FP32 summation order, and match the oracle."""
+    """Small batches integrate each ray with several lanes (each walking its own
+    subtree), large ones with one lane per ray: the same rays give the same
+    optical depth up to FP32 summation order, and match the oracle."""
     p = synth.octave_field(6000, 4, seed=5)
     f = api.Field(ctx, p)
     o, d, tr = synth.random_rays(200000, seed=9)
@@ -194,8 +194,8 @@ def test_closed_form_transmittance_matches_oracle(api, ctx, field):
 
 
 def test_closed_form_lane_groups_agree(api, ctx):
-    """Closed form with one lane per ray (large batch) and with 32 lanes taking
-    a ray's chords round robin (small batch): equal up to FP32 summation order."""
+    """Closed form with one lane per ray (large batch) and with 32 lanes walking
+    disjoint subtrees of each ray (small batch): equal up to FP32 summation order."""
     p = synth.octave_field(6000, 4, seed=5)
     f = api.Field(ctx, p)
     o, d, tr = synth.random_rays(200000, seed=9)
