@@ -174,7 +174,8 @@ typedef struct gf_render_opts {
   float albedo;
   float light_dir[3]; /* direction towards the light, normalised by the library */
   float light_irradiance;
-  int free_flight;    /* GF_FLIGHT_*: scattering only (the server and the adjoint: DELTA) */
+  int free_flight;    /* GF_FLIGHT_* (else GF_EINVAL); scattering only; the server and the
+                         adjoint take DELTA only (GF_EINVAL otherwise) */
 } gf_render_opts;
 
 /* Work counters accumulated by the kernels since the last reset. */
@@ -201,8 +202,9 @@ gf_status gf_destroy(gf_ctx* ctx);
 /* Pack the primitives (Sec. 4.2 parameters -> Sigma^-1, world carrier, amplitude,
    band/cone/cell labels; load-time binning of Sec. 4.6).  params arrays may be
    host or device memory.  Validates on the host/device: 1 <= n < 2^26, finite values,
-   |quat| > 0, k_sigma in (0,6], band labels <= 7 (GF_EINVAL).  The field keeps a
-   copy of the raw parameters for gf_render_backward. */
+   |quat| > 0, k_sigma in (0,6], clamp_eps finite and >= 0, band labels <= 7
+   (GF_EINVAL).  The field keeps a copy of the raw parameters for
+   gf_render_backward. */
 gf_status gf_load_field(gf_ctx* ctx, const gf_params* params, const gf_field_opts* opts,
                         gf_stream stream, gf_field** out);
 gf_status gf_field_free(gf_field* field);
@@ -226,8 +228,10 @@ gf_status gf_set_lod_mask(gf_field* field, const gf_lod_desc* primary, const gf_
    cells left empty are skipped by the traversal.  Decided in FP32 without
    contraction: |omega| d <= (float)(pi H / (2 tan(phi/2))).  Composes with
    gf_set_lod_mask and with adaptive clamping.  camera NULL restores every
-   kernel.  GF_ESTATE while a render server holds the field.  Synchronises
-   the stream. */
+   kernel.  camera is host memory, read during the call.  GF_EINVAL for a
+   camera with no pixels or a field of view outside (0, 180) degrees,
+   GF_ESTATE for an unbuilt field or while a render server holds it.
+   Synchronises the stream. */
 gf_status gf_set_lod_camera(gf_field* field, const gf_camera* camera, gf_stream stream);
 
 /* Transmittance of n_rays rays x(t) = o + t d, t in [trange[2r], trange[2r+1]]

@@ -708,6 +708,42 @@ def test_reduced_precision_transmittance(api, ctx, prec, u):
     assert f.info()[1] == {"fp16": 1, "bf16": 2}[prec]
 
 
+def test_reduced_precision_adaptive_clamping(api, ctx):
+    """Adaptive clamping (Sec. 4.4) reaches the 32-byte records too, whose support
+    radii come from a side array: with FP16 records no kernel the clamp drops
+    has a chord, the chord sets equal the FP32 ones at the same threshold up to
+    near-tangent chords (the records' rounding moves the ellipsoids), and the
+    clamp removes chords from the FP16 sets as it does from the FP32 ones."""
+    p = synth.absorption_field(256, seed=0)
+    eps = 2e-2
+    f32 = api.Field(ctx, p, clamp_eps=eps)
+    f16 = api.Field(ctx, p, precision="fp16", clamp_eps=eps)
+    full16 = api.Field(ctx, p, precision="fp16")
+    orc = oracle.Field(p, clamp_eps=eps)
+    gone = set(np.flatnonzero(orc.extents() == 0).tolist())
+    assert len(gone) > 20
+    o, d, tr = synth.random_rays(64, seed=3)
+    a = f32.chords(_t(o), _t(d), _t(tr), cap=512)
+    b = f16.chords(_t(o), _t(d), _t(tr), cap=512)
+    c = full16.chords(_t(o), _t(d), _t(tr), cap=512)
+    f16.sync()
+
+    def sets(res, r):
+        counts, prims, tin, tout = res
+        return {int(x): float(t1 - t0) for x, t0, t1 in
+                zip(prims[r, :counts[r]], tin[r, :counts[r]], tout[r, :counts[r]])}
+
+    n16 = nfull = 0
+    for r in range(64):
+        s32, s16, sf = sets(a, r), sets(b, r), sets(c, r)
+        assert not set(s16) & gone, r
+        for i in set(s32) ^ set(s16):
+            assert s32.get(i, s16.get(i)) < 5e-3, (r, i)
+        n16 += len(s16)
+        nfull += len(sf)
+    assert nfull > 1.2 * n16, (nfull, n16)
+
+
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
 def test_reduced_precision_image_rmse(api, ctx, prec):
     """Equal image RMSE: RMSE(I_reduced, I_ref) <= 1.01 RMSE(I_oracle, I_ref) at
