@@ -88,7 +88,7 @@ typedef struct gf_field_opts {
   int weight_mode; /* GF_WEIGHT_* */
   int omega_frame; /* GF_OMEGA_* */
   float k_sigma;   /* support radius in sigma units, (0, 6]; the paper uses 3 */
-  /* adaptive clamping (Sec. 4.4, Eq. 9): 0 = off; else each kernel's support
+  /* adaptive clamping (Sec. 4.4, Eqs. 14-15): 0 = off; else each kernel's support
      radius becomes k_i = min(k_sigma, E_i) in whitened units with
      E_i^2 = 2 ln(rho_i / clamp_eps) - |k_W,i|^2, rho_i = |A_i| sqrt(2 pi) s_max,i
      (the kernel's largest line integral through its peak, the paper's alpha K
@@ -160,8 +160,8 @@ typedef struct gf_camera {
 enum { GF_INTEG_TOMO = 0, GF_INTEG_SCATTER = 1 };
 /* Free flight of the scattering integrator.  DELTA: delta tracking on the
    per-segment majorants, NEE transmittance by ratio tracking (see gf_render).
-   CDF: the collision distance solves tau(0, t) = -ln(1 - xi) (Sec. 3
-   segment-based transfer, Sec. 4.4 distance sampling), by 32 bisections on the
+   CDF: the collision distance solves tau(0, t) = -ln(1 - xi) (Sec. 3 Eq. 5,
+   segment-based transfer; Sec. 4.4 distance sampling), by 32 bisections on the
    closed-form optical depth (see GF_TR_CLOSED_FORM), and the NEE transmittance
    is exp(-tau) in closed form; it assumes a non-negative mixture along each
    ray (the first crossing) and is rendered per thread. */

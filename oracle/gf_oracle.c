@@ -219,7 +219,7 @@ or_field* or_field_create(const or_field_desc* D) {
     double kw2 = P->kw[0] * P->kw[0] + P->kw[1] * P->kw[1] + P->kw[2] * P->kw[2];
     ksum[P->cell] += sqrt(kw2);
     kcnt[P->cell] += 1;
-    /* adaptive clamping (Sec. 4.4, Eq. 9): along a ray through the peak the
+    /* adaptive clamping (Sec. 4.4, Eqs. 14-15): along a ray through the peak the
        kernel integrates to at most rho = |A| sqrt(2 pi) s_max (the longest axis);
        the extent E where rho exp(-(E^2 + |k_W|^2)/2) falls to clamp_eps bounds
        the support, never beyond k_sigma; E^2 <= 0 drops the kernel */

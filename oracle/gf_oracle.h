@@ -46,7 +46,7 @@ typedef struct {
   int weight_mode;     /* 0 peak amplitude, 1 normalised (Eq. 6) */
   int omega_frame;     /* 0 world, 1 whitened frame (k_W) */
   double k_sigma;      /* support radius in sigma units (3 in the paper) */
-  double clamp_eps;    /* adaptive clamping (Sec. 4.4, Eq. 9); 0 = off */
+  double clamp_eps;    /* adaptive clamping (Sec. 4.4, Eqs. 14-15); 0 = off */
 } or_field_desc;
 
 typedef struct {
@@ -139,8 +139,8 @@ void or_transmittance(const or_field* f, const or_lod* lod, const float* o, cons
                       const float* trange, int64_t n_rays, int mode, int spp, uint64_t seed,
                       double* T, double* tau, int n_threads);
 
-/* free flight by inversion of the optical-depth CDF (Sec. 3 segment-based
-   transfer, Sec. 4.4 distance sampling): with xi the first uniform of the
+/* free flight by inversion of the optical-depth CDF (Sec. 3 Eq. 5, segment-based
+   transfer; Sec. 4.4 distance sampling): with xi the first uniform of the
    (seed, ray, word) stream, the distance t solves tau(tmin, t) = -ln(1 - xi),
    found by 60 bisections of [tmin, last chord exit]; returns 0 (escape) when
    the whole ray's tau does not reach the target.  The density must be

@@ -104,7 +104,7 @@ __global__ void k_pack(const __grid_constant__ PackArgs A) {
   }
   int cell = band == 0 ? 0 : 1 + kCones * (band - 1) + cone;
   float kn = sqrtf(kw[0] * kw[0] + kw[1] * kw[1] + kw[2] * kw[2]);
-  // support radius: k, or the adaptive extent of Sec. 4.4 (Eq. 9) where the
+  // support radius: k, or the adaptive extent of Sec. 4.4 (Eqs. 14-15) where the
   // kernel's largest line integral rho = |A| sqrt(2 pi) s_max, attenuated by
   // exp(-(E^2 + |k_W|^2)/2), falls to clamp_eps
   float k2i = A.ksig * A.ksig;

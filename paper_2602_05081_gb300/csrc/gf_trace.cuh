@@ -504,8 +504,8 @@ __device__ __forceinline__ float closed_tau(const DevField& F, const Mask& M, fl
   return __fadd_rn(leaf.s, leaf.c);
 }
 
-// Free flight by inversion of the optical-depth CDF (Sec. 3 segment-based
-// transfer, Sec. 4.4 distance sampling): with xi the first uniform of the
+// Free flight by inversion of the optical-depth CDF (Sec. 3 Eq. 5, segment-based
+// transfer; Sec. 4.4 distance sampling): with xi the first uniform of the
 // segment's tracking stream, the distance solves tau(0, t) = -ln(1 - xi),
 // found by 32 bisections of [0, last chord exit] on the closed-form optical
 // depth (one windowed traversal each).  Returns false when the whole ray's

@@ -339,7 +339,7 @@ def _mc_parity(api, f, orc, cam_g, cam_o, ro_g, ro_o, seed, lod_o=None, lodn_o=N
 
 
 def test_adaptive_clamping_parity(api, ctx):
-    """Adaptive clamping (Sec. 4.4, Eq. 9) at eps = 1e-2: per-primitive supports
+    """Adaptive clamping (Sec. 4.4, Eqs. 14-15) at eps = 1e-2: per-primitive supports
     shrink the chord sets, which equal the oracle's; deterministic and
     closed-form optical depths match the oracle's to 1e-5 max(1, max|tau|); the
     single-scattering image matches within 1% of the Monte Carlo noise."""
