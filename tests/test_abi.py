@@ -1,4 +1,5 @@
 """The C-ABI library builds, loads and exports every entry point of include/gf.h (CPU)."""
+import ctypes as C
 import os
 import re
 import subprocess
@@ -46,3 +47,56 @@ def test_create_without_gpu_fails_cleanly():
     from paper_2602_05081_gb300 import _abi
     with pytest.raises(_abi.GfError):
         _abi.gf_create(0)
+
+
+def _c_layout(header_dir, header, structs, tmp_path):
+    """sizeof and offsetof of every field, as a C compiler lays the structs out."""
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "%s"' % header, "int main(void) {"]
+    for cname, pyname, fields in structs:
+        lines.append('  printf("%s size %%zu\\n", sizeof(%s));' % (pyname, cname))
+        for f in fields:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (pyname, f, cname, f))
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", header_dir, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    got = {}
+    for ln in out.split("\n"):
+        if ln:
+            a, b, c = ln.split()
+            got[(a, b)] = int(c)
+    return got
+
+
+def _check(structs, got):
+    for _, py, fields in structs:
+        assert got[(py.__name__, "size")] == C.sizeof(py), py.__name__
+        for f in fields:
+            assert got[(py.__name__, f)] == getattr(py, f).offset, (py.__name__, f)
+
+
+
+def test_binding_structs_match_the_c_layout(tmp_path):
+    """Every ctypes mirror of an include/gf.h struct has the C compiler's size and
+    field offsets (the structs are passed by pointer through the C ABI)."""
+    from paper_2602_05081_gb300 import _abi
+    pys = [_abi.gf_params, _abi.gf_field_opts, _abi.gf_lod_desc, _abi.gf_camera,
+           _abi.gf_render_opts, _abi.gf_stats, _abi.gf_server_opts, _abi.gf_request,
+           _abi.gf_result, _abi.gf_server_stats]
+    structs = [(py.__name__, py, [f for f, _ in py._fields_]) for py in pys]
+    got = _c_layout(os.path.join(ROOT, "include"), "gf.h",
+                    [(c, py.__name__, fs) for c, py, fs in structs], tmp_path)
+    _check(structs, got)
+
+
+def test_oracle_structs_match_the_c_layout(tmp_path):
+    """The same for the oracle's ctypes mirrors of oracle/gf_oracle.h."""
+    import oracle
+    pairs = [("or_field_desc", oracle.FieldDesc), ("or_lod", oracle.Lod),
+             ("or_camera", oracle.Camera), ("or_render_opts", oracle.RenderOpts)]
+    structs = [(c, py, [f for f, _ in py._fields_]) for c, py in pairs]
+    got = _c_layout(os.path.join(ROOT, "oracle"), "gf_oracle.h",
+                    [(c, py.__name__, fs) for c, py, fs in structs], tmp_path)
+    _check(structs, got)
