@@ -1,7 +1,8 @@
 // gf_trace.cuh -- per-ray work shared by the render, transmittance and server
-// kernels: LoD mask sampling, deterministic optical depth, tentative points,
-// ratio and delta tracking, path samples.  One thread owns one ray (or one
-// pixel's paths); a warp advances 32 rays.
+// kernels: LoD mask sampling, deterministic optical depth (Gauss-Legendre and
+// closed-form chord integrals), tentative points, ratio and delta tracking,
+// CDF-inversion free flight, path samples.  One thread owns one ray (or one
+// pixel's paths); a warp advances 32 rays, or 32/G rays with G lanes each.
 #pragma once
 #include "gf_device.cuh"
 
