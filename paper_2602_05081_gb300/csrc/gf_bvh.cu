@@ -111,10 +111,10 @@ __global__ void k_pack(const __grid_constant__ PackArgs A) {
   if (A.clamp_eps > 0.0f) {
     const float rho = fabsf(amp) * 2.5066282746310002f * fmaxf(fmaxf(s[0], s[1]), s[2]);
     const float e2 = 2.0f * logf(rho / A.clamp_eps) - kn * kn;
-    k2i = fminf(k2i, fmaxf(e2, 0.0f));
+    k2i = e2 > 0.0f ? fminf(k2i, e2) : -1.0f;  // -1: dropped, no ray finds a chord
   }
   A.ext2[i] = k2i;
-  const float kext = sqrtf(k2i);
+  const float kext = sqrtf(fmaxf(k2i, 0.0f));
   float4* r = A.rec + 4 * i;
   r[0] = make_float4(mu[0], mu[1], mu[2], amp);
   r[1] = make_float4(P[0][0], P[0][1], P[0][2], P[1][1]);
