@@ -461,18 +461,21 @@ def test_masked_optical_depth_is_unbiased_and_jensen_bias():
         assert np.all(np.abs((enum - np.exp(-tau))[small] - approx[small]) <= 0.5 * approx[small] + 1e-6)
 
 
-def test_single_scatter_mean_matches_nested_quadrature():
+@pytest.mark.parametrize("flight,spp", [("delta", 20000), ("cdf", 20000)])
+def test_single_scatter_mean_matches_nested_quadrature(flight, spp):
     """Mean single-scattering radiance of one pixel equals
-    albedo E/(4 pi) int kappa(t) exp(-tau(0,t)) T_light(x(t)) dt (Gaussian field)."""
+    albedo E/(4 pi) int kappa(t) exp(-tau(0,t)) T_light(x(t)) dt (Gaussian field),
+    with delta tracking + ratio-tracked NEE and with CDF-inversion free flight +
+    closed-form NEE (Sec. 3 Eq. 5, Sec. 4.4): the same expectation."""
     p = _gauss_only()
     f = oracle.Field(p)
     cam = oracle.camera((0.5, 0.5, -1.0), (0.5, 0.5, 0.5), (0, 1, 0), 45.0, 64, 64)
-    ro = oracle.render_opts("scatter", spp=20000, max_bounces=1, albedo=0.8)
+    ro = oracle.render_opts("scatter", spp=spp, max_bounces=1, albedo=0.8, free_flight=flight)
     px, py = 32, 31
     smp = f.render(cam, ro, seed=5, crop=(px, py, 1, 1), samples=True).ravel()
     # reference: nested quadrature with per-sample jittered rays averaged
     ref = []
-    rng_idx = range(0, 20000, 500)
+    rng_idx = range(0, spp, spp // 40)
     light = np.array([1.0, 1.0, -1.0]) / math.sqrt(3.0)
     for s in rng_idx:
         o, v = oracle.camera_ray(cam, 5, px, py, s)
