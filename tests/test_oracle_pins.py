@@ -761,7 +761,8 @@ def test_adaptive_clamping_limits_and_frequency():
 
 
 # --------------------------------------------------------------------------- multiple scattering
-def test_second_bounce_matches_nested_quadrature():
+@pytest.mark.parametrize("flight", ["delta", "cdf"])
+def test_second_bounce_matches_nested_quadrature(flight):
     """Multiple scattering (Sec. 3 path integral with delta tracking, isotropic
     phase, NEE at every collision): on one Gaussian (tau ~ 2 through its
     centre, k = 6 so the cut is negligible) the second-bounce radiance of a
@@ -824,8 +825,10 @@ def test_second_bounce_matches_nested_quadrature():
         L2 += first[i] * np.sum(Ww * inner) / (4 * np.pi)
     L2 *= albedo * albedo / (4 * np.pi)
     spp = 40000
-    r1 = f.render(cam, oracle.render_opts("scatter", spp, 1, albedo), seed=5, crop=(px, py, 1, 1), samples=True).ravel()
-    r2 = f.render(cam, oracle.render_opts("scatter", spp, 2, albedo), seed=5, crop=(px, py, 1, 1), samples=True).ravel()
+    r1 = f.render(cam, oracle.render_opts("scatter", spp, 1, albedo, free_flight=flight), seed=5,
+                  crop=(px, py, 1, 1), samples=True).ravel()
+    r2 = f.render(cam, oracle.render_opts("scatter", spp, 2, albedo, free_flight=flight), seed=5,
+                  crop=(px, py, 1, 1), samples=True).ravel()
     d2 = r2 - r1
     se = d2.std(ddof=1) / math.sqrt(spp)
     assert abs(d2.mean() - L2) < 4.5 * se, (d2.mean(), L2, se)
