@@ -65,7 +65,14 @@ def render_opts(integrator="scatter", spp=1, max_bounces=1, albedo=0.8,
 
 
 class Field:
-    """A packed primitive set with its BVH on one GPU."""
+    """A packed primitive set with its BVH on one GPU.
+
+    precision: "fp32", "fp16" or "bf16" records (FP32 math either way);
+    k_sigma: support radius in sigma units; clamp_eps > 0 turns on adaptive
+    clamping of each kernel's support (gf_field_opts.clamp_eps);
+    transmittance modes: "det" (Gauss-Legendre), "closed" (closed form),
+    "rt" (ratio tracking); set_lod / set_lod_camera choose the LoD masks.
+    """
 
     def __init__(self, ctx: Context, params: dict, precision="fp32", weight_mode=None,
                  omega_frame=None, k_sigma=3.0, stream=None, device_inputs=True, clamp_eps=0.0):
