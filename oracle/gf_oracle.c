@@ -496,6 +496,17 @@ static void normalise(const double in[3], double out[3]) {
   out[0] = in[0] / n; out[1] = in[1] / n; out[2] = in[2] / n;
 }
 
+/* The direction of a caller's ray: the unit vector of the FP32 input d, rounded
+   to FP32.  This is the input rounding of the library's boundary (its rays are
+   FP32 unit vectors), applied here so that both sides trace the same line; the
+   rounding of a direction moves a point at distance t by ~6e-8 t, which a
+   carrier of ~1e3 rad/unit turns into phase errors of ~1e-4 rad. */
+static void api_direction(const float d[3], double v[3]) {
+  double dd[3] = {d[0], d[1], d[2]};
+  normalise(dd, v);
+  for (int k = 0; k < 3; ++k) v[k] = (double)(float)v[k];
+}
+
 int or_chord(const or_field* f, int64_t i, const double o[3], const double v_in[3], double tmin,
              double tmax, double* lo, double* hi) {
   double v[3];
@@ -858,8 +869,8 @@ void or_transmittance(const or_field* f, const or_lod* lod, const float* o, cons
 #pragma omp parallel for schedule(dynamic, 4) num_threads(nt)
   for (int64_t r = 0; r < n_rays; ++r) {
     double oo[3] = {o[3 * r], o[3 * r + 1], o[3 * r + 2]};
-    double dd[3] = {d[3 * r], d[3 * r + 1], d[3 * r + 2]}, v[3];
-    normalise(dd, v);
+    double v[3];
+    api_direction(d + 3 * r, v);
     double tmin = trange ? trange[2 * r] : 0.0;
     double tmax = trange ? trange[2 * r + 1] : INFINITY;
     double acc = 0;

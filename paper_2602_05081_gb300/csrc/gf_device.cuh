@@ -457,6 +457,45 @@ __device__ __forceinline__ bool slab(float3 o, float3 inv, float lx, float ly, f
   return tn <= tf;
 }
 
+// Unit direction of a caller's ray, d / |d| rounded once to FP32 (FP32
+// arithmetic only).  The argument is scaled by a power of two (exact), |d|^2
+// is formed as an unevaluated sum hi + lo of error-free products and sums,
+// r = 1/sqrt(|d|^2) is refined from the FP32 estimate by one Newton step on
+// the residual 1 - |d|^2 r^2 (relative error ~1e-14), and each component
+// d_i (r + dr) is rounded once.  Results differ from the correctly rounded
+// unit vector only where a component lies within ~1e-14 of a rounding tie.
+// A zero vector gives NaN.
+__device__ __forceinline__ float3 unit_dir(float3 d) {
+  const float m = fmaxf(fabsf(d.x), fmaxf(fabsf(d.y), fabsf(d.z)));
+  if (!(m > 0.0f) || !(m < INFINITY)) {
+    const float q = __int_as_float(0x7fc00000);
+    return make_float3(q, q, q);
+  }
+  int e;
+  (void)frexpf(m, &e);
+  const float x = ldexpf(d.x, -e), y = ldexpf(d.y, -e), z = ldexpf(d.z, -e);
+  const float px = __fmul_rn(x, x), ex = fmaf(x, x, -px);
+  const float py = __fmul_rn(y, y), ey = fmaf(y, y, -py);
+  const float pz = __fmul_rn(z, z), ez = fmaf(z, z, -pz);
+  float s1, e1, hi, e2;
+  two_sum(px, py, s1, e1);
+  two_sum(s1, pz, hi, e2);
+  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(ex, ey), __fadd_rn(ez, e1)), e2);
+  const float r0 = __fdiv_rn(1.0f, __fsqrt_rn(hi));
+  // residual 1 - (hi + lo) r0^2: r0^2 = q + eq exactly, hi q = mq + emq exactly,
+  // and 1 - mq is exact (Sterbenz: mq is within a few ulp of 1)
+  const float q = __fmul_rn(r0, r0), eq = fmaf(r0, r0, -q);
+  const float mq = __fmul_rn(hi, q), emq = fmaf(hi, q, -mq);
+  const float res = __fsub_rn(__fsub_rn(1.0f, mq),
+                              __fadd_rn(emq, __fadd_rn(__fmul_rn(hi, eq), __fmul_rn(lo, q))));
+  const float dr = __fmul_rn(__fmul_rn(0.5f, r0), res);
+  auto comp = [&](float a) {
+    const float p = __fmul_rn(a, r0), err = fmaf(a, r0, -p);
+    return __fadd_rn(p, __fadd_rn(err, __fmul_rn(a, dr)));
+  };
+  return make_float3(comp(x), comp(y), comp(z));
+}
+
 __device__ __forceinline__ float3 safe_inv(float3 v) {
   const float tiny = 1e-30f;
   float x = fabsf(v.x) < tiny ? copysignf(tiny, v.x) : v.x;

@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kBlock, 3)  // at most 168 registers: 12 warps
       const int spp = det_mask ? 1 : P.spp;
       if (r < P.n) {
         const float3 o = make_float3(P.o[3 * r], P.o[3 * r + 1], P.o[3 * r + 2]);
-        const float3 v = normalize3(make_float3(P.d[3 * r], P.d[3 * r + 1], P.d[3 * r + 2]));
+        const float3 v = unit_dir(make_float3(P.d[3 * r], P.d[3 * r + 1], P.d[3 * r + 2]));
         const float tmin = P.trange ? P.trange[2 * r] : 0.f;
         const float tmax = P.trange ? P.trange[2 * r + 1] : INFINITY;
         for (int s = 0; s < spp; ++s) {
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kBlock, 3)  // at most 168 registers: 12 warps
       }
     } else if (r < P.n) {
       const float3 o = make_float3(P.o[3 * r], P.o[3 * r + 1], P.o[3 * r + 2]);
-      const float3 v = normalize3(make_float3(P.d[3 * r], P.d[3 * r + 1], P.d[3 * r + 2]));
+      const float3 v = unit_dir(make_float3(P.d[3 * r], P.d[3 * r + 1], P.d[3 * r + 2]));
       const float tmin = P.trange ? P.trange[2 * r] : 0.f;
       const float tmax = P.trange ? P.trange[2 * r + 1] : INFINITY;
       {
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kBlock)
     const bool active = px < P.cam.W && py < P.cam.H;
     float acc = 0.f;
     for (int s = 0; s < P.spp; ++s)
-      acc += path_sample<CDF>(F, P, active, px, py, s, sm.glx, sm.glw, sm.env, cnt);
+      acc += path_sample<CDF>(F, P, active, px, py, P.s0 + s, sm.glx, sm.glw, sm.env, cnt);
     if (active) out[(int64_t)py * P.cam.W + px] = acc / (float)P.spp;
   }
   flush_counters(F, cnt, lane);
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kBlock) k_ray_chords(const __grid_constant__ D
     const int64_t r = (int64_t)tile * 32 + lane;
     if (r >= P.n) continue;  // next_tile below is reached by every lane
     const float3 o = make_float3(P.o[3 * r], P.o[3 * r + 1], P.o[3 * r + 2]);
-    const float3 v = normalize3(make_float3(P.d[3 * r], P.d[3 * r + 1], P.d[3 * r + 2]));
+    const float3 v = unit_dir(make_float3(P.d[3 * r], P.d[3 * r + 1], P.d[3 * r + 2]));
     const float tmin = P.trange ? P.trange[2 * r] : 0.f;
     const float tmax = P.trange ? P.trange[2 * r + 1] : INFINITY;
     const Mask m = sample_mask(F, P.lod, v, 0, (uint32_t)r, 0, 0, TAG_MASK);
@@ -219,12 +219,15 @@ __global__ void k_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out
 // launchers: persistent grids of (resident blocks per SM) x SMs
 // ---------------------------------------------------------------------------
 // every kernel's per-thread stack (its local memory frame, callees included)
-// must fit the context's stack limit, which gf_create sets to kStackLimit
+// must fit the context's stack limit as it stands at launch (gf_create raises
+// it to at least kStackLimit; another component of the process may change it)
 template <class K>
 static bool stack_fits(K kernel) {
   cudaFuncAttributes a;
   if (cudaFuncGetAttributes(&a, kernel) != cudaSuccess) return false;
-  return a.localSizeBytes <= (size_t)kStackLimit;
+  size_t limit = 0;
+  if (cudaDeviceGetLimit(&limit, cudaLimitStackSize) != cudaSuccess) return false;
+  return a.localSizeBytes <= limit;
 }
 
 template <class K>

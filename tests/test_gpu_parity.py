@@ -41,6 +41,31 @@ def _t(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
 
 
+def _tau_per_ray(tau, ref, rtol, what=""):
+    """Per-ray optical-depth bound |tau_gpu - tau_oracle| <= rtol max(1, |tau_oracle|)."""
+    tau = np.asarray(tau, np.float64)
+    err = np.abs(tau - ref)
+    lim = rtol * np.maximum(1.0, np.abs(ref))
+    print("%s tau: max |dtau| %.3e, max |dtau|/max(1,|tau|) %.3e, max |tau| %.3f"
+          % (what, err.max(), (err / np.maximum(1.0, np.abs(ref))).max(), np.abs(ref).max()))
+    assert np.all(err <= lim), (what, err.max(), int(np.argmax(err / lim)))
+
+
+def _T_abs(T, ref, what="", floor=None):
+    """Per-ray transmittance bound |T_gpu - T_oracle| <= 1e-5 (absolute).
+
+    `floor` (per ray, optional) is the FP32 arithmetic floor T 4u E of a ray
+    whose envelope mass E = int sum |A| exp(-q/2) dt is large: every chord's
+    integral carries a relative rounding of a few units u = 2^-24 (ex2.approx
+    within 2 ulp, the exponent's argument and the chord's scale within 1 ulp
+    each), so |dtau| <= 4u E and |dT| <= T 4u E; the bound is max(1e-5, floor)."""
+    err = np.abs(np.asarray(T, np.float64) - ref)
+    lim = np.full(err.shape, 1e-5) if floor is None else np.maximum(1e-5, floor)
+    print("%s T: max |dT| %.3e at T = %.4f, max T %.3f, rays above 1e-5: %d"
+          % (what, err.max(), ref[np.argmax(err)], ref.max(), int((err > 1e-5).sum())))
+    assert np.all(err <= lim), (what, err.max(), ref[np.argmax(err)])
+
+
 def _cam_pair(api, w, h):
     c = synth.DEFAULT_CAMERA
     return (api.camera(c["eye"], c["look_at"], c["up"], c["vfov_deg"], w, h),
@@ -106,9 +131,8 @@ def test_deterministic_transmittance_absorption_64x64(api, ctx):
     T, tau = f.transmittance(_t(o), _t(d), _t(tr), mode="det")
     f.sync()
     T_ref, tau_ref = oracle.Field(p).transmittance(o, d, tr, mode="det")
-    err = np.abs(T.cpu().numpy() - T_ref)
-    assert err.max() <= 1e-5, err.max()
-    assert np.abs(tau.cpu().numpy() - tau_ref).max() <= 1e-5 * max(1.0, np.abs(tau_ref).max())
+    _T_abs(T.cpu().numpy(), T_ref, "absorption 64x64")
+    _tau_per_ray(tau.cpu().numpy(), tau_ref, 1e-5, "absorption 64x64")
     assert np.abs(tau_ref).max() > 0.2  # non-trivial optical depths
 
 
@@ -123,9 +147,9 @@ def test_deterministic_transmittance_lane_groups_agree(api, ctx):
     _, tau_few = f.transmittance(_t(o[:500]), _t(d[:500]), _t(tr[:500]), mode="det")  # 32 lanes
     f.sync()
     a, b = tau_all.cpu().numpy()[:500], tau_few.cpu().numpy()
-    assert np.abs(a - b).max() <= 2e-6 * max(1.0, np.abs(a).max())
+    assert np.all(np.abs(a - b) <= 2e-6 * np.maximum(1.0, np.abs(a)))
     _, tau_ref = oracle.Field(p, omega_frame="local").transmittance(o[:64], d[:64], tr[:64], mode="det")
-    assert np.abs(np.exp(-b[:64]) - np.exp(-tau_ref)).max() <= 1e-5
+    _T_abs(np.exp(-b[:64].astype(np.float64)), np.exp(-tau_ref), "lane groups")
 
 
 def test_faddeeva_matches_library(api):
@@ -165,8 +189,8 @@ def test_faddeeva_matches_library(api):
 def test_closed_form_transmittance_matches_oracle(api, ctx, field):
     """Closed-form chord integrals (Faddeeva form of App. A.3) against the
     oracle's optical depth, whose composite quadrature is exact to rounding:
-    |dtau| <= 1e-5 max(1, max|tau|), |dT| <= 1e-5 max(1, |T|) per ray.  Ranges
-    clip chords to pieces down to 1e-7 (the midpoint branch) and to empty."""
+    per ray |dtau| <= 1e-5 max(1, |tau|) and |dT| <= 1e-5.  Ranges clip chords
+    to pieces down to 1e-7 (the midpoint branch) and to empty."""
     if field == "absorption":
         p = synth.absorption_field(256, seed=0)
     elif field == "octave":
@@ -187,8 +211,8 @@ def test_closed_form_transmittance_matches_oracle(api, ctx, field):
     f.sync()
     T_ref, tau_ref = orc.transmittance(o, d, tr, mode="det")
     tau_g = tau.cpu().numpy()
-    assert np.abs(tau_g - tau_ref).max() <= 1e-5 * max(1.0, np.abs(tau_ref).max())
-    assert (np.abs(T.cpu().numpy() - T_ref) / np.maximum(1.0, np.abs(T_ref))).max() <= 1e-5
+    _tau_per_ray(tau_g, tau_ref, 1e-5, "closed form " + field)
+    _T_abs(T.cpu().numpy(), T_ref, "closed form " + field)
     assert np.all(tau_g[200:210] == 0.0)
     assert np.abs(tau_ref[210:]).max() > 0.1  # non-trivial optical depths
 
@@ -204,8 +228,8 @@ def test_closed_form_lane_groups_agree(api, ctx):
     _, tau_gl = f.transmittance(_t(o[:500]), _t(d[:500]), _t(tr[:500]), mode="det")
     f.sync()
     a, b, c = tau_all.cpu().numpy()[:500], tau_few.cpu().numpy(), tau_gl.cpu().numpy()
-    assert np.abs(a - b).max() <= 2e-6 * max(1.0, np.abs(a).max())
-    assert np.abs(b - c).max() <= 1e-5 * max(1.0, np.abs(c).max())
+    assert np.all(np.abs(a - b) <= 2e-6 * np.maximum(1.0, np.abs(a)))
+    assert np.all(np.abs(b - c) <= 1e-5 * np.maximum(1.0, np.abs(c)))
 
 
 def test_deterministic_transmittance_edges(api, ctx):
@@ -223,7 +247,7 @@ def test_deterministic_transmittance_edges(api, ctx):
     T, _ = f.transmittance(_t(o), _t(d), _t(tr), mode="det")
     f.sync()
     T_ref, _ = orc.transmittance(o, d, tr, mode="det")
-    assert np.abs(T.cpu().numpy() - T_ref).max() <= 1e-5
+    _T_abs(T.cpu().numpy(), T_ref, "edges")
     assert np.all(T.cpu().numpy()[110:130] == 1.0)
     # host buffers through the same entry point
     Th = np.zeros(300, np.float32)
@@ -253,13 +277,13 @@ def test_deterministic_transmittance_lod_masks(api, ctx):
         T, tau = f.transmittance(_t(o), _t(d), _t(tr), mode="det")
         f.sync()
         T_ref, tau_ref = orc.transmittance(o, d, tr, mode="det", lod=oracle.Lod(1, cut, 0))
-        assert np.abs(T.cpu().numpy() - T_ref).max() <= 1e-5, cut
+        _T_abs(T.cpu().numpy(), T_ref, "cutoff %d" % cut)
+        _tau_per_ray(tau.cpu().numpy(), tau_ref, 1e-5, "cutoff %d" % cut)
     f.set_lod(api.lod("unif_cv", 7, "is"))
     T, tau = f.transmittance(_t(o), _t(d), _t(tr), mode="det", spp=16, seed=11)
     f.sync()
     T_ref, tau_ref = orc.transmittance(o, d, tr, mode="det", spp=16, seed=11, lod=oracle.Lod(2, 7, 1))
-    # masked weights up to ~W/w(a) amplify absolute rounding; compare tau relative to its scale
-    assert np.abs(tau.cpu().numpy() - tau_ref).max() <= 2e-5 * max(1.0, np.abs(tau_ref).max())
+    _tau_per_ray(tau.cpu().numpy(), tau_ref, 1e-5, "unif_cv + is, 16 draws")
 
 
 @pytest.mark.parametrize("freq,cone,beta,delta", [("power", "all", 0.3, 0.5),
@@ -282,7 +306,7 @@ def test_deterministic_transmittance_strategy_tables(api, ctx, freq, cone, beta,
     f.sync()
     lo = oracle.Lod(codes_f[freq], 7, codes_c[cone], beta, delta)
     _, tau_ref = orc.transmittance(o, d, tr, mode="det", spp=16, seed=13, lod=lo)
-    assert np.abs(tau.cpu().numpy() - tau_ref).max() <= 2e-5 * max(1.0, np.abs(tau_ref).max())
+    _tau_per_ray(tau.cpu().numpy(), tau_ref, 1e-5, "%s/%s" % (freq, cone))
 
 
 def test_single_scatter_strategy_tables_parity(api, ctx):
@@ -371,7 +395,7 @@ def test_adaptive_clamping_parity(api, ctx):
     for mode in ("det", "closed"):
         _, tau = f.transmittance(_t(o), _t(d), _t(tr), mode=mode)
         f.sync()
-        assert np.abs(tau.cpu().numpy() - tau_ref).max() <= 1e-5 * max(1.0, np.abs(tau_ref).max()), mode
+        _tau_per_ray(tau.cpu().numpy(), tau_ref, 1e-5, "clamping " + mode)
     cg, co = _cam_pair(api, 24, 24)
     diff, noise, ref = _mc_parity(api, f, orc, cg, co, api.render_opts("scatter", 8, 1),
                                   oracle.render_opts("scatter", 8, 1), 2)
@@ -421,7 +445,7 @@ def test_camera_lod_selection_parity(api, ctx):
     for mode in ("det", "closed"):
         _, tau = f.transmittance(_t(o), _t(d), _t(tr), mode=mode)
         f.sync()
-        assert np.abs(tau.cpu().numpy() - tau_ref).max() <= 1e-5 * max(1.0, np.abs(tau_ref).max()), mode
+        _tau_per_ray(tau.cpu().numpy(), tau_ref, 1e-5, "camera lod " + mode)
     diff, noise, ref = _mc_parity(api, f, orc, cg, co, api.render_opts("scatter", 8, 1),
                                   oracle.render_opts("scatter", 8, 1), 2, crop=(36, 36, 24, 24))
     assert ref.max() > 1e-3
@@ -434,7 +458,7 @@ def test_camera_lod_selection_parity(api, ctx):
     _, tau_c = fc.transmittance(_t(o), _t(d), _t(tr), mode="det")
     _, tau_cr = oc2.transmittance(o, d, tr, mode="det")
     fc.sync()
-    assert np.abs(tau_c.cpu().numpy() - tau_cr).max() <= 1e-5 * max(1.0, np.abs(tau_cr).max())
+    _tau_per_ray(tau_c.cpu().numpy(), tau_cr, 1e-5, "camera lod + clamping")
     f.set_lod_camera(None)
     _, tau1 = f.transmittance(_t(o), _t(d), _t(tr), mode="det")
     f.sync()
@@ -493,11 +517,13 @@ def test_multiple_scatter_stochastic_mask_parity(api, ctx):
 
 
 def test_tomography_render_parity(api, ctx):
-    """Tomography image: per camera ray |dT| <= 1e-5 max(1, |T|) on identical float rays, and
-    the rendered image within 1% of the MC noise of its jittered samples.  The
+    """Tomography image: per camera ray |dT| <= 1e-5 and |dtau| <= 1e-5 max(1, |tau|)
+    on identical float rays (signed densities give T up to ~11 here), and the
+    rendered image within 1% of the MC noise of its jittered samples.  The
     image's own rays are built in FP32 on the GPU: a position rounding of
     ~1e-7 times carriers of ~1e3 rad/unit moves phases by ~1e-4, which is why
-    the image is held to the Monte Carlo criterion and T to the ray-exact one."""
+    the image is held to the Monte Carlo criterion and T to the ray-exact one;
+    the API rays of the per-ray check are the same FP32 line on both sides."""
     p = synth.octave_field(3000, 4, seed=10)
     f = api.Field(ctx, p)
     orc = oracle.Field(p, omega_frame="local")
@@ -509,10 +535,14 @@ def test_tomography_render_parity(api, ctx):
     T, tau = f.transmittance(_t(o), _t(d), None, mode="det")
     f.sync()
     T_ref, tau_ref = orc.transmittance(o, d, None, mode="det")
-    # signed densities give T = exp(-tau) above 1 (up to ~11 here): an FP32 error
-    # in tau scales by |T|, so T is held per ray relative to max(1, |T|)
-    assert np.abs(tau.cpu().numpy() - tau_ref).max() <= 1e-5 * max(1.0, np.abs(tau_ref).max())
-    assert (np.abs(T.cpu().numpy() - T_ref) / np.maximum(1.0, np.abs(T_ref))).max() <= 1e-5
+    _tau_per_ray(tau.cpu().numpy(), tau_ref, 1e-5, "tomography rays")
+    # envelope mass per ray: the same kernels with |A|, no carrier
+    env = dict(p)
+    env["omega"] = np.zeros_like(p["omega"])
+    env["phase"] = np.zeros_like(p["phase"])
+    env["weight"] = np.abs(p["weight"])
+    _, E = oracle.Field(env, omega_frame="local").transmittance(o, d, None, mode="det")
+    _T_abs(T.cpu().numpy(), T_ref, "tomography rays", floor=T_ref * 4.0 * 2.0 ** -24 * E)
     diff, noise, ref = _mc_parity(api, f, orc, cg, co, api.render_opts("tomo", 4),
                                   oracle.render_opts("tomo", 4), 4)
     assert diff <= 0.01 * noise, (diff, noise)
@@ -544,28 +574,41 @@ def test_full_size_single_scatter_sampled_pixels(api, ctx):
 
 
 # --------------------------------------------------------------------------- adjoint
+def _grad_blocks(g, g_ref, n, rtol, atol, what):
+    """Element-wise gradient check per parameter block (SoA: mu, quaternion,
+    log scale, carrier, phase, weight), each against its own largest entry."""
+    for name, lo_, hi_ in (("mu", 0, 3 * n), ("quat", 3 * n, 7 * n), ("log_scale", 7 * n, 10 * n),
+                           ("omega", 10 * n, 13 * n), ("phase", 13 * n, 14 * n),
+                           ("weight", 14 * n, 15 * n)):
+        a, b = g[lo_:hi_], g_ref[lo_:hi_]
+        scale = np.abs(b).max()
+        assert scale > 0, (what, name)
+        err = np.abs(a - b)
+        lim = rtol * np.abs(b) + atol * scale
+        print("%s grad %-9s max |d| / scale %.2e, worst |d| / lim %.2f, over %d of %d"
+              % (what, name, err.max() / scale, (err / lim).max(), int((err > lim).sum()), a.size))
+        assert np.all(err <= lim), (what, name, int(np.argmax(err / lim)), (err / lim).max())
 @pytest.mark.parametrize("eps", [0.0, 1e-2])
 def test_tomography_gradient_matches_oracle(api, ctx, eps):
     """Tomography adjoint against the oracle's, without and with adaptive
-    clamping (both hold the clamped supports fixed under differentiation)."""
+    clamping (both hold the clamped supports fixed under differentiation).  The
+    target image is the oracle's render of the unperturbed field; the gradient
+    of L = sum (I - I*)^2 at the perturbed field is compared element by element,
+    every parameter block against its own scale."""
     p = synth.octave_field(340, 4, seed=13)
-    f = api.Field(ctx, p, clamp_eps=eps)
     cg, co = _cam_pair(api, 32, 32)
     ro = api.render_opts("tomo", 1)
-    img = f.render(cg, ro, seed=5)
-    target = (img * 0.97 + 0.01).detach()
+    target = oracle.Field(p, omega_frame="local", clamp_eps=eps).tomo_image(co, 1, 5).astype(np.float32)
     q = synth.perturb(p, 0.01, seed=2)
     g = api.Field(ctx, q, clamp_eps=eps)
     img2 = g.render(cg, ro, seed=5)
-    dL = (2.0 * (img2 - target)).contiguous()
+    dL = (2.0 * (img2 - _t(target))).contiguous()
     grad = g.render_backward(cg, ro, 5, dL)
     g.sync()
     L_ref, grad_ref = oracle.Field(q, omega_frame="local", clamp_eps=eps).tomo_loss_grad(
-        co, 1, 5, target.cpu().numpy())
-    gg = grad.cpu().numpy().astype(np.float64)
-    scale = np.abs(grad_ref).max()
-    bad = np.abs(gg - grad_ref) > 1e-2 * np.abs(grad_ref) + 1e-3 * scale
-    assert bad.mean() < 0.002, (np.nonzero(bad)[0][:10], gg[bad][:5], grad_ref[bad][:5])
+        co, 1, 5, target)
+    _grad_blocks(grad.cpu().numpy().astype(np.float64), grad_ref, q["phase"].shape[0], 1e-3, 1e-4,
+                 "tomography eps=%g" % eps)
 
 
 def test_autograd_function_uses_the_adjoint(api, ctx):
@@ -608,13 +651,21 @@ def test_radiance_gradient_matches_oracle(api, ctx):
     _, g_ref = orc.radiance_grad(co, oracle.render_opts("scatter", 4, 1), 21, dLdI=dLdI, lod=lo,
                                  lod_nee=lo)
     assert np.abs(g_ref).max() > 0
-    rel = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
-    assert rel <= 2e-3, rel
-    # every parameter block receives gradient
+    # element by element, each parameter block (mean, quaternion, log scale,
+    # carrier, phase, weight) against its own scale, so that a block of small
+    # entries is held to its own size
     n = 900
-    for lo_, hi_ in ((0, 3 * n), (3 * n, 7 * n), (7 * n, 10 * n), (10 * n, 13 * n),
-                     (13 * n, 14 * n), (14 * n, 15 * n)):
-        assert np.abs(g[lo_:hi_]).max() > 0
+    for name, lo_, hi_ in (("mu", 0, 3 * n), ("quat", 3 * n, 7 * n), ("log_scale", 7 * n, 10 * n),
+                           ("omega", 10 * n, 13 * n), ("phase", 13 * n, 14 * n),
+                           ("weight", 14 * n, 15 * n)):
+        a, b = g[lo_:hi_], g_ref[lo_:hi_]
+        scale = np.abs(b).max()
+        assert np.abs(a).max() > 0, name  # every parameter block receives gradient
+        err = np.abs(a - b)
+        lim = 1e-3 * np.abs(b) + 1e-4 * scale
+        print("radiance grad %-9s max |d| / scale %.2e, worst |d| / lim %.2f, over %d of %d"
+              % (name, err.max() / scale, (err / lim).max(), int((err > lim).sum()), a.size))
+        assert np.all(err <= lim), (name, int(np.argmax(err / lim)), (err / lim).max())
 
 
 def test_radiance_autograd_function_uses_the_adjoint(api, ctx):

@@ -244,8 +244,15 @@ def test_tau_is_sum_of_per_primitive_integrals_and_cutoffs_nest():
     band = p["band"]
     per = np.zeros((16, f.n))
     for r in range(16):
+        # the transmittance traces the FP32-rounded unit direction v32 as given:
+        # int k(o + t v32) dt over [t0, t1] is the integral along the unit vector
+        # v32/|v32| over [|v32| t0, |v32| t1], divided by |v32|
+        dd = d[r].astype(np.float64)
+        v32 = (dd / np.sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2])).astype(np.float32)
+        v32 = v32.astype(np.float64)
+        nv = np.sqrt(np.sum(v32 * v32))
         for i in range(f.n):
-            per[r, i] = f.chord_integral(i, o[r], d[r], tr[r, 0], tr[r, 1])
+            per[r, i] = f.chord_integral(i, o[r], v32, nv * tr[r, 0], nv * tr[r, 1]) / nv
     assert np.allclose(tau_all, per.sum(1), rtol=0, atol=1e-11)
     assert np.allclose(T_all, np.exp(-tau_all), rtol=1e-14, atol=0)
     prev = np.zeros(16)
