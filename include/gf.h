@@ -19,7 +19,14 @@
  *    cudaStream_t; NULL means the legacy default stream).  Device-side
  *    failures (a traversal stack or window that overflows, a bounded loop
  *    that gives up) set an error word in the field; gf_sync() waits on the
- *    stream and maps it to GF_EOVERFLOW / GF_ETIMEOUT.
+ *    stream and maps it to GF_EOVERFLOW / GF_ETIMEOUT.  Calls that
+ *    synchronise anyway (host buffers) read and clear the word themselves
+ *    and return that status.
+ *  - The compute calls of one field (transmittance, render, adjoint, chord
+ *    lists) share the field's work counter, error word and scratch: issue
+ *    them on one stream, or serialise them.  Two such calls on different
+ *    streams at once race (a kernel may skip work another one's counter
+ *    reset hid).  Different fields are independent.
  *  - Array arguments are plain pointers.  Unless stated, a pointer may be
  *    device memory or host memory (pageable or pinned); host buffers are
  *    staged through library-owned device memory and the call then
@@ -176,6 +183,9 @@ typedef struct gf_render_opts {
   float light_irradiance;
   int free_flight;    /* GF_FLIGHT_* (else GF_EINVAL); scattering only; the server and the
                          adjoint take DELTA only (GF_EINVAL otherwise) */
+  int first_sample;   /* samples first_sample .. first_sample + spp - 1 of every pixel are
+                         rendered (their Philox streams) and averaged, so that a frame can be
+                         accumulated over calls; >= 0 and first_sample + spp <= 2^20 */
 } gf_render_opts;
 
 /* Work counters accumulated by the kernels since the last reset. */
@@ -212,7 +222,9 @@ gf_status gf_field_free(gf_field* field);
 /* Build the BVH over the k-sigma ellipsoid bounds (Sec. 3; the per-level
    acceleration structures of Sec. 4.6 become one radix tree whose top levels
    split by cell, every node carrying the 64-bit OR of its cells).
-   Reorders the packed records along the tree. */
+   Reorders the packed records along the tree.  GF_EOVERFLOW if the tree is
+   deeper than the per-thread traversal stack (64 levels; clustered inputs
+   whose keys share long prefixes); the field then stays unbuilt. */
 gf_status gf_build_bvh(gf_field* field, gf_stream stream);
 
 /* Set the LoD mask used by subsequent calls: primary rays (camera and bounce
@@ -235,7 +247,9 @@ gf_status gf_set_lod_mask(gf_field* field, const gf_lod_desc* primary, const gf_
 gf_status gf_set_lod_camera(gf_field* field, const gf_camera* camera, gf_stream stream);
 
 /* Transmittance of n_rays rays x(t) = o + t d, t in [trange[2r], trange[2r+1]]
-   (trange NULL: [0, inf)); d is normalised by the library.
+   (trange NULL: [0, inf)); d is normalised by the library: the ray runs along
+   the FP32 vector whose components are those of d/|d| rounded once (to within
+   1e-14 of a rounding tie), so a caller can reproduce its line exactly.
    DETERMINISTIC: tau = sum over chords of the chord integral (Eq. 2), each by
    Gauss-Legendre quadrature with a node count set by the chord's whitened
    length and carrier phase span, FP32 with compensated summation; with a
@@ -409,6 +423,15 @@ gf_status gf_server_get_stats(gf_server* server, gf_server_stats* out);
 /* Stop admitting, fail the requests still queued, finish the admitted ones,
    stop the scheduler thread and free the server's memory. */
 gf_status gf_server_destroy(gf_server* server);
+
+/* Measured peaks of the two pipes a Gabor evaluation uses, for its roofline:
+   *sfu_pairs_per_s = (ex2.approx, cos.approx) pairs per second over the whole
+   GPU (one pair per evaluation of A exp(-q/2) cos(theta)), *fma_per_s = FP32
+   fused multiply-adds per second; each the best of 5 timed launches (CUDA
+   events) of independent instruction chains on every SM.  Measurement only:
+   no counterpart in the paper; allocates nothing, synchronises the device's
+   work on a stream of its own. */
+gf_status gf_measure_peaks(int device, double* sfu_pairs_per_s, double* fma_per_s);
 
 gf_status gf_get_stats(gf_field* field, gf_stats* out, int reset);
 /* Wait for the stream, then report (and clear) any device-side error of the field. */

@@ -110,6 +110,18 @@ gf_status ensure_stage(Field& F, size_t bytes) {
 }  // namespace
 
 namespace gf {
+// The field's device error word, read after the stream has been synchronised
+// (host-buffer paths): mapped to a status and cleared, as gf_sync does.
+gf_status take_device_error(Field& F) {
+  int err = 0;
+  GF_CUDA(cudaMemcpy(&err, F.err, 4, cudaMemcpyDeviceToHost), "read error word");
+  if (!err) return GF_OK;
+  GF_CUDA(cudaMemset(F.err, 0, 4), "clear error word");
+  if (err & (ERR_STACK | ERR_WINDOW | ERR_POINTS))
+    return fail(GF_EOVERFLOW, "device buffer overflow (code " + std::to_string(err) + ")");
+  if (err & ERR_GUARD) return fail(GF_ETIMEOUT, "bounded device loop gave up");
+  return fail(GF_EINVAL, "device-side input error (code " + std::to_string(err) + ")");
+}
 
 bool lod_ok(const gf_lod_desc* l) {
   return l && l->freq_policy >= 0 && l->freq_policy <= 6 && l->cone_policy >= 0 &&
@@ -152,9 +164,12 @@ gf_status camera_params(const gf_camera* c, const gf_render_opts* o, uint64_t se
   P.cam.H = c->height;
   if (o->free_flight != GF_FLIGHT_DELTA && o->free_flight != GF_FLIGHT_CDF)
     return fail(GF_EINVAL, "bad free_flight");
+  if (o->first_sample < 0 || (int64_t)o->first_sample + o->spp > (1 << 20))
+    return fail(GF_EINVAL, "first_sample must be >= 0 with first_sample + spp <= 2^20");
   P.integrator = o->integrator;
   P.free_flight = o->free_flight;
   P.spp = o->spp;
+  P.s0 = o->first_sample;
   P.max_bounces = o->max_bounces;
   P.albedo = o->albedo;
   P.irradiance = o->light_irradiance;
@@ -222,12 +237,17 @@ gf_status gf_create(int device, gf_ctx** out) {
   GF_CUDA(cudaSetDevice(device), "cudaSetDevice");
   cudaDeviceProp prop;
   GF_CUDA(cudaGetDeviceProperties(&prop, device), "cudaGetDeviceProperties");
-  // the per-thread stack of this context (a limit of the process, not of the GPU):
-  // explicit, so that every kernel's local frame is covered (launchers check it)
-  GF_CUDA(cudaDeviceSetLimit(cudaLimitStackSize, kStackLimit), "cudaDeviceSetLimit");
   if (!(prop.major == 10 && prop.minor == 3))
     return fail(GF_ECUDA, "libgf is built for sm_103a (GB300); device is sm_" +
                               std::to_string(prop.major) + std::to_string(prop.minor));
+  // the per-thread stack of this context (a limit of the process, not of the GPU):
+  // raised to kStackLimit when below it, never lowered (another library may have
+  // set a larger one); the launchers compare each kernel's frame with the limit
+  // in force at launch time
+  size_t stack = 0;
+  GF_CUDA(cudaDeviceGetLimit(&stack, cudaLimitStackSize), "cudaDeviceGetLimit");
+  if (stack < (size_t)kStackLimit)
+    GF_CUDA(cudaDeviceSetLimit(cudaLimitStackSize, kStackLimit), "cudaDeviceSetLimit");
   std::vector<float> x(kGLTotal), w(kGLTotal);
   for (int r = 0; r < kNumRules; ++r) {
     int n = gl_n(r), off = gl_off(r);
@@ -386,6 +406,10 @@ gf_status gf_build_bvh(gf_field* h, gf_stream stream) {
   GF_CUDA(cudaMalloc((void**)&F.sorted_orig, 4 * n), "alloc order");
   GF_CUDA(cudaMalloc((void**)&F.muw, 16 * n), "alloc means");
   GF_CUDA(build_bvh(F, (cudaStream_t)stream), "build_bvh");
+  if (F.depth > kStack)
+    return fail(GF_EOVERFLOW, "the tree is " + std::to_string(F.depth) +
+                                  " levels deep, beyond the per-thread traversal stack of " +
+                                  std::to_string(kStack) + " entries");
   cudaFree(F.rec_orig);
   F.rec_orig = nullptr;
   cudaFree(F.box_orig);
@@ -498,7 +522,10 @@ gf_status gf_transmittance(gf_field* h, const float* o, const float* d, const fl
     GF_CUDA(cudaMemcpyAsync(out_tau, taud, 4 * n, cudaMemcpyDeviceToHost, s), "copy tau");
     sync = true;
   }
-  if (sync) GF_CUDA(cudaStreamSynchronize(s), "sync");
+  if (sync) {
+    GF_CUDA(cudaStreamSynchronize(s), "sync");
+    return take_device_error(F);
+  }
   return GF_OK;
 }
 
@@ -522,6 +549,7 @@ gf_status gf_render(gf_field* h, const gf_camera* camera, const gf_render_opts* 
   if (od != out_image) {
     GF_CUDA(cudaMemcpyAsync(out_image, od, bytes, cudaMemcpyDeviceToHost, s), "copy image");
     GF_CUDA(cudaStreamSynchronize(s), "sync");
+    return take_device_error(F);
   }
   return GF_OK;
 }
@@ -558,6 +586,7 @@ gf_status gf_render_backward(gf_field* h, const gf_camera* camera, const gf_rend
   if (gd != grad) {
     GF_CUDA(cudaMemcpyAsync(grad, gd, gbytes, cudaMemcpyDeviceToHost, s), "copy grad");
     GF_CUDA(cudaStreamSynchronize(s), "sync");
+    return take_device_error(F);
   }
   return GF_OK;
 }
@@ -616,7 +645,7 @@ gf_status gf_ray_chords(gf_field* h, const float* o, const float* d, const float
   if (t_in && tid != t_in) GF_CUDA(cudaMemcpyAsync(t_in, tid, 4 * nc, cudaMemcpyDeviceToHost, s), "copy");
   if (t_out && tod != t_out) GF_CUDA(cudaMemcpyAsync(t_out, tod, 4 * nc, cudaMemcpyDeviceToHost, s), "copy");
   GF_CUDA(cudaStreamSynchronize(s), "sync");
-  return GF_OK;
+  return take_device_error(F);
 }
 
 gf_status gf_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n,
@@ -694,14 +723,7 @@ gf_status gf_sync(gf_field* h, gf_stream stream) {
   GF_CUDA(cudaSetDevice(F.ctx.device), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
   GF_CUDA(cudaStreamSynchronize(s), "stream sync");
-  int err = 0;
-  GF_CUDA(cudaMemcpy(&err, F.err, 4, cudaMemcpyDeviceToHost), "read error word");
-  if (!err) return GF_OK;
-  GF_CUDA(cudaMemset(F.err, 0, 4), "clear error word");
-  if (err & (ERR_STACK | ERR_WINDOW | ERR_POINTS))
-    return fail(GF_EOVERFLOW, "device buffer overflow (code " + std::to_string(err) + ")");
-  if (err & ERR_GUARD) return fail(GF_ETIMEOUT, "bounded device loop gave up");
-  return fail(GF_EINVAL, "device-side input error (code " + std::to_string(err) + ")");
+  return take_device_error(F);
 }
 
 gf_status gf_field_info(gf_field* h, int64_t* n, int* precision, uint64_t* occupied) {

@@ -375,7 +375,7 @@ __global__ void k_refit(const float* box, const float4* rec, int64_t n, Node* no
 // Four-wide collapse: binary nodes at even depth become Node4s whose children
 // are their children's children (a leaf child stays a leaf).
 // ---------------------------------------------------------------------------
-__global__ void k_depth_parity(const Node* nodes, int64_t m, int* even) {
+__global__ void k_depth_parity(const Node* nodes, int64_t m, int* even, unsigned int* max_depth) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   int d = 0;
@@ -385,6 +385,7 @@ __global__ void k_depth_parity(const Node* nodes, int64_t m, int* even) {
     ++d;
   }
   even[i] = (d & 1) == 0 ? 1 : 0;
+  atomicMax(max_depth, (unsigned int)d);
 }
 
 __device__ __forceinline__ void node_slot(const Node& N, int slot, float* b, unsigned long long& m,
@@ -486,9 +487,10 @@ cudaError_t build_bvh(Field& F, cudaStream_t s) {
   float* box_sorted = nullptr;
   void* tmp = nullptr;
   size_t tmp_bytes = 0;
-  unsigned int hb[12];
+  unsigned int hb[13];
 #define GF_TRY(x) do { e = (x); if (e != cudaSuccess) goto done; } while (0)
-  GF_TRY(dalloc((void**)&bounds, 12 * sizeof(unsigned int)));
+  GF_TRY(dalloc((void**)&bounds, 13 * sizeof(unsigned int)));  // boxes, then the depth
+  GF_TRY(cudaMemsetAsync(bounds + 12, 0, sizeof(unsigned int), s));
   GF_TRY(dalloc((void**)&keys, n * sizeof(unsigned long long)));
   GF_TRY(dalloc((void**)&keys2, n * sizeof(unsigned long long)));
   GF_TRY(dalloc((void**)&idx, n * sizeof(int)));
@@ -538,7 +540,7 @@ cudaError_t build_bvh(Field& F, cudaStream_t s) {
     GF_TRY(cudaGetLastError());
     // four-wide collapse (flags become even-depth markers, leaf_parent their scan)
     const int64_t m = n - 1;
-    k_depth_parity<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(F.nodes, m, flags);
+    k_depth_parity<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(F.nodes, m, flags, bounds + 12);
     GF_TRY(cudaGetLastError());
     size_t sb = 0;
     GF_TRY(cub::DeviceScan::ExclusiveSum(nullptr, sb, flags, leaf_parent, (int)m, s));
@@ -569,6 +571,8 @@ cudaError_t build_bvh(Field& F, cudaStream_t s) {
       memcpy(&f, &b, 4);
       return f;
     };
+    F.depth = (int)hb[12] + 1;  // levels of internal nodes (0 for a single primitive)
+    if (n < 2) F.depth = 0;
     F.dev.lo = make_float3(dec(hb[0]), dec(hb[1]), dec(hb[2]));
     F.dev.hi = make_float3(dec(hb[3]), dec(hb[4]), dec(hb[5]));
     for (int k = 0; k < 3; ++k) {

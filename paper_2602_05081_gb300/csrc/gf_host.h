@@ -76,6 +76,7 @@ struct Field {
   unsigned long long* stats = nullptr;
   int* counter = nullptr;
   float* cell_acc = nullptr;    // per-cell |k_W| sums (64) and counts (64)
+  int depth = 0;                // levels of internal nodes of the binary tree
   bool built = false;
   bool camera_lod = false;  // a camera LoD selection is active
   int server_refs = 0;      // render servers holding this field
@@ -146,6 +147,8 @@ cudaError_t launch_tomo_backward(const Field& F, const PathParams& P, const floa
 
 // sets the thread-local message returned by gf_last_error and returns s
 gf_status report(gf_status s, const std::string& msg);
+// after a stream synchronisation: the field's device error word as a status (cleared)
+gf_status take_device_error(Field& F);
 // camera and integrator options -> kernel parameters (LoD from the field)
 gf_status camera_params(const gf_camera* c, const gf_render_opts* o, uint64_t seed, const Field& F,
                         PathParams& P);

@@ -25,6 +25,8 @@ constexpr size_t kStaticScratchBytes = 8u << 20;
 // per ray: o (12 B) + d (12 B) + trange (8 B) + T (4 B) + tau (4 B) = 40 B,
 // plus 256-byte alignment slack per region and the counter's 256-byte slot
 constexpr int64_t kStaticMaxRays = 200000;
+static_assert(256 + 5 * 255 + 40 * kStaticMaxRays <= kStaticScratchBytes,
+              "the largest call's counter slot and five staged buffers fit the array");
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
@@ -125,7 +127,10 @@ extern "C" gf_status gf_transmittance_static(gf_field* h, const float* o, const 
       return report(GF_ECUDA, std::string("copy tau: ") + cudaGetErrorString(e));
     sync = true;
   }
-  if (sync && (e = cudaStreamSynchronize(s)) != cudaSuccess)
-    return report(GF_ECUDA, std::string("sync: ") + cudaGetErrorString(e));
+  if (sync) {
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return report(GF_ECUDA, std::string("sync: ") + cudaGetErrorString(e));
+    return gf::take_device_error(F);
+  }
   return GF_OK;
 }

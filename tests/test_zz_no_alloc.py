@@ -28,6 +28,12 @@ def lib():
 
 
 def test_static_scratch_transmittance_matches_the_allocating_call(lib):
+    """Every mode (Gauss-Legendre, closed form, ratio tracking) through the
+    static scratch equals gf_transmittance within 1e-5, on two calls in a row,
+    with device buffers, host buffers, and host inputs with device outputs;
+    the field's device error word stays clear after each call; and, once the
+    library's kernels are loaded, the calls leave the device's free memory
+    unchanged (nothing is allocated)."""
     _abi, api = lib
     ctx = api.Context(0)
     p = synth.absorption_field(256, seed=0)
@@ -36,25 +42,52 @@ def test_static_scratch_transmittance_matches_the_allocating_call(lib):
     n = o.shape[0]
     dev = torch.device("cuda", 0)
     od, dd, trd = (torch.from_numpy(a).to(dev) for a in (o, d, tr))
-    for mode, spp in ((_abi.GF_TR_DETERMINISTIC, 1), (_abi.GF_TR_RATIO_TRACKING, 2)):
+    modes = ((_abi.GF_TR_DETERMINISTIC, 1), (_abi.GF_TR_CLOSED_FORM, 1),
+             (_abi.GF_TR_RATIO_TRACKING, 2))
+    refs = {}
+    for mode, spp in modes:
         ref_T = torch.empty(n, device=dev)
         ref_tau = torch.empty(n, device=dev)
         _abi.gf_transmittance(field.h, od, dd, trd, n, mode, spp, 5, ref_T, ref_tau)
         field.sync()
-        ref = ref_T.cpu().numpy()
-        # two calls in a row through the static scratch: device buffers, then host buffers
+        refs[mode] = (ref_T.cpu().numpy(), ref_tau.cpu().numpy())
+    # load every kernel the static calls use, then hold the device's free memory
+    Tw = torch.empty(n, device=dev)
+    for mode, spp in modes:
+        _abi.gf_transmittance_static(field.h, od, dd, trd, n, mode, spp, 5, Tw, None)
+    field.sync()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    outs = {k: (torch.full((n,), -1.0, device=dev), torch.full((n,), -1.0, device=dev))
+            for k in range(2)}
+    for mode, spp in modes:
+        ref, ref_tau = refs[mode]
+        det = mode != _abi.GF_TR_RATIO_TRACKING
+        # two calls in a row through the static scratch: device buffers, host buffers,
+        # then host inputs with device outputs
         for call in range(2):
-            T = torch.full((n,), -1.0, device=dev)
-            tau = torch.full((n,), -1.0, device=dev)
+            T, tau = outs[call]
+            T.fill_(-1.0)
+            tau.fill_(-1.0)
             _abi.gf_transmittance_static(field.h, od, dd, trd, n, mode, spp, 5, T, tau)
             field.sync()
             assert np.abs(T.cpu().numpy() - ref).max() <= 1e-5, (mode, call)
+            if det:
+                assert np.abs(tau.cpu().numpy() - ref_tau).max() <= 1e-5, (mode, call)
             Th = np.full(n, -1.0, np.float32)
             tauh = np.full(n, -1.0, np.float32)
             _abi.gf_transmittance_static(field.h, o, d, tr, n, mode, spp, 5, Th, tauh)
+            field.sync()
             assert np.abs(Th - ref).max() <= 1e-5, (mode, call)
-            if mode == _abi.GF_TR_DETERMINISTIC:
-                assert np.abs(tauh - ref_tau.cpu().numpy()).max() <= 1e-5
+            if det:
+                assert np.abs(tauh - ref_tau).max() <= 1e-5, (mode, call)
+            T.fill_(-1.0)
+            _abi.gf_transmittance_static(field.h, o, d, tr, n, mode, spp, 5, T, None)
+            field.sync()
+            assert np.abs(T.cpu().numpy() - ref).max() <= 1e-5, (mode, call)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
     # sizes beyond the static capacity are refused before any GPU work
     big = 200001
     with pytest.raises(_abi.GfError) as e:
