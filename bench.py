@@ -1,16 +1,24 @@
 #!/usr/bin/env python
-"""Benchmark: single-scattering renders of a 100k-primitive Gabor field.
+"""Benchmark: multiple scattering with per-bounce stochastic LoD masks.
 
-Workload (one step): a 4-octave synthetic field of 100,000 Gabor primitives in
-the unit cube (the octave generator of synth.octave_field, seed 0), a 512x512
-pinhole camera, 16 samples per pixel, one directional light, isotropic phase,
-albedo 0.8, single scattering, rendered at the 4 LoD band cutoffs (all bands,
-<= 1/2, <= 1/4 and <= 1/8 of the highest band): 4 renders per step.
+Workload (the largest single-GPU configuration): a 6-octave synthetic field of
+1,000,000 Gabor primitives in the unit cube (the octave generator of
+synth.octave_field, seed 0), a 1024x1024 pinhole camera, 64 samples per pixel,
+up to 8 bounces, one directional light, isotropic phase, albedo 0.8, a new
+mask per path segment: Uniform + control-variate bands with importance-sampled
+orientation cones for camera, bounce and NEE rays.  FP32 records; the same
+frame with FP16 records beside it.
 
-Prints one JSON line: Mrays/s (traced path segments: camera rays + NEE rays),
-Gabor evaluations/s, render p50/p99 ms, the roofline of the render kernel, an
-end-to-end figure through the C ABI with host buffers, the FP64 oracle timed
-on the host cores, and the SM clocks sampled during the timed region.
+One step renders 8 of the 64 samples of every pixel (samples 8j .. 8j+7 of
+step j mod 8, through gf_render_opts.first_sample), so eight steps accumulate
+the 64-spp frame.  The line reports Mrays/s (traced path segments: camera,
+bounce and NEE rays), Gabor evaluations/s, render p50/p99 (per 8-spp step and
+per 64-spp frame), the roofline of the render kernel against measured SFU and
+FMA peaks, an end-to-end figure through the C ABI with host buffers, the
+image RMSE against the FP64 oracle on sampled pixels beside the oracle's own
+Monte Carlo noise, the oracle timed on the host cores, and the SM clocks
+sampled during the timed region.  The single-scattering configuration (100k
+primitives, 512x512, 16 spp, 4 band cutoffs) is reported as an extra key.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -33,31 +41,30 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-N_PRIMS = 100_000
-OCTAVES = 4
-RES = 512
-SPP = 16
-DEFAULT_RES, DEFAULT_SPP = RES, SPP
-CUTOFFS = (3, 2, 1, 0)
-# smaller launches of the same kernel for profiling captures (--res / --spp)
-SEED = 1
+N_PRIMS = 1_000_000
+OCTAVES = 6
+RES = 1024
+SPP = 64          # samples per pixel of the frame
+STEP_SPP = 8      # samples per pixel of one step
+BOUNCES = 8
+SEED = 3
 METRIC = "Mrays/s and Gabor evals/s at fixed RMSE vs FP64 oracle; render p50/p99 ms"
-WORKLOAD = ("single scattering, 100k-primitive 4-octave Gabor field, 512x512, 16 spp, "
-            "4 LoD band cutoffs (all, <=1/2, <=1/4, <=1/8)")
-MUFU_PER_SM_CLK = 16  # SFU results per SM per clock
-MUFU_PER_EVAL = 2     # ex2 + cos per Gabor evaluation
-# DRAM bytes (read + write) per k_render_scatter launch of this workload, from
-#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
-#       --clock-control none -k regex:k_render_scatter -s 4 -c 4 --csv
-#       python bench.py --res 512 --spp 2 --steps 1 --warmup 2 --cpu-seconds 0 --server-requests 0
-# (the 4 cutoffs: 7.32, 5.15, 3.02, 0.78 GB at 2 spp), scaled by the traced rays to 16 spp
-# (x 8.0; the traffic is the chord store's, proportional to the rays)
-TRAFFIC_BYTES_PER_LAUNCH = 4.07e9 * 8.0
+WORKLOAD = ("multiple scattering, 1M-primitive 6-octave Gabor field, 1024x1024, 64 spp "
+            "(8 per step), <= 8 bounces, per-bounce Uniform+CV bands and importance-sampled "
+            "cones (camera, bounce and NEE rays)")
+# single scattering, 100k primitives, 512x512, 16 spp, 4 band cutoffs (extra key)
+C2_PRIMS, C2_OCTAVES, C2_RES, C2_SPP, C2_CUTOFFS, C2_SEED = 100_000, 4, 512, 16, (3, 2, 1, 0), 1
+# DRAM bytes (read + write) per traced ray of k_render_scatter on this workload's field and
+# masks, from ncu on a 256x256, 8-spp launch (profiles/k_render_scatter_multiscatter_1m.md),
+# scaled to a launch by its traced rays; None until captured for the current kernel
+TRAFFIC_BYTES_PER_RAY = None
 
 
 def config(extra=None):
     c = {"workload": WORKLOAD, "primitives": N_PRIMS, "octaves": OCTAVES, "image": [RES, RES],
-         "spp": SPP, "lod_cutoffs": list(CUTOFFS), "integrator": "single scattering (delta + ratio tracking)",
+         "spp": SPP, "spp_per_step": STEP_SPP, "max_bounces": BOUNCES,
+         "lod": "unif_cv bands + is cones, primary and NEE",
+         "integrator": "delta tracking + ratio-tracked NEE, isotropic phase, albedo 0.8",
          "storage": "fp32 records", "l2": "flushed between timed steps (256 MiB write)",
          "parallelism": "replicas"}
     if extra:
@@ -122,31 +129,69 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_sample(seconds, cutoffs=CUTOFFS, crop=4):
-    """Time the FP64 oracle on crops of the same workload for ~`seconds`."""
+def _oracle_setup():
     import oracle
     p = synth.octave_field(N_PRIMS, OCTAVES, seed=0)
     f = oracle.Field(p, omega_frame="local")
     c = synth.DEFAULT_CAMERA
     cam = oracle.camera(c["eye"], c["look_at"], c["up"], c["vfov_deg"], RES, RES)
-    ro = oracle.render_opts("scatter", SPP, 1, 0.8, synth.LIGHT_DIR, 1.0)
+    ro = oracle.render_opts("scatter", SPP, BOUNCES, 0.8, synth.LIGHT_DIR, 1.0)
+    lod = oracle.Lod(2, 7, 1)  # Uniform + CV bands, importance-sampled cones
+    return oracle, f, cam, ro, lod
+
+
+def oracle_pixels(seconds, crop=(4, 2), threads=0):
+    """The FP64 oracle on crops of the benchmark frame (all 64 samples of each
+    pixel, every sample kept) for about `seconds`: its rays/s on the host cores,
+    and the per-sample values for the RMSE against the GPU frame."""
+    oracle, f, cam, ro, lod = _oracle_setup()
     rng = np.random.default_rng(0)
     oracle.rays_traced(reset=True)
     t0 = time.perf_counter()
-    crops = 0
+    crops = []
     while True:
-        for cut in cutoffs:
-            lod = oracle.Lod(1, cut, 0)
-            x, y = (int(v) for v in rng.integers(0, RES - crop, 2))
-            f.render(cam, ro, SEED, lod=lod, lod_nee=lod, crop=(x, y, crop, crop))
-            crops += 1
+        x, y = (int(v) for v in rng.integers(RES // 4, 3 * RES // 4 - 4, 2))
+        smp = f.render(cam, ro, SEED, lod=lod, lod_nee=lod, crop=(x, y, crop[0], crop[1]),
+                       samples=True, threads=threads)
+        crops.append((x, y, smp))
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
     rays = oracle.rays_traced(reset=True)
-    return {"value": rays / dt / 1e6, "unit": "Mrays/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "%d crops of %dx%d px x %d spp over the 4 cutoffs, %d rays, %.1f s"
-                      % (crops, crop, crop, SPP, rays, dt)}
+    return {"rays_per_s": rays / dt, "rays": rays, "seconds": dt, "crops": crops,
+            "threads": threads or os.cpu_count()}
+
+
+def oracle_sample(seconds):
+    """cpu_baseline: the oracle on all host cores for ~`seconds`, plus a short
+    single-thread run of one crop."""
+    r = oracle_pixels(seconds)
+    r1 = oracle_pixels(0.0, crop=(1, 1), threads=1)
+    px = sum(c[2].shape[0] * c[2].shape[1] for c in r["crops"])
+    return {"value": r["rays_per_s"] / 1e6, "unit": "Mrays/s", "cores": r["threads"],
+            "kind": "oracle",
+            "sample": "%d crops of 4x2 px of the benchmark frame at 64 spp, <= 8 bounces "
+                      "(%d px, %d rays, %.1f s)" % (len(r["crops"]), px, r["rays"], r["seconds"]),
+            "single_thread": {"value": r1["rays_per_s"] / 1e6, "unit": "Mrays/s",
+                              "sample": "one pixel at 64 spp, %d rays, %.1f s"
+                                        % (r1["rays"], r1["seconds"])}}, r["crops"]
+
+
+def rmse_vs_oracle(frame, crops):
+    """Image RMSE of the GPU frame against the oracle on the crops' pixels, beside
+    the oracle's own Monte Carlo noise (standard error of each pixel's mean over
+    its 64 samples) under the shared Philox streams."""
+    d, sig = [], []
+    for x, y, smp in crops:
+        h, w, n = smp.shape
+        d.append((frame[y:y + h, x:x + w] - smp.mean(-1)).ravel())
+        sig.append((smp.std(-1, ddof=1) / math.sqrt(n)).ravel())
+    d, sig = np.concatenate(d), np.concatenate(sig)
+    rmse = float(np.sqrt(np.mean(d ** 2)))
+    noise = float(np.sqrt(np.mean(sig ** 2)))
+    return {"pixels": int(d.size), "rmse": rmse, "oracle_mc_noise": noise,
+            "ratio": rmse / noise if noise > 0 else None,
+            "criterion": "rmse <= 0.01 x oracle MC noise (shared streams)"}
 
 
 SERVER_ASSETS = ((50_000, 4), (200_000, 4), (1_000_000, 6), (2_000_000, 6))
@@ -499,22 +544,38 @@ def run_workload(args):
 
 
 def run_reference(args, rank, world):
+    """The FP64 oracle as the comparison program: each step renders one 4x2-pixel
+    crop of the benchmark frame at its full 64 spp and <= 8 bounces on the host
+    cores; Mrays/s over the timed steps."""
     if rank != 0:
         return
-    import oracle  # noqa: F401
-    per_step = max(2.0, 20.0 / max(1, args.steps + args.warmup))
+    import oracle
+    oracle_, f, cam, ro, lod = _oracle_setup()
+    rng = np.random.default_rng(1)
+
+    def step():
+        x, y = (int(v) for v in rng.integers(RES // 4, 3 * RES // 4 - 4, 2))
+        f.render(cam, ro, SEED, lod=lod, lod_nee=lod, crop=(x, y, 4, 2))
+
     for _ in range(args.warmup):
-        oracle_sample(per_step / 4, crop=2)
-    vals = [oracle_sample(per_step, crop=2) for _ in range(args.steps)]
-    rays_per_s = statistics.mean(v["value"] for v in vals)
-    cb = dict(vals[-1])
-    cb["value"] = rays_per_s
-    line = {"impl": "reference", "metric": METRIC, "value": rays_per_s, "unit": "Mrays/s",
+        step()
+    oracle.rays_traced(reset=True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    rays = oracle.rays_traced(reset=True)
+    value = rays / dt / 1e6
+    cb = {"value": value, "unit": "Mrays/s", "cores": os.cpu_count(), "kind": "oracle",
+          "sample": "%d crops of 4x2 px of the benchmark frame at 64 spp, <= 8 bounces, %d rays, "
+                    "%.1f s" % (args.steps, rays, dt)}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mrays/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config({"engine": "FP64 CPU oracle (OpenMP)"}), "cpu_baseline": cb,
-            "e2e": {"value": rays_per_s, "unit": "Mrays/s", "h2d_bytes_per_step": 0,
+            "ms_per_step": 1000.0 * dt / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config({"engine": "FP64 CPU oracle (OpenMP)", "storage": "fp64"}),
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -534,6 +595,44 @@ def combine_ranks(total_ms, rays, evals, world, device):
     return float(tmax[0]), float(sums[0]), float(sums[1])
 
 
+def config2_leg(api, ctx, dev, stream, steps=2):
+    """Single scattering, 100k primitives, 512x512, 16 spp, the 4 band cutoffs:
+    Mrays/s and per-render times (the second configuration of the method)."""
+    import torch
+    p = synth.octave_field(C2_PRIMS, C2_OCTAVES, seed=0)
+    f = api.Field(ctx, p)
+    c = synth.DEFAULT_CAMERA
+    cam = api.camera(c["eye"], c["look_at"], c["up"], c["vfov_deg"], C2_RES, C2_RES)
+    ro = api.render_opts("scatter", C2_SPP, 1, 0.8, synth.LIGHT_DIR, 1.0)
+    out = torch.empty(C2_RES, C2_RES, device=dev)
+    lods = [api.lod("cutoff", k) for k in C2_CUTOFFS]
+    for lo in lods:
+        f.set_lod(lo)
+        f.render(cam, ro, seed=C2_SEED, out=out, stream=stream)
+    torch.cuda.synchronize()
+    f.stats(reset=True)
+    ms = {k: [] for k in C2_CUTOFFS}
+    for _ in range(steps):
+        for k, lo in zip(C2_CUTOFFS, lods):
+            f.set_lod(lo)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            f.render(cam, ro, seed=C2_SEED, out=out, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms[k].append(a.elapsed_time(b))
+    f.sync()
+    st = f.stats(reset=True)
+    f.free()
+    tot = sum(sum(v) for v in ms.values())
+    return {"workload": "single scattering, 100k-primitive 4-octave field, 512x512, 16 spp, "
+                        "4 LoD band cutoffs (all, <=1/2, <=1/4, <=1/8)",
+            "mrays_per_s": st["rays"] / (tot * 1e-3) / 1e6,
+            "gabor_evals_per_s": st["evals"] / (tot * 1e-3),
+            "render_ms_by_cutoff": {str(k): statistics.mean(v) for k, v in ms.items()},
+            "ms_per_step_of_4_renders": tot / steps}
+
+
 def run_ours(args, rank, world):
     import torch
     import torch.distributed as dist
@@ -546,44 +645,45 @@ def run_ours(args, rank, world):
     from paper_2602_05081_gb300 import _abi, api
 
     ctx = api.Context(local)
+    sfu_peak, fma_peak = _abi.gf_measure_peaks(local)
     p = synth.octave_field(N_PRIMS, OCTAVES, seed=0)
     field = api.Field(ctx, p)
+    lod = api.lod("unif_cv", 7, "is")
+    field.set_lod(lod, lod)
     c = synth.DEFAULT_CAMERA
     cam = api.camera(c["eye"], c["look_at"], c["up"], c["vfov_deg"], RES, RES)
-    ro = api.render_opts("scatter", SPP, 1, 0.8, synth.LIGHT_DIR, 1.0)
     out = torch.empty(RES, RES, dtype=torch.float32, device=dev)
+    frame_sum = torch.zeros(RES, RES, dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
     stream = torch.cuda.current_stream()
-    lods = [api.lod("cutoff", k) for k in CUTOFFS]
+    nslice = SPP // STEP_SPP
+    opts = [api.render_opts("scatter", STEP_SPP, BOUNCES, 0.8, synth.LIGHT_DIR, 1.0,
+                            first_sample=STEP_SPP * j) for j in range(nslice)]
 
-    def step(evs=None):
-        for j, lo in enumerate(lods):
-            field.set_lod(lo)
-            if evs is not None:
-                evs[j][0].record(stream)
-            _abi.gf_render(field.h, cam, ro, SEED, out, stream)
-            if evs is not None:
-                evs[j][1].record(stream)
-
-    for _ in range(args.warmup):
-        step()
+    for j in range(args.warmup):
+        _abi.gf_render(field.h, cam, opts[j % nslice], SEED, out, stream)
     field.sync(stream)
     field.stats(reset=True)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
-    render_ms = []
     step_ms = []
-    for _ in range(args.steps):
+    frames_done = 0
+    for j in range(args.steps):
         flush.fill_(1.0)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in lods]
-        step(evs)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _abi.gf_render(field.h, cam, opts[j % nslice], SEED, out, stream)
+        b.record(stream)
         torch.cuda.synchronize()
-        ms = [a.elapsed_time(b) for a, b in evs]
-        render_ms.append(ms)
-        step_ms.append(sum(ms))
+        step_ms.append(a.elapsed_time(b))
+        frame_sum += out.double()
+        if j % nslice == nslice - 1:
+            frames_done += 1
+            if frames_done == 1:
+                frame = (frame_sum / nslice).float().cpu().numpy()
+            frame_sum.zero_()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -592,70 +692,74 @@ def run_ours(args, rank, world):
     st = field.stats(reset=True)
     total_ms_max, rays_all, evals_all = combine_ranks(sum(step_ms), st["rays"], st["evals"],
                                                       world, dev)
+    if frames_done == 0:  # fewer steps than one frame: finish the frame untimed
+        for j in range(args.steps, nslice):
+            _abi.gf_render(field.h, cam, opts[j], SEED, out, stream)
+            frame_sum += out.double()
+        frame = (frame_sum / nslice).float().cpu().numpy()
+        field.stats(reset=True)
     # end to end through the C ABI with a host (pinned) output buffer
     host = torch.empty(RES, RES, dtype=torch.float32).pin_memory()
     torch.cuda.synchronize()
     field.stats(reset=True)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        for lo in lods:
-            field.set_lod(lo)
-            _abi.gf_render(field.h, cam, ro, SEED, host, stream)
+    for j in range(args.steps):
+        _abi.gf_render(field.h, cam, opts[j % nslice], SEED, host, stream)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     st_e2e = field.stats(reset=True)
-    # the same step with 32-byte FP16 / BF16 records (FP32 math)
-    prec_ms = {"fp32": sum(step_ms) / len(step_ms)}
-    for prec in ("fp16", "bf16"):
-        fr = api.Field(ctx, p, precision=prec)
-        for _ in range(max(1, args.warmup)):
-            for lo in lods:
-                fr.set_lod(lo)
-                _abi.gf_render(fr.h, cam, ro, SEED, out, stream)
+    # the whole 64-spp frame with 32-byte FP16 records (FP32 math) and with FP32 records
+    frame_ms = {}
+    for prec in ("fp32", "fp16"):
+        fr = field if prec == "fp32" else api.Field(ctx, p, precision=prec)
+        fr.set_lod(lod, lod)
+        _abi.gf_render(fr.h, cam, opts[0], SEED, out, stream)
         flush.fill_(1.0)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        for lo in lods:
-            fr.set_lod(lo)
-            _abi.gf_render(fr.h, cam, ro, SEED, out, stream)
+        for j in range(nslice):
+            _abi.gf_render(fr.h, cam, opts[j], SEED, out, stream)
         ev1.record(stream)
         torch.cuda.synchronize()
         fr.sync(stream)
-        prec_ms[prec] = ev0.elapsed_time(ev1)
-        fr.free()
+        frame_ms[prec] = ev0.elapsed_time(ev1)
+        if prec != "fp32":
+            fr.free()
     if rank != 0:
         return
     import ctypes
-    flat = [m for s in render_ms for m in s]
+    launches = args.steps  # one k_render_scatter (+ one k_fix_to_image) per step
+    evals_per_launch = st["evals"] / launches
+    achieved = evals_per_launch / (statistics.mean(step_ms) * 1e-3)
     peaks, peak_kind = measured_peaks()
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_geval = sm_count * MUFU_PER_SM_CLK / MUFU_PER_EVAL * peaks.get("sm_max_mhz", 2070.0) * 1e-3
-    achieved = (st["evals"] / (4 * args.steps)) / (statistics.mean(flat) * 1e-3) * 1e-9
-    traffic = TRAFFIC_BYTES_PER_LAUNCH if (RES, SPP) == (DEFAULT_RES, DEFAULT_SPP) else None
     value = rays_all / (total_ms_max * 1e-3) / 1e6
+    rays_per_launch = st["rays"] / launches
+    traffic = TRAFFIC_BYTES_PER_RAY * rays_per_launch if TRAFFIC_BYTES_PER_RAY else None
+    nominal = torch.cuda.get_device_properties(dev).multi_processor_count * 8 * \
+        peaks.get("sm_max_mhz", 2070.0) * 1e6
     line = {
         "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "config": config(),
         "gabor_evals_per_s": evals_all / (total_ms_max * 1e-3),
-        "render_ms_p50": float(np.percentile(flat, 50)),
-        "render_ms_p99": float(np.percentile(flat, 99)),
-        "render_ms_by_cutoff": {str(k): statistics.mean(s[j] for s in render_ms)
-                                for j, k in enumerate(CUTOFFS)},
+        "render_ms_p50": float(np.percentile(step_ms, 50)),
+        "render_ms_p99": float(np.percentile(step_ms, 99)),
+        "render_ms_per_64spp_frame": frame_ms,
         "rays_per_step": st["rays"] / args.steps,
         "evals_per_step": st["evals"] / args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_geval, "unit": "Geval/s",
-                     "frac": achieved / peak_geval, "traffic": traffic,
-                     "kernel": "k_render_scatter (delta + ratio tracking)",
-                     "peak_basis": "%d SMs x %d SFU/clk / %d SFU per eval x %.0f MHz (%s clock)"
-                                   % (sm_count, MUFU_PER_SM_CLK, MUFU_PER_EVAL,
-                                      peaks.get("sm_max_mhz", 2070.0), peak_kind)},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": sfu_peak / 1e9,
+                     "unit": "Geval/s", "frac": achieved / sfu_peak, "traffic": traffic,
+                     "kernel": "k_render_scatter (delta + ratio tracking, stochastic masks)",
+                     "peak_basis": "measured: (ex2.approx, cos.approx) pairs per second on every "
+                                   "SM (gf_measure_peaks), one pair per Gabor evaluation; nominal "
+                                   "16 MUFU/clk/SM would give %.0f Geval/s" % (nominal / 1e9),
+                     "fma_peak_per_s": fma_peak},
         "e2e": {"value": st_e2e["rays"] / e2e_s / 1e6, "unit": "Mrays/s",
-                "h2d_bytes_per_step": 4 * (ctypes.sizeof(_abi.gf_camera) + ctypes.sizeof(_abi.gf_render_opts)),
-                "d2h_bytes_per_step": 4 * RES * RES * 4},
-        "gpu_launches": 2 * 4 * args.steps,  # k_render_scatter + k_fix_to_image per render
-        "storage_ms_per_step": prec_ms,
+                "h2d_bytes_per_step": ctypes.sizeof(_abi.gf_camera) + ctypes.sizeof(_abi.gf_render_opts),
+                "d2h_bytes_per_step": RES * RES * 4},
+        "gpu_launches": 2 * args.steps,  # k_render_scatter + k_fix_to_image per step
+        "storage_ms_per_frame": frame_ms,
         "clocks": clk,
     }
     line["counters_per_ray"] = {k: st[k] / max(1, st["rays"])
@@ -664,11 +768,15 @@ def run_ours(args, rank, world):
         tot = max(1, sum(st["cycles"]))
         line["phase_cycles_share"] = dict(zip(("traversal_steps", "leaf_rounds", "chord_walks",
                                                "point_evaluation", "decisions"),
-                                              (c / tot for c in st["cycles"])))
+                                              (c_ / tot for c_ in st["cycles"])))
+    if world == 1 and args.config2:
+        line["config2"] = config2_leg(api, ctx, dev, stream)
     if world == 1 and args.server_requests > 0:
         line["server"] = server_leg(api, ctx, args.server_requests)
     if world == 1 and args.cpu_seconds > 0:
-        line["cpu_baseline"] = oracle_sample(args.cpu_seconds)
+        cb, crops = oracle_sample(args.cpu_seconds)
+        line["cpu_baseline"] = cb
+        line["rmse_vs_oracle"] = rmse_vs_oracle(frame, crops)
     print(json.dumps(line), flush=True)
 
 
@@ -679,18 +787,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--server-requests", type=int, default=16,
+    ap.add_argument("--server-requests", type=int, default=0,
                     help="requests of the render-server leg (0: skip)")
+    ap.add_argument("--config2", type=int, default=1,
+                    help="add the single-scattering configuration as an extra key (0: skip)")
     ap.add_argument("--workload", choices=["scatter", "transmittance", "multiscatter", "adjoint",
                                            "clamping", "free_flight", "precision"],
-                    default="scatter", help="workload of the JSON line (default: the single-"
+                    default="scatter", help="workload of the JSON line (default: the multiple-"
                     "scattering benchmark)")
     ap.add_argument("--res", type=int, default=None, help="profiling only: image size")
     ap.add_argument("--spp", type=int, default=None, help="profiling only: samples per pixel")
     args = ap.parse_args()
     if args.workload == "scatter":
         globals()["RES"] = args.res or RES
-        globals()["SPP"] = args.spp or SPP
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

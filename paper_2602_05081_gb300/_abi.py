@@ -60,7 +60,8 @@ class gf_camera(C.Structure):
 class gf_render_opts(C.Structure):
     _fields_ = [("integrator", C.c_int), ("spp", C.c_int), ("max_bounces", C.c_int),
                 ("albedo", C.c_float), ("light_dir", C.c_float * 3),
-                ("light_irradiance", C.c_float), ("free_flight", C.c_int)]
+                ("light_irradiance", C.c_float), ("free_flight", C.c_int),
+                ("first_sample", C.c_int)]
 
 
 class gf_stats(C.Structure):
@@ -126,6 +127,7 @@ _SIGS = {
     "gf_server_wait": [_vp, _u64, C.c_double, C.POINTER(gf_result)],
     "gf_server_get_stats": [_vp, C.POINTER(gf_server_stats)],
     "gf_server_destroy": [_vp],
+    "gf_measure_peaks": [_int, C.POINTER(C.c_double), C.POINTER(C.c_double)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(lib, _name)
@@ -306,6 +308,13 @@ def gf_server_get_stats(server) -> dict:
 
 def gf_server_destroy(server):
     _check(lib.gf_server_destroy(server))
+
+
+def gf_measure_peaks(device: int = 0):
+    """(ex2, cos) pairs per second and FP32 FMAs per second, measured on the device."""
+    sfu, fma = C.c_double(), C.c_double()
+    _check(lib.gf_measure_peaks(int(device), C.byref(sfu), C.byref(fma)))
+    return sfu.value, fma.value
 
 
 EXPORTED = tuple(_SIGS) + ("gf_last_error",)

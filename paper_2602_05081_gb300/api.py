@@ -56,12 +56,14 @@ def camera(eye, look_at, up, vfov_deg, width, height):
 
 
 def render_opts(integrator="scatter", spp=1, max_bounces=1, albedo=0.8,
-                light_dir=(1.0, 1.0, -1.0), light_irradiance=1.0, free_flight="delta"):
-    """free_flight: "delta" (delta tracking) or "cdf" (inversion of the optical-depth CDF)."""
+                light_dir=(1.0, 1.0, -1.0), light_irradiance=1.0, free_flight="delta",
+                first_sample=0):
+    """free_flight: "delta" (delta tracking) or "cdf" (inversion of the optical-depth CDF);
+    samples first_sample .. first_sample + spp - 1 of each pixel are averaged."""
     return A.gf_render_opts(A.GF_INTEG_TOMO if integrator == "tomo" else A.GF_INTEG_SCATTER,
                             int(spp), int(max_bounces), float(albedo),
                             (C.c_float * 3)(*light_dir), float(light_irradiance),
-                            {"delta": 0, "cdf": 1}[free_flight])
+                            {"delta": 0, "cdf": 1}[free_flight], int(first_sample))
 
 
 class Field:

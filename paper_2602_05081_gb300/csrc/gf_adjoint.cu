@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(kBackBlock)
     if (px >= P.cam.W || py >= P.cam.H) continue;  // every lane returns to the tile fetch
     const float gI = dLdI[(int64_t)py * P.cam.W + px];
     if (gI == 0.f) continue;
-    for (int s = 0; s < P.spp; ++s) {
+    for (int s = P.s0; s < P.s0 + P.spp; ++s) {
       float3 o, v;
       camera_ray(P.cam, P.seed, px, py, s, o, v);
       cnt.rays += 1;
@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(kBackBlock)
     const float gI = dLdI[pix];
     if (gI == 0.f) continue;
     const float base = gI / (float)P.spp;
-    for (int s = 0; s < P.spp; ++s) {
+    for (int s = P.s0; s < P.s0 + P.spp; ++s) {
       float3 o, v;
       camera_ray(P.cam, P.seed, px, py, s, o, v);
       cnt.rays += 1;

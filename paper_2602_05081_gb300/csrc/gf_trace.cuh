@@ -818,6 +818,7 @@ struct PathParams {
   CamDev cam;
   int integrator, spp, max_bounces;
   int free_flight;  // GF_FLIGHT_DELTA or GF_FLIGHT_CDF
+  int s0;           // first sample index (samples s0 .. s0 + spp - 1)
   float albedo, irradiance;
   float3 light;
   uint64_t seed;

@@ -497,8 +497,8 @@ struct ImageWork {
     rq = 0;
     if (u >= npix * nchunk) return false;
     pix = u / nchunk;
-    s0 = (u - pix * nchunk) * chunk;
-    s1 = min(s0 + chunk, P->spp);
+    s0 = P->s0 + (u - pix * nchunk) * chunk;
+    s1 = min(s0 + chunk, P->s0 + P->spp);
     return true;
   }
   __device__ void finish(int, int pix, long long acc) const {
@@ -527,8 +527,8 @@ struct ServerWork {
     const ServerItem it = L->items[lo];
     rq = it.req;
     pix = it.pix0 + (f - it.base);
-    s0 = 0;
-    s1 = L->reqs[rq].P.spp;
+    s0 = L->reqs[rq].P.s0;
+    s1 = s0 + L->reqs[rq].P.spp;
     return true;
   }
   // a lane renders all samples of a pixel
