@@ -33,6 +33,12 @@
  *    synchronises the stream before returning.  The caller owns every
  *    input and output buffer; the library owns packed records, the BVH and
  *    scratch, all released by gf_field_free / gf_destroy.
+ *  - Device memory: every device buffer the library owns comes from the
+ *    context's allocator (gf_create_ex; cudaMalloc/cudaFree by default), so a
+ *    caller's memory manager (e.g. a framework's caching allocator) holds it.
+ *    Fields allocate at gf_load_field, gf_build_bvh and gf_reserve; compute
+ *    calls allocate only when a host buffer, image or adjoint is larger than
+ *    what the field has reserved so far (then through the same allocator).
  *  - Layouts are structure-of-arrays, float32, row-major per element.
  *  - Random numbers: Philox4x32-10 (Salmon et al. 2011) keyed by the 64-bit
  *    seed, counter = (draw, primitive index or 0xFFFFFFFF, ray or pixel
@@ -203,10 +209,30 @@ typedef struct gf_stats {
                          library was built with GF_PHASE_TIMERS */
 } gf_stats;
 
+/* Caller-supplied device allocator.  alloc returns at least `bytes` bytes of
+   device memory on the context's device, aligned to 256 bytes, for use on
+   `stream` (the stream of the call that needs it; NULL = legacy default), or
+   NULL when it cannot (the call then fails with GF_ENOMEM).  free returns a
+   pointer alloc gave, with the size that was asked for; the library calls it
+   only after every piece of work that used the memory has completed (it
+   synchronises the stream or device first), so the memory may be reused at
+   once.  Both may be called from any thread of the process, including the
+   render server's scheduler thread; `user` is passed through. */
+typedef struct gf_allocator {
+  void* (*alloc)(void* user, size_t bytes, gf_stream stream);
+  void (*free)(void* user, void* ptr, size_t bytes, gf_stream stream);
+  void* user;
+} gf_allocator;
+
 /* Context on one CUDA device (cudaSetDevice(device) is made current by every
    call that takes the context or a field created from it).  Computes the
-   Gauss-Legendre tables.  GF_ECUDA if the device is missing or not sm_103. */
+   Gauss-Legendre tables.  GF_ECUDA if the device is missing or not sm_103.
+   gf_create uses cudaMalloc/cudaFree; gf_create_ex takes the allocator of
+   every device buffer of the context, its fields and its render servers
+   (copied; NULL = cudaMalloc/cudaFree).  GF_EINVAL for an allocator with a
+   null alloc or free. */
 gf_status gf_create(int device, gf_ctx** out);
+gf_status gf_create_ex(int device, const gf_allocator* allocator, gf_ctx** out);
 gf_status gf_destroy(gf_ctx* ctx);
 
 /* Pack the primitives (Sec. 4.2 parameters -> Sigma^-1, world carrier, amplitude,
@@ -226,6 +252,23 @@ gf_status gf_field_free(gf_field* field);
    deeper than the per-thread traversal stack (64 levels; clustered inputs
    whose keys share long prefixes); the field then stays unbuilt. */
 gf_status gf_build_bvh(gf_field* field, gf_stream stream);
+
+/* Scratch of the compute calls, allocated ahead (through the context's
+   allocator) so that later calls within these sizes allocate nothing:
+   max_rays rays of gf_transmittance / gf_ray_chords with host buffers (cap
+   chords each for gf_ray_chords), max_pixels pixels of gf_render (the pixel
+   sums of the scattering renderer and the staging of a host image), and
+   the per-warp chord store of the scattering renderer when render != 0, and
+   the per-thread lists of the radiance adjoint when adjoint != 0.  Sizes only
+   grow; zeros leave a part as it is.  GF_ESTATE before gf_build_bvh. */
+typedef struct gf_reserve_opts {
+  int64_t max_rays;
+  int max_chords;
+  int64_t max_pixels;
+  int render;
+  int adjoint;
+} gf_reserve_opts;
+gf_status gf_reserve(gf_field* field, const gf_reserve_opts* opts, gf_stream stream);
 
 /* Set the LoD mask used by subsequent calls: primary rays (camera and bounce
    segments, transmittance API) and NEE rays (nee may be NULL = same as primary). */
@@ -349,19 +392,21 @@ gf_status gf_transmittance_static(gf_field* field, const float* o, const float* 
    fields.  No counterpart in the paper (a serving layer around gf_render).
 
    Requests queue in arrival order.  A request is admitted when one of
-   max_inflight slots is free and its framebuffer (width x height floats,
-   256-byte aligned) fits in the server's device pool of mem_budget bytes;
+   max_inflight slots is free and its framebuffer (width x height 64-bit
+   fixed-point sums and width x height floats, each 256-byte aligned: 12
+   bytes per pixel) fits in the server's device pool of mem_budget bytes;
    the head of the queue waits for memory (no overtaking).  Every batched
    launch gives each admitted request an equal share of batch_samples pixel
    samples (at least 32 pixels), taken as its next contiguous pixel range;
    one kernel launch renders the ranges of all admitted requests on all
    fields together, and two launches are kept in flight on two streams so
    that one launch's tail overlaps the next launch.  Requests admitted while
-   launches run join the next launch.  A pixel is rendered by one lane from
-   its first sample to its last, so a request's image does not depend on
-   what it was batched with (up to FP32 summation order inside the
-   majorant sums, as between two gf_render calls).  When a request's last
-   range completes, its framebuffer is copied to request.out (host or device)
+   launches run join the next launch.  Lanes take units of up to 8
+   consecutive samples of one pixel; each sample's radiance is summed in
+   64-bit fixed point (exact, in any order), so a request's image is bit for
+   bit the one gf_render gives, whatever it was batched with.  When a
+   request's last range completes, its sums become the image (sum / spp) and
+   are copied to request.out (host or device)
    and its memory and slot are released; then it is DONE.
    A scheduler thread inside the library drives the device; submit, poll and
    wait may be called from any thread.  The fields must outlive the server. */

@@ -70,6 +70,20 @@ class gf_stats(C.Structure):
                 ("steps", C.c_uint64), ("leaves", C.c_uint64), ("cycles", C.c_uint64 * 5)]
 
 
+# device allocator callbacks (include/gf.h gf_allocator)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
+class gf_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
+class gf_reserve_opts(C.Structure):
+    _fields_ = [("max_rays", C.c_int64), ("max_chords", C.c_int), ("max_pixels", C.c_int64),
+                ("render", C.c_int), ("adjoint", C.c_int)]
+
+
 GF_REQ_QUEUED, GF_REQ_RUNNING, GF_REQ_DONE, GF_REQ_FAILED = range(4)
 
 
@@ -103,6 +117,8 @@ lib = C.CDLL(LIB_PATH)
 _vp, _i64, _u64, _int = C.c_void_p, C.c_int64, C.c_uint64, C.c_int
 _SIGS = {
     "gf_create": [_int, C.POINTER(_vp)],
+    "gf_create_ex": [_int, C.POINTER(gf_allocator), C.POINTER(_vp)],
+    "gf_reserve": [_vp, C.POINTER(gf_reserve_opts), _vp],
     "gf_destroy": [_vp],
     "gf_load_field": [_vp, C.POINTER(gf_params), C.POINTER(gf_field_opts), _vp, C.POINTER(_vp)],
     "gf_field_free": [_vp],
@@ -176,6 +192,22 @@ def gf_create(device: int = 0):
     h = _vp()
     _check(lib.gf_create(int(device), C.byref(h)))
     return h
+
+
+def gf_create_ex(device: int, allocator: "gf_allocator | None"):
+    """Context whose device memory comes from `allocator` (None: cudaMalloc/cudaFree);
+    the caller keeps the allocator and its callbacks alive as long as the context."""
+    h = _vp()
+    _check(lib.gf_create_ex(int(device), None if allocator is None else C.byref(allocator),
+                            C.byref(h)))
+    return h
+
+
+def gf_reserve(field, max_rays=0, max_chords=0, max_pixels=0, render=False, adjoint=False,
+               stream=None):
+    o = gf_reserve_opts(int(max_rays), int(max_chords), int(max_pixels), int(bool(render)),
+                        int(bool(adjoint)))
+    _check(lib.gf_reserve(field, C.byref(o), stream_handle(stream)))
 
 
 def gf_destroy(ctx):

@@ -20,10 +20,53 @@ _WMODES = {"peak": A.GF_WEIGHT_PEAK, "normalized": A.GF_WEIGHT_NORMALIZED}
 _PRECS = {"fp32": A.GF_PREC_FP32, "fp16": A.GF_PREC_FP16, "bf16": A.GF_PREC_BF16}
 
 
-class Context:
-    def __init__(self, device: int = 0):
+class TorchAllocator:
+    """Device memory of the library from PyTorch's caching allocator
+    (gf_create_ex): the library's records, trees and scratch show up in
+    torch.cuda.memory_reserved and are reused by torch once the library returns
+    them.  Counts the calls, so a caller can check that a stretch of work
+    allocated nothing."""
+
+    def __init__(self, device: int):
         self.device = int(device)
-        self.h = A.gf_create(self.device)
+        self.calls_alloc = 0
+        self.calls_free = 0
+        self.live_bytes = 0
+        self._sizes = {}
+        self._alloc = A.ALLOC_FN(self._on_alloc)
+        self._free = A.FREE_FN(self._on_free)
+        self.c = A.gf_allocator(self._alloc, self._free, None)
+
+    def _on_alloc(self, user, nbytes, stream):
+        try:
+            p = torch.cuda.caching_allocator_alloc(int(nbytes), self.device, int(stream or 0))
+        except Exception:  # reported to the library as a failed allocation
+            return None
+        self.calls_alloc += 1
+        self.live_bytes += int(nbytes)
+        self._sizes[int(p)] = int(nbytes)
+        return int(p)
+
+    def _on_free(self, user, ptr, nbytes, stream):
+        self.calls_free += 1
+        self.live_bytes -= self._sizes.pop(int(ptr), int(nbytes))
+        try:
+            torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:  # interpreter shutdown: the process releases the memory
+            pass
+
+
+class Context:
+    """A gf context on one GPU.  allocator: "torch" (default; PyTorch's caching
+    allocator holds every device buffer of the library), None (cudaMalloc and
+    cudaFree inside the library) or a TorchAllocator."""
+
+    def __init__(self, device: int = 0, allocator="torch"):
+        self.device = int(device)
+        if allocator == "torch":
+            allocator = TorchAllocator(self.device)
+        self.allocator = allocator
+        self.h = A.gf_create_ex(self.device, None if allocator is None else allocator.c)
 
     def close(self):
         if getattr(self, "h", None):
@@ -94,6 +137,12 @@ class Field:
         A.gf_build_bvh(self.h, stream)
         if not device_inputs:
             self._keep = None
+
+    def reserve(self, max_rays=0, max_chords=0, max_pixels=0, render=False, adjoint=False,
+                stream=None):
+        """Allocate the compute calls' scratch ahead (gf_reserve), so that calls within
+        these sizes allocate nothing."""
+        A.gf_reserve(self.h, max_rays, max_chords, max_pixels, render, adjoint, stream)
 
     def free(self):
         if getattr(self, "h", None):

@@ -316,17 +316,6 @@ __global__ void __launch_bounds__(kBackBlock)
   flush_counters(F, cnt, lane);
 }
 
-// per-thread primitive lists of the adjoint kernels (2 per thread, grown on demand)
-static cudaError_t ensure_lists(const Field& F, int64_t threads) {
-  const size_t lbytes = (size_t)threads * 2 * kRayList * sizeof(int);
-  if (F.rlist_bytes >= lbytes) return cudaSuccess;
-  if (F.rlist) cudaFree(F.rlist);
-  F.rlist = nullptr;
-  F.rlist_bytes = 0;
-  const cudaError_t e = cudaMalloc((void**)&F.rlist, lbytes);
-  if (e == cudaSuccess) F.rlist_bytes = lbytes;
-  return e;
-}
 
 cudaError_t launch_tomo_backward(const Field& F, const PathParams& P, const float* dLdI,
                                  float* grad, cudaStream_t s) {
@@ -624,6 +613,18 @@ static BackArgs back_args(const Field& F, float* grad) {
   return B;
 }
 
+// per-thread primitive lists of the radiance adjoint (2 per thread of a full
+// persistent grid), grown through the field's allocator
+cudaError_t ensure_adjoint_lists(const Field& F, cudaStream_t s) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_radiance_backward, kBackBlock, 0) !=
+      cudaSuccess)
+    (void)cudaGetLastError();
+  if (per_sm < 1) per_sm = 1;
+  const int64_t threads = (int64_t)F.ctx.sm_count * per_sm * kBackBlock;
+  return grow(F, (void**)&F.rlist, F.rlist_bytes, (size_t)threads * 2 * kRayList * sizeof(int), s);
+}
+
 cudaError_t launch_radiance_backward(const Field& F, const PathParams& P, const float* dLdI,
                                      float* grad, cudaStream_t s) {
   (void)cudaGetLastError();  // a stale error of an unrelated call is not ours
@@ -640,7 +641,8 @@ cudaError_t launch_radiance_backward(const Field& F, const PathParams& P, const 
   int64_t g = (int64_t)F.ctx.sm_count * per_sm;
   if (need < g) g = need;
   if (g < 1) g = 1;
-  if ((e = ensure_lists(F, g * kBackBlock)) != cudaSuccess) return e;
+  // lists sized for a full grid (allocated ahead by gf_reserve, else here)
+  if ((e = ensure_adjoint_lists(F, s)) != cudaSuccess) return e;
   k_radiance_backward<<<(unsigned)g, kBackBlock, 0, s>>>(F.dev, P, B, dLdI, F.counter, F.rlist);
   return cudaGetLastError();
 }

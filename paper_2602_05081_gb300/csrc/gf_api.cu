@@ -2,9 +2,11 @@
 // host-buffer staging and error mapping around the kernels.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -97,19 +99,65 @@ gf_status stage(Field& F, const void* p, size_t bytes, bool in, cudaStream_t s, 
   return GF_OK;
 }
 
-gf_status ensure_stage(Field& F, size_t bytes) {
-  if (bytes <= F.stage_bytes) return GF_OK;
-  if (F.stage) cudaFree(F.stage);
-  F.stage = nullptr;
-  F.stage_bytes = 0;
-  GF_CUDA(cudaMalloc(&F.stage, bytes), "staging alloc");
-  F.stage_bytes = bytes;
+// Host buffers of the context-free test helpers (gf_philox, gf_faddeeva) pass
+// through this fixed device array in chunks, so those calls allocate nothing;
+// a mutex serialises them.
+constexpr size_t kHelperBytes = 1u << 20;
+static __device__ __align__(256) unsigned char g_helper[kHelperBytes];
+std::mutex g_helper_mu;
+void* g_helper_dev[64] = {nullptr};
+
+gf_status helper_area(void** out) {
+  int dev = 0;
+  GF_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev < 0 || dev >= 64) return fail(GF_EINVAL, "device index beyond 63");
+  if (!g_helper_dev[dev]) GF_CUDA(cudaGetSymbolAddress(&g_helper_dev[dev], g_helper), "helper area");
+  *out = g_helper_dev[dev];
+  return GF_OK;
+}
+
+gf_status ensure_stage(Field& F, size_t bytes, cudaStream_t s) {
+  GF_CUDA(grow(F, &F.stage, F.stage_bytes, bytes, s), "staging alloc");
   return GF_OK;
 }
 
 }  // namespace
 
 namespace gf {
+cudaError_t dev_alloc(const Ctx& c, void** p, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 16;
+  if (!c.alloc.alloc) return cudaMalloc(p, bytes);
+  void* q = c.alloc.alloc(c.alloc.user, bytes, (gf_stream)s);
+  if (!q) return cudaErrorMemoryAllocation;
+  *p = q;
+  return cudaSuccess;
+}
+
+void dev_free(const Ctx& c, void* p, size_t bytes, cudaStream_t s) {
+  if (!p) return;
+  if (bytes == 0) bytes = 16;
+  if (!c.alloc.free) {
+    cudaFree(p);
+    return;
+  }
+  c.alloc.free(c.alloc.user, p, bytes, (gf_stream)s);
+}
+
+cudaError_t grow(const Field& F, void** p, size_t& have, size_t bytes, cudaStream_t s) {
+  if (bytes <= have && *p) return cudaSuccess;
+  if (*p) {
+    // earlier calls (on any stream) may still read the old buffer
+    const cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return e;
+    F.mem.release(*p, s);
+    *p = nullptr;
+    have = 0;
+  }
+  const cudaError_t e = F.mem.alloc(p, bytes, s);
+  if (e == cudaSuccess) have = bytes;
+  return e;
+}
+
 // The field's device error word, read after the stream has been synchronised
 // (host-buffer paths): mapped to a status and cleared, as gf_sync does.
 gf_status take_device_error(Field& F) {
@@ -209,13 +257,10 @@ void weideman_coefficients(Weideman& W) {
 
 namespace {
 
+// every buffer of the field goes back to its allocator once no work uses it
 void free_field(Field& F) {
-  void* ptrs[] = {F.p_mu, F.p_quat, F.p_ls, F.p_om, F.p_ph, F.p_w, F.rec_orig, F.box_orig,
-                  F.kw_orig, F.rec, F.rec16, F.nodes, F.nodes4, F.sorted_orig, F.labels, F.err,
-                  F.stats, F.counter, F.cell_acc, F.stage, F.wscratch, F.acc64, F.rlist, F.gl,
-                  F.ext2_orig, F.ext2, F.keff2, F.muw, F.cells_dev};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+  cudaDeviceSynchronize();
+  F.mem.release_all();
 }
 
 }  // namespace
@@ -228,9 +273,15 @@ extern "C" {
 
 const char* gf_last_error(void) { return g_err.c_str(); }
 
-gf_status gf_create(int device, gf_ctx** out) {
+gf_status gf_create(int device, gf_ctx** out) { return gf_create_ex(device, nullptr, out); }
+
+gf_status gf_create_ex(int device, const gf_allocator* allocator, gf_ctx** out) {
   if (!out) return fail(GF_EINVAL, "out null");
   *out = nullptr;
+  if (allocator && (!allocator->alloc || !allocator->free))
+    return fail(GF_EINVAL, "allocator with a null alloc or free");
+  Ctx base;
+  if (allocator) base.alloc = *allocator;
   int ndev = 0;
   GF_CUDA(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
   if (device < 0 || device >= ndev) return fail(GF_EINVAL, "no such device");
@@ -259,11 +310,16 @@ gf_status gf_create(int device, gf_ctx** out) {
     }
   }
   float* gl = nullptr;
-  GF_CUDA(cudaMalloc((void**)&gl, 2 * kGLTotal * sizeof(float)), "alloc GL tables");
-  GF_CUDA(cudaMemcpy(gl, x.data(), kGLTotal * sizeof(float), cudaMemcpyHostToDevice), "GL tables");
-  GF_CUDA(cudaMemcpy(gl + kGLTotal, w.data(), kGLTotal * sizeof(float), cudaMemcpyHostToDevice),
-          "GL tables");
+  GF_CUDA(dev_alloc(base, (void**)&gl, 2 * kGLTotal * sizeof(float), nullptr), "alloc GL tables");
+  cudaError_t e = cudaMemcpy(gl, x.data(), kGLTotal * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(gl + kGLTotal, w.data(), kGLTotal * sizeof(float), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    dev_free(base, gl, 2 * kGLTotal * sizeof(float), nullptr);
+    return cuda_fail(e, "GL tables");
+  }
   gf_ctx* c = new gf_ctx;
+  c->c = base;
   c->c.gl = gl;
   c->c.device = device;
   c->c.sm_count = prop.multiProcessorCount;
@@ -276,7 +332,8 @@ gf_status gf_create(int device, gf_ctx** out) {
 gf_status gf_destroy(gf_ctx* ctx) {
   if (ctx) {
     cudaSetDevice(ctx->c.device);
-    cudaFree(ctx->c.gl);
+    cudaDeviceSynchronize();
+    dev_free(ctx->c, ctx->c.gl, 2 * kGLTotal * sizeof(float), nullptr);
   }
   delete ctx;
   return GF_OK;
@@ -301,10 +358,11 @@ gf_status gf_load_field(gf_ctx* ctx, const gf_params* p, const gf_field_opts* op
   gf_field* h = new gf_field;
   Field& F = h->f;
   F.ctx = ctx->c;
+  F.mem.ctx = ctx->c;
   F.n = p->n;
   F.opts = *opts;
   const int64_t n = p->n;
-  auto A = [&](void** q, size_t bytes) { return cudaMalloc(q, bytes ? bytes : 16); };
+  auto A = [&](void** q, size_t bytes) { return F.mem.alloc(q, bytes, s); };
   cudaError_t e = cudaSuccess;
   void* band_dev = nullptr;
   do {
@@ -335,8 +393,7 @@ gf_status gf_load_field(gf_ctx* ctx, const gf_params* p, const gf_field_opts* op
       break;
   } while (0);
   if (e != cudaSuccess) {
-    free_field(F);
-    if (band_dev) cudaFree(band_dev);
+    free_field(F);  // band_dev included
     delete h;
     return cuda_fail(e, "gf_load_field alloc/copy");
   }
@@ -355,7 +412,7 @@ gf_status gf_load_field(gf_ctx* ctx, const gf_params* p, const gf_field_opts* op
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, F.err, 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(acc, F.cell_acc, 512, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (band_dev) cudaFree(band_dev);
+  if (e == cudaSuccess) F.mem.release(band_dev, s);
   if (e != cudaSuccess) {
     free_field(F);
     delete h;
@@ -401,25 +458,26 @@ gf_status gf_build_bvh(gf_field* h, gf_stream stream) {
   GF_CUDA(cudaSetDevice(F.ctx.device), "cudaSetDevice");
   if (F.built) return GF_OK;
   const int64_t n = F.n;
-  GF_CUDA(cudaMalloc((void**)&F.rec, 64 * n), "alloc records");
-  GF_CUDA(cudaMalloc((void**)&F.nodes, n > 1 ? (n - 1) * sizeof(Node) : 16), "alloc nodes");
-  GF_CUDA(cudaMalloc((void**)&F.sorted_orig, 4 * n), "alloc order");
-  GF_CUDA(cudaMalloc((void**)&F.muw, 16 * n), "alloc means");
-  GF_CUDA(build_bvh(F, (cudaStream_t)stream), "build_bvh");
+  cudaStream_t s = (cudaStream_t)stream;
+  GF_CUDA(F.mem.get(&F.rec, 64 * n, s), "alloc records");
+  GF_CUDA(F.mem.get(&F.nodes, n > 1 ? (n - 1) * sizeof(Node) : 16, s), "alloc nodes");
+  GF_CUDA(F.mem.get(&F.sorted_orig, 4 * n, s), "alloc order");
+  GF_CUDA(F.mem.get(&F.muw, 16 * n, s), "alloc means");
+  GF_CUDA(build_bvh(F, s), "build_bvh");
   if (F.depth > kStack)
     return fail(GF_EOVERFLOW, "the tree is " + std::to_string(F.depth) +
                                   " levels deep, beyond the per-thread traversal stack of " +
                                   std::to_string(kStack) + " entries");
-  cudaFree(F.rec_orig);
+  GF_CUDA(cudaStreamSynchronize(s), "sync");  // the build has read the original-order data
+  F.mem.release(F.rec_orig, s);
   F.rec_orig = nullptr;
-  cudaFree(F.box_orig);
+  F.mem.release(F.box_orig, s);
   F.box_orig = nullptr;
-  cudaFree(F.ext2_orig);
+  F.mem.release(F.ext2_orig, s);
   F.ext2_orig = nullptr;
   if (F.opts.precision != GF_PREC_FP32) {
     // 32-byte records replace the 64-byte ones on the rendering path
-    GF_CUDA(cudaMalloc((void**)&F.rec16, 32 * n), "alloc reduced records");
-    cudaStream_t s = (cudaStream_t)stream;
+    GF_CUDA(F.mem.get(&F.rec16, 32 * n, s), "alloc reduced records");
     int herr = 0;
     GF_CUDA(launch_pack16(F, s), "pack reduced records");
     GF_CUDA(cudaMemcpyAsync(&herr, F.err, 4, cudaMemcpyDeviceToHost, s), "read error word");
@@ -430,7 +488,7 @@ gf_status gf_build_bvh(gf_field* h, gf_stream stream) {
     }
     F.dev.rec16 = F.rec16;
     F.dev.orig16 = F.sorted_orig;
-    cudaFree(F.rec);  // the 64-byte records are not read again
+    F.mem.release(F.rec, s);  // the 64-byte records are not read again (stream synchronised)
     F.rec = nullptr;
     F.dev.rec = nullptr;
   }
@@ -448,8 +506,8 @@ gf_status gf_set_lod_camera(gf_field* h, const gf_camera* cam, gf_stream stream)
   GF_CUDA(cudaSetDevice(F.ctx.device), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
   const bool reduced = F.opts.precision != GF_PREC_FP32;
-  if (!F.cells_dev) GF_CUDA(cudaMalloc((void**)&F.cells_dev, sizeof(unsigned long long)), "alloc");
-  if (reduced && !F.keff2) GF_CUDA(cudaMalloc((void**)&F.keff2, 4 * F.n), "alloc");
+  if (!F.cells_dev) GF_CUDA(F.mem.get(&F.cells_dev, sizeof(unsigned long long), s), "alloc");
+  if (reduced && !F.keff2) GF_CUDA(F.mem.get(&F.keff2, 4 * F.n, s), "alloc");
   // the finest resolved carrier at distance d is c / d (pixel pitch 2 d tan(phi/2) / H)
   const double pi = 3.14159265358979323846;
   float3 eye = make_float3(0.f, 0.f, 0.f);
@@ -466,6 +524,29 @@ gf_status gf_set_lod_camera(gf_field* h, const gf_camera* cam, gf_stream stream)
   F.dev.cells_on = cam ? cells : ~0ull;
   F.camera_lod = cam != nullptr;
   if (reduced) F.dev.ext2 = cam ? F.keff2 : F.ext2;
+  return GF_OK;
+}
+
+gf_status gf_reserve(gf_field* h, const gf_reserve_opts* o, gf_stream stream) {
+  if (!h || !o) return fail(GF_EINVAL, "null argument");
+  Field& F = h->f;
+  if (!F.built) return fail(GF_ESTATE, "gf_build_bvh has not run");
+  if (o->max_rays < 0 || o->max_rays > (1ll << 31) - 1 || o->max_chords < 0 || o->max_pixels < 0 ||
+      o->max_pixels > (1ll << 31) - 1)
+    return fail(GF_EINVAL, "reserve sizes out of range");
+  GF_CUDA(cudaSetDevice(F.ctx.device), "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)o->max_rays, nc = n * (size_t)o->max_chords;
+  const size_t npix = (size_t)o->max_pixels;
+  // the largest staging any call within these sizes asks for
+  size_t stage = 0;
+  if (n) stage = std::max(256 * 6 + n * 4 * 10, 256 * 8 + n * 4 * 9 + nc * 12);
+  if (npix) stage = std::max(stage, npix * 4 + 256);
+  if (npix && o->adjoint) stage = std::max(stage, npix * 4 + (size_t)F.n * 60 + 512);
+  gf_status st;
+  if (stage && (st = ensure_stage(F, stage, s))) return st;
+  if (o->render && npix) GF_CUDA(ensure_render_scratch(F, (int64_t)npix, s), "render scratch");
+  if (o->adjoint) GF_CUDA(ensure_adjoint_lists(F, s), "adjoint lists");
   return GF_OK;
 }
 
@@ -491,7 +572,7 @@ gf_status gf_transmittance(gf_field* h, const float* o, const float* d, const fl
   GF_CUDA(cudaSetDevice(F.ctx.device), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
   size_t n = (size_t)n_rays;
-  gf_status st = ensure_stage(F, 256 * 6 + n * 4 * (3 + 3 + 2 + 1 + 1));
+  gf_status st = ensure_stage(F, 256 * 6 + n * 4 * (3 + 3 + 2 + 1 + 1), s);
   if (st) return st;
   size_t off = 0;
   void *od, *dd, *td, *Td, *taud;
@@ -542,7 +623,7 @@ gf_status gf_render(gf_field* h, const gf_camera* camera, const gf_render_opts* 
   size_t bytes = (size_t)P.cam.W * P.cam.H * 4;
   void* od = out_image;
   if (!is_device_ptr(out_image)) {
-    if ((st = ensure_stage(F, bytes + 256))) return st;
+    if ((st = ensure_stage(F, bytes + 256, s))) return st;
     od = F.stage;
   }
   GF_CUDA(launch_render(F, P, (float*)od, s), "render launch");
@@ -572,7 +653,7 @@ gf_status gf_render_backward(gf_field* h, const gf_camera* camera, const gf_rend
   cudaStream_t s = (cudaStream_t)stream;
   size_t npix = (size_t)P.cam.W * P.cam.H;
   size_t gbytes = (size_t)F.n * 15 * 4;
-  if ((st = ensure_stage(F, npix * 4 + gbytes + 512))) return st;
+  if ((st = ensure_stage(F, npix * 4 + gbytes + 512, s))) return st;
   size_t off = 0;
   void *dl, *gd;
   if ((st = stage(F, dL_dimage, npix * 4, true, s, off, &dl)) ||
@@ -616,7 +697,7 @@ gf_status gf_ray_chords(gf_field* h, const float* o, const float* d, const float
   GF_CUDA(cudaSetDevice(F.ctx.device), "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
   size_t n = (size_t)n_rays, nc = n * (size_t)cap;
-  gf_status st = ensure_stage(F, 256 * 8 + n * 4 * 9 + nc * 12);
+  gf_status st = ensure_stage(F, 256 * 8 + n * 4 * 9 + nc * 12, s);
   if (st) return st;
   size_t off = 0;
   void *od, *dd, *td, *cd, *pd, *tid, *tod;
@@ -658,18 +739,23 @@ gf_status gf_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int
     GF_CUDA(launch_philox(ctr, key, out, n, s), "philox launch");
     return GF_OK;
   }
-  uint32_t *c = nullptr, *k = nullptr, *r = nullptr;
-  GF_CUDA(cudaMalloc((void**)&c, 16 * n), "alloc");
-  GF_CUDA(cudaMalloc((void**)&k, 8 * n), "alloc");
-  GF_CUDA(cudaMalloc((void**)&r, 16 * n), "alloc");
-  cudaError_t e = cudaMemcpyAsync(c, ctr, 16 * n, cudaMemcpyDefault, s);
-  if (!e) e = cudaMemcpyAsync(k, key, 8 * n, cudaMemcpyDefault, s);
-  if (!e) e = launch_philox(c, k, r, n, s);
-  if (!e) e = cudaMemcpyAsync(out, r, 16 * n, cudaMemcpyDefault, s);
-  if (!e) e = cudaStreamSynchronize(s);
-  cudaFree(c);
-  cudaFree(k);
-  cudaFree(r);
+  std::lock_guard<std::mutex> lock(g_helper_mu);
+  void* area = nullptr;
+  gf_status st = helper_area(&area);
+  if (st) return st;
+  const int64_t chunk = kHelperBytes / 40;  // counter 16 B + key 8 B + block 16 B
+  uint32_t* c = (uint32_t*)area;
+  uint32_t* k = c + 4 * chunk;
+  uint32_t* r = k + 2 * chunk;
+  cudaError_t e = cudaSuccess;
+  for (int64_t i = 0; i < n && !e; i += chunk) {
+    const int64_t m = n - i < chunk ? n - i : chunk;
+    e = cudaMemcpyAsync(c, ctr + 4 * i, 16 * m, cudaMemcpyDefault, s);
+    if (!e) e = cudaMemcpyAsync(k, key + 2 * i, 8 * m, cudaMemcpyDefault, s);
+    if (!e) e = launch_philox(c, k, r, m, s);
+    if (!e) e = cudaMemcpyAsync(out + 4 * i, r, 16 * m, cudaMemcpyDefault, s);
+    if (!e) e = cudaStreamSynchronize(s);
+  }
   if (e) return cuda_fail(e, "gf_philox");
   return GF_OK;
 }
@@ -684,15 +770,21 @@ gf_status gf_faddeeva(const float* z, float* w, int64_t n, gf_stream stream) {
     GF_CUDA(launch_faddeeva(W, z, w, n, s), "faddeeva launch");
     return GF_OK;
   }
-  float *zd = nullptr, *wd = nullptr;
-  GF_CUDA(cudaMalloc((void**)&zd, 8 * n), "alloc");
-  cudaError_t e = cudaMalloc((void**)&wd, 8 * n);
-  if (!e) e = cudaMemcpyAsync(zd, z, 8 * n, cudaMemcpyDefault, s);
-  if (!e) e = launch_faddeeva(W, zd, wd, n, s);
-  if (!e) e = cudaMemcpyAsync(w, wd, 8 * n, cudaMemcpyDefault, s);
-  if (!e) e = cudaStreamSynchronize(s);
-  cudaFree(zd);
-  cudaFree(wd);
+  std::lock_guard<std::mutex> lock(g_helper_mu);
+  void* area = nullptr;
+  gf_status st = helper_area(&area);
+  if (st) return st;
+  const int64_t chunk = kHelperBytes / 16;  // z 8 B + w 8 B
+  float* zd = (float*)area;
+  float* wd = zd + 2 * chunk;
+  cudaError_t e = cudaSuccess;
+  for (int64_t i = 0; i < n && !e; i += chunk) {
+    const int64_t m = n - i < chunk ? n - i : chunk;
+    e = cudaMemcpyAsync(zd, z + 2 * i, 8 * m, cudaMemcpyDefault, s);
+    if (!e) e = launch_faddeeva(W, zd, wd, m, s);
+    if (!e) e = cudaMemcpyAsync(w + 2 * i, wd, 8 * m, cudaMemcpyDefault, s);
+    if (!e) e = cudaStreamSynchronize(s);
+  }
   if (e) return cuda_fail(e, "gf_faddeeva");
   return GF_OK;
 }

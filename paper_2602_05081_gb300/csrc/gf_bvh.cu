@@ -475,7 +475,6 @@ __global__ void k_pad_mean_step(float* box, int64_t n, const unsigned int* bound
   }
 }
 
-static cudaError_t dalloc(void** p, size_t bytes) { return cudaMalloc(p, bytes ? bytes : 16); }
 
 cudaError_t build_bvh(Field& F, cudaStream_t s) {
   (void)cudaGetLastError();  // a stale error of an unrelated call is not ours
@@ -489,15 +488,15 @@ cudaError_t build_bvh(Field& F, cudaStream_t s) {
   size_t tmp_bytes = 0;
   unsigned int hb[13];
 #define GF_TRY(x) do { e = (x); if (e != cudaSuccess) goto done; } while (0)
-  GF_TRY(dalloc((void**)&bounds, 13 * sizeof(unsigned int)));  // boxes, then the depth
+  GF_TRY(F.mem.alloc((void**)&bounds, 13 * sizeof(unsigned int), s));  // boxes, then the depth
   GF_TRY(cudaMemsetAsync(bounds + 12, 0, sizeof(unsigned int), s));
-  GF_TRY(dalloc((void**)&keys, n * sizeof(unsigned long long)));
-  GF_TRY(dalloc((void**)&keys2, n * sizeof(unsigned long long)));
-  GF_TRY(dalloc((void**)&idx, n * sizeof(int)));
-  GF_TRY(dalloc((void**)&idx2, n * sizeof(int)));
-  GF_TRY(dalloc((void**)&leaf_parent, n * sizeof(int)));
-  GF_TRY(dalloc((void**)&flags, n * sizeof(int)));
-  GF_TRY(dalloc((void**)&box_sorted, n * 6 * sizeof(float)));
+  GF_TRY(F.mem.alloc((void**)&keys, n * sizeof(unsigned long long), s));
+  GF_TRY(F.mem.alloc((void**)&keys2, n * sizeof(unsigned long long), s));
+  GF_TRY(F.mem.alloc((void**)&idx, n * sizeof(int), s));
+  GF_TRY(F.mem.alloc((void**)&idx2, n * sizeof(int), s));
+  GF_TRY(F.mem.alloc((void**)&leaf_parent, n * sizeof(int), s));
+  GF_TRY(F.mem.alloc((void**)&flags, n * sizeof(int), s));
+  GF_TRY(F.mem.alloc((void**)&box_sorted, n * 6 * sizeof(float), s));
   {
     unsigned int init[12];
     for (int j = 0; j < 12; ++j) {
@@ -525,7 +524,7 @@ cudaError_t build_bvh(Field& F, cudaStream_t s) {
     GF_TRY(cudaGetLastError());
   }
   GF_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys, keys2, idx, idx2, (int)n, 0, 36, s));
-  GF_TRY(dalloc(&tmp, tmp_bytes));
+  GF_TRY(F.mem.alloc(&tmp, tmp_bytes, s));
   GF_TRY(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys, keys2, idx, idx2, (int)n, 0, 36, s));
   k_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(F.rec_orig, F.box_orig, F.ext2_orig, idx2,
                                                       n, F.rec, box_sorted, F.ext2, F.muw,
@@ -545,9 +544,10 @@ cudaError_t build_bvh(Field& F, cudaStream_t s) {
     size_t sb = 0;
     GF_TRY(cub::DeviceScan::ExclusiveSum(nullptr, sb, flags, leaf_parent, (int)m, s));
     if (sb > tmp_bytes) {
-      cudaFree(tmp);
+      GF_TRY(cudaStreamSynchronize(s));
+      F.mem.release(tmp, s);
       tmp = nullptr;
-      GF_TRY(dalloc(&tmp, sb));
+      GF_TRY(F.mem.alloc(&tmp, sb, s));
       tmp_bytes = sb;
     }
     GF_TRY(cub::DeviceScan::ExclusiveSum(tmp, sb, flags, leaf_parent, (int)m, s));
@@ -556,9 +556,9 @@ cudaError_t build_bvh(Field& F, cudaStream_t s) {
     GF_TRY(cudaMemcpyAsync(&last[1], flags + (m - 1), sizeof(int), cudaMemcpyDeviceToHost, s));
     GF_TRY(cudaStreamSynchronize(s));
     const int64_t m4 = (int64_t)last[0] + last[1];
-    if (F.nodes4) cudaFree(F.nodes4);
+    F.mem.release(F.nodes4, s);  // a rebuild (the stream was synchronised above)
     F.nodes4 = nullptr;
-    GF_TRY(dalloc((void**)&F.nodes4, (size_t)m4 * sizeof(Node4)));
+    GF_TRY(F.mem.alloc((void**)&F.nodes4, (size_t)m4 * sizeof(Node4), s));
     k_collapse4<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(F.nodes, m, flags, leaf_parent, F.nodes4);
     GF_TRY(cudaGetLastError());
   }
@@ -587,15 +587,10 @@ cudaError_t build_bvh(Field& F, cudaStream_t s) {
   F.dev.root = n >= 2 ? 0 : -1;
 done:
 #undef GF_TRY
-  cudaFree(bounds);
-  cudaFree(keys);
-  cudaFree(keys2);
-  cudaFree(idx);
-  cudaFree(idx2);
-  cudaFree(leaf_parent);
-  cudaFree(flags);
-  cudaFree(box_sorted);
-  cudaFree(tmp);
+  cudaStreamSynchronize(s);  // the temporaries are no longer read
+  for (void* t : {(void*)bounds, (void*)keys, (void*)keys2, (void*)idx, (void*)idx2,
+                  (void*)leaf_parent, (void*)flags, (void*)box_sorted, tmp})
+    F.mem.release(t, s);
   return e;
 }
 

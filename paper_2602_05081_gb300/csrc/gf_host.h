@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <unordered_map>
 
 #include "../../include/gf.h"
 #include "gf_device.cuh"
@@ -15,6 +16,43 @@ struct Ctx {
   int sm_count = 0;
   int cc_major = 0, cc_minor = 0;
   float* gl = nullptr;  // device Gauss-Legendre tables
+  gf_allocator alloc{nullptr, nullptr, nullptr};  // null alloc: cudaMalloc / cudaFree
+};
+
+// Device memory through the context's allocator (bytes == 0 allocates 16)
+cudaError_t dev_alloc(const Ctx& c, void** p, size_t bytes, cudaStream_t s);
+// Return memory that no pending work uses any more (callers synchronise first)
+void dev_free(const Ctx& c, void* p, size_t bytes, cudaStream_t s);
+
+// The device buffers of one owner (a field, a render server), each returned to
+// the allocator with the size it was asked for.
+struct DevMem {
+  Ctx ctx;
+  std::unordered_map<void*, size_t> sizes;
+  cudaError_t alloc(void** p, size_t bytes, cudaStream_t s) {
+    void* q = nullptr;
+    const cudaError_t e = dev_alloc(ctx, &q, bytes, s);
+    if (e != cudaSuccess) return e;
+    sizes[q] = bytes;
+    *p = q;
+    return cudaSuccess;
+  }
+  template <class T>
+  cudaError_t get(T** p, size_t bytes, cudaStream_t s) {
+    return alloc(reinterpret_cast<void**>(p), bytes, s);
+  }
+  // p == nullptr is allowed; the caller has synchronised the work that used p
+  void release(void* p, cudaStream_t s) {
+    if (!p) return;
+    auto it = sizes.find(p);
+    if (it == sizes.end()) return;
+    dev_free(ctx, p, it->second, s);
+    sizes.erase(it);
+  }
+  void release_all() {
+    for (auto& kv : sizes) dev_free(ctx, kv.first, kv.second, nullptr);
+    sizes.clear();
+  }
 };
 
 struct TrParams {
@@ -47,6 +85,7 @@ struct ChordParams {
 
 struct Field {
   Ctx ctx;                     // copy: a field outlives the gf_ctx it came from
+  mutable DevMem mem;          // every device buffer of the field, through ctx.alloc
   float* gl = nullptr;         // the field's own Gauss-Legendre tables
   int64_t n = 0;
   gf_field_opts opts{};
@@ -99,14 +138,16 @@ struct Field {
 
 // Render server batch (one launch of k_render_server): items of many requests
 // on several fields.  Item i covers pixels [pix0, pix0 + npix) of request
-// req and the batch's flat pixel numbers [base, base + npix); bases ascend.
+// req, every pixel split into nchunk units of chunk consecutive samples, and
+// the batch's flat unit numbers [base, base + npix * nchunk); bases ascend.
 struct ServerItem {
   int req, pix0, npix, base;
 };
 struct ServerReqDev {
   PathParams P;
-  float* fb;   // device framebuffer of the request (W x H floats)
-  int asset;   // index into ServerLaunch::fields
+  unsigned long long* acc;  // fixed-point sample sums of the request (W x H, 2^-32 units)
+  int asset;                // index into ServerLaunch::fields
+  int chunk, nchunk;        // samples per unit, units per pixel
   int pad_;
 };
 struct ServerLaunch {
@@ -114,9 +155,9 @@ struct ServerLaunch {
   int64_t max_n;           // largest primitive count over the assets
   const ServerItem* items;
   int n_items;
-  int total;               // pixels in the batch
   const ServerReqDev* reqs;
   int* counter;            // zero at launch
+  int total;               // units in the batch
 };
 
 // launchers (return cudaError_t of the launch)
@@ -140,6 +181,16 @@ size_t scatter_store_bytes(int64_t grid);
 cudaError_t server_grid(int sm_count, int64_t& grid);
 cudaError_t launch_render_server(const ServerLaunch& L, int64_t grid, float4* chord_store,
                                  cudaStream_t s);
+// image = fixed-point sums / spp
+cudaError_t launch_fix_to_image(const unsigned long long* acc, int64_t npix, int spp, float* out,
+                                cudaStream_t s);
+// scratch of the compute calls, grown through the field's allocator: the pixel sums and
+// chord store of the scattering renderer, the radiance adjoint's primitive lists
+cudaError_t ensure_render_scratch(const Field& F, int64_t npix, cudaStream_t s);
+cudaError_t ensure_adjoint_lists(const Field& F, cudaStream_t s);
+// grow a field-owned buffer to at least `bytes` (synchronises the device before
+// returning the old one)
+cudaError_t grow(const Field& F, void** p, size_t& have, size_t bytes, cudaStream_t s);
 cudaError_t launch_radiance_backward(const Field& F, const PathParams& P, const float* dLdI,
                                      float* grad, cudaStream_t s);
 cudaError_t launch_tomo_backward(const Field& F, const PathParams& P, const float* dLdI,

@@ -22,6 +22,19 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def test_header_declares_the_caller_allocator():
+    """Device memory of the library comes from a caller-supplied allocator: the
+    header declares the callback struct (alloc and free, with the stream), the
+    context constructor that takes it, and the reserve call that sizes the
+    compute calls' scratch ahead."""
+    src = open(os.path.join(ROOT, "include", "gf.h")).read()
+    assert re.search(r"void\*\s*\(\*alloc\)\(void\*\s*user,\s*size_t\s*bytes,\s*gf_stream\s*stream\)", src)
+    assert re.search(r"void\s*\(\*free\)\(void\*\s*user,\s*void\*\s*ptr,\s*size_t\s*bytes,\s*gf_stream\s*stream\)",
+                     src)
+    names = _declared()
+    assert "gf_create_ex" in names and "gf_reserve" in names
+
+
 def test_library_builds_and_exports_every_declared_symbol():
     from paper_2602_05081_gb300 import build
     lib = build.build()
@@ -84,7 +97,7 @@ def test_binding_structs_match_the_c_layout(tmp_path):
     from paper_2602_05081_gb300 import _abi
     pys = [_abi.gf_params, _abi.gf_field_opts, _abi.gf_lod_desc, _abi.gf_camera,
            _abi.gf_render_opts, _abi.gf_stats, _abi.gf_server_opts, _abi.gf_request,
-           _abi.gf_result, _abi.gf_server_stats]
+           _abi.gf_result, _abi.gf_server_stats, _abi.gf_allocator, _abi.gf_reserve_opts]
     structs = [(py.__name__, py, [f for f, _ in py._fields_]) for py in pys]
     got = _c_layout(os.path.join(ROOT, "include"), "gf.h",
                     [(c, py.__name__, fs) for c, py, fs in structs], tmp_path)
