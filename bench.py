@@ -200,19 +200,22 @@ SERVER_ASSETS = ((50_000, 4), (200_000, 4), (1_000_000, 6), (2_000_000, 6))
 def server_leg(api, ctx, n_requests, load=0.7):
     """Render server on a Poisson stream of mixed requests over 4 resident assets.
 
-    The first n_requests of the seeded request stream (resolution uniform over
+    First, per asset, one request (512x512, 16 spp, all bands) through
+    gf_render and through the server alone: Mrays/s of each.  Then the first
+    n_requests of the seeded request stream (resolution uniform over
     128^2..1024^2, spp over {1,4,16,64}, LoD over the 4 band cutoffs, random
-    cameras on a sphere) are first submitted all at once to measure the
-    saturated request rate, then replayed at load x that rate as Poisson
-    arrivals; latency = submit -> image in the caller's (pinned host) buffer.
+    cameras on a sphere) are submitted all at once to measure the saturated
+    request rate, then replayed at load x that rate as Poisson arrivals;
+    latency = submit -> image in the caller's (pinned host) buffer.
     """
+    import torch
     fields = [api.Field(ctx, synth.octave_field(n, o, seed=10 + k))
               for k, (n, o) in enumerate(SERVER_ASSETS)]
     stream = synth.request_stream(n_requests, 1.0, seed=0, lods=(0, 1, 2, 3))
-    srv = api.Server(ctx, fields, mem_budget=256 << 20, max_inflight=32, max_queue=100000)
+    srv = api.Server(ctx, fields, mem_budget=512 << 20, max_inflight=32, max_queue=100000)
     c = synth.DEFAULT_CAMERA
 
-    def submit(r):
+    def request_args(r):
         eye = r["eye"]
         d = np.subtract(c["look_at"], eye)
         up = (0.0, 1.0, 0.0) if abs(d[1]) < 0.99 * np.linalg.norm(d) else (0.0, 0.0, 1.0)
@@ -220,10 +223,64 @@ def server_leg(api, ctx, n_requests, load=0.7):
         ro = api.render_opts("scatter", r["spp"], 1, 0.8, synth.LIGHT_DIR, 1.0)
         top = SERVER_ASSETS[r["asset"]][1] - 1
         lo = api.lod("cutoff", top - r["lod"])
+        return cam, ro, lo
+
+    def submit(r):
+        cam, ro, lo = request_args(r)
         t, _ = srv.submit(r["asset"], cam, ro, lo, lo, r["seed"])
         return t
 
     try:
+        # one request per asset, alone: through gf_render and through the server
+        per_asset = {}
+        for k, (n, _) in enumerate(SERVER_ASSETS):
+            r = {"eye": (0.5, 0.5, -1.0), "res": 512, "spp": 16, "asset": k, "lod": 0, "seed": 7}
+            cam, ro, lo = request_args(r)
+            f = fields[k]
+            f.set_lod(lo, lo)
+            out = torch.empty(512, 512, device="cuda")
+            f.render(cam, ro, seed=7, out=out)
+            torch.cuda.synchronize()
+            f.stats(reset=True)
+            t0 = time.perf_counter()
+            f.render(cam, ro, seed=7, out=out)
+            torch.cuda.synchronize()
+            t_render = time.perf_counter() - t0
+            rays = f.stats(reset=True)["rays"]
+            s0 = srv.stats()
+            t0 = time.perf_counter()
+            srv.wait(submit(r))
+            t_server = time.perf_counter() - t0
+            s1 = srv.stats()
+            per_asset[str(n)] = {"gf_render_mrays_per_s": rays / t_render / 1e6,
+                                 "server_alone_mrays_per_s":
+                                     (s1["work"]["rays"] - s0["work"]["rays"]) / t_server / 1e6,
+                                 "gf_render_ms": 1e3 * t_render, "server_ms": 1e3 * t_server}
+        # the first 16 requests of the stream through gf_render one after another,
+        # and through the server queued at once
+        same = stream[:16]
+        rays_r, t_r = 0, 0.0
+        for r in same:
+            cam, ro, lo = request_args(r)
+            f = fields[r["asset"]]
+            f.set_lod(lo, lo)
+            out = torch.empty(r["res"], r["res"], device="cuda")
+            torch.cuda.synchronize()
+            f.stats(reset=True)
+            t0 = time.perf_counter()
+            f.render(cam, ro, seed=r["seed"], out=out)
+            torch.cuda.synchronize()
+            t_r += time.perf_counter() - t0
+            rays_r += f.stats(reset=True)["rays"]
+        s0 = srv.stats()
+        t0 = time.perf_counter()
+        for t in [submit(r) for r in same]:
+            srv.wait(t)
+        t_s = time.perf_counter() - t0
+        s1 = srv.stats()
+        same_requests = {"requests": len(same), "gf_render_mrays_per_s": rays_r / t_r / 1e6,
+                         "server_mrays_per_s": (s1["work"]["rays"] - s0["work"]["rays"]) / t_s / 1e6,
+                         "gf_render_s": t_r, "server_s": t_s}
         # saturated throughput: the whole sample queued at once
         s0 = srv.stats()
         t0 = time.perf_counter()
@@ -259,11 +316,14 @@ def server_leg(api, ctx, n_requests, load=0.7):
         "requests": n_requests, "sample": "first %d requests of the seeded 2000-request stream"
                                           % n_requests,
         "assets": [n for n, _ in SERVER_ASSETS], "failed": int(s2["failed"]),
+        "per_asset_512x512_16spp": per_asset,
+        "same_requests_gf_render_vs_server": same_requests,
         "saturated_requests_per_s": n_requests / sat_s,
         "saturated_mrays_per_s": (s1["work"]["rays"] - s0["work"]["rays"]) / sat_s / 1e6,
         "poisson_rate_per_s": rate, "load": load,
         "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
         "queue_wait_ms_p50": float(np.percentile(wait, 50)),
+        "queue_wait_ms_p99": float(np.percentile(wait, 99)),
         "mrays_per_s": rays / span_s / 1e6, "msamples_per_s": samples / span_s / 1e6,
         "launches": int(s2["launches"] - s1["launches"]),
         "gpu_busy_frac": (s2["busy_ms"] - s1["busy_ms"]) / (span_s * 1e3),
@@ -787,7 +847,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--server-requests", type=int, default=0,
+    ap.add_argument("--server-requests", type=int, default=100,
                     help="requests of the render-server leg (0: skip)")
     ap.add_argument("--config2", type=int, default=1,
                     help="add the single-scattering configuration as an extra key (0: skip)")

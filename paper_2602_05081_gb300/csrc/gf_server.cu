@@ -8,12 +8,16 @@
 //           the launch's sample budget (water-filling: requests that need
 //           less than the share free the rest for the others), as its next
 //           contiguous pixel range;
-//   launch  one k_render_server launch renders every range of the batch;
+//   launch  one k_render_server launch renders every range of the batch, in
+//           units of up to 8 consecutive samples of one pixel (so a 64-spp
+//           request spreads over 8 times as many lanes as pixels), summed in
+//           64-bit fixed point per pixel;
 //           two launches stay in flight on two streams, so the blocks of the
 //           next launch fill the SMs that the previous launch's tail frees;
 //   retire  when a launch's event completes, its ranges are done; a request
-//           whose last range is done has its framebuffer copied to the
-//           caller's buffer, then releases its memory and slot.
+//           whose last range is done has its sums turned into the image (sum
+//           / spp) and copied to the caller's buffer, then releases its
+//           memory and slot.
 // Requests that arrive while launches run join the next launch: the batch is
 // re-formed at every launch (iteration-level scheduling), never drained.
 #include <cuda_runtime.h>
@@ -42,6 +46,7 @@ constexpr int kBatches = 2;        // launches in flight
 constexpr size_t kHead = 1024;     // counter | error word | work counters
 constexpr size_t kErrOff = 256, kStatsOff = 512;
 constexpr int kMinRangePix = 32;
+constexpr int kUnitSamples = 8;    // samples per work unit of a lane
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -53,7 +58,8 @@ struct Req {
   int status = GF_OK;
   double t_submit = 0, t_admit = 0, t_done = 0;
   int64_t npix = 0, next_pix = 0, outstanding = 0, launches = 0;
-  size_t fb_off = 0, fb_bytes = 0;
+  size_t fb_off = 0, fb_bytes = 0;  // pool block: fixed-point sums, then the float image
+  float* fb = nullptr;
   bool copying = false;
   cudaEvent_t copy_ev = nullptr;
 };
@@ -80,6 +86,7 @@ gf_status status_of_err(int err) {
 
 struct gf_server {
   Ctx ctx;
+  DevMem mem;                   // device buffers, through the context's allocator
   std::vector<DevField> views;  // per asset, as given (host copies)
   std::vector<const Field*> fields;
   gf_server_opts opts{};
@@ -129,7 +136,9 @@ struct gf_server {
       if (!pool.alloc(r->fb_bytes, off)) break;
       queue.pop_front();
       r->fb_off = off;
-      r->dev.fb = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(pool_mem) + off);
+      unsigned char* base = reinterpret_cast<unsigned char*>(pool_mem) + off;
+      r->dev.acc = reinterpret_cast<unsigned long long*>(base);
+      r->fb = reinterpret_cast<float*>(base + align256((size_t)r->npix * 8));
       r->state = GF_REQ_RUNNING;
       r->t_admit = now_ms();
       running.push_back(r);
@@ -165,6 +174,7 @@ struct gf_server {
     ServerReqDev* rq = reinterpret_cast<ServerReqDev*>(b.host + b.reqs_off);
     int total = 0;
     b.members.clear();
+    cudaError_t e = cudaSuccess;
     for (size_t i = 0; i < n; ++i) {
       Req* r = act[i];
       const int64_t spp = r->dev.P.spp;
@@ -175,7 +185,10 @@ struct gf_server {
       items[i].pix0 = (int)r->next_pix;
       items[i].npix = (int)pix;
       items[i].base = total;
-      total += (int)pix;
+      total += (int)(pix * r->dev.nchunk);
+      // the request's sums start at zero, before its first range is rendered
+      if (r->launches == 0 && e == cudaSuccess)
+        e = cudaMemsetAsync(r->dev.acc, 0, (size_t)r->npix * 8, b.stream);
       rq[i] = r->dev;
       r->next_pix += pix;
       r->outstanding += 1;
@@ -192,7 +205,7 @@ struct gf_server {
     L.total = total;
     L.reqs = reinterpret_cast<const ServerReqDev*>(b.dev + b.reqs_off);
     L.counter = reinterpret_cast<int*>(b.dev);
-    cudaError_t e = cudaMemcpyAsync(b.dev, b.host, up, cudaMemcpyHostToDevice, b.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.dev, b.host, up, cudaMemcpyHostToDevice, b.stream);
     if (e == cudaSuccess) e = cudaEventRecord(b.start, b.stream);
     if (e == cudaSuccess) e = launch_render_server(L, std::min<int64_t>(grid, (total + 127) / 128), b.store, b.stream);
     if (e == cudaSuccess)
@@ -262,9 +275,10 @@ struct gf_server {
         continue;
       }
       if (r->next_pix < r->npix) continue;
-      // last range done: copy the image out, then release
-      cudaError_t e = cudaMemcpyAsync(r->r.out, r->dev.fb, (size_t)r->npix * 4, cudaMemcpyDefault,
-                                      copy_stream);
+      // last range done: sums -> image, copied out, then release
+      cudaError_t e = launch_fix_to_image(r->dev.acc, r->npix, r->dev.P.spp, r->fb, copy_stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(r->r.out, r->fb, (size_t)r->npix * 4, cudaMemcpyDefault, copy_stream);
       if (e == cudaSuccess) e = cudaEventRecord(r->copy_ev, copy_stream);
       if (e != cudaSuccess) {
         (void)cudaGetLastError();
@@ -348,19 +362,17 @@ gf_status fail_cuda(cudaError_t e, const char* where) {
 }
 
 void free_server(gf_server* S) {
+  cudaDeviceSynchronize();  // no launch or copy of the server is in flight
   for (Batch& b : S->batches) {
     if (b.stream) cudaStreamDestroy(b.stream);
     if (b.start) cudaEventDestroy(b.start);
     if (b.done) cudaEventDestroy(b.done);
-    if (b.host) cudaFreeHost(b.host);
-    if (b.dev) cudaFree(b.dev);
-    if (b.fields) cudaFree(b.fields);
-    if (b.store) cudaFree(b.store);
+    if (b.host) cudaFreeHost(b.host);  // pinned host mirror (host memory)
   }
   for (auto& kv : S->reqs)
     if (kv.second->copy_ev) cudaEventDestroy(kv.second->copy_ev);
   if (S->copy_stream) cudaStreamDestroy(S->copy_stream);
-  if (S->pool_mem) cudaFree(S->pool_mem);
+  S->mem.release_all();  // pool, batch buffers, field views, chord stores
   delete S;
 }
 
@@ -389,6 +401,7 @@ gf_status gf_server_create(gf_ctx* ctx, gf_field* const* fields, int n_fields,
   if (e != cudaSuccess) return fail_cuda(e, "cudaSetDevice");
   gf_server* S = new gf_server;
   S->ctx = ctx->c;
+  S->mem.ctx = ctx->c;
   S->opts = *opts;
   S->opts.mem_budget = opts->mem_budget & ~size_t(255);
   for (int i = 0; i < n_fields; ++i) {
@@ -400,8 +413,9 @@ gf_status gf_server_create(gf_ctx* ctx, gf_field* const* fields, int n_fields,
     free_server(S);
     return fail_cuda(e, "occupancy");
   }
-  if (S->opts.batch_samples == 0) S->opts.batch_samples = S->grid * 128 * 16;
-  if ((e = cudaMalloc((void**)&S->pool_mem, S->opts.mem_budget)) != cudaSuccess) {
+  // about four units of kUnitSamples samples per resident lane
+  if (S->opts.batch_samples == 0) S->opts.batch_samples = S->grid * 128 * 4 * kUnitSamples;
+  if ((e = S->mem.get(&S->pool_mem, S->opts.mem_budget, nullptr)) != cudaSuccess) {
     free_server(S);
     return fail_cuda(e, "framebuffer pool");
   }
@@ -419,9 +433,9 @@ gf_status gf_server_create(gf_ctx* ctx, gf_field* const* fields, int n_fields,
     if ((e = cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreate(&b.start)) != cudaSuccess || (e = cudaEventCreate(&b.done)) != cudaSuccess ||
         (e = cudaHostAlloc((void**)&b.host, bytes, cudaHostAllocDefault)) != cudaSuccess ||
-        (e = cudaMalloc((void**)&b.dev, bytes)) != cudaSuccess ||
-        (e = cudaMalloc((void**)&b.fields, sizeof(DevField) * n_fields)) != cudaSuccess ||
-        (e = cudaMalloc((void**)&b.store, scatter_store_bytes(S->grid))) != cudaSuccess) {
+        (e = S->mem.get(&b.dev, bytes, b.stream)) != cudaSuccess ||
+        (e = S->mem.get(&b.fields, sizeof(DevField) * n_fields, b.stream)) != cudaSuccess ||
+        (e = S->mem.get(&b.store, scatter_store_bytes(S->grid), b.stream)) != cudaSuccess) {
       free_server(S);
       return fail_cuda(e, "server buffers");
     }
@@ -458,7 +472,9 @@ gf_status gf_server_submit(gf_server* S, const gf_request* rq, uint64_t* ticket)
   r->dev.asset = rq->asset;
   r->r = *rq;
   r->npix = (int64_t)rq->camera.width * rq->camera.height;
-  r->fb_bytes = align256((size_t)r->npix * 4);
+  r->fb_bytes = align256((size_t)r->npix * 8) + align256((size_t)r->npix * 4);
+  r->dev.chunk = std::min(r->dev.P.spp, kUnitSamples);
+  r->dev.nchunk = (r->dev.P.spp + r->dev.chunk - 1) / r->dev.chunk;
   if (r->fb_bytes > S->opts.mem_budget) return report(GF_EINVAL, "framebuffer larger than the pool");
   if (r->npix > (1ll << 30)) return report(GF_EINVAL, "image too large");
   cudaError_t e = cudaSetDevice(S->ctx.device);

@@ -513,8 +513,9 @@ struct ServerWork {
   __device__ int64_t max_n() const { return L->max_n; }
   __device__ const PathParams& params(int rq) const { return L->reqs[rq].P; }
   __device__ int asset(int rq) const { return L->reqs[rq].asset; }
-  // the batch's pixels are numbered 0..total-1 item after item; a lane takes
-  // the next number and finds its item by binary search over the item bases
+  // the batch's units (chunk consecutive samples of one pixel) are numbered
+  // 0..total-1 item after item; a lane takes the next number and finds its
+  // item by binary search over the item bases
   __device__ bool next(int& rq, int& pix, int& s0, int& s1) const {
     const int f = atomicAdd(L->counter, 1);
     if (f >= L->total) return false;
@@ -526,14 +527,16 @@ struct ServerWork {
     }
     const ServerItem it = L->items[lo];
     rq = it.req;
-    pix = it.pix0 + (f - it.base);
-    s0 = L->reqs[rq].P.s0;
-    s1 = s0 + L->reqs[rq].P.spp;
+    const ServerReqDev& R = L->reqs[rq];
+    const int u = f - it.base, q = u / R.nchunk;
+    pix = it.pix0 + q;
+    s0 = R.P.s0 + (u - q * R.nchunk) * R.chunk;
+    s1 = min(s0 + R.chunk, R.P.s0 + R.P.spp);
     return true;
   }
-  // a lane renders all samples of a pixel
+  // partial sums of a pixel's samples meet in the request's fixed-point sums
   __device__ void finish(int rq, int pix, long long acc) const {
-    L->reqs[rq].fb[pix] = fix_mean(acc, L->reqs[rq].P.spp);
+    atomicAdd(L->reqs[rq].acc + pix, (unsigned long long)acc);
   }
 };
 
@@ -802,6 +805,16 @@ static cudaError_t scatter_grid(K kernel, int sm_count, int64_t pixels, int64_t&
   return cudaSuccess;
 }
 
+// pixel sums (8 bytes per pixel) and the per-warp chord store of a full
+// persistent grid, grown through the field's allocator
+cudaError_t ensure_render_scratch(const Field& F, int64_t npix, cudaStream_t s) {
+  int64_t g = 1;
+  cudaError_t e = scatter_grid(k_render_scatter, F.ctx.sm_count, (int64_t)1 << 40, g);
+  if (e != cudaSuccess) return e;
+  if ((e = grow(F, (void**)&F.acc64, F.acc_bytes, (size_t)npix * 8, s)) != cudaSuccess) return e;
+  return grow(F, (void**)&F.wscratch, F.wscratch_bytes, scatter_store_bytes(g), s);
+}
+
 cudaError_t launch_render_scatter(const Field& F, const PathParams& P, float* out, cudaStream_t s) {
   (void)cudaGetLastError();  // a stale error of an unrelated call is not ours
   cudaError_t e = cudaMemsetAsync(F.counter, 0, sizeof(int), s);
@@ -815,25 +828,9 @@ cudaError_t launch_render_scatter(const Field& F, const PathParams& P, float* ou
   chunk = chunk < 1 ? 1 : (chunk > P.spp ? P.spp : chunk);
   const int64_t nchunk = (P.spp + chunk - 1) / chunk;
   if (npix * nchunk >= (int64_t)INT_MAX) return cudaErrorInvalidValue;
-  // fixed-point pixel sums (8 bytes per pixel, grown on demand)
-  if (F.acc_bytes < (size_t)npix * 8) {
-    if (F.acc64) cudaFree(F.acc64);
-    F.acc64 = nullptr;
-    F.acc_bytes = 0;
-    if ((e = cudaMalloc((void**)&F.acc64, (size_t)npix * 8)) != cudaSuccess) return e;
-    F.acc_bytes = (size_t)npix * 8;
-  }
+  // fixed-point pixel sums and the chord store (allocated ahead by gf_reserve, else here)
+  if ((e = ensure_render_scratch(F, npix, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(F.acc64, 0, (size_t)npix * 8, s)) != cudaSuccess) return e;
-  // per-warp chord store: 32 slots x kSlotCh records of 3 float4
-  const size_t store = scatter_store_bytes(g);
-  if (F.wscratch_bytes < store) {
-    if (F.wscratch) cudaFree(F.wscratch);
-    F.wscratch = nullptr;
-    F.wscratch_bytes = 0;
-    e = cudaMalloc((void**)&F.wscratch, store);
-    if (e != cudaSuccess) return e;
-    F.wscratch_bytes = store;
-  }
   k_render_scatter<<<(unsigned)g, kWWarps * 32, scatter_smem_bytes(), s>>>(
       F.dev, P, F.acc64, F.counter, (int)chunk, F.wscratch);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -844,6 +841,12 @@ cudaError_t launch_render_scatter(const Field& F, const PathParams& P, float* ou
 cudaError_t server_grid(int sm_count, int64_t& g) {
   (void)cudaGetLastError();
   return scatter_grid(k_render_server, sm_count, (int64_t)1 << 40, g);
+}
+
+cudaError_t launch_fix_to_image(const unsigned long long* acc, int64_t npix, int spp, float* out,
+                                cudaStream_t s) {
+  k_fix_to_image<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(acc, npix, spp, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_render_server(const ServerLaunch& L, int64_t grid, float4* chord_store,

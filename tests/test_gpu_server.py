@@ -69,8 +69,11 @@ def _lod(api, d):
 
 def test_server_images_equal_alone_and_in_the_mix(api, ctx, assets):
     _, fields = assets
-    # room for three of the largest framebuffers: admission is limited by memory
-    budget = 3 * (((48 * 24 * 4) + 255) // 256 * 256)
+    # room for three of the largest framebuffers (64-bit sums and floats, 12 bytes
+    # per pixel, each part 256-byte aligned): admission is limited by memory
+    def fb(w, h):
+        return ((w * h * 8 + 255) // 256 + (w * h * 4 + 255) // 256) * 256
+    budget = 3 * fb(48, 24)
     srv = api.Server(ctx, fields, mem_budget=budget, max_inflight=8, batch_samples=1024)
     try:
         tickets = []
@@ -84,8 +87,8 @@ def test_server_images_equal_alone_and_in_the_mix(api, ctx, assets):
         srv.close()
     assert all(r["state"] == 2 and r["status"] == 0 for r in res), res
     assert st["completed"] == len(MIX) and st["failed"] == 0
-    # the first three requests fill the pool (5120 + 2304 + 4096 bytes; the
-    # fourth's 3072 would not fit), later ones join as memory frees up
+    # the first three requests fill the pool (15360 + 6912 + 12288 bytes of the
+    # 41472; the fourth's 9216 would not fit), later ones join as memory frees up
     assert 3 <= st["max_inflight_seen"] <= 8, st
     assert st["max_bytes_seen"] <= budget
     # requests were split over several launches and shared them
@@ -131,7 +134,8 @@ def test_server_request_matches_oracle(api, ctx, assets):
 def test_server_admission_queue_and_errors(api, ctx, assets):
     from paper_2602_05081_gb300 import _abi
     _, fields = assets
-    srv = api.Server(ctx, fields[:1], mem_budget=64 * 64 * 4, max_inflight=2, max_queue=3,
+    full = 64 * 64 * 12  # one 64x64 framebuffer: 64-bit sums and floats
+    srv = api.Server(ctx, fields[:1], mem_budget=full, max_inflight=2, max_queue=3,
                      batch_samples=256)
     try:
         ro = api.render_opts("scatter", 1, 1)
@@ -170,10 +174,10 @@ def test_server_admission_queue_and_errors(api, ctx, assets):
     # a field with a selection cannot be served; without it, again it can
     fields[0].set_lod_camera(_cam(api, 8, 8))
     with pytest.raises(_abi.GfError) as e:
-        api.Server(ctx, fields[:1], mem_budget=64 * 64 * 4)
+        api.Server(ctx, fields[:1], mem_budget=full)
     assert e.value.status == _abi.GF_ESTATE
     fields[0].set_lod_camera(None)
-    api.Server(ctx, fields[:1], mem_budget=64 * 64 * 4).close()
+    api.Server(ctx, fields[:1], mem_budget=full).close()
     # admissions are in arrival order: each admitted after the previous finished
     for a, b in zip(res, res[1:]):
         assert b["t_admit_ms"] >= a["t_done_ms"] - 1e-3
