@@ -1329,12 +1329,19 @@ static void add_dkappa(const or_field* f, const or_gprim* G, const or_hit* h, in
   }
 }
 
+static double path_grad_sample(const or_field* f, const or_gprim* G, const or_lod* lod,
+                               const or_lod* lodn, const or_render_opts* ro, const double o0[3],
+                               const double v0[3], uint64_t seed, uint32_t ray, uint32_t s,
+                               double dLdI, double* g15);
+
 /* one sample of the estimator along o + t v; adds dLdI * d sample/d theta
-   to g15 and returns the sample */
+   to g15 and returns the sample (max_bounces >= 2: path_grad_sample) */
 static double radiance_grad_sample(const or_field* f, const or_gprim* G, const or_lod* lod,
                                    const or_lod* lodn, const or_render_opts* ro,
                                    const double o[3], const double v[3], uint64_t seed,
                                    uint32_t ray, uint32_t s, double dLdI, double* g15) {
+  if (ro->max_bounces >= 2)
+    return path_grad_sample(f, G, lod, lodn, ro, o, v, seed, ray, s, dLdI, g15);
   double l[3] = {ro->light_dir[0], ro->light_dir[1], ro->light_dir[2]};
   normalise(l, l);
   uint64_t mask;
@@ -1418,6 +1425,127 @@ static double radiance_grad_sample(const or_field* f, const or_gprim* G, const o
   free(pt);
   free(h);
   return value;
+}
+
+/* ------------------------------------------------------------------------ */
+/* multiple-scattering radiance adjoint (max_bounces >= 2)                   */
+/*                                                                            */
+/* A path of delta tracking (Sec. 3) chooses, on segment b, the collision at */
+/* its first accepted tentative point js_b (probability                      */
+/* P_b = prod_{i<js} (1 - p_i) p_js, p = max(kappa,0)/kappa_bar), or escapes */
+/* (prod over all points of 1 - p_i).  At the collision x_{b+1}: throughput  */
+/* thr_b = albedo^(b+1), NEE by ratio tracking T_b = prod_k (1 - q_k), so    */
+/* the sample is L = sum_b C_b, C_b = thr_b E/(4 pi) T_b.  C_b depends on the */
+/* segments 0..b and on NEE b.  With the tentative points and kappa_bar held */
+/* fixed (as for single scattering), the derivative of the expected sample  */
+/* is the expectation of                                                    */
+/*   sum_b S_b d log P_b + sum_b C_b d log T_b,   S_b = sum_{b' >= b} C_b',   */
+/*   d log P_b = sum_{i<js} -dp_i/(1 - p_i) + dp_js/p_js,                    */
+/*   d T_b     = -sum_k dq_k prod_{m != k} (1 - q_m),                        */
+/* dp = 1[kappa > 0] d kappa / kappa_bar; an escaping segment has S = 0.     */
+/* The path, its masks, points and decisions are those of path_sample.       */
+/* ------------------------------------------------------------------------ */
+#define OR_MAX_SEG 16
+static double path_grad_sample(const or_field* f, const or_gprim* G, const or_lod* lod,
+                               const or_lod* lodn, const or_render_opts* ro, const double o0[3],
+                               const double v0[3], uint64_t seed, uint32_t ray, uint32_t s,
+                               double dLdI, double* g15) {
+  double l[3] = {ro->light_dir[0], ro->light_dir[1], ro->light_dir[2]};
+  normalise(l, l);
+  const double E0 = ro->light_irradiance / (4.0 * OR_PI);
+  double o[3] = {o0[0], o0[1], o0[2]}, v[3] = {v0[0], v0[1], v0[2]};
+  /* per collision segment: its ray, accepted point, NEE origin and C_b, thr_b */
+  double so[OR_MAX_SEG][3], sv[OR_MAX_SEG][3], sx[OR_MAX_SEG][3], C[OR_MAX_SEG], thrs[OR_MAX_SEG];
+  int js[OR_MAX_SEG];
+  int nseg = 0;
+  double thr = 1.0, L = 0.0;
+  for (int b = 0; b < ro->max_bounces && b < OR_MAX_SEG; ++b) {
+    uint64_t mask;
+    double w64[OR_MAX_CELLS];
+    or_sample_mask(f, lod, v, seed, ray, s, (uint32_t)b, OR_TAG_MASK, &mask, w64);
+    or_hit* h;
+    int nh;
+    or_rpt* pt;
+    int np = ray_points(f, o, v, mask, w64, seed, ray, stream_word(s, (uint32_t)b, OR_TAG_TRACK),
+                        &h, &nh, &pt);
+    int acc = -1;
+    for (int j = 0; j < np && acc < 0; ++j) {
+      double kp = pt[j].kap > 0 ? pt[j].kap : 0.0;
+      if (pt[j].ua * pt[j].kb < kp) acc = j;
+    }
+    double th = acc >= 0 ? pt[acc].t : 0.0;
+    free(pt);
+    free(h);
+    if (acc < 0) break; /* escapes: no contribution depends on this segment */
+    double x[3] = {o[0] + th * v[0], o[1] + th * v[1], o[2] + th * v[2]};
+    thr *= ro->albedo;
+    uint64_t nmask;
+    double nw[OR_MAX_CELLS];
+    or_sample_mask(f, lodn, l, seed, ray, s, (uint32_t)b, OR_TAG_NEE_MASK, &nmask, nw);
+    double Tl = ratio_track(f, x, l, 0.0, INFINITY, nmask, nw, seed, ray,
+                            stream_word(s, (uint32_t)b, OR_TAG_NEE), 1);
+    for (int k = 0; k < 3; ++k) {
+      so[nseg][k] = o[k];
+      sv[nseg][k] = v[k];
+      sx[nseg][k] = x[k];
+    }
+    js[nseg] = acc;
+    thrs[nseg] = thr;
+    C[nseg] = thr * E0 * Tl;
+    L += C[nseg];
+    ++nseg;
+    uint32_t y[4];
+    rng4(seed, 0, OR_NO_PRIM, ray, stream_word(s, (uint32_t)b, OR_TAG_SCATTER), y);
+    double z = 1.0 - 2.0 * u01(y[0]);
+    double rr = sqrt(fmax(0.0, 1.0 - z * z));
+    double ph = 2.0 * OR_PI * u01(y[1]);
+    v[0] = rr * cos(ph); v[1] = rr * sin(ph); v[2] = z;
+    for (int k = 0; k < 3; ++k) o[k] = x[k];
+  }
+  if (dLdI == 0.0 || nseg == 0) return L;
+  double S = 0.0;
+  for (int b = nseg - 1; b >= 0; --b) {
+    S += C[b];
+    /* segment b: the tracking points up to the accepted one */
+    uint64_t mask;
+    double w64[OR_MAX_CELLS];
+    or_sample_mask(f, lod, sv[b], seed, ray, s, (uint32_t)b, OR_TAG_MASK, &mask, w64);
+    or_hit* h;
+    int nh;
+    or_rpt* pt;
+    ray_points(f, so[b], sv[b], mask, w64, seed, ray, stream_word(s, (uint32_t)b, OR_TAG_TRACK), &h,
+               &nh, &pt);
+    for (int i = 0; i <= js[b]; ++i) {
+      if (!(pt[i].kap > 0) || !(pt[i].kb > 0)) continue;
+      const double p = pt[i].kap / pt[i].kb;
+      const double coef = i == js[b] ? S / p : -S / (1.0 - p);
+      add_dkappa(f, G, h, nh, so[b], sv[b], pt[i].t, dLdI * coef / pt[i].kb, g15);
+    }
+    free(pt);
+    free(h);
+    /* NEE b: d C_b = -thr_b E0 sum_k dq_k prod_{m != k} (1 - q_m) */
+    uint64_t nmask;
+    double nw[OR_MAX_CELLS];
+    or_sample_mask(f, lodn, l, seed, ray, s, (uint32_t)b, OR_TAG_NEE_MASK, &nmask, nw);
+    or_hit* hl;
+    int nhl;
+    or_rpt* ql;
+    int nq = ray_points(f, sx[b], l, nmask, nw, seed, ray, stream_word(s, (uint32_t)b, OR_TAG_NEE),
+                        &hl, &nhl, &ql);
+    for (int k = 0; k < nq; ++k) {
+      if (!(ql[k].kap > 0) || !(ql[k].kb > 0)) continue;
+      double pr = 1.0;
+      for (int m = 0; m < nq; ++m) {
+        if (m == k) continue;
+        double kp = ql[m].kap > 0 ? ql[m].kap : 0.0;
+        if (ql[m].kb > 0) pr *= 1.0 - kp / ql[m].kb;
+      }
+      add_dkappa(f, G, hl, nhl, sx[b], l, ql[k].t, -dLdI * thrs[b] * E0 * pr / ql[k].kb, g15);
+    }
+    free(ql);
+    free(hl);
+  }
+  return L;
 }
 
 static void soa_grad(const double* g15, int64_t N, double* grad) {

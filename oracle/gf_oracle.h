@@ -21,7 +21,9 @@
  * second-bounce radiance of a pixel on one Gaussian equals the nested
  * quadrature of the path integral (collision on the camera ray, isotropic
  * direction, collision on the second leg, NEE), with closed-form
- * transmittances; later bounces repeat the same loop step.
+ * transmittances; later bounces repeat the same loop step.  Its adjoint is
+ * pinned the same way: the two-bounce gradient equals the central finite
+ * differences of that quadrature.
  */
 #ifndef GF_ORACLE_H
 #define GF_ORACLE_H
@@ -178,13 +180,15 @@ void or_camera_ray(const or_camera* cam, uint64_t seed, int px, int py, int s, d
 double or_tomo_loss_grad(const or_field_desc* desc, const or_camera* cam, int spp, uint64_t seed,
                          const float* target, double* grad, int n_threads);
 /* tomography image only (same estimator, deterministic quadrature, all cells) */
-/* single-scattering radiance adjoint: expected-value estimator over all
-   tentative points of the ray, one NEE point drawn in proportion to its
-   weight; derivatives with the points, the majorant and the draw
-   probabilities held fixed (see the .c file).  Per ray (or pixel) the mean
-   of spp samples goes to value/image; grad (15 N, SoA as the inputs)
-   receives sum dLdI[r] / spp * d sample / d theta.  ro->max_bounces must be
-   1.  Rays: o, v double[3 n]. */
+/* radiance adjoint.  max_bounces 1 (single scattering): expected-value
+   estimator over all tentative points of the ray, one NEE point drawn in
+   proportion to its weight.  max_bounces >= 2: the delta-tracking path of
+   the renderer (same streams and decisions), differentiated through the
+   probability of each segment's accepted point and each NEE product.  Both
+   hold the points, the majorant and the draw probabilities fixed (see the
+   .c file).  Per ray (or pixel) the mean of spp samples goes to value/image;
+   grad (15 N, SoA as the inputs) receives sum dLdI[r] / spp * d sample /
+   d theta.  Rays: o, v double[3 n]. */
 void or_radiance_grad_rays(const or_field_desc* desc, const or_lod* lod, const or_lod* lod_nee,
                            const or_render_opts* ro, const double* o, const double* v,
                            int64_t n_rays, int spp, uint64_t seed, const double* dLdI,
