@@ -250,7 +250,8 @@ class TomoRender(torch.autograd.Function):
 
 
 class RadianceRender(torch.autograd.Function):
-    """I = single-scattering image of the field given by the parameter tensors.
+    """I = scattering image (max_bounces collisions per path, 1 = single
+    scattering) of the field given by the parameter tensors.
 
     Forward packs the field and renders with delta tracking (seed); backward runs
     the radiance adjoint kernel with its own seed (grad_seed), so the image and
@@ -260,12 +261,13 @@ class RadianceRender(torch.autograd.Function):
     @staticmethod
     def forward(ctx_, mu, quat, log_scale, omega, phase, weight, gctx, cam, spp, seed, grad_seed,
                 lod_primary, lod_nee, omega_frame, weight_mode, k_sigma, albedo=0.8,
-                light_dir=(1.0, 1.0, -1.0)):
+                light_dir=(1.0, 1.0, -1.0), max_bounces=1):
         params = {"mu": mu, "quat": quat, "log_scale": log_scale, "omega": omega, "phase": phase,
                   "weight": weight}
         f = Field(gctx, params, omega_frame=omega_frame, weight_mode=weight_mode, k_sigma=k_sigma)
         f.set_lod(lod_primary, lod_nee)
-        opts = render_opts("scatter", spp=spp, max_bounces=1, albedo=albedo, light_dir=light_dir)
+        opts = render_opts("scatter", spp=spp, max_bounces=max_bounces, albedo=albedo,
+                           light_dir=light_dir)
         img = f.render(cam, opts, seed)
         ctx_.field = f
         ctx_.cam, ctx_.opts, ctx_.grad_seed = cam, opts, grad_seed
@@ -278,7 +280,7 @@ class RadianceRender(torch.autograd.Function):
         parts = split_grad(g, f.n)
         f.free()
         return (parts["mu"], parts["quat"], parts["log_scale"], parts["omega"], parts["phase"],
-                parts["weight"]) + (None,) * 12
+                parts["weight"]) + (None,) * 13
 
 
 class Server:

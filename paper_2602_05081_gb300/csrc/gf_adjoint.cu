@@ -492,6 +492,149 @@ struct RadSmem {
   float env[8];
 };
 
+// ---------------------------------------------------------------------------
+// Adjoint of the multiple-scattering radiance (max_bounces >= 2).
+//
+// The delta-tracking path: segment b accepts its first tentative point js_b
+// (probability P_b = prod_{i<js} (1 - p_i) p_js) or escapes; the collision
+// x_{b+1} adds C_b = thr_b E0 T_b with thr_b = albedo^(b+1), E0 = E/(4 pi) and
+// T_b the ratio-tracked NEE product prod_k (1 - q_k).  C_b depends on the
+// segments 0..b and on NEE b, so with the points and majorants held fixed
+//   d E[L] = E[ sum_b S_b d log P_b + sum_b C_b d log T_b ],  S_b = sum_{b'>=b} C_b',
+//   d log P_b = sum_{i<js} -dp_i / (1 - p_i) + dp_js / p_js,
+//   C_b d log T_b = -thr_b E0 sum_k dq_k T_b / (1 - q_k),
+// dp = 1[kappa > 0] d kappa / kappa_bar.  Pass 1 follows the path (the
+// renderer's streams and decisions) and keeps only T_b per collision; pass 2
+// follows it again, scattering each segment's points up to the accepted one
+// and each NEE ray's points with those coefficients.  Nothing per tentative
+// point or per segment ray is stored.
+// ---------------------------------------------------------------------------
+constexpr int kMaxSeg = 15;
+
+// one segment of the path from (o, v): delta tracking to the first accepted
+// point (returns false on escape, else t); with coefficients (S != 0), the
+// points up to the accepted one are scattered, -S/(1 - p) before it, S/p at it
+__device__ __forceinline__ bool path_segment(const DevField& F, const PathParams& P,
+                                             const BackArgs& Bk, float3 o, float3 v,
+                                             uint32_t pix, uint32_t s, int b, float S,
+                                             const float* env, Counters& cnt, RayList& L,
+                                             float& th) {
+  const Mask M = sample_mask_impl<true>(F, P.lod, v, P.seed, pix, s, (uint32_t)b, TAG_MASK);
+  const uint32_t wt = stream_word(s, (uint32_t)b, TAG_TRACK);
+  gather_list(F, M, o, v, L, cnt);
+  bool hit = false;
+  for_windows(F, M, o, v, P.seed, pix, wt, env, cnt, &L,
+              [&](const PointBuf& B, int n, const float* kap, const float* kb) {
+                float coef[kPts];
+                int acc = -1;
+#pragma unroll
+                for (int i = 0; i < kPts; ++i) {
+                  coef[i] = 0.f;
+                  if (i < n && acc < 0) {
+                    const bool take = B.u[i] * kb[i] < fmaxf(kap[i], 0.f);
+                    if (S != 0.f && kap[i] > 0.f && kb[i] > 0.f) {
+                      const float p = kap[i] / kb[i];
+                      coef[i] = (take ? S / p : -S / (1.f - p)) / kb[i];
+                    }
+                    if (take) acc = i;
+                  }
+                }
+                if (S != 0.f) scatter_window(F, Bk, M, o, v, B, coef, n, &L, cnt);
+                if (acc >= 0) {
+                  hit = true;
+                  th = B.t[acc];
+                  return false;
+                }
+                return true;
+              });
+  return hit;
+}
+
+// NEE ray of collision b from x: returns T = prod (1 - q_k); with cn != 0 the
+// points are scattered with cn / (1 - q_k) / kappa_bar_k
+__device__ __forceinline__ float path_nee(const DevField& F, const PathParams& P,
+                                          const BackArgs& Bk, float3 x, uint32_t pix,
+                                          uint32_t s, int b, float cn, const float* env,
+                                          Counters& cnt, RayList& L) {
+  const Mask Mn = sample_mask_impl<true>(F, P.lod_nee, P.light, P.seed, pix, s, (uint32_t)b,
+                                         TAG_NEE_MASK);
+  const uint32_t wn = stream_word(s, (uint32_t)b, TAG_NEE);
+  gather_list(F, Mn, x, P.light, L, cnt);
+  float Tl = 1.f;
+  for_windows(F, Mn, x, P.light, P.seed, pix, wn, env, cnt, &L,
+              [&](const PointBuf& B, int n, const float* kap, const float* kb) {
+                float coef[kPts];
+#pragma unroll
+                for (int i = 0; i < kPts; ++i) {
+                  coef[i] = 0.f;
+                  if (i < n && kb[i] > 0.f) {
+                    const float q = fmaxf(kap[i], 0.f) / kb[i];
+                    Tl *= 1.f - q;
+                    if (cn != 0.f && kap[i] > 0.f && 1.f - q > 0.f) coef[i] = cn / (1.f - q) / kb[i];
+                  }
+                }
+                if (cn != 0.f) scatter_window(F, Bk, Mn, x, P.light, B, coef, n, &L, cnt);
+                return true;
+              });
+  return Tl;
+}
+
+__device__ __forceinline__ float3 path_scatter_dir(const PathParams& P, uint32_t pix, uint32_t s,
+                                                   int b) {
+  const uint4 y = rng4(P.seed, 0, kNoPrim, pix, stream_word(s, (uint32_t)b, TAG_SCATTER));
+  const float z = 1.0f - 2.0f * u01(y.x);
+  const float rr = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+  float sn, cs;
+  sincosf(2.0f * 3.14159265358979f * u01(y.y), &sn, &cs);
+  return make_float3(rr * cs, rr * sn, z);
+}
+
+__device__ void path_backward(const DevField& F, const PathParams& P, const BackArgs& Bk,
+                              float3 o0, float3 v0, uint32_t pix, uint32_t s, float base,
+                              const float* env, Counters& cnt, RayList& Lc, RayList& Ln) {
+  const float E0 = P.irradiance * (0.25f / 3.14159265358979f);
+  float Tb[kMaxSeg];
+  int nseg = 0;
+  // pass 1: the path, its NEE products
+  {
+    float3 o = o0, v = v0;
+    for (int b = 0; b < P.max_bounces && b < kMaxSeg; ++b) {
+      float th = 0.f;
+      cnt.rays += 1;
+      if (!path_segment(F, P, Bk, o, v, pix, s, b, 0.f, env, cnt, Lc, th)) break;
+      const float3 x = make_float3(fmaf(th, v.x, o.x), fmaf(th, v.y, o.y), fmaf(th, v.z, o.z));
+      cnt.rays += 1;
+      Tb[nseg++] = path_nee(F, P, Bk, x, pix, s, b, 0.f, env, cnt, Ln);
+      o = x;
+      v = path_scatter_dir(P, pix, s, b);
+    }
+  }
+  if (nseg == 0) return;
+  // S_b = sum_{b' >= b} C_b', C_b = albedo^(b+1) E0 T_b
+  float Ssuf = 0.f, thr = 1.f;
+  for (int b = 0; b < nseg; ++b) {
+    thr *= P.albedo;
+    Ssuf += thr * E0 * Tb[b];
+  }
+  // pass 2: the same path again, scattering the coefficients
+  float3 o = o0, v = v0;
+  thr = 1.f;
+  for (int b = 0; b < nseg; ++b) {
+    float th = 0.f;
+    if (!path_segment(F, P, Bk, o, v, pix, s, b, base * Ssuf, env, cnt, Lc, th)) break;
+    const float3 x = make_float3(fmaf(th, v.x, o.x), fmaf(th, v.y, o.y), fmaf(th, v.z, o.z));
+    thr *= P.albedo;
+    const float Cb = thr * E0 * Tb[b];
+    if (Tb[b] > 0.f) (void)path_nee(F, P, Bk, x, pix, s, b, -base * Cb, env, cnt, Ln);
+    Ssuf -= Cb;
+    o = x;
+    v = path_scatter_dir(P, pix, s, b);
+  }
+}
+
+// PATH = false: single scattering (the expected-value estimator above);
+// PATH = true: multiple scattering (path_backward), each with its own frame
+template <bool PATH>
 __global__ void __launch_bounds__(kBackBlock)
     k_radiance_backward(const __grid_constant__ DevField F, const PathParams P, const BackArgs Bk,
                         const float* dLdI, int* counter, int* lists) {
@@ -520,6 +663,10 @@ __global__ void __launch_bounds__(kBackBlock)
     for (int s = P.s0; s < P.s0 + P.spp; ++s) {
       float3 o, v;
       camera_ray(P.cam, P.seed, px, py, s, o, v);
+      if constexpr (PATH) {
+        path_backward(F, P, Bk, o, v, pix, (uint32_t)s, base, sm.env, cnt, Lc, Ln);
+        continue;
+      }
       cnt.rays += 1;
       const Mask M = sample_mask_impl<true>(F, P.lod, v, P.seed, pix, (uint32_t)s, 0, TAG_MASK);
       const uint32_t wt = stream_word((uint32_t)s, 0, TAG_TRACK);
@@ -617,9 +764,12 @@ static BackArgs back_args(const Field& F, float* grad) {
 // persistent grid), grown through the field's allocator
 cudaError_t ensure_adjoint_lists(const Field& F, cudaStream_t s) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_radiance_backward, kBackBlock, 0) !=
-      cudaSuccess)
-    (void)cudaGetLastError();
+  for (auto k : {k_radiance_backward<false>, k_radiance_backward<true>}) {
+    int q = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k, kBackBlock, 0) != cudaSuccess)
+      (void)cudaGetLastError();
+    per_sm = q > per_sm ? q : per_sm;
+  }
   if (per_sm < 1) per_sm = 1;
   const int64_t threads = (int64_t)F.ctx.sm_count * per_sm * kBackBlock;
   return grow(F, (void**)&F.rlist, F.rlist_bytes, (size_t)threads * 2 * kRayList * sizeof(int), s);
@@ -631,9 +781,15 @@ cudaError_t launch_radiance_backward(const Field& F, const PathParams& P, const 
   cudaError_t e = cudaMemsetAsync(F.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   const BackArgs B = back_args(F, grad);
+  auto kernel = P.max_bounces >= 2 ? k_radiance_backward<true> : k_radiance_backward<false>;
+  // the kernel's local frame must fit the context's stack limit as it stands
+  cudaFuncAttributes fa;
+  size_t limit = 0;
+  if ((e = cudaFuncGetAttributes(&fa, kernel)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetLimit(&limit, cudaLimitStackSize)) != cudaSuccess) return e;
+  if (fa.localSizeBytes > limit) return cudaErrorLaunchOutOfResources;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_radiance_backward, kBackBlock, 0) !=
-      cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBackBlock, 0) != cudaSuccess)
     (void)cudaGetLastError();
   if (per_sm < 1) per_sm = 1;
   const int64_t tiles = (int64_t)((P.cam.W + 7) / 8) * ((P.cam.H + 3) / 4);
@@ -643,7 +799,7 @@ cudaError_t launch_radiance_backward(const Field& F, const PathParams& P, const 
   if (g < 1) g = 1;
   // lists sized for a full grid (allocated ahead by gf_reserve, else here)
   if ((e = ensure_adjoint_lists(F, s)) != cudaSuccess) return e;
-  k_radiance_backward<<<(unsigned)g, kBackBlock, 0, s>>>(F.dev, P, B, dLdI, F.counter, F.rlist);
+  kernel<<<(unsigned)g, kBackBlock, 0, s>>>(F.dev, P, B, dLdI, F.counter, F.rlist);
   return cudaGetLastError();
 }
 

@@ -645,8 +645,8 @@ gf_status gf_render_backward(gf_field* h, const gf_camera* camera, const gf_rend
   gf_status st = camera_params(camera, opts, seed, F, P);
   if (st) return st;
   if (P.free_flight != GF_FLIGHT_DELTA) return fail(GF_EINVAL, "the adjoint differentiates GF_FLIGHT_DELTA");
-  if (opts->integrator == GF_INTEG_SCATTER && opts->max_bounces != 1)
-    return fail(GF_EINVAL, "the radiance adjoint covers single scattering (max_bounces 1)");
+  if (opts->integrator == GF_INTEG_SCATTER && opts->max_bounces < 1)
+    return fail(GF_EINVAL, "the radiance adjoint needs max_bounces >= 1");
   if (F.opts.precision != GF_PREC_FP32)
     return fail(GF_EINVAL, "the adjoint needs FP32 records");
   GF_CUDA(cudaSetDevice(F.ctx.device), "cudaSetDevice");
