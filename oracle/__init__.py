@@ -62,7 +62,9 @@ class Camera(C.Structure):
 class RenderOpts(C.Structure):
     _fields_ = [("integrator", C.c_int), ("spp", C.c_int), ("max_bounces", C.c_int),
                 ("albedo", C.c_float), ("light_dir", C.c_float * 3),
-                ("light_irradiance", C.c_float), ("free_flight", C.c_int)]
+                ("light_irradiance", C.c_float), ("free_flight", C.c_int),
+                ("foveation", C.c_int), ("gaze", C.c_float * 2), ("fov_f0", C.c_float),
+                ("fov_slope", C.c_float), ("fov_smooth", C.c_float)]
 
 
 def _load():
@@ -97,6 +99,8 @@ def _load():
                                          vp, i32]
         lib.or_cdf_flight.restype = i32
         lib.or_cdf_flight.argtypes = [vp, vp, vp, dbl, dbl, u64, vp, u64, u32, u32, vp]
+        lib.or_segment_flight.restype = i32
+        lib.or_segment_flight.argtypes = [vp, vp, vp, dbl, dbl, u64, vp, u64, u32, u32, vp]
         lib.or_delta_track.restype = i32
         lib.or_delta_track.argtypes = [vp, vp, vp, dbl, dbl, u64, vp, u64, u32, u32, vp]
         lib.or_render.argtypes = [vp, C.POINTER(Lod), C.POINTER(Lod), C.POINTER(Camera),
@@ -243,6 +247,16 @@ class Field:
                                      int(seed), int(ray), int(word), _ptr(t))
         return bool(hit), float(t[0])
 
+    def segment_flight(self, o, v, seed, ray, word, tmin=0.0, tmax=np.inf, mask=(1 << 64) - 1,
+                       w64=None):
+        """Free flight by uniform sampling within the crossing segment."""
+        t = np.zeros(1)
+        hit = self.lib.or_segment_flight(self.h, _ptr(_f64(o)), _ptr(_f64(v)), float(tmin),
+                                         float(tmax), int(mask),
+                                         None if w64 is None else _ptr(_f64(w64)), int(seed),
+                                         int(ray), int(word), _ptr(t))
+        return bool(hit), float(t[0])
+
     def delta_track(self, o, v, seed, ray, word, tmin=0.0, tmax=np.inf, mask=(1 << 64) - 1,
                     w64=None):
         t = np.zeros(1)
@@ -332,10 +346,14 @@ def camera_ray(cam, seed, px, py, s):
 
 
 def render_opts(integrator="scatter", spp=1, max_bounces=1, albedo=0.8,
-                light_dir=(1.0, 1.0, -1.0), light_irradiance=1.0, free_flight="delta"):
+                light_dir=(1.0, 1.0, -1.0), light_irradiance=1.0, free_flight="delta",
+                foveation=None):
+    fv = foveation or {}
     return RenderOpts(0 if integrator == "tomo" else 1, int(spp), int(max_bounces), float(albedo),
                       (C.c_float * 3)(*light_dir), float(light_irradiance),
-                      {"delta": 0, "cdf": 1}[free_flight])
+                      {"delta": 0, "cdf": 1, "segment": 2}[free_flight], 1 if foveation else 0,
+                      (C.c_float * 2)(*fv.get("gaze", (0.0, 0.0))), float(fv.get("f0", 0.0)),
+                      float(fv.get("slope", 0.0)), float(fv.get("smooth", 0.0)))
 
 
 def rays_traced(reset=False):

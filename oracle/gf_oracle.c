@@ -86,6 +86,7 @@ struct or_field {
   uint64_t occupied;
   double kbar[OR_MAX_CELLS];
   double axes[OR_N_CONES][3];
+  double band_wmax[8]; /* largest world carrier |omega| per band (foveation) */
 };
 
 int64_t or_field_size(const or_field* f) { return f->n; }
@@ -231,6 +232,8 @@ or_field* or_field_create(const or_field_desc* D) {
       P->k = e2 <= 0 ? 0.0 : fmin(D->k_sigma, sqrt(e2));
     }
     P->k_own = P->k;
+    double wn = sqrt(P->omega[0] * P->omega[0] + P->omega[1] * P->omega[1] + P->omega[2] * P->omega[2]);
+    if (wn > f->band_wmax[P->band]) f->band_wmax[P->band] = wn;
   }
   for (int c = 0; c < OR_MAX_CELLS; ++c) f->kbar[c] = kcnt[c] > 0 ? ksum[c] / kcnt[c] : 0.0;
   return f;
@@ -851,6 +854,52 @@ int or_cdf_flight(const or_field* f, const double o[3], const double v_in[3], do
   return 1;
 }
 
+/* Free flight by uniform sampling within the crossing segment (Sec. 3,
+   segment-based transfer: uniform sampling within segments as the cheap
+   approximation of the CDF inversion; Sec. 4.4 distance sampling).  The ray is
+   cut into segments at tmin and at every chord entry and exit; with xi the
+   first uniform of the segment's tracking stream and target -ln(1 - xi), the
+   crossing segment [e_{k-1}, e_k] is the first whose end reaches
+   tau(tmin, e_k) >= target, and the collision is e_{k-1} + u (e_k - e_{k-1})
+   with u the stream's second uniform.  Returns 0 when the ray's whole optical
+   depth stays below the target. */
+static int cmp_dbl(const void* A, const void* B) {
+  double a = *(const double*)A, b = *(const double*)B;
+  return (a > b) - (a < b);
+}
+
+int or_segment_flight(const or_field* f, const double o[3], const double v_in[3], double tmin,
+                      double tmax, uint64_t mask, const double* w64, uint64_t seed, uint32_t ray,
+                      uint32_t word, double* t_hit) {
+  gl_init();
+  double v[3];
+  normalise(v_in, v);
+  uint32_t x[4];
+  rng4(seed, 0, OR_NO_PRIM, ray, word, x);
+  const double target = -log(1.0 - u01(x[0]));
+  or_hit* h;
+  int nh = collect_hits(f, o, v, tmin, tmax, mask, w64, &h);
+  double* ev = (double*)malloc(sizeof(double) * (size_t)(2 * nh + 1));
+  int ne = 0;
+  ev[ne++] = tmin;
+  for (int j = 0; j < nh; ++j) {
+    ev[ne++] = h[j].c.lo;
+    ev[ne++] = h[j].c.hi;
+  }
+  free(h);
+  qsort(ev, (size_t)ne, sizeof(double), cmp_dbl);
+  int hit = 0;
+  for (int k = 1; k < ne && !hit; ++k) {
+    if (!(ev[k] > ev[k - 1])) continue;
+    if (det_tau(f, o, v, tmin, ev[k], mask, w64) >= target) {
+      *t_hit = ev[k - 1] + u01(x[1]) * (ev[k] - ev[k - 1]);
+      hit = 1;
+    }
+  }
+  free(ev);
+  return hit;
+}
+
 static int nthreads_of(int n) {
 #ifdef _OPENMP
   return n > 0 ? n : omp_get_max_threads();
@@ -946,16 +995,58 @@ static void count_ray(void) {
   g_rays += 1;
 }
 
+/* Foveation (Supp., Foveated Rendering): the cells a sample's path keeps.  The
+   frequency threshold falls linearly with the eccentricity e of the camera ray
+   v (its angle to the ray through the gaze point), f = max(0, f0 - slope e),
+   perturbed per sample by the third uniform of the camera stream (stochastic
+   smoothing); Gabor bands whose largest carrier exceeds f leave, the Gaussian
+   band stays. */
+static uint64_t fov_cells(const or_field* f, const or_camera* C, const or_render_opts* ro,
+                          const double v[3], uint64_t seed, uint32_t pix, uint32_t s) {
+  if (!ro->foveation) return ~0ull;
+  double eye[3] = {C->eye[0], C->eye[1], C->eye[2]};
+  double fw[3] = {C->look_at[0] - eye[0], C->look_at[1] - eye[1], C->look_at[2] - eye[2]};
+  normalise(fw, fw);
+  double up[3] = {C->up[0], C->up[1], C->up[2]};
+  double rt[3] = {up[1] * fw[2] - up[2] * fw[1], up[2] * fw[0] - up[0] * fw[2],
+                  up[0] * fw[1] - up[1] * fw[0]};
+  normalise(rt, rt);
+  double uv[3] = {fw[1] * rt[2] - fw[2] * rt[1], fw[2] * rt[0] - fw[0] * rt[2],
+                  fw[0] * rt[1] - fw[1] * rt[0]};
+  double th = tan(0.5 * (double)C->vfov_deg * OR_PI / 180.0);
+  double asp = (double)C->width / (double)C->height;
+  double sx = (2.0 * ro->gaze[0] / C->width - 1.0) * th * asp;
+  double sy = (1.0 - 2.0 * ro->gaze[1] / C->height) * th;
+  double g[3] = {fw[0] + sx * rt[0] + sy * uv[0], fw[1] + sx * rt[1] + sy * uv[1],
+                 fw[2] + sx * rt[2] + sy * uv[2]};
+  normalise(g, g);
+  double c = v[0] * g[0] + v[1] * g[1] + v[2] * g[2];
+  c = c > 1.0 ? 1.0 : (c < -1.0 ? -1.0 : c);
+  double thr = ro->fov_f0 - ro->fov_slope * acos(c);
+  if (thr < 0) thr = 0;
+  if (ro->fov_smooth > 0) {
+    uint32_t x[4];
+    rng4(seed, 0, OR_NO_PRIM, pix, stream_word(s, 0, OR_TAG_CAMERA), x);
+    thr *= 1.0 + ro->fov_smooth * (2.0 * u01(x[2]) - 1.0);
+  }
+  uint64_t m = 1ull;
+  for (int b = 1; b < 8; ++b)
+    if (f->band_wmax[b] <= thr) m |= 0xFFull << (1 + OR_N_CONES * (b - 1));
+  return m;
+}
+
 static double path_sample(const or_field* f, const or_lod* lod, const or_lod* lodn,
                           const or_camera* C, const or_render_opts* ro, uint64_t seed, int px,
                           int py, int s) {
   double o[3], v[3];
   or_camera_ray(C, seed, px, py, s, o, v);
   uint32_t pix = (uint32_t)py * (uint32_t)C->width + (uint32_t)px;
+  const uint64_t allow = fov_cells(f, C, ro, v, seed, pix, (uint32_t)s);
   if (ro->integrator == 0) {
     uint64_t mask;
     double w64[OR_MAX_CELLS];
     or_sample_mask(f, lod, v, seed, pix, (uint32_t)s, 0, OR_TAG_MASK, &mask, w64);
+    mask &= allow;
     count_ray();
     return exp(-det_tau(f, o, v, 0.0, INFINITY, mask, w64));
   }
@@ -966,17 +1057,21 @@ static double path_sample(const or_field* f, const or_lod* lod, const or_lod* lo
     uint64_t mask;
     double w64[OR_MAX_CELLS];
     or_sample_mask(f, lod, v, seed, pix, (uint32_t)s, (uint32_t)b, OR_TAG_MASK, &mask, w64);
+    mask &= allow;
     double th;
     count_ray();
     const uint32_t tw = stream_word((uint32_t)s, (uint32_t)b, OR_TAG_TRACK);
-    if (ro->free_flight ? !or_cdf_flight(f, o, v, 0.0, INFINITY, mask, w64, seed, pix, tw, &th)
-                        : !or_delta_track(f, o, v, 0.0, INFINITY, mask, w64, seed, pix, tw, &th))
+    if (ro->free_flight == 2
+            ? !or_segment_flight(f, o, v, 0.0, INFINITY, mask, w64, seed, pix, tw, &th)
+        : ro->free_flight ? !or_cdf_flight(f, o, v, 0.0, INFINITY, mask, w64, seed, pix, tw, &th)
+                          : !or_delta_track(f, o, v, 0.0, INFINITY, mask, w64, seed, pix, tw, &th))
       break;
     double x[3] = {o[0] + th * v[0], o[1] + th * v[1], o[2] + th * v[2]};
     thr *= ro->albedo;
     uint64_t nmask;
     double nw[OR_MAX_CELLS];
     or_sample_mask(f, lodn, l, seed, pix, (uint32_t)s, (uint32_t)b, OR_TAG_NEE_MASK, &nmask, nw);
+    nmask &= allow;
     count_ray();
     double Tl = ro->free_flight
                     ? exp(-det_tau(f, x, l, 0.0, INFINITY, nmask, nw))

@@ -76,7 +76,15 @@ typedef struct {
   float light_dir[3]; /* direction towards the light */
   float light_irradiance;
   int free_flight;    /* 0 delta tracking (NEE by ratio tracking); 1 inversion of the
-                         optical-depth CDF by bisection (NEE transmittance exp(-tau)) */
+                         optical-depth CDF by bisection (NEE transmittance exp(-tau));
+                         2 uniform sampling within the crossing segment (NEE as 1) */
+  int foveation;      /* 1: per-sample band cutoff by eccentricity (Supp., Foveated
+                         Rendering): f = max(0, f0 - slope e) (1 + smooth (2 xi - 1)), e the
+                         angle between the camera ray and the ray through the gaze pixel
+                         coordinates, xi the camera stream's third uniform; Gabor bands whose
+                         largest |omega| exceeds f leave every mask of the path */
+  float gaze[2];
+  float fov_f0, fov_slope, fov_smooth;
 } or_render_opts;
 
 typedef struct or_field or_field;
@@ -150,6 +158,16 @@ void or_transmittance(const or_field* f, const or_lod* lod, const float* o, cons
 int or_cdf_flight(const or_field* f, const double o[3], const double v[3], double tmin,
                   double tmax, uint64_t mask, const double* w64, uint64_t seed, uint32_t ray,
                   uint32_t word, double* t_hit);
+
+/* free flight by uniform sampling within the crossing segment (Sec. 3: the cheap
+   approximation of the inversion): segments are cut at tmin and at every chord
+   entry and exit; the first segment [e_{k-1}, e_k] with tau(tmin, e_k) >= the
+   target -ln(1 - xi) holds the collision e_{k-1} + u (e_k - e_{k-1}), xi and u
+   the first two uniforms of the (seed, ray, word) stream.  Returns 0 when the
+   whole ray's tau does not reach the target. */
+int or_segment_flight(const or_field* f, const double o[3], const double v[3], double tmin,
+                      double tmax, uint64_t mask, const double* w64, uint64_t seed,
+                      uint32_t ray, uint32_t word, double* t_hit);
 
 /* delta tracking along one ray: returns 1 and the collision t, or 0 if the ray escapes */
 int or_delta_track(const or_field* f, const double o[3], const double v[3], double tmin,

@@ -1012,6 +1012,113 @@ def test_camera_lod_selection_limits():
     assert np.array_equal(f.transmittance(o, d, tr)[1], g0)
 
 
+# --------------------------------------------------------------------------- foveation
+def test_foveation_keeps_the_bands_below_the_eccentricity_threshold():
+    """Foveation (Supp., Foveated Rendering; reading G23): every sample's path
+    keeps the Gaussian band and the Gabor bands whose largest carrier |omega| is
+    at most f = max(0, f0 - slope e) (1 + smooth (2 xi - 1)), e the camera ray's
+    angle to the gaze ray and xi the camera stream's third uniform.  The
+    threshold law is rebuilt here from the camera's own rays and Philox blocks;
+    each sample of a foveated render then equals, bit for bit, the same sample
+    rendered with the matching band cutoff.  f0 = 0 leaves the Gaussian band
+    alone, and an unbounded threshold changes nothing."""
+    p = synth.octave_field(2000, 4, seed=6)
+    f = oracle.Field(p, omega_frame="local")
+    band = f.labels()[0]
+    wn = np.array([np.linalg.norm(f.prim(i)[1]) for i in range(f.n)])
+    bmax = np.array([wn[band == b].max() if np.any(band == b) else 0.0 for b in range(8)])
+    assert np.all(np.diff(bmax[:4]) > 0)  # octaves: carriers grow band by band
+    c = synth.DEFAULT_CAMERA
+    W = H = 12
+    cam = oracle.camera(c["eye"], c["look_at"], c["up"], 30.0, W, H)
+    gaze = (3.5, 8.0)
+    f0, slope, smooth = 1.1 * bmax[3], 1.1 * bmax[3] / 0.25, 0.3
+    fov = {"gaze": gaze, "f0": f0, "slope": slope, "smooth": smooth}
+    spp, seed = 4, 5
+    ro = oracle.render_opts("scatter", spp, 2, foveation=fov)
+    got = f.render(cam, ro, seed, samples=True)
+    cuts = [f.render(cam, oracle.render_opts("scatter", spp, 2), seed, lod=oracle.Lod(1, k, 0),
+                     samples=True) for k in range(4)]
+    # the gaze ray and each sample's threshold, from the camera's float fields
+    eye = np.array(cam.eye[:], np.float64)
+    fw = np.array(cam.look_at[:], np.float64) - eye
+    fw /= np.linalg.norm(fw)
+    rt = np.cross(np.array(cam.up[:], np.float64), fw)
+    rt /= np.linalg.norm(rt)
+    uv = np.cross(fw, rt)
+    th = math.tan(0.5 * float(cam.vfov_deg) * math.pi / 180.0)
+    g = fw + (2 * float(np.float32(gaze[0])) / W - 1) * th * (W / H) * rt + \
+        (1 - 2 * float(np.float32(gaze[1])) / H) * th * uv
+    g /= np.linalg.norm(g)
+    seen = set()
+    for py in range(H):
+        for px in range(W):
+            for s in range(spp):
+                _, v = oracle.camera_ray(cam, seed, px, py, s)
+                e = math.acos(min(1.0, max(-1.0, float(v @ g))))
+                word = oracle.stream_word(s, 0, oracle.TAG_CAMERA)
+                xi = (oracle.philox4x32_10([0, 0xFFFFFFFF, py * W + px, word], [seed, 0])[2] >> 8) / 2.0 ** 24
+                thr = max(0.0, f0 - slope * e) * (1 + smooth * (2 * xi - 1))
+                k = max(b for b in range(4) if bmax[b] <= thr or b == 0)
+                if min(abs(thr - bmax[b]) for b in range(1, 4)) < 1e-9 * bmax[3]:
+                    continue  # a threshold on a band's carrier: FP rounding decides
+                seen.add(k)
+                assert got[py, px, s] == cuts[k][py, px, s], (px, py, s, k)
+    assert seen == {0, 1, 2, 3}  # every regime occurs in the frame
+    zero = f.render(cam, oracle.render_opts("scatter", spp, 2, foveation=dict(fov, f0=0.0)), seed)
+    assert np.array_equal(zero, cuts[0].mean(-1))
+    wide = f.render(cam, oracle.render_opts("scatter", spp, 2, foveation=dict(fov, f0=1e30, slope=0.0)), seed)
+    assert np.array_equal(wide, f.render(cam, oracle.render_opts("scatter", spp, 2), seed))
+
+
+# --------------------------------------------------------------------------- uniform-in-segment free flight
+def test_segment_free_flight_samples_the_crossing_segment_uniformly():
+    """Free flight by uniform sampling within the crossing segment (Sec. 3: the
+    cheap approximation of the CDF inversion).  The segments are rebuilt here
+    from the chords (entries and exits, and the ray start) and their optical
+    depths from a trapezoid integral of the density: every sample lies in the
+    segment where tau first reaches its own -ln(1 - xi), at exactly
+    e_a + u (e_b - e_a) with u its stream's second uniform; rays whose whole
+    tau stays below the target escape; and the segments' frequencies follow
+    the CDF increments exp(-tau(e_a)) - exp(-tau(e_b)) (chi^2)."""
+    p = _gauss_only()
+    f = oracle.Field(p)
+    o = np.array([0.5, 0.5, -0.5]); v = np.array([0.0, 0.0, 1.0])
+    ev = [0.0]
+    for i in range(f.n):
+        has, lo, hi = f.chord(i, o, v)
+        if has:
+            ev += [lo, hi]
+    ev = np.unique(np.array(ev))
+    assert len(ev) >= 5  # several overlapping chords: several segments
+    grid = np.linspace(0.0, 2.0, 40001)
+    kap = np.array([f.density(o + t * v) for t in grid])
+    cum = np.concatenate([[0.0], np.cumsum(0.5 * (kap[1:] + kap[:-1]) * np.diff(grid))])
+    tau_e = np.interp(ev, grid, cum)
+    word = oracle.stream_word(0, 0, oracle.TAG_TRACK)
+    n = 4000
+    seg = np.full(n, -1)
+    for r in range(n):
+        h, t = f.segment_flight(o, v, seed=3, ray=r, word=word)
+        x = oracle.philox4x32_10([0, 0xFFFFFFFF, r, word], [3, 0])
+        xi, u = (x[0] >> 8) / 2.0 ** 24, (x[1] >> 8) / 2.0 ** 24
+        target = -math.log1p(-xi)
+        k = int(np.searchsorted(tau_e, target))  # first event with tau >= target
+        if k >= len(ev):
+            assert not h, r
+            continue
+        if abs(tau_e[k] - target) < 1e-6 or abs(tau_e[k - 1] - target) < 1e-6:
+            continue  # within the trapezoid rule's error of a segment end
+        assert h, r
+        assert abs(t - (ev[k - 1] + u * (ev[k] - ev[k - 1]))) < 1e-12, (r, t, ev[k - 1], ev[k], u)
+        seg[r] = k
+    probs = np.exp(-tau_e[:-1]) - np.exp(-tau_e[1:])
+    counts = np.array([np.sum(seg == k) for k in range(1, len(ev))])
+    keep = probs * n > 5
+    chi2 = np.sum((counts[keep] - n * probs[keep]) ** 2 / (n * probs[keep]))
+    assert chi2 < stats.chi2.ppf(0.9999, max(1, keep.sum() - 1))
+
+
 # --------------------------------------------------------------------------- CDF-inversion free flight
 def test_cdf_inversion_free_flight_distribution():
     """Free flight by inversion of the optical-depth CDF (Sec. 3, Sec. 4.4): on a
