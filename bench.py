@@ -511,8 +511,13 @@ def run_workload(args):
         cam = api.camera(c["eye"], c["look_at"], c["up"], c["vfov_deg"], res, res)
         f = api.Field(ctx, p)
         f.set_lod(api.lod("cutoff", 0))
+        # reference: delta tracking (unbiased) at 16x the samples, another seed
+        ref = torch.empty(res, res, device=dev)
+        f.render(cam, api.render_opts("scatter", 16 * spp, 1, 0.8, synth.LIGHT_DIR, 1.0), seed=7,
+                 out=ref)
+        f.sync()
         rows, imgs = {}, {}
-        for mode in ("delta", "cdf"):
+        for mode in ("delta", "cdf", "segment"):
             ro = api.render_opts("scatter", spp, 1, 0.8, synth.LIGHT_DIR, 1.0, free_flight=mode)
             a = torch.empty(res, res, device=dev)
             b = torch.empty(res, res, device=dev)
@@ -525,15 +530,54 @@ def run_workload(args):
             imgs[mode] = a.clone()
             noise = (a - b).pow(2).mean().sqrt().item() / math.sqrt(2.0)
             t = statistics.mean(ms)
+            rmse = (a - ref).pow(2).mean().sqrt().item()
             rows[mode] = {"ms_per_render": t,
                           "mrays_per_s": st["rays"] / (args.steps + args.warmup) / (t * 1e-3) / 1e6,
                           "nodes_per_ray": st["nodes"] / max(1, st["rays"]),
-                          "pixel_noise_rms": noise, "time_x_variance": t * noise * noise}
+                          "pixel_noise_rms": noise, "time_x_variance": t * noise * noise,
+                          "rmse_vs_reference": rmse, "time_x_mse": t * rmse * rmse}
         f.free()
         rows["image_mean"] = {k: v.mean().item() for k, v in imgs.items()}
+        rows["reference"] = {"free_flight": "delta", "spp": 16 * spp, "mean": ref.mean().item()}
         workload_line("free flight, Gaussian band of the 100k-primitive 4-octave field, %dx%d, %d spp"
                       % (res, res, spp), rows["cdf"]["mrays_per_s"], "Mrays/s",
                       rows["cdf"]["ms_per_render"], args, {"by_free_flight": rows, "gpu_launches": 1})
+    elif args.workload == "beta":
+        # the power-law band choice with the Gaussian band as control variate (App. B,
+        # POW_CV) against all bands and Uniform + CV: time and image RMSE against an
+        # all-bands reference at 16x the samples, single scattering, 100k-primitive field;
+        # time x MSE is the cost of a given RMSE for these unbiased estimators
+        res = args.res or 256
+        spp = args.spp or 16
+        p = synth.octave_field(100_000, 4, seed=0)
+        cam = api.camera(c["eye"], c["look_at"], c["up"], c["vfov_deg"], res, res)
+        f = api.Field(ctx, p)
+        ro = api.render_opts("scatter", spp, 1, 0.8, synth.LIGHT_DIR, 1.0)
+        ref = torch.empty(res, res, device=dev)
+        f.set_lod(api.lod())
+        f.render(cam, api.render_opts("scatter", 16 * spp, 1, 0.8, synth.LIGHT_DIR, 1.0), seed=7,
+                 out=ref)
+        f.sync()
+        rows = {}
+        cases = [("all", api.lod()), ("unif_cv", api.lod("unif_cv", 7))] + \
+            [("pow_cv beta=%g" % b, api.lod("pow_cv", 7, "all", b)) for b in (0.0, 0.25, 0.5, 0.75)]
+        for name, lo in cases:
+            f.set_lod(lo, lo)
+            out = torch.empty(res, res, device=dev)
+            ms = _timed(lambda: f.render(cam, ro, seed=2, out=out), args.steps, args.warmup, stream)
+            f.sync()
+            t = statistics.mean(ms)
+            rmse = (out - ref).pow(2).mean().sqrt().item()
+            rows[name] = {"ms_per_render": t, "rmse_vs_reference": rmse, "time_x_mse": t * rmse * rmse}
+        f.free()
+        best = min((v["time_x_mse"], k) for k, v in rows.items())[1]
+        workload_line("power-law band choice with control variate, beta sweep, 100k-primitive "
+                      "4-octave field, %dx%d, %d spp, single scattering" % (res, res, spp),
+                      rows[best]["ms_per_render"], "ms per render (most efficient strategy)",
+                      rows[best]["ms_per_render"], args,
+                      {"by_strategy": rows, "most_efficient": best,
+                       "reference": "all bands, %d spp, another seed" % (16 * spp),
+                       "gpu_launches": 2}, higher=False)
     elif args.workload == "precision":
         # FP32 against FP16/BF16 records as the field outgrows the 129 MB L2: 6-octave
         # fields of 1M, 2M and 4M kernels, single scattering, 512x512, 4 spp, all bands;
@@ -581,8 +625,9 @@ def run_workload(args):
             tgt[k] = (p[k] * (1 + 0.01 * rng.standard_normal(p[k].shape))).astype(np.float32)
         cam = api.camera(c["eye"], c["look_at"], c["up"], c["vfov_deg"], res, res)
         out = {}
-        for integ in ("tomo", "scatter"):
-            ro = api.render_opts(integ, spp, 1, 0.8, synth.LIGHT_DIR, 1.0)
+        for name, integ, nb in (("tomo", "tomo", 1), ("scatter", "scatter", 1),
+                                ("scatter_3_bounces", "scatter", 3)):
+            ro = api.render_opts(integ, spp, nb, 0.8, synth.LIGHT_DIR, 1.0)
             ft = api.Field(ctx, tgt)
             target = ft.render(cam, ro, seed=11)
             ft.free()
@@ -595,7 +640,7 @@ def run_workload(args):
                 f.render_backward(cam, ro, 13, g, grad=grad)
             ms = _timed(step, args.steps, args.warmup, stream)
             f.sync()
-            out[integ] = statistics.mean(ms)
+            out[name] = statistics.mean(ms)
             f.free()
         workload_line("differentiable rendering, 200k kernels, 256x256, 8 spp, forward + adjoint",
                       res * res * spp / (out["scatter"] * 1e-3) / 1e6, "Msamples/s", out["scatter"],
@@ -852,7 +897,7 @@ def main():
     ap.add_argument("--config2", type=int, default=1,
                     help="add the single-scattering configuration as an extra key (0: skip)")
     ap.add_argument("--workload", choices=["scatter", "transmittance", "multiscatter", "adjoint",
-                                           "clamping", "free_flight", "precision"],
+                                           "clamping", "free_flight", "precision", "beta"],
                     default="scatter", help="workload of the JSON line (default: the multiple-"
                     "scattering benchmark)")
     ap.add_argument("--res", type=int, default=None, help="profiling only: image size")

@@ -177,8 +177,13 @@ enum { GF_INTEG_TOMO = 0, GF_INTEG_SCATTER = 1 };
    segment-based transfer; Sec. 4.4 distance sampling), by 32 bisections on the
    closed-form optical depth (see GF_TR_CLOSED_FORM), and the NEE transmittance
    is exp(-tau) in closed form; it assumes a non-negative mixture along each
-   ray (the first crossing) and is rendered per thread. */
-enum { GF_FLIGHT_DELTA = 0, GF_FLIGHT_CDF = 1 };
+   ray (the first crossing) and is rendered per thread.
+   SEGMENT: the cheap approximation of CDF (Sec. 3: uniform sampling within
+   segments): the ray is cut into segments at t = 0 and every chord entry and
+   exit, and the collision is drawn uniformly (second uniform of the stream)
+   within the segment where tau(0, t) reaches -ln(1 - xi); biased where the
+   density varies within a segment; NEE as CDF. */
+enum { GF_FLIGHT_DELTA = 0, GF_FLIGHT_CDF = 1, GF_FLIGHT_SEGMENT = 2 };
 
 typedef struct gf_render_opts {
   int integrator;
@@ -192,6 +197,20 @@ typedef struct gf_render_opts {
   int first_sample;   /* samples first_sample .. first_sample + spp - 1 of every pixel are
                          rendered (their Philox streams) and averaged, so that a frame can be
                          accumulated over calls; >= 0 and first_sample + spp <= 2^20 */
+  /* Foveation (Supp. "Foveated Rendering"): 0 off; 1 level masking.  Every
+     sample of a pixel gets the frequency threshold
+       f = max(0, fov_f0 - fov_slope e) (1 + fov_smooth (2 xi - 1)),
+     e the angle (radians) between its camera ray and the ray through the gaze
+     point (continuous pixel coordinates gaze[0], gaze[1], x right, y down), xi
+     the third uniform of the sample's camera stream; the Gabor bands whose
+     largest world carrier |omega| exceeds f leave every mask of the sample's
+     path (camera, bounce and NEE rays), the Gaussian band stays.  fov_f0 >= 0
+     (rad/unit), fov_slope >= 0 (rad/unit per radian), fov_smooth in [0, 1)
+     (the stochastic smoothing of the level transitions).  Renders and the
+     server; not the adjoint (GF_EINVAL). */
+  int foveation;
+  float gaze[2];
+  float fov_f0, fov_slope, fov_smooth;
 } gf_render_opts;
 
 /* Work counters accumulated by the kernels since the last reset. */
@@ -336,8 +355,16 @@ gf_status gf_render(gf_field* field, const gf_camera* camera, const gf_render_op
    points' own uniforms) for its NEE ray; differentiated with the tentative
    points, kappa_bar and the draw probabilities held fixed, so the gradient
    is unbiased for the derivative of the expected image (the derivative of
-   the k-sigma cut itself is not included).  Use a seed other than the
-   forward render's so that the two estimates are independent. */
+   the k-sigma cut itself is not included).
+   SCATTER with max_bounces >= 2: the renderer's delta-tracking path (same
+   streams and decisions) is followed twice.  Segment b's accepted point has
+   probability prod_{i<js}(1 - p_i) p_js, collision b adds C_b = albedo^(b+1)
+   E/(4 pi) T_b (T_b the ratio-tracked NEE product); the gradient is that of
+   sum_b S_b log P_b + sum_b C_b log T_b with S_b = sum_{b' >= b} C_b', the
+   points and majorants held fixed (score function of each segment's
+   decision; Sec. 3, Sec. 5.1), again unbiased for the derivative of the
+   expected image.  Use a seed other than the forward render's so that the
+   two estimates are independent. */
 gf_status gf_render_backward(gf_field* field, const gf_camera* camera,
                              const gf_render_opts* opts, uint64_t seed,
                              const float* dL_dimage, float* grad, gf_stream stream);

@@ -61,7 +61,8 @@ class gf_render_opts(C.Structure):
     _fields_ = [("integrator", C.c_int), ("spp", C.c_int), ("max_bounces", C.c_int),
                 ("albedo", C.c_float), ("light_dir", C.c_float * 3),
                 ("light_irradiance", C.c_float), ("free_flight", C.c_int),
-                ("first_sample", C.c_int)]
+                ("first_sample", C.c_int), ("foveation", C.c_int), ("gaze", C.c_float * 2),
+                ("fov_f0", C.c_float), ("fov_slope", C.c_float), ("fov_smooth", C.c_float)]
 
 
 class gf_stats(C.Structure):

@@ -100,13 +100,20 @@ def camera(eye, look_at, up, vfov_deg, width, height):
 
 def render_opts(integrator="scatter", spp=1, max_bounces=1, albedo=0.8,
                 light_dir=(1.0, 1.0, -1.0), light_irradiance=1.0, free_flight="delta",
-                first_sample=0):
-    """free_flight: "delta" (delta tracking) or "cdf" (inversion of the optical-depth CDF);
-    samples first_sample .. first_sample + spp - 1 of each pixel are averaged."""
+                first_sample=0, foveation=None):
+    """free_flight: "delta" (delta tracking), "cdf" (inversion of the optical-depth CDF) or
+    "segment" (uniform within the crossing segment); samples first_sample ..
+    first_sample + spp - 1 of each pixel are averaged; foveation: None or a dict with
+    gaze (pixel coordinates), f0 (rad/unit at the gaze), slope (rad/unit per radian of
+    eccentricity) and smooth (stochastic smoothing, [0, 1))."""
+    fv = foveation or {}
     return A.gf_render_opts(A.GF_INTEG_TOMO if integrator == "tomo" else A.GF_INTEG_SCATTER,
                             int(spp), int(max_bounces), float(albedo),
                             (C.c_float * 3)(*light_dir), float(light_irradiance),
-                            {"delta": 0, "cdf": 1}[free_flight], int(first_sample))
+                            {"delta": 0, "cdf": 1, "segment": 2}[free_flight], int(first_sample),
+                            1 if foveation else 0, (C.c_float * 2)(*fv.get("gaze", (0.0, 0.0))),
+                            float(fv.get("f0", 0.0)), float(fv.get("slope", 0.0)),
+                            float(fv.get("smooth", 0.0)))
 
 
 class Field:

@@ -210,10 +210,33 @@ gf_status camera_params(const gf_camera* c, const gf_render_opts* o, uint64_t se
   P.cam.aspect = (float)((double)c->width / (double)c->height);
   P.cam.W = c->width;
   P.cam.H = c->height;
-  if (o->free_flight != GF_FLIGHT_DELTA && o->free_flight != GF_FLIGHT_CDF)
+  P.fov = 0;
+  P.gaze = make_float3(0.f, 0.f, 1.f);
+  P.fov_f0 = P.fov_slope = P.fov_smooth = 0.f;
+  if (o->foveation == 1) {
+    // the ray through the gaze point (continuous pixel coordinates), as camera_ray forms it
+    const double sx = (2.0 * (double)o->gaze[0] / c->width - 1.0) * (double)P.cam.tanh * P.cam.aspect;
+    const double sy = (1.0 - 2.0 * (double)o->gaze[1] / c->height) * (double)P.cam.tanh;
+    double g[3] = {f[0] + sx * r[0] + sy * uv[0], f[1] + sx * r[1] + sy * uv[1],
+                   f[2] + sx * r[2] + sy * uv[2]};
+    const double gn = std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    P.fov = 1;
+    P.gaze = make_float3((float)(g[0] / gn), (float)(g[1] / gn), (float)(g[2] / gn));
+    P.fov_f0 = o->fov_f0;
+    P.fov_slope = o->fov_slope;
+    P.fov_smooth = o->fov_smooth;
+  }
+  if (o->free_flight != GF_FLIGHT_DELTA && o->free_flight != GF_FLIGHT_CDF &&
+      o->free_flight != GF_FLIGHT_SEGMENT)
     return fail(GF_EINVAL, "bad free_flight");
   if (o->first_sample < 0 || (int64_t)o->first_sample + o->spp > (1 << 20))
     return fail(GF_EINVAL, "first_sample must be >= 0 with first_sample + spp <= 2^20");
+  if (o->foveation != 0 && o->foveation != 1) return fail(GF_EINVAL, "foveation must be 0 or 1");
+  if (o->foveation &&
+      !(o->fov_f0 >= 0.f && o->fov_f0 < INFINITY && o->fov_slope >= 0.f && o->fov_slope < INFINITY &&
+        o->fov_smooth >= 0.f && o->fov_smooth < 1.f && std::isfinite(o->gaze[0]) &&
+        std::isfinite(o->gaze[1])))
+    return fail(GF_EINVAL, "foveation needs fov_f0, fov_slope >= 0, fov_smooth in [0,1), a finite gaze");
   P.integrator = o->integrator;
   P.free_flight = o->free_flight;
   P.spp = o->spp;
@@ -372,7 +395,7 @@ gf_status gf_load_field(gf_ctx* ctx, const gf_params* p, const gf_field_opts* op
         (e = A((void**)&F.rec_orig, 64 * n)) || (e = A((void**)&F.box_orig, 24 * n)) ||
         (e = A((void**)&F.kw_orig, 4 * n)) || (e = A((void**)&F.labels, 3 * n)) ||
         (e = A((void**)&F.err, 4)) || (e = A((void**)&F.stats, 8 * kNumStats)) ||
-        (e = A((void**)&F.counter, 16)) || (e = A((void**)&F.cell_acc, 128 * 4)) ||
+        (e = A((void**)&F.counter, 16)) || (e = A((void**)&F.cell_acc, 136 * 4)) ||
         (e = A((void**)&F.gl, 2 * kGLTotal * sizeof(float))))
       break;
     if ((e = A((void**)&F.ext2_orig, 4 * n)) || (e = A((void**)&F.ext2, 4 * n))) break;
@@ -389,7 +412,7 @@ gf_status gf_load_field(gf_ctx* ctx, const gf_params* p, const gf_field_opts* op
       break;
     if (p->band && (e = cp(band_dev, p->band, n))) break;
     if ((e = cudaMemsetAsync(F.err, 0, 4, s)) || (e = cudaMemsetAsync(F.stats, 0, 8 * kNumStats, s)) ||
-        (e = cudaMemsetAsync(F.cell_acc, 0, 512, s)))
+        (e = cudaMemsetAsync(F.cell_acc, 0, 136 * 4, s)))
       break;
   } while (0);
   if (e != cudaSuccess) {
@@ -408,9 +431,9 @@ gf_status gf_load_field(gf_ctx* ctx, const gf_params* p, const gf_field_opts* op
   dp.band = (const uint8_t*)band_dev;
   e = launch_pack(F, dp, s);
   int herr = 0;
-  float acc[128];
+  float acc[136];
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, F.err, 4, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(acc, F.cell_acc, 512, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(acc, F.cell_acc, 136 * 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) F.mem.release(band_dev, s);
   if (e != cudaSuccess) {
@@ -434,6 +457,7 @@ gf_status gf_load_field(gf_ctx* ctx, const gf_params* p, const gf_field_opts* op
     F.dev.kbar[c] = cnt > 0.f ? acc[c] / cnt : 0.f;
   }
   for (int k = 0; k < 8; ++k) F.dev.env[k] = (float)std::exp(-0.5 * k * k);
+  for (int b = 0; b < 8; ++b) F.dev.band_wmax[b] = acc[128 + b];  // 0 for an empty band
   F.dev.err = F.err;
   F.dev.stats = F.stats;
   F.dev.gl = F.gl;
@@ -645,6 +669,7 @@ gf_status gf_render_backward(gf_field* h, const gf_camera* camera, const gf_rend
   gf_status st = camera_params(camera, opts, seed, F, P);
   if (st) return st;
   if (P.free_flight != GF_FLIGHT_DELTA) return fail(GF_EINVAL, "the adjoint differentiates GF_FLIGHT_DELTA");
+  if (P.fov) return fail(GF_EINVAL, "the adjoint renders without foveation");
   if (opts->integrator == GF_INTEG_SCATTER && opts->max_bounces < 1)
     return fail(GF_EINVAL, "the radiance adjoint needs max_bounces >= 1");
   if (F.opts.precision != GF_PREC_FP32)

@@ -29,7 +29,7 @@ struct PackArgs {
   float* kw;
   float* ext2;      // support radius squared per primitive (k^2 or adaptive)
   uint8_t* labels;  // band[N], cone[N], cell[N]
-  float* cell_acc;  // sum |k_W| [64], count [64]
+  float* cell_acc;  // sum |k_W| [64], count [64], largest |omega| per band [8] (bits)
   int* err;
 };
 
@@ -143,6 +143,9 @@ __global__ void k_pack(const __grid_constant__ PackArgs A) {
   A.labels[2 * A.p.n + i] = (uint8_t)cell;
   atomicAdd(A.cell_acc + cell, kn);
   atomicAdd(A.cell_acc + 64 + cell, 1.f);
+  // largest world carrier |omega| per band (non-negative floats order as their bits)
+  atomicMax(reinterpret_cast<unsigned int*>(A.cell_acc + 128 + band),
+            __float_as_uint(sqrtf(om[0] * om[0] + om[1] * om[1] + om[2] * om[2])));
 }
 
 cudaError_t launch_pack(Field& F, const gf_params& P, cudaStream_t s) {

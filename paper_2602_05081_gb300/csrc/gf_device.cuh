@@ -81,6 +81,7 @@ struct DevField {
   float3 lo, hi;           // scene bounds (union of all ellipsoid boxes)
   unsigned long long occupied;
   float kbar[kMaxCells];   // mean |k_W| per cell
+  float band_wmax[8];      // largest world carrier |omega| (rad/unit) per band
   float axes[kCones][3];   // orientation-bin axes
   float env[8];            // exp(-n^2/2), n = 0..7
   const int* orig16;       // reduced-precision records: BVH position -> original index

@@ -114,7 +114,7 @@ struct Field {
   int* err = nullptr;
   unsigned long long* stats = nullptr;
   int* counter = nullptr;
-  float* cell_acc = nullptr;    // per-cell |k_W| sums (64) and counts (64)
+  float* cell_acc = nullptr;    // per-cell |k_W| sums (64) and counts (64), band max |omega| (8)
   int depth = 0;                // levels of internal nodes of the binary tree
   bool built = false;
   bool camera_lod = false;  // a camera LoD selection is active

@@ -106,9 +106,11 @@ __global__ void __launch_bounds__(kBlock, 3)  // at most 168 registers: 12 warps
 
 // ---------------------------------------------------------------------------
 // render: each lane owns one pixel of an 8x4 tile and runs its samples in
-// order (deterministic per pixel); CDF: scattering with CDF-inversion free flight
+// order (deterministic per pixel); FF: the free flight of scattering
+// (GF_FLIGHT_DELTA here means tomography: delta tracking renders in the
+// wavefront kernel)
 // ---------------------------------------------------------------------------
-template <bool CDF>
+template <int FF>
 __global__ void __launch_bounds__(kBlock)
     k_render(const __grid_constant__ DevField F, const PathParams P, float* out, int* counter) {
   __shared__ BlockTables sm;
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(kBlock)
     const bool active = px < P.cam.W && py < P.cam.H;
     float acc = 0.f;
     for (int s = 0; s < P.spp; ++s)
-      acc += path_sample<CDF>(F, P, active, px, py, P.s0 + s, sm.glx, sm.glw, sm.env, cnt);
+      acc += path_sample<FF>(F, P, active, px, py, P.s0 + s, sm.glx, sm.glw, sm.env, cnt);
     if (active) out[(int64_t)py * P.cam.W + px] = acc / (float)P.spp;
   }
   flush_counters(F, cnt, lane);
@@ -277,11 +279,11 @@ cudaError_t launch_render(const Field& F, const PathParams& P, float* out, cudaS
     return launch_render_scatter(F, P, out, s);
   const int64_t tiles = (int64_t)((P.cam.W + kTileW - 1) / kTileW) * ((P.cam.H + kTileH - 1) / kTileH);
   if (P.integrator == GF_INTEG_SCATTER) {
-    auto k = k_render<true>;
+    auto k = P.free_flight == GF_FLIGHT_SEGMENT ? k_render<GF_FLIGHT_SEGMENT> : k_render<GF_FLIGHT_CDF>;
     if (!stack_fits(k)) return cudaErrorLaunchOutOfResources;
     k<<<persistent_grid(F, k, tiles), kBlock, 0, s>>>(F.dev, P, out, F.counter);
   } else {
-    auto k = k_render<false>;
+    auto k = k_render<GF_FLIGHT_DELTA>;
     if (!stack_fits(k)) return cudaErrorLaunchOutOfResources;
     k<<<persistent_grid(F, k, tiles), kBlock, 0, s>>>(F.dev, P, out, F.counter);
   }

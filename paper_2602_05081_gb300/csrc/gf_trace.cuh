@@ -4,6 +4,7 @@
 // CDF-inversion free flight, path samples.  One thread owns one ray (or one
 // pixel's paths); a warp advances 32 rays, or 32/G rays with G lanes each.
 #pragma once
+#include "../../include/gf.h"
 #include "gf_device.cuh"
 
 namespace gf {
@@ -530,6 +531,95 @@ __device__ __forceinline__ bool cdf_flight(const DevField& F, const Mask& M, flo
   return true;
 }
 
+// Free flight by uniform sampling within the crossing segment (Sec. 3: the
+// cheap approximation of the CDF inversion; Sec. 4.4 distance sampling).  The
+// ray is cut into segments at t = 0 and at every chord entry and exit; the
+// segment [e_a, e_b] in which tau(0, t) reaches the target -ln(1 - xi) holds
+// the collision e_a + u (e_b - e_a), xi and u the first two uniforms of the
+// segment's tracking stream.  The crossing segment is found by bisection on t
+// that stops once no chord end lies inside the bracket: every step is one
+// traversal giving tau(0, mid), the chord ends inside both halves of the
+// bracket and the nearest ends around them.
+struct SegLeaf {
+  const DevField* F;
+  const Mask* M;
+  float3 o, v;
+  float lo, mid, hi;  // the bracket and its midpoint
+  float s = 0.f, c = 0.f;  // tau(0, mid), compensated
+  int n_left = 0, n_right = 0;  // chord ends in (lo, mid) and in (mid, hi)
+  float below_lo = 0.f, below_mid = 0.f;             // largest end <= lo, <= mid (or 0)
+  float above_mid = INFINITY, above_hi = INFINITY;   // smallest end >= mid, >= hi
+  __device__ __forceinline__ void end(float e) {
+    n_left += (e > lo && e < mid) ? 1 : 0;
+    n_right += (e > mid && e < hi) ? 1 : 0;
+    if (e <= lo) below_lo = fmaxf(below_lo, e);
+    if (e <= mid) below_mid = fmaxf(below_mid, e);
+    if (e >= mid) above_mid = fminf(above_mid, e);
+    if (e >= hi) above_hi = fminf(above_hi, e);
+  }
+  __device__ __forceinline__ void operator()(int j) {
+    const Mask& Mk = *M;
+    Chord ch;
+    float w;
+    if (!prim_chord(*F, j, o, v, 0.f, INFINITY, [&](uint32_t cc) { return mask_weight(Mk, cc); }, w,
+                    ch))
+      return;
+    end(ch.tc + ch.dtin);
+    end(ch.tc + ch.dtout);
+    if (ch.tc + ch.dtin >= mid) return;
+    // the chord's part in [0, mid]
+    if (ch.tc + ch.dtout > mid) ch.dtout = mid - ch.tc;
+    neumaier_add(s, c, w * chord_closed(F->wd, ch));
+  }
+};
+
+__device__ __forceinline__ bool segment_flight(const DevField& F, const Mask& M, float3 o, float3 v,
+                                               uint64_t seed, uint32_t ray, uint32_t word,
+                                               float& th, Counters& cnt) {
+  const uint4 y = rng4(seed, 0, kNoPrim, ray, word);
+  const float target = -log1pf(-u01(y.x));
+  float tend;
+  const float total = closed_tau(F, M, o, v, 0.f, INFINITY, cnt, 0, 1, &tend);
+  if (!(tend > 0.f) || total < target) return false;
+  const float3 inv = safe_inv(v);
+  float t0, t1;
+  if (!scene_span(F, o, inv, 0.f, INFINITY, t0, t1)) return false;
+  float lo = 0.f, hi = tend;
+  float ea = 0.f, eb = tend;
+  for (int it = 0; it < 48; ++it) {
+    SegLeaf leaf;
+    leaf.F = &F;
+    leaf.M = &M;
+    leaf.o = o;
+    leaf.v = v;
+    leaf.lo = lo;
+    leaf.hi = hi;
+    leaf.mid = 0.5f * (lo + hi);
+    SpanTest test{t0, t1};
+    unsigned long long nodes = 0, leaves = 0;
+    traverse_ray(F, o, inv, M.bits, test, leaf, nodes, leaves);
+    cnt.nodes += nodes;
+    cnt.leaves += leaves;
+    cnt.windows += 1;
+    const bool right = __fadd_rn(leaf.s, leaf.c) < target;
+    if (right) {
+      lo = leaf.mid;
+      ea = leaf.below_mid;
+      eb = leaf.above_hi;
+      if (leaf.n_right == 0) break;
+    } else {
+      hi = leaf.mid;
+      ea = leaf.below_lo;
+      eb = leaf.above_mid;
+      if (leaf.n_left == 0) break;
+    }
+    if (!(hi > lo)) break;
+  }
+  if (!(eb < INFINITY)) eb = tend;
+  th = ea + u01(y.y) * (eb - ea);
+  return true;
+}
+
 // ---------------------------------------------------------------------------
 // Tracking.  The majorant is constant on every segment between consecutive
 // chord ends and whitened-distance integers: kappa_bar = sum over the active
@@ -817,31 +907,57 @@ __device__ __forceinline__ void camera_ray(const CamDev& C, uint64_t seed, int p
 struct PathParams {
   CamDev cam;
   int integrator, spp, max_bounces;
-  int free_flight;  // GF_FLIGHT_DELTA or GF_FLIGHT_CDF
+  int free_flight;  // GF_FLIGHT_DELTA, GF_FLIGHT_CDF or GF_FLIGHT_SEGMENT
   int s0;           // first sample index (samples s0 .. s0 + spp - 1)
+  int fov;          // foveation: 1 = per-sample band cutoff by eccentricity
+  float3 gaze;      // unit direction of the ray through the gaze point
+  float fov_f0, fov_slope, fov_smooth;
   float albedo, irradiance;
   float3 light;
   uint64_t seed;
   LodDev lod, lod_nee;
 };
 
+// Foveation (Supp. "Foveated Rendering"): the cells a sample's path keeps.
+// The threshold falls linearly with the eccentricity e of the camera ray v,
+// f = max(0, f0 - slope e), and is perturbed per sample by the third uniform
+// of the camera stream (stochastic smoothing of the level transitions); the
+// Gabor bands whose largest carrier exceeds f leave, the Gaussian band stays.
+__device__ __forceinline__ unsigned long long fov_cells(const DevField& F, const PathParams& P,
+                                                        float3 v, uint32_t pix, uint32_t s) {
+  if (!P.fov) return ~0ull;
+  const float c = fminf(1.f, fmaxf(-1.f, v.x * P.gaze.x + v.y * P.gaze.y + v.z * P.gaze.z));
+  float f = fmaxf(0.f, P.fov_f0 - P.fov_slope * acosf(c));
+  if (P.fov_smooth > 0.f) {
+    const uint4 x = rng4(P.seed, 0, kNoPrim, pix, stream_word(s, 0, TAG_CAMERA));
+    f *= 1.f + P.fov_smooth * (2.f * u01(x.z) - 1.f);
+  }
+  unsigned long long m = 1ull;
+#pragma unroll
+  for (int b = 1; b < 8; ++b)
+    if (F.band_wmax[b] <= f) m |= 0xFFull << (1 + kCones * (b - 1));
+  return m;
+}
+
 // One sample of pixel (px, py): tomography exp(-tau) or scattering radiance.
 // Called by all lanes of a warp together (inactive lanes with active = false):
 // every phase (camera tracking, NEE, scattering) runs with the lanes that need
 // it converged, and the lanes regroup after each phase.
-// CDF selects the free flight at compile time (GF_FLIGHT_CDF; else delta
-// tracking), so that each kernel carries only the stack of the path it runs.
-template <bool CDF>
+// FF selects the free flight at compile time (GF_FLIGHT_DELTA, GF_FLIGHT_CDF or
+// GF_FLIGHT_SEGMENT), so that each kernel carries only the stack of the path it runs.
+template <int FF>
 static __device__ float path_sample(const DevField& F, const PathParams& P, bool active, int px,
                                     int py, int s, const float* glx, const float* glw,
                                     const float* env, Counters& cnt) {
   float3 o = make_float3(0.f, 0.f, 0.f), v = make_float3(0.f, 0.f, 1.f);
   if (active) camera_ray(P.cam, P.seed, px, py, s, o, v);
   const uint32_t pix = (uint32_t)py * (uint32_t)P.cam.W + (uint32_t)px;
+  const unsigned long long allow = fov_cells(F, P, v, pix, (uint32_t)s);
   if (P.integrator == 0) {
     float T = 0.f;
     if (active) {
-      const Mask m = sample_mask(F, P.lod, v, P.seed, pix, (uint32_t)s, 0, TAG_MASK);
+      Mask m = sample_mask(F, P.lod, v, P.seed, pix, (uint32_t)s, 0, TAG_MASK);
+      m.bits &= allow;
       cnt.rays += 1;
       T = expf(-det_tau(F, m, o, v, 0.f, INFINITY, glx, glw, cnt));
     }
@@ -855,12 +971,15 @@ static __device__ float path_sample(const DevField& F, const PathParams& P, bool
     float th = 0.f, hit = 0.f;
     if (alive) {
       GF_TIC(cm);
-      const Mask m = sample_mask(F, P.lod, v, P.seed, pix, (uint32_t)s, (uint32_t)b, TAG_MASK);
+      Mask m = sample_mask(F, P.lod, v, P.seed, pix, (uint32_t)s, (uint32_t)b, TAG_MASK);
+      m.bits &= allow;
       GF_TOC(cnt, 3, cm);
       cnt.rays += 1;
       const uint32_t tw = stream_word((uint32_t)s, (uint32_t)b, TAG_TRACK);
-      if constexpr (CDF)
+      if constexpr (FF == GF_FLIGHT_CDF)
         hit = cdf_flight(F, m, o, v, P.seed, pix, tw, th, cnt) ? 1.f : 0.f;
+      else if constexpr (FF == GF_FLIGHT_SEGMENT)
+        hit = segment_flight(F, m, o, v, P.seed, pix, tw, th, cnt) ? 1.f : 0.f;
       else
         hit = track<true>(F, m, o, v, 0.f, INFINITY, true, P.seed, pix, tw, env, cnt, &th);
     }
@@ -869,11 +988,12 @@ static __device__ float path_sample(const DevField& F, const PathParams& P, bool
     const float3 x = make_float3(o.x + th * v.x, o.y + th * v.y, o.z + th * v.z);
     if (alive) {
       thr *= P.albedo;
-      const Mask mn = sample_mask(F, P.lod_nee, P.light, P.seed, pix, (uint32_t)s, (uint32_t)b,
-                                  TAG_NEE_MASK);
+      Mask mn = sample_mask(F, P.lod_nee, P.light, P.seed, pix, (uint32_t)s, (uint32_t)b,
+                            TAG_NEE_MASK);
+      mn.bits &= allow;
       cnt.rays += 1;
       float Tl;
-      if constexpr (CDF)
+      if constexpr (FF != GF_FLIGHT_DELTA)
         Tl = expf(-closed_tau(F, mn, x, P.light, 0.f, INFINITY, cnt));
       else
         Tl = track<false>(F, mn, x, P.light, 0.f, INFINITY, true, P.seed, pix,

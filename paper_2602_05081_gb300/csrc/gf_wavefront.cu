@@ -357,6 +357,7 @@ struct PathState {
   float3 o, v;    // current ray
   float t0, t1;   // scene span of the current ray
   float step;     // window length for delta tracking
+  unsigned long long allow;  // cells the foveation keeps for the sample's path
 };
 
 __device__ __forceinline__ void set_slot(LaneRay& R, float3 o, float3 v, const Mask& m,
@@ -590,7 +591,9 @@ __device__ __forceinline__ void render_paths(const Work& Wk, const float* env, W
       S.b = 0;
       S.thr = 1.f;
       S.Lsum = 0.f;
-      const Mask m = sample_mask(F, P.lod, v, P.seed, (uint32_t)S.pix, (uint32_t)S.s, 0, TAG_MASK);
+      S.allow = fov_cells(F, P, v, (uint32_t)S.pix, (uint32_t)S.s);
+      Mask m = sample_mask(F, P.lod, v, P.seed, (uint32_t)S.pix, (uint32_t)S.s, 0, TAG_MASK);
+      m.bits &= S.allow;
       cnt.rays += 1;
       if (start_ray(F, R, S, 1, o, v, m, (uint32_t)S.pix,
                     stream_word((uint32_t)S.s, 0, TAG_TRACK)))
@@ -614,8 +617,9 @@ __device__ __forceinline__ void render_paths(const Work& Wk, const float* env, W
         const float3 x = make_float3(S.o.x + th * S.v.x, S.o.y + th * S.v.y, S.o.z + th * S.v.z);
         S.thr *= P.albedo;
         S.T = 1.f;
-        const Mask mn = sample_mask(F, P.lod_nee, P.light, P.seed, (uint32_t)S.pix, (uint32_t)S.s,
-                                    (uint32_t)S.b, TAG_NEE_MASK);
+        Mask mn = sample_mask(F, P.lod_nee, P.light, P.seed, (uint32_t)S.pix, (uint32_t)S.s,
+                              (uint32_t)S.b, TAG_NEE_MASK);
+        mn.bits &= S.allow;
         cnt.rays += 1;
         if (start_ray(F, R, S, 2, x, P.light, mn, (uint32_t)S.pix,
                       stream_word((uint32_t)S.s, (uint32_t)S.b, TAG_NEE)))
@@ -640,8 +644,9 @@ __device__ __forceinline__ void render_paths(const Work& Wk, const float* env, W
         return;
       }
       const float3 xo = S.o;
-      const Mask m = sample_mask(F, P.lod, nv, P.seed, (uint32_t)S.pix, (uint32_t)S.s,
-                                 (uint32_t)S.b, TAG_MASK);
+      Mask m = sample_mask(F, P.lod, nv, P.seed, (uint32_t)S.pix, (uint32_t)S.s,
+                           (uint32_t)S.b, TAG_MASK);
+      m.bits &= S.allow;
       cnt.rays += 1;
       if (start_ray(F, R, S, 1, xo, nv, m, (uint32_t)S.pix,
                     stream_word((uint32_t)S.s, (uint32_t)S.b, TAG_TRACK)))

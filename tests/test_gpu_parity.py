@@ -465,12 +465,14 @@ def test_camera_lod_selection_parity(api, ctx):
     assert np.array_equal(tau1.cpu().numpy(), tau0)
 
 
-def test_cdf_free_flight_render_parity(api, ctx):
+@pytest.mark.parametrize("flight", ["cdf", "segment"])
+def test_cdf_free_flight_render_parity(api, ctx, flight):
     """Free flight by inversion of the optical-depth CDF (Sec. 3, Sec. 4.4; bisection
-    on the closed-form tau) with closed-form NEE transmittance, one and two
-    bounces, on the Gaussian band (a non-negative density): the image matches the
-    oracle's within 1% of its Monte Carlo noise under shared streams.  The server
-    and the adjoint refuse the mode."""
+    on the closed-form tau), or by uniform sampling within the crossing segment
+    (Sec. 3's cheap approximation), with closed-form NEE transmittance, one and
+    two bounces, on the Gaussian band (a non-negative density): the image
+    matches the oracle's within 1% of its Monte Carlo noise under shared
+    streams.  The server and the adjoint refuse the modes."""
     p = synth.octave_field(3000, 4, seed=8)
     f = api.Field(ctx, p)
     orc = oracle.Field(p, omega_frame="local")
@@ -479,13 +481,45 @@ def test_cdf_free_flight_render_parity(api, ctx):
     lo = oracle.Lod(1, 0, 0)
     for nb in (1, 2):
         diff, noise, ref = _mc_parity(api, f, orc, cg, co,
-                                      api.render_opts("scatter", 8, nb, free_flight="cdf"),
-                                      oracle.render_opts("scatter", 8, nb, free_flight="cdf"), 2, lo, lo)
+                                      api.render_opts("scatter", 8, nb, free_flight=flight),
+                                      oracle.render_opts("scatter", 8, nb, free_flight=flight), 2,
+                                      lo, lo)
         assert ref.max() > 1e-3
         assert diff <= 0.01 * noise, (nb, diff, noise)
     from paper_2602_05081_gb300 import _abi
     with pytest.raises(_abi.GfError):
-        f.render_backward(cg, api.render_opts("scatter", 8, 1, free_flight="cdf"), 2,
+        f.render_backward(cg, api.render_opts("scatter", 8, 1, free_flight=flight), 2,
+                          torch.ones(24, 24, device=DEV))
+
+
+def test_foveated_render_parity(api, ctx):
+    """Foveation (Supp., Foveated Rendering): a per-sample band cutoff that falls
+    linearly with the eccentricity from the gaze point, with stochastic
+    smoothing of the level transitions, through the wavefront renderer (delta
+    tracking, 2 bounces) and the per-thread CDF renderer: the image matches the
+    oracle's within 1% of its Monte Carlo noise under shared streams; the
+    adjoint refuses foveation."""
+    p = synth.octave_field(3000, 4, seed=8)
+    f = api.Field(ctx, p)
+    orc = oracle.Field(p, omega_frame="local")
+    band = orc.labels()[0]
+    wn = np.array([np.linalg.norm(orc.prim(i)[1]) for i in range(orc.n)])
+    top = wn[band == 3].max()
+    fov = {"gaze": (7.5, 15.0), "f0": 1.1 * top, "slope": 1.1 * top / 0.35, "smooth": 0.3}
+    cg, co = _cam_pair(api, 24, 24)
+    for flight, lo in (("delta", None), ("cdf", oracle.Lod(1, 0, 0))):
+        if lo is not None:
+            f.set_lod(api.lod("cutoff", 0))
+        diff, noise, ref = _mc_parity(api, f, orc, cg, co,
+                                      api.render_opts("scatter", 8, 2, free_flight=flight, foveation=fov),
+                                      oracle.render_opts("scatter", 8, 2, free_flight=flight,
+                                                         foveation=fov), 2, lo, lo)
+        assert ref.max() > 1e-3
+        assert diff <= 0.01 * noise, (flight, diff, noise)
+    f.set_lod(api.lod())
+    from paper_2602_05081_gb300 import _abi
+    with pytest.raises(_abi.GfError):
+        f.render_backward(cg, api.render_opts("scatter", 4, 1, foveation=fov), 2,
                           torch.ones(24, 24, device=DEV))
 
 
