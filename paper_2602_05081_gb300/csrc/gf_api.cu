@@ -168,6 +168,7 @@ gf_status take_device_error(Field& F) {
   if (err & (ERR_STACK | ERR_WINDOW | ERR_POINTS))
     return fail(GF_EOVERFLOW, "device buffer overflow (code " + std::to_string(err) + ")");
   if (err & ERR_GUARD) return fail(GF_ETIMEOUT, "bounded device loop gave up");
+  if (err & ERR_INDEX) return fail(GF_ECUDA, "a tree index left its array (access skipped)");
   return fail(GF_EINVAL, "device-side input error (code " + std::to_string(err) + ")");
 }
 

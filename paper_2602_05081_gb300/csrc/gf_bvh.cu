@@ -559,6 +559,7 @@ cudaError_t build_bvh(Field& F, cudaStream_t s) {
     GF_TRY(cudaMemcpyAsync(&last[1], flags + (m - 1), sizeof(int), cudaMemcpyDeviceToHost, s));
     GF_TRY(cudaStreamSynchronize(s));
     const int64_t m4 = (int64_t)last[0] + last[1];
+    F.n_nodes4 = m4;
     F.mem.release(F.nodes4, s);  // a rebuild (the stream was synchronised above)
     F.nodes4 = nullptr;
     GF_TRY(F.mem.alloc((void**)&F.nodes4, (size_t)m4 * sizeof(Node4), s));
@@ -587,6 +588,7 @@ cudaError_t build_bvh(Field& F, cudaStream_t s) {
   F.dev.ext2 = F.ext2;  // read by the reduced-precision path (FP32 records carry their own)
   F.dev.nodes = F.nodes;
   F.dev.nodes4 = F.nodes4;
+  F.dev.n_nodes4 = n >= 2 ? F.n_nodes4 : 0;
   F.dev.root = n >= 2 ? 0 : -1;
 done:
 #undef GF_TRY

@@ -23,7 +23,11 @@ enum : uint32_t {
   TAG_SCATTER = 6
 };
 
-enum : int { ERR_STACK = 1, ERR_WINDOW = 2, ERR_POINTS = 4, ERR_GUARD = 8, ERR_INPUT = 16 };
+// ERR_INDEX: a tree index out of its array (the traversals check every node and
+// leaf index they follow and skip the access)
+enum : int {
+  ERR_STACK = 1, ERR_WINDOW = 2, ERR_POINTS = 4, ERR_GUARD = 8, ERR_INPUT = 16, ERR_INDEX = 32
+};
 
 // Binary BVH node holding the boxes, children and cell masks of both children
 // (one 80-byte fetch tests two boxes).  child >= 0: internal node; child < 0:
@@ -75,6 +79,7 @@ struct DevField {
   const Node* nodes;
   const Node4* nodes4;     // four-wide collapse of nodes (root 0 when n >= 2)
   int64_t n;
+  int64_t n_nodes4;        // four-wide nodes
   int root;                // internal root node, -1 when n == 1
   int precision;           // 0 FP32, 1 FP16, 2 BF16
   float ksig, k2;
@@ -562,6 +567,10 @@ __device__ __forceinline__ void traverse_from(const DevField& F, int start, floa
                                               unsigned long long& nleaves) {
   if (start == kNoStart) return;
   if (start < 0) {
+    if ((int64_t)~start >= F.n) {
+      set_err(F, ERR_INDEX);
+      return;
+    }
     ++nleaves;
     leaf(~start);
     return;
@@ -586,6 +595,11 @@ __device__ __forceinline__ void traverse_from(const DevField& F, int start, floa
         node = -1;
         break;
       }
+      if ((int64_t)node >= F.n - 1) {  // internal nodes 0 .. n-2
+        set_err(F, ERR_INDEX);
+        node = -1;
+        break;
+      }
       const Node* N = F.nodes + node;
       const float4 a = __ldg(&N->a), b = __ldg(&N->b), c = __ldg(&N->c);
       const int4 d = __ldg(&N->d);
@@ -596,9 +610,19 @@ __device__ __forceinline__ void traverse_from(const DevField& F, int start, floa
       float tn0, tf0, tn1, tf1;
       slab_interval(o, inv, a.x, a.y, a.z, a.w, b.x, b.y, tn0, tf0);
       slab_interval(o, inv, b.z, b.w, c.x, c.y, c.z, c.w, tn1, tf1);
-      const bool h0 = (m0 & mask) && test(tn0, tf0);
-      const bool h1 = (m1 & mask) && test(tn1, tf1);
-      const int c0 = d.x, c1 = d.y;
+      bool h0 = (m0 & mask) && test(tn0, tf0);
+      bool h1 = (m1 & mask) && test(tn1, tf1);
+      int c0 = d.x, c1 = d.y;
+      if (c0 < 0 && (int64_t)~c0 >= F.n) {  // a leaf beyond the records
+        set_err(F, ERR_INDEX);
+        c0 = 0;
+        h0 = false;
+      }
+      if (c1 < 0 && (int64_t)~c1 >= F.n) {
+        set_err(F, ERR_INDEX);
+        c1 = 0;
+        h1 = false;
+      }
       if (h0 && c0 < 0) pend0 = ~c0;
       if (h1 && c1 < 0) {
         if (pend0 < 0) pend0 = ~c1;

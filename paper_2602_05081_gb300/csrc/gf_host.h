@@ -116,6 +116,7 @@ struct Field {
   int* counter = nullptr;
   float* cell_acc = nullptr;    // per-cell |k_W| sums (64) and counts (64), band max |omega| (8)
   int depth = 0;                // levels of internal nodes of the binary tree
+  int64_t n_nodes4 = 0;         // four-wide nodes
   bool built = false;
   bool camera_lod = false;  // a camera LoD selection is active
   int server_refs = 0;      // render servers holding this field

@@ -79,6 +79,7 @@ struct Batch {
 gf_status status_of_err(int err) {
   if (err & (ERR_STACK | ERR_WINDOW | ERR_POINTS)) return GF_EOVERFLOW;
   if (err & ERR_GUARD) return GF_ETIMEOUT;
+  if (err & ERR_INDEX) return GF_ECUDA;
   return GF_EINVAL;
 }
 

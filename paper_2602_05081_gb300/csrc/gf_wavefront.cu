@@ -194,7 +194,9 @@ __device__ void warp_phase(const Work& Wk, WarpQ& Q, bool want, uint32_t lane, c
     int slot = 0;
     int ch[4] = {0, 0, 0, 0};
     unsigned hit = 0u;  // bit k: child k overlaps the window and the ray's cells
-    if (ent >= 0) {
+    if (ent >= 0 && (int64_t)(ent >> 5) >= Wk.field(Q.r[ent & 31].asset).n_nodes4) {
+      set_err(Wk.err_field(), ERR_INDEX);  // a node beyond the tree: skipped
+    } else if (ent >= 0) {
       const int node = ent >> 5;
       slot = ent & 31;
       const LaneRay& R = Q.r[slot];
@@ -264,12 +266,16 @@ __device__ void warp_phase(const Work& Wk, WarpQ& Q, bool want, uint32_t lane, c
     // ---------------- leaf rounds: 32 leaves of any slots' rays at a time
     while (lq_n >= 32 || (!any_trav && lq_n > 0)) {
       const int tk = lq_n < 32 ? lq_n : 32;
-      const bool have = (int)lane < tk;
+      bool have = (int)lane < tk;
       int j = 0, own = 0;
       if (have) {
         const int e = Q.lq[lq_n - tk + (int)lane];
         j = e >> 5;
         own = e & 31;
+        if ((int64_t)j >= Wk.field(Q.r[own].asset).n) {  // a leaf beyond the records
+          set_err(Wk.err_field(), ERR_INDEX);
+          have = false;
+        }
       }
       __syncwarp();
       lq_n -= tk;
