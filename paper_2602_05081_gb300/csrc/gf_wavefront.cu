@@ -563,106 +563,96 @@ __device__ __forceinline__ void render_paths(const Work& Wk, const float* env, W
   S.pix = -1;
   S.kind = 0;
   S.acc = 0;
+  S.allow = ~0ull;
 
-  // begin the next sample of the lane's pixel (or the next pixel); kind = 0 if none left
-  auto begin_sample = [&]() {
-    for (;;) {
-      if (S.pix < 0) {
-        int rq = 0, pix = -1, s0 = 0, s1 = 0;
-        if (!Wk.next(rq, pix, s0, s1)) {
-          S.pix = -1;
-          S.kind = 0;
-          return;
-        }
-        const PathParams& P = Wk.params(rq);
-        S.rq = rq;
-        S.pix = pix;
-        S.s = s0;
-        S.s_end = s1;
-        S.acc = 0;
-        R.asset = Wk.asset(rq);
-        R.seed_lo = (uint32_t)P.seed;
-        R.seed_hi = (uint32_t)(P.seed >> 32);
-      }
-      const PathParams& P = Wk.params(S.rq);
-      if (S.s >= S.s_end) {
-        Wk.finish(S.rq, S.pix, S.acc);
-        S.pix = -1;
-        continue;
-      }
-      const DevField& F = Wk.field(R.asset);
-      const int px = S.pix % P.cam.W, py = S.pix / P.cam.W;
-      float3 o, v;
-      camera_ray(P.cam, P.seed, px, py, S.s, o, v);
-      S.b = 0;
-      S.thr = 1.f;
-      S.Lsum = 0.f;
-      S.allow = fov_cells(F, P, v, (uint32_t)S.pix, (uint32_t)S.s);
-      Mask m = sample_mask(F, P.lod, v, P.seed, (uint32_t)S.pix, (uint32_t)S.s, 0, TAG_MASK);
-      m.bits &= S.allow;
-      cnt.rays += 1;
-      if (start_ray(F, R, S, 1, o, v, m, (uint32_t)S.pix,
-                    stream_word((uint32_t)S.s, 0, TAG_TRACK)))
-        return;
-      // the camera ray misses the field: the sample is 0
-      S.s += 1;
-    }
-  };
-  // the lane's current ray is finished: move the path on
-  auto finish_ray = [&](bool hit, float th) {
-    const PathParams& P = Wk.params(S.rq);
-    const DevField& F = Wk.field(R.asset);
-    for (;;) {
-      if (S.kind == 1) {
-        if (!hit) {
-          S.acc += fix_sample(S.Lsum);
-          S.s += 1;
-          begin_sample();
-          return;
-        }
-        const float3 x = make_float3(S.o.x + th * S.v.x, S.o.y + th * S.v.y, S.o.z + th * S.v.z);
+  // Move the lane's path on from its finished ray (hit: a collision at th on a
+  // tracking ray; kind 0: the lane has no path yet) until a new ray starts or
+  // no work is left: collision -> NEE, NEE -> isotropic scattering, escape or
+  // the last bounce -> the next sample (or pixel).  Every kind of ray is
+  // started from one site, which keeps the loop small for the instruction cache.
+  auto advance = [&](bool hit, float th) {
+    for (int guard = 0; guard < (1 << 20); ++guard) {
+      int kind = 0;  // the ray to start: 1 tracking (camera or bounce), 2 NEE
+      float3 ro = S.o, rv = S.v;
+      bool nee = false;
+      if (S.kind == 1 && hit) {
+        // collision: next-event estimation towards the light
+        const PathParams& P = Wk.params(S.rq);
+        ro = make_float3(S.o.x + th * S.v.x, S.o.y + th * S.v.y, S.o.z + th * S.v.z);
+        rv = P.light;
         S.thr *= P.albedo;
         S.T = 1.f;
-        Mask mn = sample_mask(F, P.lod_nee, P.light, P.seed, (uint32_t)S.pix, (uint32_t)S.s,
-                              (uint32_t)S.b, TAG_NEE_MASK);
-        mn.bits &= S.allow;
-        cnt.rays += 1;
-        if (start_ray(F, R, S, 2, x, P.light, mn, (uint32_t)S.pix,
-                      stream_word((uint32_t)S.s, (uint32_t)S.b, TAG_NEE)))
-          return;
-        // NEE ray misses every primitive: T = 1
-        S.o = x;
+        kind = 2;
+        nee = true;
+      } else if (S.kind == 2) {
+        // NEE finished with transmittance S.T: add it, then scatter isotropically
+        const PathParams& P = Wk.params(S.rq);
+        S.Lsum += S.thr * P.irradiance * S.T * inv4pi;
+        const uint4 y = rng4(P.seed, 0, kNoPrim, (uint32_t)S.pix,
+                             stream_word((uint32_t)S.s, (uint32_t)S.b, TAG_SCATTER));
+        const float z = 1.0f - 2.0f * u01(y.x);
+        const float rr = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+        float sn, cs;
+        sincosf(2.0f * 3.14159265358979f * u01(y.y), &sn, &cs);
+        S.b += 1;
+        if (S.b < P.max_bounces) {
+          rv = make_float3(rr * cs, rr * sn, z);
+          kind = 1;
+        }
       }
-      // S.kind == 2: NEE finished with transmittance S.T
-      S.Lsum += S.thr * P.irradiance * S.T * inv4pi;
-      const uint4 y = rng4(P.seed, 0, kNoPrim, (uint32_t)S.pix,
-                           stream_word((uint32_t)S.s, (uint32_t)S.b, TAG_SCATTER));
-      const float z = 1.0f - 2.0f * u01(y.x);
-      const float rr = sqrtf(fmaxf(0.0f, 1.0f - z * z));
-      float sn, cs;
-      sincosf(2.0f * 3.14159265358979f * u01(y.y), &sn, &cs);
-      const float3 nv = make_float3(rr * cs, rr * sn, z);
-      S.b += 1;
-      if (S.b >= P.max_bounces) {
-        S.acc += fix_sample(S.Lsum);
-        S.s += 1;
-        begin_sample();
-        return;
+      if (kind == 0) {
+        // the sample is over (escape or last bounce): the next sample, or pixel
+        if (S.kind != 0) {
+          S.acc += fix_sample(S.Lsum);
+          S.s += 1;
+        }
+        for (;;) {
+          if (S.pix < 0) {
+            int rq = 0, pix = -1, s0 = 0, s1 = 0;
+            if (!Wk.next(rq, pix, s0, s1)) {
+              S.pix = -1;
+              S.kind = 0;
+              return;
+            }
+            const PathParams& P = Wk.params(rq);
+            S.rq = rq;
+            S.pix = pix;
+            S.s = s0;
+            S.s_end = s1;
+            S.acc = 0;
+            R.asset = Wk.asset(rq);
+            R.seed_lo = (uint32_t)P.seed;
+            R.seed_hi = (uint32_t)(P.seed >> 32);
+          }
+          if (S.s < S.s_end) break;
+          Wk.finish(S.rq, S.pix, S.acc);
+          S.pix = -1;
+        }
+        const PathParams& P = Wk.params(S.rq);
+        camera_ray(P.cam, P.seed, S.pix % P.cam.W, S.pix / P.cam.W, S.s, ro, rv);
+        S.b = 0;
+        S.thr = 1.f;
+        S.Lsum = 0.f;
+        S.allow = fov_cells(Wk.field(R.asset), P, rv, (uint32_t)S.pix, (uint32_t)S.s);
+        kind = 1;
       }
-      const float3 xo = S.o;
-      Mask m = sample_mask(F, P.lod, nv, P.seed, (uint32_t)S.pix, (uint32_t)S.s,
-                           (uint32_t)S.b, TAG_MASK);
+      const PathParams& P = Wk.params(S.rq);
+      const DevField& F = Wk.field(R.asset);
+      Mask m = sample_mask(F, nee ? P.lod_nee : P.lod, rv, P.seed, (uint32_t)S.pix, (uint32_t)S.s,
+                           (uint32_t)S.b, nee ? TAG_NEE_MASK : TAG_MASK);
       m.bits &= S.allow;
       cnt.rays += 1;
-      if (start_ray(F, R, S, 1, xo, nv, m, (uint32_t)S.pix,
-                    stream_word((uint32_t)S.s, (uint32_t)S.b, TAG_TRACK)))
+      if (start_ray(F, R, S, kind, ro, rv, m, (uint32_t)S.pix,
+                    stream_word((uint32_t)S.s, (uint32_t)S.b, nee ? TAG_NEE : TAG_TRACK)))
         return;
-      S.kind = 1;
-      hit = false;  // the scattered ray leaves the field at once
+      // the ray misses every primitive: it is over at once (no collision; T = 1 for NEE)
+      hit = false;
     }
+    set_err(Wk.err_field(), ERR_GUARD);
+    S.kind = 0;
   };
 
-  begin_sample();
+  advance(false, 0.f);
   for (int guard = 0; guard < (1 << 30); ++guard) {
     const bool want = S.kind != 0;
     if (!__any_sync(kFull, want)) break;
@@ -702,51 +692,46 @@ __device__ __forceinline__ void render_paths(const Work& Wk, const float* env, W
     GF_TIC(t_eval);
     if (__any_sync(kFull, want && n > 0)) eval_stored(Q, wch, env, lane, cnt);
     if (lane == 0) GF_TOC(cnt, 3, t_eval);
-    // ---- decisions
+    // ---- decisions: the window either continues the ray or finishes it
     GF_TIC(t_dec);
+    bool fin = false, fhit = false;
+    float fth = 0.f;
     if (want) {
       const bool last = R.te >= S.t1;
+      bool next_window = false;
       if (ovf) {
         const float w = R.te - R.ta;
         if (w <= 1e-6f * (1.0f + fabsf(R.ta))) {
           // more than kPK points at one t: give up on this ray
           set_err(Wk.err_field(), ERR_POINTS);
-          finish_ray(false, 0.f);
+          fin = true;
         } else {
           R.te = R.ta + 0.5f * w;
           S.step = 0.5f * w;
         }
       } else if (S.kind == 1) {
-        float th = 0.f;
-        bool acc = false;
-        for (int i = 0; i < n && !acc; ++i) {
+        for (int i = 0; i < n && !fhit; ++i) {
           if (R.pu[i] * R.kb[i] < fmaxf(R.kap[i], 0.f)) {
-            acc = true;
-            th = R.pt[i];
+            fhit = true;
+            fth = R.pt[i];
           }
         }
-        if (acc) {
-          finish_ray(true, th);
-        } else if (!last) {
-          R.ta = R.te;
-          R.te = fminf(S.t1, R.ta + S.step);
-          if (R.te >= S.t1) R.te = S.t1 * (1.0f + 1e-7f) + 1e-30f;
-        } else {
-          finish_ray(false, 0.f);
-        }
+        fin = fhit || last;
+        next_window = !fin;
       } else {
         for (int i = 0; i < n; ++i)
           if (R.kb[i] > 0.f) S.T *= 1.f - fmaxf(R.kap[i], 0.f) / R.kb[i];
-        if (!last) {
-          S.step *= 2.0f;
-          R.ta = R.te;
-          R.te = fminf(S.t1, R.ta + S.step);
-          if (R.te >= S.t1) R.te = S.t1 * (1.0f + 1e-7f) + 1e-30f;
-        } else {
-          finish_ray(false, 0.f);
-        }
+        if (!last) S.step *= 2.0f;
+        fin = last;
+        next_window = !last;
+      }
+      if (next_window) {
+        R.ta = R.te;
+        R.te = fminf(S.t1, R.ta + S.step);
+        if (R.te >= S.t1) R.te = S.t1 * (1.0f + 1e-7f) + 1e-30f;
       }
     }
+    if (fin) advance(fhit, fth);
     __syncwarp();
     if (lane == 0) GF_TOC(cnt, 4, t_dec);
   }
