@@ -263,8 +263,10 @@ __device__ void warp_phase(const Work& Wk, WarpQ& Q, bool want, uint32_t lane, c
     }
     const bool any_trav = sp > 0;
     if (lane == 0) GF_TOC(cnt, 0, t_step);
-    // ---------------- leaf rounds: 32 leaves of any slots' rays at a time
-    while (lq_n >= 32 || (!any_trav && lq_n > 0)) {
+    // ---------------- leaf rounds: 32 leaves of any slots' rays at a time; once
+    // the traversal is over, the last leaves and then the last chords (one
+    // walk site, for the instruction cache)
+    while (lq_n >= 32 || (!any_trav && (lq_n > 0 || cq_n > 0))) {
       const int tk = lq_n < 32 ? lq_n : 32;
       bool have = (int)lane < tk;
       int j = 0, own = 0;
@@ -323,28 +325,18 @@ __device__ void warp_phase(const Work& Wk, WarpQ& Q, bool want, uint32_t lane, c
       __syncwarp();
       if (lane == 0) GF_TOC(cnt, 1, t_leaf);
       GF_TIC(t_walk);
-      while (cq_n >= 32) {
-        const bool hv = true;
-        ChordItem cw = Q.cq[cq_n - 32 + (int)lane];
+      const bool drain = !any_trav && lq_n == 0;
+      while (cq_n >= 32 || (drain && cq_n > 0)) {
+        const int tw = cq_n < 32 ? cq_n : 32;
+        const bool hv = (int)lane < tw;
+        ChordItem cw;
+        if (hv) cw = Q.cq[cq_n - tw + (int)lane];
         __syncwarp();
-        cq_n -= 32;
+        cq_n -= tw;
         if (hv) walk_chord(Wk.err_field(), Q, cw, env, cnt.points);
         __syncwarp();
       }
       if (lane == 0) GF_TOC(cnt, 2, t_walk);
-    }
-    if (!any_trav && lq_n == 0) {
-      // traversal over and no leaf left: walk the remaining chords
-      while (cq_n > 0) {
-        const int tk = cq_n < 32 ? cq_n : 32;
-        const bool hv = (int)lane < tk;
-        ChordItem cw;
-        if (hv) cw = Q.cq[cq_n - tk + (int)lane];
-        __syncwarp();
-        cq_n -= tk;
-        if (hv) walk_chord(Wk.err_field(), Q, cw, env, cnt.points);
-        __syncwarp();
-      }
     }
     if (!any_trav && lq_n == 0 && cq_n == 0) break;
   }
@@ -463,10 +455,9 @@ __device__ void eval_stored(WarpQ& Q, const float4* wch, const float* env, uint3
     const float S = __int_as_float((127 + 54 - ex) << 23);     // 2^(54 - ex)
     const float invS = __int_as_float((127 - 54 + ex) << 23);  // 2^(ex - 54)
     const float4* base = wch + (size_t)s * kSlotCh * kRecF4;
-    // the point count is the same for every lane: size the unrolled loops to it
-    if (ns <= 2) eval_slot<2>(R, base, ns, S, invS, env, lane, cnt);
-    else if (ns <= 4) eval_slot<4>(R, base, ns, S, invS, env, lane, cnt);
-    else eval_slot<kPK>(R, base, ns, S, invS, env, lane, cnt);
+    // one copy of the unrolled loop (points beyond ns sit at t = inf): copies
+    // sized to the point count cost more in instruction fetch than they save
+    eval_slot<kPK>(R, base, ns, S, invS, env, lane, cnt);
   }
   __syncwarp();
 }
@@ -652,88 +643,92 @@ __device__ __forceinline__ void render_paths(const Work& Wk, const float* env, W
     S.kind = 0;
   };
 
-  advance(false, 0.f);
+  // the first pass takes each lane's first work; every later pass is one window
+  bool first = true;
   for (int guard = 0; guard < (1 << 30); ++guard) {
-    const bool want = S.kind != 0;
-    if (!__any_sync(kFull, want)) break;
-    // ---- pass 1: tentative points of the window
-    R.npts = 0;
-    R.nch = 0;
-    R.hmax = 0;
-    __syncwarp();
-    warp_phase(Wk, Q, want, lane, env, wch, cnt);
-    // owner: a window whose points overflowed the slots is halved and redone;
-    // otherwise its points are sorted by t for the decisions
-    int n = 0;
-    bool ovf = false;
-    if (want) {
-      ovf = R.npts > kPK || R.nch > kSlotCh;
-      n = ovf ? 0 : R.npts;
-      for (int k = 1; k < n; ++k) {
-        const float t = R.pt[k], u = R.pu[k];
-        int q = k;
-        while (q > 0 && R.pt[q - 1] > t) {
-          R.pt[q] = R.pt[q - 1];
-          R.pu[q] = R.pu[q - 1];
-          --q;
-        }
-        R.pt[q] = t;
-        R.pu[q] = u;
-      }
-      R.npts = n;
-      for (int i = 0; i < n; ++i) {
-        R.kap[i] = 0.f;
-        R.kb[i] = 0.f;
-      }
-    }
-    cnt.windows += want ? 1ull : 0ull;
-    __syncwarp();
-    // ---- kappa and kappa_bar at the points, from the stored chords
-    GF_TIC(t_eval);
-    if (__any_sync(kFull, want && n > 0)) eval_stored(Q, wch, env, lane, cnt);
-    if (lane == 0) GF_TOC(cnt, 3, t_eval);
-    // ---- decisions: the window either continues the ray or finishes it
-    GF_TIC(t_dec);
-    bool fin = false, fhit = false;
+    bool fin = first, fhit = false;
     float fth = 0.f;
-    if (want) {
-      const bool last = R.te >= S.t1;
-      bool next_window = false;
-      if (ovf) {
-        const float w = R.te - R.ta;
-        if (w <= 1e-6f * (1.0f + fabsf(R.ta))) {
-          // more than kPK points at one t: give up on this ray
-          set_err(Wk.err_field(), ERR_POINTS);
-          fin = true;
-        } else {
-          R.te = R.ta + 0.5f * w;
-          S.step = 0.5f * w;
-        }
-      } else if (S.kind == 1) {
-        for (int i = 0; i < n && !fhit; ++i) {
-          if (R.pu[i] * R.kb[i] < fmaxf(R.kap[i], 0.f)) {
-            fhit = true;
-            fth = R.pt[i];
+    const bool want = S.kind != 0;
+    if (!first && !__any_sync(kFull, want)) break;
+    if (!first) {
+      // ---- pass 1: tentative points of the window
+      R.npts = 0;
+      R.nch = 0;
+      R.hmax = 0;
+      __syncwarp();
+      warp_phase(Wk, Q, want, lane, env, wch, cnt);
+      // owner: a window whose points overflowed the slots is halved and redone;
+      // otherwise its points are sorted by t for the decisions
+      int n = 0;
+      bool ovf = false;
+      if (want) {
+        ovf = R.npts > kPK || R.nch > kSlotCh;
+        n = ovf ? 0 : R.npts;
+        for (int k = 1; k < n; ++k) {
+          const float t = R.pt[k], u = R.pu[k];
+          int q = k;
+          while (q > 0 && R.pt[q - 1] > t) {
+            R.pt[q] = R.pt[q - 1];
+            R.pu[q] = R.pu[q - 1];
+            --q;
           }
+          R.pt[q] = t;
+          R.pu[q] = u;
         }
-        fin = fhit || last;
-        next_window = !fin;
-      } else {
-        for (int i = 0; i < n; ++i)
-          if (R.kb[i] > 0.f) S.T *= 1.f - fmaxf(R.kap[i], 0.f) / R.kb[i];
-        if (!last) S.step *= 2.0f;
-        fin = last;
-        next_window = !last;
+        R.npts = n;
+        for (int i = 0; i < n; ++i) {
+          R.kap[i] = 0.f;
+          R.kb[i] = 0.f;
+        }
       }
-      if (next_window) {
-        R.ta = R.te;
-        R.te = fminf(S.t1, R.ta + S.step);
-        if (R.te >= S.t1) R.te = S.t1 * (1.0f + 1e-7f) + 1e-30f;
+      cnt.windows += want ? 1ull : 0ull;
+      __syncwarp();
+      // ---- kappa and kappa_bar at the points, from the stored chords
+      GF_TIC(t_eval);
+      if (__any_sync(kFull, want && n > 0)) eval_stored(Q, wch, env, lane, cnt);
+      if (lane == 0) GF_TOC(cnt, 3, t_eval);
+      // ---- decisions: the window either continues the ray or finishes it
+      GF_TIC(t_dec);
+      if (want) {
+        const bool last = R.te >= S.t1;
+        bool next_window = false;
+        if (ovf) {
+          const float w = R.te - R.ta;
+          if (w <= 1e-6f * (1.0f + fabsf(R.ta))) {
+            // more than kPK points at one t: give up on this ray
+            set_err(Wk.err_field(), ERR_POINTS);
+            fin = true;
+          } else {
+            R.te = R.ta + 0.5f * w;
+            S.step = 0.5f * w;
+          }
+        } else if (S.kind == 1) {
+          for (int i = 0; i < n && !fhit; ++i) {
+            if (R.pu[i] * R.kb[i] < fmaxf(R.kap[i], 0.f)) {
+              fhit = true;
+              fth = R.pt[i];
+            }
+          }
+          fin = fhit || last;
+          next_window = !fin;
+        } else {
+          for (int i = 0; i < n; ++i)
+            if (R.kb[i] > 0.f) S.T *= 1.f - fmaxf(R.kap[i], 0.f) / R.kb[i];
+          if (!last) S.step *= 2.0f;
+          fin = last;
+          next_window = !last;
+        }
+        if (next_window) {
+          R.ta = R.te;
+          R.te = fminf(S.t1, R.ta + S.step);
+          if (R.te >= S.t1) R.te = S.t1 * (1.0f + 1e-7f) + 1e-30f;
+        }
       }
+      if (lane == 0) GF_TOC(cnt, 4, t_dec);
     }
+    first = false;
     if (fin) advance(fhit, fth);
     __syncwarp();
-    if (lane == 0) GF_TOC(cnt, 4, t_dec);
   }
   flush_counters(Wk.err_field(), cnt, lane);
 }
