@@ -548,7 +548,7 @@ gf_status gf_set_lod_camera(gf_field* h, const gf_camera* cam, gf_stream stream)
   GF_CUDA(cudaStreamSynchronize(s), "sync");
   F.dev.cells_on = cam ? cells : ~0ull;
   F.camera_lod = cam != nullptr;
-  if (reduced) F.dev.ext2 = cam ? F.keff2 : F.ext2;
+  if (reduced) F.dev.ext2 = cam ? F.keff2 : (F.opts.clamp_eps > 0.f ? F.ext2 : nullptr);
   return GF_OK;
 }
 

@@ -585,7 +585,9 @@ cudaError_t build_bvh(Field& F, cudaStream_t s) {
     }
   }
   F.dev.rec = F.rec;
-  F.dev.ext2 = F.ext2;  // read by the reduced-precision path (FP32 records carry their own)
+  // read by the reduced-precision path (FP32 records carry their own); without
+  // adaptive clamping every support radius is k_sigma and none is read
+  F.dev.ext2 = F.opts.clamp_eps > 0.f ? F.ext2 : nullptr;
   F.dev.nodes = F.nodes;
   F.dev.nodes4 = F.nodes4;
   F.dev.n_nodes4 = n >= 2 ? F.n_nodes4 : 0;
@@ -637,6 +639,11 @@ __global__ void k_pack16(const __grid_constant__ Pack16Args A) {
   qn = rsqrtf(qn);
   int qs[4];
   for (int k = 0; k < 4; ++k) qs[k] = (int)rintf(q[k] * qn * 32767.f);
+  // the decoder's rotation is M(qs) / |qs|^2 with 1/32767^2 applied there:
+  // the inverse scales carry the remaining factor 32767^2 / |qs|^2 (~1)
+  unsigned long long qq = 0ull;  // exact: at most 4 x 32767^2
+  for (int k = 0; k < 4; ++k) qq += (unsigned long long)((long long)qs[k] * qs[k]);
+  const float fold = (32767.0f * 32767.0f) / (float)qq;
   float s[3];
   for (int k = 0; k < 3; ++k) s[k] = expf(A.ls[3 * i + k]);
   const float w = q[0] * qn, x = q[1] * qn, y = q[2] * qn, z = q[3] * qn;
@@ -662,8 +669,8 @@ __global__ void k_pack16(const __grid_constant__ Pack16Args A) {
   r0.x = mc[0] | (mc[1] << 16);
   r0.y = mc[2] | ((uint32_t)(qs[0] & 0xFFFF) << 16);
   r0.z = (uint32_t)(qs[1] & 0xFFFF) | ((uint32_t)(qs[2] & 0xFFFF) << 16);
-  r0.w = (uint32_t)(qs[3] & 0xFFFF) | (to_half_bits(1.f / s[0], A.prec) << 16);
-  r1.x = to_half_bits(1.f / s[1], A.prec) | (to_half_bits(1.f / s[2], A.prec) << 16);
+  r0.w = (uint32_t)(qs[3] & 0xFFFF) | (to_half_bits(fold / s[0], A.prec) << 16);
+  r1.x = to_half_bits(fold / s[1], A.prec) | (to_half_bits(fold / s[2], A.prec) << 16);
   r1.y = to_half_bits(kw[0], A.prec) | (to_half_bits(kw[1], A.prec) << 16);
   r1.z = to_half_bits(kw[2], A.prec) | (to_half_bits(amp, A.prec) << 16);
   r1.w = pc | (cell << 16);

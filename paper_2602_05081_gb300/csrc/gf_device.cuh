@@ -94,7 +94,8 @@ struct DevField {
   const float* gl;         // Gauss-Legendre nodes then weights (2 x kGLTotal)
   Weideman wd;             // Faddeeva expansion (closed-form chord integrals)
   const float* ext2;       // reduced-precision records: support radius squared per primitive,
-                           // BVH order, -1 = not in the mixture (FP32 records carry their own)
+                           // BVH order, -1 = not in the mixture (FP32 records carry their own);
+                           // null when every radius is k_sigma (no clamping, no camera selection)
   unsigned long long cells_on;  // cells holding a primitive of the mixture (all ones by default)
   int* err;
   unsigned long long* stats;  // rays, chords, evals, nodes, points
@@ -362,12 +363,12 @@ __device__ __forceinline__ bool chord_setup16(const DevField& F, uint4 r0, uint4
   const float k2 = half_bits_to_float(r1.z & 0xFFFFu, prec);
   const float A = half_bits_to_float(r1.z >> 16, prec);
   const float phi = u16_float(r1.w & 0xFFFFu) * (6.28318530717958647692f / 65536.0f);
-  // rotation of the unnormalised quaternion, R = M(q) / |q|^2: the 1/|q|^2
-  // is folded into the inverse scales
-  const float in2 = __frcp_rn(qw * qw + qx * qx + qy * qy + qz * qz);
-  const float is0 = half_bits_to_float(r0.w >> 16, prec) * in2;
-  const float is1 = half_bits_to_float(r1.x & 0xFFFFu, prec) * in2;
-  const float is2 = half_bits_to_float(r1.x >> 16, prec) * in2;
+  // rotation of the quaternion codes, R = M(q) / |q|^2: the record's inverse
+  // scales carry 32767^2 / |q|^2 (folded at pack time), so 1/32767^2 remains
+  const float kq = 1.0f / (32767.0f * 32767.0f);
+  const float is0 = half_bits_to_float(r0.w >> 16, prec) * kq;
+  const float is1 = half_bits_to_float(r1.x & 0xFFFFu, prec) * kq;
+  const float is2 = half_bits_to_float(r1.x >> 16, prec) * kq;
   const float R00 = qw * qw + qx * qx - qy * qy - qz * qz;
   const float R01 = 2.f * (qx * qy - qw * qz), R02 = 2.f * (qx * qz + qw * qy);
   const float R10 = 2.f * (qx * qy + qw * qz);
@@ -386,28 +387,16 @@ __device__ __forceinline__ bool chord_setup16(const DevField& F, uint4 r0, uint4
   const float w0z = is2 * fmaf(R02, d0x, fmaf(R12, d0y, R22 * d0z));
   const float ia = __frcp_rn(a);
   const float tc = -fmaf(ux, w0x, fmaf(uy, w0y, uz * w0z)) * ia;
-  // offset at tc in world space with compensated arithmetic, then whitened
-  float ex, ey, ez;
-  {
-    float sx = d0x, bb = __fsub_rn(sx, o.x);
-    ex = __fsub_rn(__fsub_rn(o.x, __fsub_rn(sx, bb)), __fadd_rn(mu.x, bb));
-    sx = d0y; bb = __fsub_rn(sx, o.y);
-    ey = __fsub_rn(__fsub_rn(o.y, __fsub_rn(sx, bb)), __fadd_rn(mu.y, bb));
-    sx = d0z; bb = __fsub_rn(sx, o.z);
-    ez = __fsub_rn(__fsub_rn(o.z, __fsub_rn(sx, bb)), __fadd_rn(mu.z, bb));
-  }
-  const float prx = __fmul_rn(tc, v.x), pry = __fmul_rn(tc, v.y), prz = __fmul_rn(tc, v.z);
-  const float px = __fadd_rn(__fadd_rn(d0x, prx), __fadd_rn(ex, fmaf(tc, v.x, -prx)));
-  const float py = __fadd_rn(__fadd_rn(d0y, pry), __fadd_rn(ey, fmaf(tc, v.y, -pry)));
-  const float pz = __fadd_rn(__fadd_rn(d0z, prz), __fadd_rn(ez, fmaf(tc, v.z, -prz)));
-  const float pwx = is0 * fmaf(R00, px, fmaf(R10, py, R20 * pz));
-  const float pwy = is1 * fmaf(R01, px, fmaf(R11, py, R21 * pz));
-  const float pwz = is2 * fmaf(R02, px, fmaf(R12, py, R22 * pz));
+  // whitened offset at tc, W (o + tc v - mu) = W d0 + tc W v: its FP32 rounding,
+  // ~2^-24 |W d0|, stays below the record's own (the FP16 inverse scales round by
+  // 2^-12 of the whitened offset), so no compensated world offset is needed here
+  const float pwx = fmaf(tc, ux, w0x), pwy = fmaf(tc, uy, w0y), pwz = fmaf(tc, uz, w0z);
+  const float px = fmaf(tc, v.x, d0x), py = fmaf(tc, v.y, d0y), pz = fmaf(tc, v.z, d0z);
   const float b = fmaf(ux, pwx, fmaf(uy, pwy, uz * pwz));
   const float g = fmaf(pwx, pwx, fmaf(pwy, pwy, pwz * pwz));
   const float dts = -b * ia;
   const float qmin = fmaf(b, dts, g);
-  const float disc = __ldg(F.ext2 + j) - qmin;
+  const float disc = (F.ext2 ? __ldg(F.ext2 + j) : F.k2) - qmin;
   if (!(disc > 0.0f)) return false;
   const float hw = sqrtf(disc * ia);
   const float lo = fmaxf(dts - hw, tmin - tc);

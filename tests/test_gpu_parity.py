@@ -783,7 +783,8 @@ def test_reduced_precision_transmittance(api, ctx, prec, u):
     A exp(-|z|^2/2) cos(k_W . z + phi).  The record perturbs
       z      by dz <= k u (1/s rounded) + sqrt(3) h_mu / s_min (u16 means,
              half step h_mu) + (2/32767) k s_max / s_min (snorm16 quaternion:
-             rotation angle error <= 2 |dq|),
+             rotation angle error <= 2 |dq|) + 4 2^-24 |o - mu| / s_min (the
+             whitened offset formed as W (o - mu) + tc W v in FP32),
       A      by u A,  k_W by u |k_W|,  phi by pi/65536 (u16 phase),
     so |d integrand| <= A exp(-q/2) [u + k dz + k u |k_W| + |k_W| dz + pi/65536]
     and, summed over a ray's chords, |d tau| <= C E with E the envelope
@@ -807,7 +808,9 @@ def test_reduced_precision_transmittance(api, ctx, prec, u):
     mu = p["mu"].astype(np.float64)
     h_mu = (mu.max(0) - mu.min(0)).max() / 65535.0 / 2.0
     kw = np.max(np.linalg.norm(p["omega"], axis=1) * s.max(1))
-    dz = k * u + np.sqrt(3.0) * h_mu / s_min + (2.0 / 32767.0) * k * s_max / s_min
+    d0 = np.max(np.linalg.norm(o[:, None, :].astype(np.float64) - mu[None], axis=2))
+    dz = k * u + np.sqrt(3.0) * h_mu / s_min + (2.0 / 32767.0) * k * s_max / s_min + \
+        4.0 * 2.0 ** -24 * d0 / s_min
     C_rel = u + k * dz + k * u * kw + kw * dz + np.pi / 65536.0
     n_ch = np.zeros(o.shape[0])
     for r in range(o.shape[0]):
