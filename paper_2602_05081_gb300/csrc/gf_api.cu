@@ -396,7 +396,7 @@ gf_status gf_load_field(gf_ctx* ctx, const gf_params* p, const gf_field_opts* op
         (e = A((void**)&F.rec_orig, 64 * n)) || (e = A((void**)&F.box_orig, 24 * n)) ||
         (e = A((void**)&F.kw_orig, 4 * n)) || (e = A((void**)&F.labels, 3 * n)) ||
         (e = A((void**)&F.err, 4)) || (e = A((void**)&F.stats, 8 * kNumStats)) ||
-        (e = A((void**)&F.counter, 16)) || (e = A((void**)&F.cell_acc, 136 * 4)) ||
+        (e = A((void**)&F.counter, 16)) || (e = A((void**)&F.cell_acc, sizeof(CellAcc))) ||
         (e = A((void**)&F.gl, 2 * kGLTotal * sizeof(float))))
       break;
     if ((e = A((void**)&F.ext2_orig, 4 * n)) || (e = A((void**)&F.ext2, 4 * n))) break;
@@ -413,7 +413,7 @@ gf_status gf_load_field(gf_ctx* ctx, const gf_params* p, const gf_field_opts* op
       break;
     if (p->band && (e = cp(band_dev, p->band, n))) break;
     if ((e = cudaMemsetAsync(F.err, 0, 4, s)) || (e = cudaMemsetAsync(F.stats, 0, 8 * kNumStats, s)) ||
-        (e = cudaMemsetAsync(F.cell_acc, 0, 136 * 4, s)))
+        (e = cudaMemsetAsync(F.cell_acc, 0, sizeof(CellAcc), s)))
       break;
   } while (0);
   if (e != cudaSuccess) {
@@ -432,9 +432,9 @@ gf_status gf_load_field(gf_ctx* ctx, const gf_params* p, const gf_field_opts* op
   dp.band = (const uint8_t*)band_dev;
   e = launch_pack(F, dp, s);
   int herr = 0;
-  float acc[136];
+  CellAcc acc;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, F.err, 4, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(acc, F.cell_acc, 136 * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&acc, F.cell_acc, sizeof(CellAcc), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) F.mem.release(band_dev, s);
   if (e != cudaSuccess) {
@@ -453,12 +453,18 @@ gf_status gf_load_field(gf_ctx* ctx, const gf_params* p, const gf_field_opts* op
   F.dev.k2 = opts->k_sigma * opts->k_sigma;
   F.dev.occupied = 0;
   for (int c = 0; c < kMaxCells; ++c) {
-    float cnt = acc[64 + c];
-    if (cnt > 0.f) F.dev.occupied |= 1ull << c;
-    F.dev.kbar[c] = cnt > 0.f ? acc[c] / cnt : 0.f;
+    const unsigned long long cnt = acc.count[c];
+    if (cnt > 0) F.dev.occupied |= 1ull << c;
+    F.dev.kbar[c] = cnt > 0 ? (float)((double)acc.kw_fix[c] *
+                                      std::ldexp(1.0, cell_fix_exp(acc.kw_max) - 36) / (double)cnt)
+                            : 0.f;
   }
   for (int k = 0; k < 8; ++k) F.dev.env[k] = (float)std::exp(-0.5 * k * k);
-  for (int b = 0; b < 8; ++b) F.dev.band_wmax[b] = acc[128 + b];  // 0 for an empty band
+  for (int b = 0; b < 8; ++b) {  // 0 for an empty band
+    float w;
+    std::memcpy(&w, &acc.band_wmax[b], 4);
+    F.dev.band_wmax[b] = w;
+  }
   F.dev.err = F.err;
   F.dev.stats = F.stats;
   F.dev.gl = F.gl;

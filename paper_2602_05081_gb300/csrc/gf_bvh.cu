@@ -29,7 +29,7 @@ struct PackArgs {
   float* kw;
   float* ext2;      // support radius squared per primitive (k^2 or adaptive)
   uint8_t* labels;  // band[N], cone[N], cell[N]
-  float* cell_acc;  // sum |k_W| [64], count [64], largest |omega| per band [8] (bits)
+  CellAcc* cell_acc;
   int* err;
 };
 
@@ -141,11 +141,22 @@ __global__ void k_pack(const __grid_constant__ PackArgs A) {
   A.labels[i] = (uint8_t)band;
   A.labels[A.p.n + i] = (uint8_t)cone;
   A.labels[2 * A.p.n + i] = (uint8_t)cell;
-  atomicAdd(A.cell_acc + cell, kn);
-  atomicAdd(A.cell_acc + 64 + cell, 1.f);
-  // largest world carrier |omega| per band (non-negative floats order as their bits)
-  atomicMax(reinterpret_cast<unsigned int*>(A.cell_acc + 128 + band),
+  // largest |k_W| and largest world carrier |omega| per band (the per-cell sums
+  // follow in k_cell_sums, on the scale the first one sets)
+  atomicMax(&A.cell_acc->kw_max, __float_as_uint(kn));
+  atomicMax(&A.cell_acc->band_wmax[band],
             __float_as_uint(sqrtf(om[0] * om[0] + om[1] * om[1] + om[2] * om[2])));
+}
+
+// per cell: the sum of |k_W| in exact fixed point and the member count
+__global__ void k_cell_sums(const float* kw, const uint8_t* cell, int64_t n, CellAcc* acc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int e = cell_fix_exp(acc->kw_max);
+  const float sc = __int_as_float((127 + 36 - e) << 23);  // 2^(36 - e)
+  const unsigned c = cell[i] & 63u;
+  atomicAdd(&acc->kw_fix[c], (unsigned long long)__float2ull_rn(kw[i] * sc));
+  atomicAdd(&acc->count[c], 1ull);
 }
 
 cudaError_t launch_pack(Field& F, const gf_params& P, cudaStream_t s) {
@@ -168,6 +179,7 @@ cudaError_t launch_pack(Field& F, const gf_params& P, cudaStream_t s) {
   A.err = F.err;
   int64_t blocks = (P.n + 127) / 128;
   k_pack<<<(unsigned)blocks, 128, 0, s>>>(A);
+  k_cell_sums<<<(unsigned)((P.n + 255) / 256), 256, 0, s>>>(A.kw, A.labels + 2 * P.n, P.n, A.cell_acc);
   return cudaGetLastError();
 }
 

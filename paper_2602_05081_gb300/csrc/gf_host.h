@@ -83,6 +83,24 @@ struct ChordParams {
   int* counter;
 };
 
+// Label statistics of a field, gathered at load time with integer atomics only,
+// so that they (and every render that uses them) do not depend on the order in
+// which threads arrive: per cell the sum of |k_W| in fixed point (units of
+// 2^(e - 36), 2^e above the largest |k_W|; at most 2^36 per kernel and 2^26
+// kernels) and the member count; per band the largest world carrier |omega|;
+// and the largest |k_W| (non-negative floats order as their bits).
+struct CellAcc {
+  unsigned long long kw_fix[64];
+  unsigned long long count[64];
+  unsigned int band_wmax[8];
+  unsigned int kw_max;
+};
+// exponent e of the fixed-point unit: 2^e > the largest |k_W| (bits mb), clamped
+// so that 2^(36 - e) is a normal float
+inline __host__ __device__ int cell_fix_exp(unsigned int mb) {
+  int e = (int)((mb >> 23) & 0xFFu) - 126;
+  return e < -60 ? -60 : (e > 100 ? 100 : e);
+}
 struct Field {
   Ctx ctx;                     // copy: a field outlives the gf_ctx it came from
   mutable DevMem mem;          // every device buffer of the field, through ctx.alloc
@@ -114,7 +132,7 @@ struct Field {
   int* err = nullptr;
   unsigned long long* stats = nullptr;
   int* counter = nullptr;
-  float* cell_acc = nullptr;    // per-cell |k_W| sums (64) and counts (64), band max |omega| (8)
+  CellAcc* cell_acc = nullptr;  // label statistics of the load (exact, order-free)
   int depth = 0;                // levels of internal nodes of the binary tree
   int64_t n_nodes4 = 0;         // four-wide nodes
   bool built = false;

@@ -11,10 +11,11 @@
 // queued chords are walked 32 at a time, drawing the chord's tentative points
 // of Sec. 3's per-segment majorant from its own Philox stream.  Points land in
 // the owner's buffer through shared-memory atomics.  kappa and kappa_bar at
-// the points are then summed from the stored records (the warp scans each
-// lane's list and reduces by shuffles), after which each lane takes its
-// delta-tracking or ratio-tracking decision and moves its path on (camera
-// ray -> collision -> NEE -> scattering).
+// the points are then summed from the stored records (the lanes share out the
+// (slot, chord) pairs of all slots and add into per-point sums in shared
+// memory), after which each lane takes its delta-tracking or
+// ratio-tracking decision and moves its path on (camera ray -> collision ->
+// NEE -> scattering).
 //
 // The tentative points are a function of the chords and their Philox streams
 // only, so results equal a per-ray formulation up to floating-point summation
@@ -29,13 +30,14 @@
 namespace gf {
 
 constexpr int kWWarps = 4;      // warps per block
+constexpr int kBlocksPerSM = 4; // resident blocks per SM the kernels are built for
 constexpr int kLeafQ = 160;     // queued leaves per warp (<= 31 left + 128 new)
 constexpr int kChordQ = 64;     // queued chords per warp (<= 31 left + 32 new)
 constexpr int kPK = 8;          // tentative points per lane and window
 constexpr int kSlotCh = 256;    // stored chords per lane and window (global scratch)
 constexpr int kRecF4 = 2;       // float4s per stored chord record
 
-// One slot per lane, 63 words: an odd stride keeps same-field accesses of the
+// One slot per lane, 47 words: an odd stride keeps same-field accesses of the
 // 32 slots in distinct shared-memory banks.
 struct LaneRay {
   float o[3], v[3], inv[3];
@@ -49,26 +51,38 @@ struct LaneRay {
   int npts;                     // points emitted in the window (may exceed kPK)
   int nch;                      // chords stored for the window (may exceed kSlotCh)
   int hmax;                     // bits of the largest chord peak h of the window (h >= 0)
-  float pt[kPK], pu[kPK], kap[kPK], kb[kPK];
+  float pt[kPK], pu[kPK];       // the window's tentative points (t, acceptance uniform)
 };
 static_assert(sizeof(LaneRay) % 8 == 4, "odd word stride");
 struct ChordItem {
   float tc, dtin, dtout, h, sa, dts, smax;
-  uint32_t orig;
-  int owner;
+  uint32_t orig_own;  // original primitive index | owning slot << 26
 };
+static_assert(sizeof(ChordItem) == 32, "chord items of 32 bytes");
 // Shared (node, slot) stack entries per warp.  A step pushes at most 128
 // entries (32 four-wide nodes); above kWStack - kStackMargin the warp goes
 // depth first (one entry per step, net growth <= 3 per tree level), so the
-// stack holds a full step plus 40 levels of descent.  Four blocks of four
-// warps fit one SM.
-constexpr int kWStack = 768;
+// stack holds a full step plus 40 levels of descent.
+constexpr int kWStack = 640;
 constexpr int kStackMargin = 248;
-struct WarpQ {
-  LaneRay r[32];
+struct TravQ {
   int stk[kWStack];   // (node << 5) | slot
   int lq[kLeafQ];     // (sorted primitive << 5) | slot
   ChordItem cq[kChordQ];
+};
+// The point evaluation that follows a traversal phase reuses the queues' space:
+// 64-bit fixed-point sums of kappa and kappa_bar per (slot, point), and the
+// running ends of the slots' chord lists.
+struct EvalQ {
+  unsigned long long kap[32 * kPK], kb[32 * kPK];
+  int end[33];  // chords of slots 0..s-1 to evaluate: end[s]
+};
+struct WarpQ {
+  LaneRay r[32];
+  union {
+    TravQ t;  // traversal phase
+    EvalQ e;  // point evaluation
+  };
 };
 
 __device__ __forceinline__ int ord_f(float f) {
@@ -106,7 +120,7 @@ __device__ __forceinline__ bool slot_chord(const DevField& F, const LaneRay& R, 
 // walk one queued chord: emit its tentative points in [ta, te) to the owner
 __device__ __forceinline__ void walk_chord(const DevField& F, WarpQ& Q, const ChordItem& c,
                                            const float* env, unsigned long long& npt) {
-  LaneRay& R = Q.r[c.owner];
+  LaneRay& R = Q.r[c.orig_own >> 26];
   const uint64_t seed = slot_seed(R);
   const float ta = R.ta, te = R.te;
   const float invs = 1.0f / c.sa;
@@ -120,7 +134,7 @@ __device__ __forceinline__ void walk_chord(const DevField& F, WarpQ& Q, const Ch
     else break;
   }
   for (uint32_t draw = 0; draw < (1u << 16); ++draw) {
-    const uint4 x = rng4(seed, draw, c.orig, R.ray, R.word);
+    const uint4 x = rng4(seed, draw, c.orig_own & kOrigMask, R.ray, R.word);
     float z = -__logf(1.0f - u01(x.x));
     bool emit = false;
     for (int q = 0; q < 2 * J + 2; ++q) {
@@ -171,8 +185,8 @@ __device__ void warp_phase(const Work& Wk, WarpQ& Q, bool want, uint32_t lane, c
     const int root = want ? Wk.field(Q.r[lane].asset).root : -1;
     const unsigned bs = __ballot_sync(kFull, want && root >= 0);
     const unsigned bl = __ballot_sync(kFull, want && root < 0);
-    if (want && root >= 0) Q.stk[__popc(bs & lt)] = (root << 5) | (int)lane;
-    if (want && root < 0) Q.lq[__popc(bl & lt)] = (0 << 5) | (int)lane;
+    if (want && root >= 0) Q.t.stk[__popc(bs & lt)] = (root << 5) | (int)lane;
+    if (want && root < 0) Q.t.lq[__popc(bl & lt)] = (0 << 5) | (int)lane;
     sp = __popc(bs);
     lq_n = __popc(bl);
     __syncwarp();
@@ -187,7 +201,7 @@ __device__ void warp_phase(const Work& Wk, WarpQ& Q, bool want, uint32_t lane, c
     GF_TIC(t_step);
     int take = sp < 32 ? sp : 32;
     if (sp > kWStack - kStackMargin) take = 1;  // near capacity: depth first
-    const int ent = (int)lane < take ? Q.stk[sp - take + (int)lane] : -1;
+    const int ent = (int)lane < take ? Q.t.stk[sp - take + (int)lane] : -1;
     __syncwarp();
     sp -= take;
     if (lane == 0) ++cnt.steps;
@@ -247,9 +261,9 @@ __device__ void warp_phase(const Work& Wk, WarpQ& Q, bool want, uint32_t lane, c
         const unsigned bl = __ballot_sync(kFull, h && ch[k] < 0);
         if (h && ch[k] >= 0) {
           const int pos = sp + np + __popc(bp & lt);
-          if (pos < kWStack) Q.stk[pos] = (ch[k] << 5) | slot;
+          if (pos < kWStack) Q.t.stk[pos] = (ch[k] << 5) | slot;
         }
-        if (h && ch[k] < 0) Q.lq[lq_n + nl + __popc(bl & lt)] = (~ch[k] << 5) | slot;
+        if (h && ch[k] < 0) Q.t.lq[lq_n + nl + __popc(bl & lt)] = (~ch[k] << 5) | slot;
         np += __popc(bp);
         nl += __popc(bl);
       }
@@ -271,7 +285,7 @@ __device__ void warp_phase(const Work& Wk, WarpQ& Q, bool want, uint32_t lane, c
       bool have = (int)lane < tk;
       int j = 0, own = 0;
       if (have) {
-        const int e = Q.lq[lq_n - tk + (int)lane];
+        const int e = Q.t.lq[lq_n - tk + (int)lane];
         j = e >> 5;
         own = e & 31;
         if ((int64_t)j >= Wk.field(Q.r[own].asset).n) {  // a leaf beyond the records
@@ -313,13 +327,12 @@ __device__ void warp_phase(const Work& Wk, WarpQ& Q, bool want, uint32_t lane, c
             ci.sa = sa;
             ci.dts = ch.dts;
             ci.smax = ci.sa * ch.hw;
-            ci.orig = ch.orig;
-            ci.owner = own;
+            ci.orig_own = ch.orig | ((uint32_t)own << 26);
           }
         }
       }
       const unsigned bc = __ballot_sync(kFull, ok);
-      if (ok) Q.cq[cq_n + __popc(bc & lt)] = ci;
+      if (ok) Q.t.cq[cq_n + __popc(bc & lt)] = ci;
       cq_n += __popc(bc);
       cnt.chords += ok ? 1ull : 0ull;
       __syncwarp();
@@ -330,7 +343,7 @@ __device__ void warp_phase(const Work& Wk, WarpQ& Q, bool want, uint32_t lane, c
         const int tw = cq_n < 32 ? cq_n : 32;
         const bool hv = (int)lane < tw;
         ChordItem cw;
-        if (hv) cw = Q.cq[cq_n - tw + (int)lane];
+        if (hv) cw = Q.t.cq[cq_n - tw + (int)lane];
         __syncwarp();
         cq_n -= tw;
         if (hv) walk_chord(Wk.err_field(), Q, cw, env, cnt.points);
@@ -394,72 +407,96 @@ __device__ __forceinline__ bool start_ray(const DevField& F, LaneRay& R, PathSta
   return true;
 }
 
-// the points of slot R (ns <= NP of them) against its stored chords
-template <int NP>
-__device__ __forceinline__ void eval_slot(LaneRay& R, const float4* base, int ns, float S,
-                                          float invS, const float* env, uint32_t lane,
-                                          Counters& cnt) {
-  const int mc = R.nch;
-  float pt[NP];
-  long long kap[NP], kb[NP];
-#pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    pt[i] = i < ns ? R.pt[i] : INFINITY;
-    kap[i] = 0;
-    kb[i] = 0;
-  }
-  for (int c = (int)lane; c < mc; c += 32) {
-    const float4 a = base[kRecF4 * c], b = base[kRecF4 * c + 1];
-#pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      const float t = pt[i];
-      if (t >= a.y && t <= a.z) {
-        const float dt = t - a.x;
-        kap[i] += __float2ll_rn(ex2f(fmaf(b.x, dt * dt, b.y)) * cosf_fast(fmaf(a.w, dt, b.z)) * S);
-        int m = (int)(fabsf(dt) * b.w);
-        m = m > 7 ? 7 : m;
-        kb[i] += __float2ll_rn(ex2f(b.y + env[8 + m]) * S);  // h exp(-m^2/2)
-        ++cnt.evals;
-      }
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    if (i < ns) {
-      const long long k1 = warp_sum_ll(kap[i]), k2 = warp_sum_ll(kb[i]);
-      if (lane == 0) {
-        R.kap[i] = __ll2float_rn(k1) * invS;
-        R.kb[i] = __ll2float_rn(k2) * invS;
-      }
-    }
-  }
-}
-
 // kappa and kappa_bar at the points of every slot, from the chords pass 1
-// stored: the warp scans each slot's list (lanes over chords), then reduces.
+// stored.  The lanes share out the (slot, chord) pairs of all slots evenly, so
+// no lane waits on one slot's short list; each pair tests the chord against
+// the slot's points and adds its terms to the slot's sums in shared memory.
 // The sums are exact in 64-bit fixed point: a term is at most the peak h of
 // its chord, so with H the largest peak of the slot's window and at most
 // kSlotCh = 2^8 chords, scaling by 2^(54 - e) (H < 2^e) keeps every partial
 // sum below 2^62.  Each term is rounded once (to 2^(e-54), far below FP32
-// resolution); the integer sum does not depend on the order in which the
-// chords were stored, so a path's decisions do not depend on which other
-// rays shared its warp.
+// resolution) and integer addition does not depend on order, so a path's
+// decisions do not depend on which other rays shared its warp or on the order
+// in which its chords were stored or evaluated.
+__device__ __forceinline__ int slot_exp(const LaneRay& R) {
+  const int ex = ((R.hmax >> 23) & 0xFF) - 126;  // H < 2^ex
+  return ex < -70 ? -70 : ex;
+}
 __device__ void eval_stored(WarpQ& Q, const float4* wch, const float* env, uint32_t lane,
                             Counters& cnt) {
-  for (int s = 0; s < 32; ++s) {
-    LaneRay& R = Q.r[s];
-    const int ns = R.npts;
-    if (ns <= 0) continue;  // uniform: every lane reads the same slot
-    int ex = ((R.hmax >> 23) & 0xFF) - 126;  // H < 2^ex
-    ex = ex < -70 ? -70 : ex;
-    const float S = __int_as_float((127 + 54 - ex) << 23);     // 2^(54 - ex)
-    const float invS = __int_as_float((127 - 54 + ex) << 23);  // 2^(ex - 54)
-    const float4* base = wch + (size_t)s * kSlotCh * kRecF4;
-    // one copy of the unrolled loop (points beyond ns sit at t = inf): copies
-    // sized to the point count cost more in instruction fetch than they save
-    eval_slot<kPK>(R, base, ns, S, invS, env, lane, cnt);
+  LaneRay& Rl = Q.r[lane];
+  const int ns_l = Rl.npts;  // 0: no points (or an overflowed window)
+  const int m = ns_l > 0 ? Rl.nch : 0;
+  int incl = m;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, incl, o);
+    if ((int)lane >= o) incl += y;
+  }
+  const int total = __shfl_sync(kFull, incl, 31);
+  EvalQ& E = Q.e;
+  E.end[lane + 1] = incl;
+  if (lane == 0) E.end[0] = 0;
+#pragma unroll
+  for (int i = 0; i < kPK; ++i) {
+    E.kap[i * 32 + lane] = 0ull;
+    E.kb[i * 32 + lane] = 0ull;
   }
   __syncwarp();
+  // lane l takes the pairs [l per, (l + 1) per): a lane stays within one slot
+  // for most of its pairs, and lanes of a long list sit in different slots at
+  // any moment, so the atomics below rarely meet on one address.  Each pair's
+  // record is loaded one pair ahead, so that its latency overlaps the work on
+  // the pair before.
+  const int per = (total + 31) >> 5;
+  int f = (int)lane * per;
+  const int fe = min(f + per, total);
+  int s = 0;  // the slot of pair f: the number of slot ends at or below f
+  float4 an = make_float4(0.f, 0.f, 0.f, 0.f), bn = an;
+  if (f < fe) {
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1)
+      if (E.end[s + w] <= f) s += w;
+    const float4* rec = wch + ((size_t)s * kSlotCh + (f - E.end[s])) * kRecF4;
+    an = rec[0];
+    bn = rec[1];
+  }
+  for (; f < fe; ++f) {
+    const float4 a = an, b = bn;
+    const int sc = s;
+    if (f + 1 < fe) {
+      while (E.end[s + 1] <= f + 1) ++s;  // the next slot with chords (f + 1 < end[32])
+      const float4* rec = wch + ((size_t)s * kSlotCh + (f + 1 - E.end[s])) * kRecF4;
+      an = rec[0];
+      bn = rec[1];
+    }
+    const LaneRay& R = Q.r[sc];
+    const int ex = slot_exp(R);
+    const float S = __int_as_float((127 + 54 - ex) << 23);  // 2^(54 - ex)
+    const int ns = R.npts;
+    for (int i = 0; i < ns; ++i) {
+      const float t = R.pt[i];
+      if (t > a.z) break;  // the points are sorted by t
+      if (t >= a.y) {
+        const float dt = t - a.x;
+        const long long k1 =
+            __float2ll_rn(ex2f(fmaf(b.x, dt * dt, b.y)) * cosf_fast(fmaf(a.w, dt, b.z)) * S);
+        int mm = (int)(fabsf(dt) * b.w);
+        mm = mm > 7 ? 7 : mm;
+        const long long k2 = __float2ll_rn(ex2f(b.y + env[8 + mm]) * S);  // h exp(-m^2/2)
+        atomicAdd(&E.kap[i * 32 + sc], (unsigned long long)k1);
+        atomicAdd(&E.kb[i * 32 + sc], (unsigned long long)k2);
+        ++cnt.evals;
+      }
+    }
+  }
+  __syncwarp();
+}
+// kappa (k = 0) or kappa_bar (k = 1) at point i of the calling lane's slot,
+// from the sums eval_stored left
+__device__ __forceinline__ float slot_sum(const WarpQ& Q, uint32_t lane, int i, int k) {
+  const unsigned long long v = (k ? Q.e.kb : Q.e.kap)[i * 32 + lane];
+  return __ll2float_rn((long long)v) * __int_as_float((127 - 54 + slot_exp(Q.r[lane])) << 23);
 }
 
 // ---------------------------------------------------------------------------
@@ -676,10 +713,6 @@ __device__ __forceinline__ void render_paths(const Work& Wk, const float* env, W
           R.pu[q] = u;
         }
         R.npts = n;
-        for (int i = 0; i < n; ++i) {
-          R.kap[i] = 0.f;
-          R.kb[i] = 0.f;
-        }
       }
       cnt.windows += want ? 1ull : 0ull;
       __syncwarp();
@@ -704,7 +737,7 @@ __device__ __forceinline__ void render_paths(const Work& Wk, const float* env, W
           }
         } else if (S.kind == 1) {
           for (int i = 0; i < n && !fhit; ++i) {
-            if (R.pu[i] * R.kb[i] < fmaxf(R.kap[i], 0.f)) {
+            if (R.pu[i] * slot_sum(Q, lane, i, 1) < fmaxf(slot_sum(Q, lane, i, 0), 0.f)) {
               fhit = true;
               fth = R.pt[i];
             }
@@ -712,8 +745,10 @@ __device__ __forceinline__ void render_paths(const Work& Wk, const float* env, W
           fin = fhit || last;
           next_window = !fin;
         } else {
-          for (int i = 0; i < n; ++i)
-            if (R.kb[i] > 0.f) S.T *= 1.f - fmaxf(R.kap[i], 0.f) / R.kb[i];
+          for (int i = 0; i < n; ++i) {
+            const float kb = slot_sum(Q, lane, i, 1);
+            if (kb > 0.f) S.T *= 1.f - fmaxf(slot_sum(Q, lane, i, 0), 0.f) / kb;
+          }
           if (!last) S.step *= 2.0f;
           fin = last;
           next_window = !last;
@@ -749,7 +784,7 @@ __device__ __forceinline__ float4* warp_store(float4* chord_store) {
   return chord_store + ((size_t)blockIdx.x * kWWarps + (threadIdx.x >> 5)) * 32 * kSlotCh * kRecF4;
 }
 
-__global__ void __launch_bounds__(kWWarps * 32, 4)
+__global__ void __launch_bounds__(kWWarps * 32, kBlocksPerSM)
     k_render_scatter(const __grid_constant__ DevField F, const __grid_constant__ PathParams P,
                      unsigned long long* acc64, int* counter, int chunk, float4* chord_store) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -763,7 +798,7 @@ __global__ void k_fix_to_image(const unsigned long long* acc64, int64_t npix, in
   if (i < npix) out[i] = fix_mean((long long)acc64[i], spp);
 }
 
-__global__ void __launch_bounds__(kWWarps * 32, 4)
+__global__ void __launch_bounds__(kWWarps * 32, kBlocksPerSM)
     k_render_server(const __grid_constant__ ServerLaunch L, float4* chord_store) {
   extern __shared__ __align__(16) unsigned char smraw[];
   WarpQ& Q = setup_block(smraw, L.fields[0].env);
@@ -772,7 +807,9 @@ __global__ void __launch_bounds__(kWWarps * 32, 4)
 }
 
 size_t scatter_smem_bytes() { return 64 + sizeof(WarpQ) * kWWarps; }
-static_assert(64 + sizeof(WarpQ) * kWWarps <= 57344, "four blocks per SM (56 KB each)");
+// 228 KB of shared memory per SM, 1 KB of it reserved per resident block
+static_assert((64 + sizeof(WarpQ) * kWWarps + 1024) * kBlocksPerSM <= 233472,
+              "kBlocksPerSM blocks fit one SM's shared memory");
 
 size_t scatter_store_bytes(int64_t grid) {
   return (size_t)grid * kWWarps * 32 * kSlotCh * kRecF4 * sizeof(float4);
