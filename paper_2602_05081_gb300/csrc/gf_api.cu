@@ -515,7 +515,7 @@ gf_status gf_build_bvh(gf_field* h, gf_stream stream) {
     GF_CUDA(cudaStreamSynchronize(s), "sync");
     if (herr) {
       cudaMemset(F.err, 0, 4);
-      return fail(GF_EINVAL, "amplitude outside the FP16 range: use BF16 records");
+      return fail(GF_EINVAL, "amplitude or whitened carrier outside the FP16 range (use BF16 records), or scales beyond 2^126");
     }
     F.dev.rec16 = F.rec16;
     F.dev.orig16 = F.sorted_orig;

@@ -120,19 +120,23 @@ __global__ void k_pack(const __grid_constant__ PackArgs A) {
   r[1] = make_float4(P[0][0], P[0][1], P[0][2], P[1][1]);
   r[2] = make_float4(P[1][2], P[2][2], phi, k2i);
   r[3] = make_float4(om[0], om[1], om[2], __uint_as_float((uint32_t)i | ((uint32_t)cell << 26)));
-  // box of the k-sigma ellipsoid: half-extent k sqrt(Sigma_jj), padded
+  // box of the k-sigma ellipsoid: half-extent k sqrt(Sigma_jj), padded.
+  // Reduced-precision records store the whitening factor T (upper triangular,
+  // T^T T = Sigma^-1) with every entry rounded by u = 2^-11 (FP16) or 2^-8
+  // (BF16) of itself: with dT that rounding, |dT z| <= u ||T||_F |z| and
+  // |z| <= ||T^-1||_2 |T z|, so the decoded ellipsoid lies within the exact one
+  // grown by eps = u ||T||_F ||T^-1||_2 = u s_max sqrt(sum 1/s_i^2) of itself
+  // (2e-7 more covers entries that round as FP16 subnormals); pad with a 1.5x
+  // margin (the mean's u16 step is added once the means' box is known, in
+  // build_bvh)
+  const float urel = A.precision == GF_PREC_BF16 ? 3.90625e-3f
+                   : A.precision == GF_PREC_FP16 ? 4.8828125e-4f : 0.f;
+  const float tcond = fmaxf(fmaxf(s[0], s[1]), s[2]) * sqrtf(is2[0] + is2[1] + is2[2]);
+  const float rel = urel > 0.f ? 1.5f * (urel + 2e-7f) * tcond : 1e-5f;
   for (int a = 0; a < 3; ++a) {
     float sjj = R[a][0] * R[a][0] * s[0] * s[0] + R[a][1] * R[a][1] * s[1] * s[1] +
                 R[a][2] * R[a][2] * s[2] * s[2];
     float hw = kext * sqrtf(sjj);
-    // reduced-precision records change the decoded ellipsoid: inverse scales by
-    // 2^-11 (FP16) or 2^-8 (BF16) of themselves, the rotation by an angle of at
-    // most 6.1e-5 (snorm16 quaternion), which moves an extent by that angle
-    // times the longest semi-axis; pad for both with a 1.5x margin (the mean's
-    // u16 step is added once the means' box is known, in build_bvh)
-    const float aniso = fmaxf(fmaxf(s[0], s[1]), s[2]) / fminf(fminf(s[0], s[1]), s[2]);
-    const float rel = A.precision == GF_PREC_BF16 ? 5.9e-3f + 9.2e-5f * aniso
-                    : A.precision == GF_PREC_FP16 ? 7.4e-4f + 9.2e-5f * aniso : 1e-5f;
     float pad = rel * hw + 1e-6f * (1.f + fabsf(mu[a]));
     A.box[6 * i + a] = mu[a] - hw - pad;
     A.box[6 * i + 3 + a] = mu[a] + hw + pad;
@@ -649,43 +653,67 @@ __global__ void k_pack16(const __grid_constant__ Pack16Args A) {
     qn += q[k] * q[k];
   }
   qn = rsqrtf(qn);
-  int qs[4];
-  for (int k = 0; k < 4; ++k) qs[k] = (int)rintf(q[k] * qn * 32767.f);
-  // the decoder's rotation is M(qs) / |qs|^2 with 1/32767^2 applied there:
-  // the inverse scales carry the remaining factor 32767^2 / |qs|^2 (~1)
-  unsigned long long qq = 0ull;  // exact: at most 4 x 32767^2
-  for (int k = 0; k < 4; ++k) qq += (unsigned long long)((long long)qs[k] * qs[k]);
-  const float fold = (32767.0f * 32767.0f) / (float)qq;
   float s[3];
   for (int k = 0; k < 3; ++k) s[k] = expf(A.ls[3 * i + k]);
   const float w = q[0] * qn, x = q[1] * qn, y = q[2] * qn, z = q[3] * qn;
   const float R[3][3] = {{1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y)},
                          {2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x)},
                          {2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)}};
-  float kw[3];
+  // whitened carrier in the frame of W = S^-1 R^T
+  float kl[3];
   for (int k = 0; k < 3; ++k) {
     if (A.omega_frame == GF_OMEGA_LOCAL) {
-      kw[k] = A.om[3 * i + k];
+      kl[k] = A.om[3 * i + k];
     } else {
-      kw[k] = s[k] * (R[0][k] * A.om[3 * i] + R[1][k] * A.om[3 * i + 1] + R[2][k] * A.om[3 * i + 2]);
+      kl[k] = s[k] * (R[0][k] * A.om[3 * i] + R[1][k] * A.om[3 * i + 1] + R[2][k] * A.om[3 * i + 2]);
     }
   }
+  // W = Q T (modified Gram-Schmidt on W's columns, W_kj = R_jk / s_k): then
+  // T^T T = W^T W = Sigma^-1, T is upper triangular with T_kk > 0, and the
+  // carrier in T's frame is Q^T times the one in W's frame (omega . z =
+  // k_W . W z = (Q^T k_W) . T z)
+  float c[3][3];  // c[j]: column j of W
+  for (int j = 0; j < 3; ++j)
+    for (int k = 0; k < 3; ++k) c[j][k] = R[j][k] / s[k];
+  float T[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  for (int j = 0; j < 3; ++j) {
+    for (int r = 0; r < j; ++r) {
+      const float d = c[r][0] * c[j][0] + c[r][1] * c[j][1] + c[r][2] * c[j][2];
+      T[r][j] = d;
+      for (int k = 0; k < 3; ++k) c[j][k] -= d * c[r][k];
+    }
+    const float nrm = sqrtf(c[j][0] * c[j][0] + c[j][1] * c[j][1] + c[j][2] * c[j][2]);
+    T[j][j] = nrm;
+    for (int k = 0; k < 3; ++k) c[j][k] /= nrm;  // c[j] is now q_j
+  }
+  float kw[3];
+  for (int j = 0; j < 3; ++j) kw[j] = c[j][0] * kl[0] + c[j][1] * kl[1] + c[j][2] * kl[2];
+  // one power of two for T: its largest entry scaled into [0.5, 1)
+  const float tmax = fmaxf(fmaxf(fmaxf(T[0][0], fabsf(T[0][1])), fmaxf(fabsf(T[0][2]), T[1][1])),
+                           fmaxf(fabsf(T[1][2]), T[2][2]));
+  int E = 0;
+  (void)frexpf(tmax, &E);
+  if (E < -126 || E > 127) atomicOr(A.err, ERR_INPUT);
+  E = E < -126 ? -126 : (E > 127 ? 127 : E);
   float amp = A.w[i];
   if (A.weight_mode == GF_WEIGHT_NORMALIZED) amp = amp / (15.749609945722419f * s[0] * s[1] * s[2]);
-  if (A.prec == GF_PREC_FP16 && !(fabsf(amp) <= 65504.f)) atomicOr(A.err, ERR_INPUT);
+  if (A.prec == GF_PREC_FP16 && !(fabsf(amp) <= 65504.f && fabsf(kw[0]) <= 65504.f &&
+                                  fabsf(kw[1]) <= 65504.f && fabsf(kw[2]) <= 65504.f))
+    atomicOr(A.err, ERR_INPUT);
   float ph = fmodf(A.ph[i], 6.28318530717958647692f);
   if (ph < 0.f) ph += 6.28318530717958647692f;
   const uint32_t pc = (uint32_t)rintf(ph * (65536.0f / 6.28318530717958647692f)) & 0xFFFFu;
   const uint32_t cell = A.cell[i];
+  auto th = [&](float v) { return to_half_bits(ldexpf(v, -E), A.prec); };
   uint4 r0, r1;
   r0.x = mc[0] | (mc[1] << 16);
-  r0.y = mc[2] | ((uint32_t)(qs[0] & 0xFFFF) << 16);
-  r0.z = (uint32_t)(qs[1] & 0xFFFF) | ((uint32_t)(qs[2] & 0xFFFF) << 16);
-  r0.w = (uint32_t)(qs[3] & 0xFFFF) | (to_half_bits(fold / s[0], A.prec) << 16);
-  r1.x = to_half_bits(fold / s[1], A.prec) | (to_half_bits(fold / s[2], A.prec) << 16);
-  r1.y = to_half_bits(kw[0], A.prec) | (to_half_bits(kw[1], A.prec) << 16);
-  r1.z = to_half_bits(kw[2], A.prec) | (to_half_bits(amp, A.prec) << 16);
-  r1.w = pc | (cell << 16);
+  r0.y = mc[2] | (th(T[0][0]) << 16);
+  r0.z = th(T[0][1]) | (th(T[0][2]) << 16);
+  r0.w = th(T[1][1]) | (th(T[1][2]) << 16);
+  r1.x = th(T[2][2]) | (to_half_bits(kw[0], A.prec) << 16);
+  r1.y = to_half_bits(kw[1], A.prec) | (to_half_bits(kw[2], A.prec) << 16);
+  r1.z = to_half_bits(amp, A.prec) | (pc << 16);
+  r1.w = (cell & 63u) | ((uint32_t)(E + 127) << 8);
   A.out[2 * j] = r0;
   A.out[2 * j + 1] = r1;
 }

@@ -328,22 +328,21 @@ __device__ __forceinline__ bool chord_setup(const Prim& P, float3 o, float3 v, f
 // ---------------------------------------------------------------------------
 // Reduced-precision record (32 B = 2 x uint4), BVH order:
 //   x0 = mu.x | mu.y << 16            (u16 fixed point in the means' box)
-//   y0 = mu.z | q.w << 16             (quaternion as snorm16)
-//   z0 = q.x  | q.y << 16
-//   w0 = q.z  | 1/s0 << 16            (1/s, k_W and A as FP16 or BF16)
-//   x1 = 1/s1 | 1/s2 << 16
-//   y1 = kW.x | kW.y << 16
-//   z1 = kW.z | A << 16
-//   w1 = phase | cell << 16           (phase as u16 in [0, 2 pi))
-// Decoded to FP32; the chord is set up in the whitened frame W = S^-1 R^T
-// (Sec. 4.4): u = W v, p_W = W (o + tc v - mu), phase k_W . p_W + phi.
+//   y0 = mu.z | T00 << 16             (T: 6 entries as FP16 or BF16, times 2^-E)
+//   z0 = T01  | T02 << 16
+//   w0 = T11  | T12 << 16
+//   x1 = T22  | kT.x << 16            (kT, A as FP16 or BF16)
+//   y1 = kT.y | kT.z << 16
+//   z1 = A    | phase << 16           (phase as u16 in [0, 2 pi))
+//   w1 = cell | (E + 127) << 8
+// T is the upper-triangular whitening factor, T^T T = Sigma^-1 (Sec. 4.4 with
+// the whitening matrix taken triangular), and kT the whitened carrier in its
+// frame.  Decoded to FP32; the chord is set up in T's frame: u = T v,
+// p_T = T (o + tc v - mu), phase kT . p_T + phi.
 // ---------------------------------------------------------------------------
 // exact integer-to-float conversions by exponent insertion (0x4B000000 is 2^23)
 __device__ __forceinline__ float u16_float(uint32_t x) {
   return __int_as_float((int)(0x4B000000u | x)) - 8388608.0f;
-}
-__device__ __forceinline__ float s16_float(uint32_t x) {  // two's complement 16-bit value
-  return __int_as_float((int)(0x4B000000u | (x ^ 0x8000u))) - 8421376.0f;
 }
 __device__ __forceinline__ float half_bits_to_float(uint32_t h, int prec) {
   return prec == 2 ? __uint_as_float(h << 16) : __half2float(__ushort_as_half((unsigned short)h));
@@ -356,40 +355,27 @@ __device__ __forceinline__ bool chord_setup16(const DevField& F, uint4 r0, uint4
   const float3 mu = make_float3(fmaf(u16_float(r0.x & 0xFFFFu), F.qscale.x, F.qlo.x),
                                 fmaf(u16_float(r0.x >> 16), F.qscale.y, F.qlo.y),
                                 fmaf(u16_float(r0.y & 0xFFFFu), F.qscale.z, F.qlo.z));
-  const float qw = s16_float(r0.y >> 16), qx = s16_float(r0.z & 0xFFFFu);
-  const float qy = s16_float(r0.z >> 16), qz = s16_float(r0.w & 0xFFFFu);
-  const float k0 = half_bits_to_float(r1.y & 0xFFFFu, prec);
-  const float k1 = half_bits_to_float(r1.y >> 16, prec);
-  const float k2 = half_bits_to_float(r1.z & 0xFFFFu, prec);
-  const float A = half_bits_to_float(r1.z >> 16, prec);
-  const float phi = u16_float(r1.w & 0xFFFFu) * (6.28318530717958647692f / 65536.0f);
-  // rotation of the quaternion codes, R = M(q) / |q|^2: the record's inverse
-  // scales carry 32767^2 / |q|^2 (folded at pack time), so 1/32767^2 remains
-  const float kq = 1.0f / (32767.0f * 32767.0f);
-  const float is0 = half_bits_to_float(r0.w >> 16, prec) * kq;
-  const float is1 = half_bits_to_float(r1.x & 0xFFFFu, prec) * kq;
-  const float is2 = half_bits_to_float(r1.x >> 16, prec) * kq;
-  const float R00 = qw * qw + qx * qx - qy * qy - qz * qz;
-  const float R01 = 2.f * (qx * qy - qw * qz), R02 = 2.f * (qx * qz + qw * qy);
-  const float R10 = 2.f * (qx * qy + qw * qz);
-  const float R11 = qw * qw - qx * qx + qy * qy - qz * qz;
-  const float R12 = 2.f * (qy * qz - qw * qx), R20 = 2.f * (qx * qz - qw * qy);
-  const float R21 = 2.f * (qy * qz + qw * qx);
-  const float R22 = qw * qw - qx * qx - qy * qy + qz * qz;
-  // whitened direction and offset
-  const float ux = is0 * fmaf(R00, v.x, fmaf(R10, v.y, R20 * v.z));
-  const float uy = is1 * fmaf(R01, v.x, fmaf(R11, v.y, R21 * v.z));
-  const float uz = is2 * fmaf(R02, v.x, fmaf(R12, v.y, R22 * v.z));
+  const float sT = __uint_as_float(((r1.w >> 8) & 0xFFu) << 23);  // 2^E
+  const float T00 = half_bits_to_float(r0.y >> 16, prec) * sT;
+  const float T01 = half_bits_to_float(r0.z & 0xFFFFu, prec) * sT;
+  const float T02 = half_bits_to_float(r0.z >> 16, prec) * sT;
+  const float T11 = half_bits_to_float(r0.w & 0xFFFFu, prec) * sT;
+  const float T12 = half_bits_to_float(r0.w >> 16, prec) * sT;
+  const float T22 = half_bits_to_float(r1.x & 0xFFFFu, prec) * sT;
+  // whitened direction and offset (T upper triangular)
+  const float ux = fmaf(T00, v.x, fmaf(T01, v.y, T02 * v.z));
+  const float uy = fmaf(T11, v.y, T12 * v.z);
+  const float uz = T22 * v.z;
   const float a = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
   const float d0x = __fsub_rn(o.x, mu.x), d0y = __fsub_rn(o.y, mu.y), d0z = __fsub_rn(o.z, mu.z);
-  const float w0x = is0 * fmaf(R00, d0x, fmaf(R10, d0y, R20 * d0z));
-  const float w0y = is1 * fmaf(R01, d0x, fmaf(R11, d0y, R21 * d0z));
-  const float w0z = is2 * fmaf(R02, d0x, fmaf(R12, d0y, R22 * d0z));
+  const float w0x = fmaf(T00, d0x, fmaf(T01, d0y, T02 * d0z));
+  const float w0y = fmaf(T11, d0y, T12 * d0z);
+  const float w0z = T22 * d0z;
   const float ia = __frcp_rn(a);
   const float tc = -fmaf(ux, w0x, fmaf(uy, w0y, uz * w0z)) * ia;
-  // whitened offset at tc, W (o + tc v - mu) = W d0 + tc W v: its FP32 rounding,
-  // ~2^-24 |W d0|, stays below the record's own (the FP16 inverse scales round by
-  // 2^-12 of the whitened offset), so no compensated world offset is needed here
+  // whitened offset at tc, T (o + tc v - mu) = T d0 + tc T v: its FP32 rounding,
+  // ~2^-24 |T d0|, stays below the record's own (T's entries round by 2^-11 or
+  // 2^-8 of themselves), so no compensated world offset is needed here
   const float pwx = fmaf(tc, ux, w0x), pwy = fmaf(tc, uy, w0y), pwz = fmaf(tc, uz, w0z);
   const float px = fmaf(tc, v.x, d0x), py = fmaf(tc, v.y, d0y), pz = fmaf(tc, v.z, d0z);
   const float b = fmaf(ux, pwx, fmaf(uy, pwy, uz * pwz));
@@ -408,6 +394,11 @@ __device__ __forceinline__ bool chord_setup16(const DevField& F, uint4 r0, uint4
   c.a = a;
   c.b = b;
   c.g = g;
+  const float k0 = half_bits_to_float(r1.x >> 16, prec);
+  const float k1 = half_bits_to_float(r1.y & 0xFFFFu, prec);
+  const float k2 = half_bits_to_float(r1.y >> 16, prec);
+  const float A = half_bits_to_float(r1.z & 0xFFFFu, prec);
+  const float phi = u16_float(r1.z >> 16) * (6.28318530717958647692f / 65536.0f);
   c.B = fmaf(k0, ux, fmaf(k1, uy, k2 * uz));
   float ph = fmaf(k0, pwx, fmaf(k1, pwy, fmaf(k2, pwz, phi)));
   if (A < 0.0f) ph += 3.14159265358979f;
@@ -417,7 +408,7 @@ __device__ __forceinline__ bool chord_setup16(const DevField& F, uint4 r0, uint4
   c.dts = dts;
   c.hw = hw;
   c.p = make_float3(px, py, pz);
-  c.cell = (r1.w >> 16) & 63u;
+  c.cell = r1.w & 63u;
   c.orig = (uint32_t)__ldg(F.orig16 + j);
   return true;
 }
@@ -436,7 +427,7 @@ __device__ __forceinline__ bool prim_chord(const DevField& F, int j, float3 o, f
   }
   const uint4* r = F.rec16 + 2 * (int64_t)j;
   const uint4 r0 = __ldg(r), r1 = __ldg(r + 1);
-  w = weight((r1.w >> 16) & 63u);
+  w = weight(r1.w & 63u);
   if (!(w > 0.f)) return false;
   return chord_setup16(F, r0, r1, j, o, v, tmin, tmax, ch);
 }

@@ -779,14 +779,18 @@ def test_reduced_precision_transmittance(api, ctx, prec, u):
     """32-byte records against the FP64 oracle, within a bound derived from
     every rounding the record applies (FP32 math after decoding).
 
-    With z the whitened offset (|z| <= k inside the support) the integrand is
-    A exp(-|z|^2/2) cos(k_W . z + phi).  The record perturbs
-      z      by dz <= k u (1/s rounded) + sqrt(3) h_mu / s_min (u16 means,
-             half step h_mu) + (2/32767) k s_max / s_min (snorm16 quaternion:
-             rotation angle error <= 2 |dq|) + 4 2^-24 |o - mu| / s_min (the
-             whitened offset formed as W (o - mu) + tc W v in FP32),
-      A      by u A,  k_W by u |k_W|,  phi by pi/65536 (u16 phase),
-    so |d integrand| <= A exp(-q/2) [u + k dz + k u |k_W| + |k_W| dz + pi/65536]
+    The record holds the upper-triangular whitening factor T (T^T T =
+    Sigma^-1, singular values 1/s_i) and the carrier kT in its frame.  With
+    z = T (x - mu) (|z| <= k inside the support) the integrand is
+    A exp(-|z|^2/2) cos(kT . z + phi).  The record perturbs
+      z      by dz <= k eps (T's entries rounded by u of themselves, plus the
+             FP32 factorisation: |dT y| <= (u + 1e-6) ||T||_F |y| and
+             |y| <= s_max |z|, so eps = (u + 1e-6) s_max sqrt(sum 1/s_i^2))
+             + sqrt(3) h_mu / s_min (u16 means, half step h_mu; ||T||_2 =
+             1/s_min) + 4 2^-24 |o - mu| sqrt(3) / s_min (the whitened offset
+             formed as T (o - mu) + tc T v in FP32),
+      A      by u A,  kT by (u + 1e-6) |kT|,  phi by pi/65536 (u16 phase),
+    so |d integrand| <= A exp(-q/2) [u + k dz + k u |kT| + |kT| dz + pi/65536]
     and, summed over a ray's chords, |d tau| <= C E with E the envelope
     integral.  The k-sigma cut moves too: a chord end shifts by at most
     2 s_max sqrt(2 k dz) where the integrand is at most A e^{-k^2/2}, which
@@ -805,13 +809,14 @@ def test_reduced_precision_transmittance(api, ctx, prec, u):
     k = 3.0
     s = np.exp(p["log_scale"].astype(np.float64))
     s_min, s_max = s.min(), s.max()
+    tcond = np.max(s.max(1) * np.sqrt(np.sum(1.0 / s ** 2, axis=1)))
     mu = p["mu"].astype(np.float64)
     h_mu = (mu.max(0) - mu.min(0)).max() / 65535.0 / 2.0
     kw = np.max(np.linalg.norm(p["omega"], axis=1) * s.max(1))
     d0 = np.max(np.linalg.norm(o[:, None, :].astype(np.float64) - mu[None], axis=2))
-    dz = k * u + np.sqrt(3.0) * h_mu / s_min + (2.0 / 32767.0) * k * s_max / s_min + \
-        4.0 * 2.0 ** -24 * d0 / s_min
-    C_rel = u + k * dz + k * u * kw + kw * dz + np.pi / 65536.0
+    dz = k * (u + 1e-6) * tcond + np.sqrt(3.0) * h_mu / s_min + \
+        4.0 * 2.0 ** -24 * d0 * np.sqrt(3.0) / s_min
+    C_rel = u + k * dz + k * (u + 1e-6) * kw + kw * dz + np.pi / 65536.0
     n_ch = np.zeros(o.shape[0])
     for r in range(o.shape[0]):
         v = d[r] / np.linalg.norm(d[r])
