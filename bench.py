@@ -55,9 +55,10 @@ WORKLOAD = ("multiple scattering, 1M-primitive 6-octave Gabor field, 1024x1024, 
 # single scattering, 100k primitives, 512x512, 16 spp, 4 band cutoffs (extra key)
 C2_PRIMS, C2_OCTAVES, C2_RES, C2_SPP, C2_CUTOFFS, C2_SEED = 100_000, 4, 512, 16, (3, 2, 1, 0), 1
 # DRAM bytes (read + write) per traced ray of k_render_scatter on this workload's field and
-# masks, from ncu on a 256x256, 8-spp launch (profiles/k_render_scatter_multiscatter_1m.md),
-# scaled to a launch by its traced rays; None until captured for the current kernel
-TRAFFIC_BYTES_PER_RAY = None
+# masks, from ncu on a 256x256, 8-spp launch (profiles/k_render_scatter_full_cfg3_256x256_8spp.md:
+# 2.391 GB for 3,516,025 rays), scaled to a launch by its traced rays; set to None whenever
+# the kernel changes until it is captured again
+TRAFFIC_BYTES_PER_RAY = 680.0
 
 
 def config(extra=None):
