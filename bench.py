@@ -59,6 +59,11 @@ C2_PRIMS, C2_OCTAVES, C2_RES, C2_SPP, C2_CUTOFFS, C2_SEED = 100_000, 4, 512, 16,
 # 2.391 GB for 3,516,025 rays), scaled to a launch by its traced rays; set to None whenever
 # the kernel changes until it is captured again
 TRAFFIC_BYTES_PER_RAY = 680.0
+# warp instructions issued per traced ray by k_render_scatter on this workload (the same
+# capture: 12.458 G for 3,516,025 rays); with the launch's rays per second, the median SM
+# clock sampled during the timed steps and 4 schedulers per SM issuing one instruction a
+# cycle, this gives the share of issue slots the kernel fills
+INST_PER_RAY = 3543.0
 
 
 def config(extra=None):
@@ -868,6 +873,14 @@ def run_ours(args, rank, world):
         "storage_ms_per_frame": frame_ms,
         "clocks": clk,
     }
+    if INST_PER_RAY and clk.get("sm_mhz"):
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        issued = INST_PER_RAY * rays_per_launch / (statistics.mean(step_ms) * 1e-3)
+        slots = 4.0 * sms * clk["sm_mhz"] * 1e6
+        line["issue_utilisation"] = {
+            "warp_inst_per_s": issued, "issue_slots_per_s": slots, "frac": issued / slots,
+            "basis": "ncu warp instructions per traced ray of the 256x256 capture x traced "
+                     "rays per second / (4 schedulers x SMs x median SM clock)"}
     line["counters_per_ray"] = {k: st[k] / max(1, st["rays"])
                                 for k in ("chords", "evals", "nodes", "points", "windows", "steps", "leaves")}
     if any(st["cycles"]):

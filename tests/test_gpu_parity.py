@@ -550,6 +550,28 @@ def test_multiple_scatter_stochastic_mask_parity(api, ctx):
     assert diff <= 0.01 * noise, (diff, noise)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_render_is_reproducible_across_loads(api, ctx, prec):
+    """A field loaded twice from the same parameters renders bit for bit the same
+    image, with importance-sampled cones (whose weights use each cell's mean
+    carrier) on camera, bounce and NEE rays: the load's cell statistics are
+    integer sums, and every sum that decides a path is exact, so nothing depends
+    on the order in which threads arrive."""
+    p = synth.octave_field(20_000, 6, seed=4)
+    cg, _ = _cam_pair(api, 64, 64)
+    ro = api.render_opts("scatter", 8, 4)
+    lo = api.lod("unif_cv", 7, "is")
+    imgs = []
+    for _ in range(2):
+        f = api.Field(ctx, p, precision=prec)
+        f.set_lod(lo, lo)
+        imgs.append(f.render(cg, ro, seed=5).cpu().numpy())
+        f.sync()
+        f.free()
+    assert imgs[0].max() > 0.0
+    assert np.array_equal(imgs[0], imgs[1])
+
+
 def test_tomography_render_parity(api, ctx):
     """Tomography image: per camera ray |dT| <= 1e-5 and |dtau| <= 1e-5 max(1, |tau|)
     on identical float rays (signed densities give T up to ~11 here), and the
