@@ -8,8 +8,10 @@
 // queued the whole warp sets up their chords at once (chord set-up on the
 // owning lane's ray).  Each chord that overlaps the owner's window [ta, te)
 // is stored (its evaluation record, in a per-warp global store) and queued;
-// queued chords are walked 32 at a time, drawing the chord's tentative points
-// of Sec. 3's per-segment majorant from its own Philox stream.  Points land in
+// queued chords are walked 32 at a time, one draw per chord and round, each
+// drawing the chord's next tentative point of Sec. 3's per-segment majorant
+// from its own Philox stream (chords that may hold more points go back to the
+// queue, so the lanes stay busy).  Points land in
 // the owner's buffer through shared-memory atomics.  kappa and kappa_bar at
 // the points are then summed from the stored records (the lanes share out the
 // (slot, chord) pairs of all slots and add into per-point sums in shared
@@ -55,7 +57,11 @@ struct LaneRay {
 };
 static_assert(sizeof(LaneRay) % 8 == 4, "odd word stride");
 struct ChordItem {
-  float tc, dtin, dtout, h, sa, dts, smax;
+  float tc;
+  float dt;           // where the walk stands (relative to tc): the chord's entry, then
+                      // the last point drawn
+  float dtout, h, sa, dts;
+  uint32_t jd;        // majorant pieces per side J (3 bits) | next draw << 3
   uint32_t orig_own;  // original primitive index | owning slot << 26
 };
 static_assert(sizeof(ChordItem) == 32, "chord items of 32 bytes");
@@ -117,57 +123,61 @@ __device__ __forceinline__ bool slot_chord(const DevField& F, const LaneRay& R, 
                     0.f, INFINITY, [&](uint32_t c) { return ray_weight(R, c); }, w, ch);
 }
 
-// walk one queued chord: emit its tentative points in [ta, te) to the owner
-__device__ __forceinline__ void walk_chord(const DevField& F, WarpQ& Q, const ChordItem& c,
-                                           const float* env, unsigned long long& npt) {
+// One draw of a queued chord's walk: the next tentative point of its majorant
+// (Sec. 3) from the chord's own Philox stream, recorded for the owner when it
+// falls in the window [ta, te).  Returns true when the chord may hold further
+// points (c then stands at the point drawn, with the next draw index); false
+// when the walk left the chord or the window, or the owner's point buffer is
+// full (the owner then halves the window and redoes it).
+__device__ __forceinline__ bool walk_step(const DevField& F, WarpQ& Q, ChordItem& c,
+                                          const float* env, unsigned long long& npt) {
   LaneRay& R = Q.r[c.orig_own >> 26];
-  const uint64_t seed = slot_seed(R);
-  const float ta = R.ta, te = R.te;
+  const uint32_t draw = c.jd >> 3;
+  if (draw >= (1u << 16)) {
+    set_err(F, ERR_GUARD);
+    return false;
+  }
   const float invs = 1.0f / c.sa;
-  int J = (int)ceilf(c.smax) - 1;
-  J = J < 0 ? 0 : (J > 6 ? 6 : J);
-  float dt = c.dtin;
-  int p = 0;
+  const int J = (int)(c.jd & 7u);
+  float dt = c.dt;
+  int p = 0;  // the majorant piece holding dt
   while (p < 2 * J) {
     const float bp = p < J ? c.dts - (float)(J - p) * invs : c.dts + (float)(p - J + 1) * invs;
     if (bp <= dt) ++p;
     else break;
   }
-  for (uint32_t draw = 0; draw < (1u << 16); ++draw) {
-    const uint4 x = rng4(seed, draw, c.orig_own & kOrigMask, R.ray, R.word);
-    float z = -__logf(1.0f - u01(x.x));
-    bool emit = false;
-    for (int q = 0; q < 2 * J + 2; ++q) {
-      const float bp = p < J ? c.dts - (float)(J - p) * invs : c.dts + (float)(p - J + 1) * invs;
-      const float end = p < 2 * J ? fminf(bp, c.dtout) : c.dtout;
-      const int nn = p < J ? J - p : p - J;
-      const float lam = c.h * env[nn];
-      const float capz = lam * (end - dt);
-      if (z < capz) {
-        dt += z / lam;
-        emit = true;
-        break;
-      }
-      z -= capz;
-      dt = end;
-      if (dt >= c.dtout) return;
-      ++p;
+  const uint4 x = rng4(slot_seed(R), draw, c.orig_own & kOrigMask, R.ray, R.word);
+  float z = -__logf(1.0f - u01(x.x));
+  bool emit = false;
+  for (int q = 0; q < 2 * J + 2; ++q) {
+    const float bp = p < J ? c.dts - (float)(J - p) * invs : c.dts + (float)(p - J + 1) * invs;
+    const float end = p < 2 * J ? fminf(bp, c.dtout) : c.dtout;
+    const int nn = p < J ? J - p : p - J;
+    const float lam = c.h * env[nn];
+    const float capz = lam * (end - dt);
+    if (z < capz) {
+      dt += z / lam;
+      emit = true;
+      break;
     }
-    if (!emit) return;
-    const float t = c.tc + dt;
-    if (t >= te) return;
-    if (t >= ta) {
-      ++npt;
-      const int slot = atomicAdd(&R.npts, 1);
-      if (slot < kPK) {
-        R.pt[slot] = t;
-        R.pu[slot] = u01(x.y);
-      } else {
-        return;  // overflow: the owner halves the window and redoes it
-      }
-    }
+    z -= capz;
+    dt = end;
+    if (dt >= c.dtout) return false;
+    ++p;
   }
-  set_err(F, ERR_GUARD);
+  if (!emit) return false;
+  const float t = c.tc + dt;
+  if (t >= R.te) return false;
+  if (t >= R.ta) {
+    ++npt;
+    const int slot = atomicAdd(&R.npts, 1);
+    if (slot >= kPK) return false;  // overflow: the owner halves the window and redoes it
+    R.pt[slot] = t;
+    R.pu[slot] = u01(x.y);
+  }
+  c.dt = dt;
+  c.jd += 8u;
+  return true;
 }
 
 // One traversal phase for the slots with want = true.  The warp shares one
@@ -321,12 +331,15 @@ __device__ void warp_phase(const Work& Wk, WarpQ& Q, bool want, uint32_t lane, c
                                    reduce_2pi(fmaf(ch.B, ch.dts, ch.delta)), sa);
             }
             ci.tc = ch.tc;
-            ci.dtin = ch.dtin;
+            ci.dt = ch.dtin;
             ci.dtout = ch.dtout;
             ci.h = h;
             ci.sa = sa;
             ci.dts = ch.dts;
-            ci.smax = ci.sa * ch.hw;
+            // majorant pieces per side: whitened half-length sa hw rounded up, less one
+            int J = (int)ceilf(sa * ch.hw) - 1;
+            J = J < 0 ? 0 : (J > 6 ? 6 : J);
+            ci.jd = (uint32_t)J;
             ci.orig_own = ch.orig | ((uint32_t)own << 26);
           }
         }
@@ -346,7 +359,12 @@ __device__ void warp_phase(const Work& Wk, WarpQ& Q, bool want, uint32_t lane, c
         if (hv) cw = Q.t.cq[cq_n - tw + (int)lane];
         __syncwarp();
         cq_n -= tw;
-        if (hv) walk_chord(Wk.err_field(), Q, cw, env, cnt.points);
+        // one draw per chord and round; chords that may hold more points go back
+        // to the queue, so every round keeps the lanes busy
+        const bool again = hv && walk_step(Wk.err_field(), Q, cw, env, cnt.points);
+        const unsigned ba = __ballot_sync(kFull, again);
+        if (again) Q.t.cq[cq_n + __popc(ba & lt)] = cw;
+        cq_n += __popc(ba);
         __syncwarp();
       }
       if (lane == 0) GF_TOC(cnt, 2, t_walk);
