@@ -97,7 +97,12 @@ enum { GF_WEIGHT_PEAK = 0, GF_WEIGHT_NORMALIZED = 1 };
 enum { GF_OMEGA_WORLD = 0, GF_OMEGA_LOCAL = 1 };
 
 typedef struct gf_field_opts {
-  int precision;   /* GF_PREC_*: storage of the packed records (math is FP32) */
+  int precision;   /* GF_PREC_*: storage of the packed records (math is FP32).  FP16/BF16:
+                      32-byte records (u16 means, the triangular whitening factor T with
+                      T^T T = Sigma^-1 under one power-of-two exponent, the carrier in T's
+                      frame and the amplitude as FP16/BF16, u16 phase); gf_build_bvh fails
+                      with GF_EINVAL when an amplitude or carrier exceeds the FP16 range or
+                      a scale lies beyond 2^+-126.  The adjoints need FP32 records. */
   int weight_mode; /* GF_WEIGHT_* */
   int omega_frame; /* GF_OMEGA_* */
   float k_sigma;   /* support radius in sigma units, (0, 6]; the paper uses 3 */
