@@ -56,14 +56,14 @@ WORKLOAD = ("multiple scattering, 1M-primitive 6-octave Gabor field, 1024x1024, 
 C2_PRIMS, C2_OCTAVES, C2_RES, C2_SPP, C2_CUTOFFS, C2_SEED = 100_000, 4, 512, 16, (3, 2, 1, 0), 1
 # DRAM bytes (read + write) per traced ray of k_render_scatter on this workload's field and
 # masks, from ncu on a 256x256, 8-spp launch (profiles/k_render_scatter_full_cfg3_256x256_8spp.md:
-# 2.391 GB for 3,516,025 rays), scaled to a launch by its traced rays; set to None whenever
+# 2.371 GB for 3,516,025 rays), scaled to a launch by its traced rays; set to None whenever
 # the kernel changes until it is captured again
-TRAFFIC_BYTES_PER_RAY = 680.0
+TRAFFIC_BYTES_PER_RAY = 674.0
 # warp instructions issued per traced ray by k_render_scatter on this workload (the same
-# capture: 12.458 G for 3,516,025 rays); with the launch's rays per second, the median SM
+# capture: 11.807 G for 3,516,025 rays); with the launch's rays per second, the median SM
 # clock sampled during the timed steps and 4 schedulers per SM issuing one instruction a
 # cycle, this gives the share of issue slots the kernel fills
-INST_PER_RAY = 3543.0
+INST_PER_RAY = 3358.0
 
 
 def config(extra=None):
