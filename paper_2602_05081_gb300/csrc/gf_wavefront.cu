@@ -91,12 +91,6 @@ struct WarpQ {
   };
 };
 
-__device__ __forceinline__ int ord_f(float f) {
-  int i = __float_as_int(f);
-  return i >= 0 ? i : i ^ 0x7FFFFFFF;
-}
-__device__ __forceinline__ float unord_f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF); }
-
 __device__ __forceinline__ unsigned long long slot_mask(const LaneRay& R) {
   return (unsigned long long)R.mask_lo | ((unsigned long long)R.mask_hi << 32);
 }
