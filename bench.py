@@ -622,8 +622,8 @@ def run_workload(args):
                       big["fp16"]["ms_per_render"], args, {"by_kernels": rows, "gpu_launches": 2})
     elif args.workload == "adjoint":
         # 200k kernels, 256x256 at 8 spp: forward render plus hand-written adjoint of an
-        # L2 loss against a target rendered from perturbed parameters
-        res, spp = 256, 8
+        # L2 loss against a target rendered from perturbed parameters (--res/--spp: profiling)
+        res, spp = args.res or 256, args.spp or 8
         p = synth.octave_field(200_000, 4, seed=0)
         rng = np.random.default_rng(1)
         tgt = dict(p)
@@ -648,7 +648,8 @@ def run_workload(args):
             f.sync()
             out[name] = statistics.mean(ms)
             f.free()
-        workload_line("differentiable rendering, 200k kernels, 256x256, 8 spp, forward + adjoint",
+        workload_line("differentiable rendering, 200k kernels, %dx%d, %d spp, forward + adjoint"
+                      % (res, res, spp),
                       res * res * spp / (out["scatter"] * 1e-3) / 1e6, "Msamples/s", out["scatter"],
                       args, {"ms_per_forward_backward": out, "gpu_launches": 3})
     ctx.close()
