@@ -105,6 +105,213 @@ __global__ void __launch_bounds__(kBlock, 3)  // at most 168 registers: 12 warps
 }
 
 // ---------------------------------------------------------------------------
+// Deterministic optical depth of small batches, one ray per warp.  The warp
+// traverses the ray's tree together (a shared stack of binary nodes, up to 32
+// per step) and sets up the chords of the leaves it reaches 32 at a time.
+// Gauss-Legendre mode: the nodes of those chords are shared out evenly among
+// the lanes (the rule per chord as in det_tau); closed form: each lane
+// integrates its own chord.  Every term goes into its lane's compensated sum;
+// the lanes' sums are combined in a fixed butterfly order.
+// ---------------------------------------------------------------------------
+constexpr int kCoopStack = 512;   // node entries per warp
+constexpr int kCoopMargin = 128;  // a step pushes <= 64; depth first above kCoopStack - margin
+constexpr int kCoopLeafQ = 96;    // <= 31 left + 64 new
+struct CoopChord {
+  float mid, hl, y2, y1, y0, scale, B, delta;
+  int off;  // first node of the chord's rule in the tables
+};
+struct CoopQ {
+  int stk[kCoopStack];
+  int lq[kCoopLeafQ];
+  CoopChord ch[32];  // the round's chords, one per lane
+  int end[33];       // end[c]: nodes of chords 0..c-1
+};
+
+template <int MODE>  // GF_TR_DETERMINISTIC or GF_TR_CLOSED_FORM
+__device__ void coop_tau(const DevField& F, CoopQ& Q, const Mask& M, float3 o, float3 v,
+                         float3 inv, float tmin, float tmax, float t0, float t1, const float* glx,
+                         const float* glw, uint32_t lane, float& s_acc, float& c_acc,
+                         Counters& cnt) {
+  const unsigned lt = (1u << lane) - 1u;
+  const SpanTest test{t0, t1};
+  int sp = F.root >= 0 ? 1 : 0, lq_n = F.root >= 0 ? 0 : 1;
+  if (lane == 0) {
+    if (F.root >= 0) Q.stk[0] = F.root;
+    else Q.lq[0] = 0;  // a one-primitive field has no internal node
+  }
+  __syncwarp();
+  // every internal node enters the stack at most once
+  const long long max_it = F.n + 64;
+  for (long long it = 0;; ++it) {
+    if (it > max_it) {
+      if (lane == 0) set_err(F, ERR_GUARD);
+      break;
+    }
+    int take = sp < 32 ? sp : 32;
+    if (sp > kCoopStack - kCoopMargin) take = 1;  // near capacity: depth first
+    const int node = (int)lane < take ? Q.stk[sp - take + (int)lane] : -1;
+    __syncwarp();
+    sp -= take;
+    int c0 = 0, c1 = 0;
+    bool h0 = false, h1 = false;
+    if (node >= 0 && (int64_t)node >= F.n - 1) {  // internal nodes 0 .. n-2
+      set_err(F, ERR_INDEX);
+    } else if (node >= 0) {
+      const Node* N = F.nodes + node;
+      const float4 a = __ldg(&N->a), b = __ldg(&N->b), c = __ldg(&N->c);
+      const int4 d = __ldg(&N->d);
+      const uint4 e = __ldg(&N->e);
+      ++cnt.nodes;
+      const unsigned long long m0 = (unsigned long long)e.x | ((unsigned long long)e.y << 32);
+      const unsigned long long m1 = (unsigned long long)e.z | ((unsigned long long)e.w << 32);
+      float tn0, tf0, tn1, tf1;
+      slab_interval(o, inv, a.x, a.y, a.z, a.w, b.x, b.y, tn0, tf0);
+      slab_interval(o, inv, b.z, b.w, c.x, c.y, c.z, c.w, tn1, tf1);
+      c0 = d.x;
+      c1 = d.y;
+      h0 = (m0 & M.bits) && test(tn0, tf0);
+      h1 = (m1 & M.bits) && test(tn1, tf1);
+      if (c0 < 0 && (int64_t)~c0 >= F.n) {  // a leaf beyond the records
+        set_err(F, ERR_INDEX);
+        h0 = false;
+      }
+      if (c1 < 0 && (int64_t)~c1 >= F.n) {
+        set_err(F, ERR_INDEX);
+        h1 = false;
+      }
+    }
+    // push internal children, queue leaves (ballots keep the entries contiguous)
+    int np = 0, nl = 0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const bool h = k ? h1 : h0;
+      const int ch = k ? c1 : c0;
+      const unsigned bp = __ballot_sync(kFull, h && ch >= 0);
+      const unsigned bl = __ballot_sync(kFull, h && ch < 0);
+      if (h && ch >= 0) {
+        const int pos = sp + np + __popc(bp & lt);
+        if (pos < kCoopStack) Q.stk[pos] = ch;
+      }
+      if (h && ch < 0) Q.lq[lq_n + nl + __popc(bl & lt)] = ~ch;
+      np += __popc(bp);
+      nl += __popc(bl);
+    }
+    if (sp + np > kCoopStack) {
+      if (lane == 0) set_err(F, ERR_STACK);
+      np = kCoopStack - sp;
+    }
+    sp += np;
+    lq_n += nl;
+    __syncwarp();
+    const bool more = sp > 0;
+    // leaf rounds: 32 chords set up at once, then their nodes shared out
+    while (lq_n >= 32 || (!more && lq_n > 0)) {
+      const int tk = lq_n < 32 ? lq_n : 32;
+      const int j = (int)lane < tk ? Q.lq[lq_n - tk + (int)lane] : -1;
+      __syncwarp();
+      lq_n -= tk;
+      int n = 0;
+      if (j >= 0) {
+        ++cnt.leaves;
+        Chord ch;
+        float w;
+        if (prim_chord(F, j, o, v, tmin, tmax, [&](uint32_t cl) { return mask_weight(M, cl); }, w,
+                       ch)) {
+          ++cnt.chords;
+          if (MODE == GF_TR_CLOSED_FORM) {
+            neumaier_add(s_acc, c_acc, w * chord_closed(F.wd, ch));
+          } else {
+            const float len = ch.dtout - ch.dtin;
+            int off;
+            gl_pick(gl_rule(sqrtf(ch.a) * len + 0.5f * fabsf(ch.B) * len), n, off);
+            CoopChord C;
+            C.mid = 0.5f * (ch.dtin + ch.dtout);
+            C.hl = 0.5f * len;
+            C.y2 = -0.5f * kLog2e * ch.a;
+            C.y1 = -kLog2e * ch.b;
+            C.y0 = -0.5f * kLog2e * ch.g;
+            C.scale = w * ch.absA * C.hl;
+            C.B = ch.B;
+            C.delta = ch.delta;
+            C.off = off;
+            Q.ch[lane] = C;
+          }
+        }
+      }
+      int incl = n;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, d);
+        if ((int)lane >= d) incl += y;
+      }
+      const int total = __shfl_sync(kFull, incl, 31);
+      Q.end[lane + 1] = incl;
+      if (lane == 0) Q.end[0] = 0;
+      __syncwarp();
+      for (int f = (int)lane; f < total; f += 32) {
+        int c = 0;  // the chord of node f: the largest c with end[c] <= f
+#pragma unroll
+        for (int w = 16; w > 0; w >>= 1)
+          if (Q.end[c + w] <= f) c += w;
+        const CoopChord& C = Q.ch[c];
+        const int k = C.off + (f - Q.end[c]);
+        const float dt = fmaf(C.hl, glx[k], C.mid);
+        const float y = fmaf(fmaf(C.y2, dt, C.y1), dt, C.y0);
+        neumaier_add(s_acc, c_acc, C.scale * glw[k] * ex2f(y) * cosf(fmaf(C.B, dt, C.delta)));
+        ++cnt.evals;
+      }
+      __syncwarp();
+    }
+    if (!more && lq_n == 0) break;
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kBlock, 3)
+    k_transmittance_coop(const __grid_constant__ DevField F, const TrParams P) {
+  __shared__ BlockTables sm;
+  __shared__ CoopQ qs[kBlock / 32];
+  init_tables(sm, F);
+  const uint32_t lane = threadIdx.x & 31u;
+  CoopQ& Q = qs[threadIdx.x >> 5];
+  Counters cnt;
+  const int spp = lod_is_deterministic(P.lod) ? 1 : P.spp;
+  for (;;) {
+    const int64_t r = next_tile(P.counter, lane);  // one ray per warp
+    if (r >= P.n) break;
+    const float3 o = make_float3(P.o[3 * r], P.o[3 * r + 1], P.o[3 * r + 2]);
+    const float3 v = unit_dir(make_float3(P.d[3 * r], P.d[3 * r + 1], P.d[3 * r + 2]));
+    const float tmin = P.trange ? P.trange[2 * r] : 0.f;
+    const float tmax = P.trange ? P.trange[2 * r + 1] : INFINITY;
+    const float3 inv = safe_inv(v);
+    float s_acc = 0.f, c_acc = 0.f;
+    for (int s = 0; s < spp; ++s) {
+      const Mask m = sample_mask(F, P.lod, v, P.seed, (uint32_t)r, (uint32_t)s, 0, TAG_MASK);
+      if (lane == 0) cnt.rays += 1;
+      float t0, t1;
+      if (m.bits == 0ull || !scene_span(F, o, inv, tmin, tmax, t0, t1)) continue;
+      if (lane == 0) cnt.windows += 1;
+      coop_tau<MODE>(F, Q, m, o, v, inv, tmin, tmax, t0, t1, sm.glx, sm.glw, lane, s_acc, c_acc,
+                     cnt);
+    }
+    // compensated sum over the warp's lanes (fixed butterfly order)
+    for (int off = 1; off < 32; off <<= 1) {
+      const float so = __shfl_xor_sync(kFull, s_acc, off), co = __shfl_xor_sync(kFull, c_acc, off);
+      float t, e;
+      two_sum(s_acc, so, t, e);
+      s_acc = t;
+      c_acc = __fadd_rn(__fadd_rn(c_acc, co), e);
+    }
+    if (lane == 0) {
+      const float tau = __fadd_rn(s_acc, c_acc) / (float)spp;
+      P.out_T[r] = expf(-tau);
+      if (P.out_tau) P.out_tau[r] = tau;
+    }
+  }
+  flush_counters(F, cnt, lane);
+}
+
+// ---------------------------------------------------------------------------
 // render: each lane owns one pixel of an 8x4 tile and runs its samples in
 // order (deterministic per pixel); FF: the free flight of scattering
 // (GF_FLIGHT_DELTA here means tomography: delta tracking renders in the
@@ -256,7 +463,16 @@ cudaError_t launch_transmittance(const Field& F, const TrParams& P, cudaStream_t
     Q.group = 1;
     while (Q.group < 32 && P.n * Q.group <= lanes) Q.group *= 2;
     const int64_t tiles_g = (P.n + 32 / Q.group - 1) / (32 / Q.group);
-    if (P.mode == GF_TR_DETERMINISTIC) {
+    if (Q.group >= 16) {
+      // few rays: the whole warp on each ray (k_transmittance_coop)
+      if (P.mode == GF_TR_DETERMINISTIC) {
+        auto k = k_transmittance_coop<GF_TR_DETERMINISTIC>;
+        k<<<persistent_grid(F, k, P.n), kBlock, 0, s>>>(F.dev, Q);
+      } else {
+        auto k = k_transmittance_coop<GF_TR_CLOSED_FORM>;
+        k<<<persistent_grid(F, k, P.n), kBlock, 0, s>>>(F.dev, Q);
+      }
+    } else if (P.mode == GF_TR_DETERMINISTIC) {
       auto k = k_transmittance<GF_TR_DETERMINISTIC>;
       k<<<persistent_grid(F, k, tiles_g), kBlock, 0, s>>>(F.dev, Q);
     } else {

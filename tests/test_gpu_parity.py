@@ -137,17 +137,22 @@ def test_deterministic_transmittance_absorption_64x64(api, ctx):
 
 
 def test_deterministic_transmittance_lane_groups_agree(api, ctx):
-    """Small batches integrate each ray with several lanes (each walking its own
-    subtree), large ones with one lane per ray: the same rays give the same
-    optical depth up to FP32 summation order, and match the oracle."""
+    """Large batches integrate each ray on one lane; mid-size ones on a group of
+    lanes, each walking its own subtree; small ones on a whole warp (one shared
+    traversal, the chords' quadrature nodes shared out over the lanes).  The
+    same rays give the same optical depth up to FP32 summation order in all
+    three, and match the oracle."""
     p = synth.octave_field(6000, 4, seed=5)
     f = api.Field(ctx, p)
     o, d, tr = synth.random_rays(200000, seed=9)
     _, tau_all = f.transmittance(_t(o), _t(d), _t(tr), mode="det")   # one lane per ray
-    _, tau_few = f.transmittance(_t(o[:500]), _t(d[:500]), _t(tr[:500]), mode="det")  # 32 lanes
+    _, tau_mid = f.transmittance(_t(o[:20000]), _t(d[:20000]), _t(tr[:20000]), mode="det")  # 4 lanes
+    _, tau_few = f.transmittance(_t(o[:500]), _t(d[:500]), _t(tr[:500]), mode="det")  # a warp
     f.sync()
     a, b = tau_all.cpu().numpy()[:500], tau_few.cpu().numpy()
     assert np.all(np.abs(a - b) <= 2e-6 * np.maximum(1.0, np.abs(a)))
+    am, m = tau_all.cpu().numpy()[:20000], tau_mid.cpu().numpy()
+    assert np.all(np.abs(am - m) <= 2e-6 * np.maximum(1.0, np.abs(am)))
     _, tau_ref = oracle.Field(p, omega_frame="local").transmittance(o[:64], d[:64], tr[:64], mode="det")
     _T_abs(np.exp(-b[:64].astype(np.float64)), np.exp(-tau_ref), "lane groups")
 
@@ -218,8 +223,9 @@ def test_closed_form_transmittance_matches_oracle(api, ctx, field):
 
 
 def test_closed_form_lane_groups_agree(api, ctx):
-    """Closed form with one lane per ray (large batch) and with 32 lanes walking
-    disjoint subtrees of each ray (small batch): equal up to FP32 summation order."""
+    """Closed form with one lane per ray (large batch) and with a whole warp per ray
+    (small batch: one shared traversal, each lane integrating its own chords):
+    equal up to FP32 summation order."""
     p = synth.octave_field(6000, 4, seed=5)
     f = api.Field(ctx, p)
     o, d, tr = synth.random_rays(200000, seed=9)
