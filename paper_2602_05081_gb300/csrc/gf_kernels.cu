@@ -116,22 +116,28 @@ __global__ void __launch_bounds__(kBlock, 3)  // at most 168 registers: 12 warps
 constexpr int kCoopStack = 512;   // node entries per warp
 constexpr int kCoopMargin = 128;  // a step pushes <= 64; depth first above kCoopStack - margin
 constexpr int kCoopLeafQ = 96;    // <= 31 left + 64 new
+struct CoopTrav {
+  int stk[kCoopStack];
+  int lq[kCoopLeafQ];
+};
 struct CoopChord {
   float mid, hl, y2, y1, y0, scale, B, delta;
   int off;  // first node of the chord's rule in the tables
 };
 struct CoopQ {
-  int stk[kCoopStack];
-  int lq[kCoopLeafQ];
+  CoopTrav t;
   CoopChord ch[32];  // the round's chords, one per lane
   int end[33];       // end[c]: nodes of chords 0..c-1
 };
 
-template <int MODE>  // GF_TR_DETERMINISTIC or GF_TR_CLOSED_FORM
-__device__ void coop_tau(const DevField& F, CoopQ& Q, const Mask& M, float3 o, float3 v,
-                         float3 inv, float tmin, float tmax, float t0, float t1, const float* glx,
-                         const float* glw, uint32_t lane, float& s_acc, float& c_acc,
-                         Counters& cnt) {
+// The tree of one ray, traversed by the whole warp: a shared stack of binary
+// nodes (up to 32 popped per step, their hit children pushed), the leaves
+// reached queued; every 32 queued leaves (and the last ones) make a round, in
+// which round(j) is called by every lane, j the sorted primitive of the lane's
+// leaf or -1.
+template <class Round>
+__device__ void coop_traverse(const DevField& F, CoopTrav& Q, const Mask& M, float3 o, float3 inv,
+                              float t0, float t1, uint32_t lane, Counters& cnt, Round&& round) {
   const unsigned lt = (1u << lane) - 1u;
   const SpanTest test{t0, t1};
   int sp = F.root >= 0 ? 1 : 0, lq_n = F.root >= 0 ? 0 : 1;
@@ -204,66 +210,80 @@ __device__ void coop_tau(const DevField& F, CoopQ& Q, const Mask& M, float3 o, f
     lq_n += nl;
     __syncwarp();
     const bool more = sp > 0;
-    // leaf rounds: 32 chords set up at once, then their nodes shared out
     while (lq_n >= 32 || (!more && lq_n > 0)) {
       const int tk = lq_n < 32 ? lq_n : 32;
       const int j = (int)lane < tk ? Q.lq[lq_n - tk + (int)lane] : -1;
       __syncwarp();
       lq_n -= tk;
-      int n = 0;
-      if (j >= 0) {
-        ++cnt.leaves;
-        Chord ch;
-        float w;
-        if (prim_chord(F, j, o, v, tmin, tmax, [&](uint32_t cl) { return mask_weight(M, cl); }, w,
-                       ch)) {
-          ++cnt.chords;
-          if (MODE == GF_TR_CLOSED_FORM) {
-            neumaier_add(s_acc, c_acc, w * chord_closed(F.wd, ch));
-          } else {
-            const float len = ch.dtout - ch.dtin;
-            int off;
-            gl_pick(gl_rule(sqrtf(ch.a) * len + 0.5f * fabsf(ch.B) * len), n, off);
-            CoopChord C;
-            C.mid = 0.5f * (ch.dtin + ch.dtout);
-            C.hl = 0.5f * len;
-            C.y2 = -0.5f * kLog2e * ch.a;
-            C.y1 = -kLog2e * ch.b;
-            C.y0 = -0.5f * kLog2e * ch.g;
-            C.scale = w * ch.absA * C.hl;
-            C.B = ch.B;
-            C.delta = ch.delta;
-            C.off = off;
-            Q.ch[lane] = C;
-          }
-        }
-      }
-      int incl = n;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const int y = __shfl_up_sync(kFull, incl, d);
-        if ((int)lane >= d) incl += y;
-      }
-      const int total = __shfl_sync(kFull, incl, 31);
-      Q.end[lane + 1] = incl;
-      if (lane == 0) Q.end[0] = 0;
-      __syncwarp();
-      for (int f = (int)lane; f < total; f += 32) {
-        int c = 0;  // the chord of node f: the largest c with end[c] <= f
-#pragma unroll
-        for (int w = 16; w > 0; w >>= 1)
-          if (Q.end[c + w] <= f) c += w;
-        const CoopChord& C = Q.ch[c];
-        const int k = C.off + (f - Q.end[c]);
-        const float dt = fmaf(C.hl, glx[k], C.mid);
-        const float y = fmaf(fmaf(C.y2, dt, C.y1), dt, C.y0);
-        neumaier_add(s_acc, c_acc, C.scale * glw[k] * ex2f(y) * cosf(fmaf(C.B, dt, C.delta)));
-        ++cnt.evals;
-      }
+      if (j >= 0) ++cnt.leaves;
+      round(j);
       __syncwarp();
     }
     if (!more && lq_n == 0) break;
   }
+}
+
+// inclusive prefix sum over the warp's lanes
+__device__ __forceinline__ int warp_incl_sum(int x, uint32_t lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(kFull, x, d);
+    if ((int)lane >= d) x += y;
+  }
+  return x;
+}
+
+template <int MODE>  // GF_TR_DETERMINISTIC or GF_TR_CLOSED_FORM
+__device__ void coop_tau(const DevField& F, CoopQ& Q, const Mask& M, float3 o, float3 v,
+                         float3 inv, float tmin, float tmax, float t0, float t1, const float* glx,
+                         const float* glw, uint32_t lane, float& s_acc, float& c_acc,
+                         Counters& cnt) {
+  coop_traverse(F, Q.t, M, o, inv, t0, t1, lane, cnt, [&](int j) {
+    // chords set up one per lane, then their nodes shared out
+    int n = 0;
+    Chord ch;
+    float w;
+    if (j >= 0 &&
+        prim_chord(F, j, o, v, tmin, tmax, [&](uint32_t cl) { return mask_weight(M, cl); }, w, ch)) {
+      ++cnt.chords;
+      if (MODE == GF_TR_CLOSED_FORM) {
+        neumaier_add(s_acc, c_acc, w * chord_closed(F.wd, ch));
+      } else {
+        const float len = ch.dtout - ch.dtin;
+        int off;
+        gl_pick(gl_rule(sqrtf(ch.a) * len + 0.5f * fabsf(ch.B) * len), n, off);
+        CoopChord C;
+        C.mid = 0.5f * (ch.dtin + ch.dtout);
+        C.hl = 0.5f * len;
+        C.y2 = -0.5f * kLog2e * ch.a;
+        C.y1 = -kLog2e * ch.b;
+        C.y0 = -0.5f * kLog2e * ch.g;
+        C.scale = w * ch.absA * C.hl;
+        C.B = ch.B;
+        C.delta = ch.delta;
+        C.off = off;
+        Q.ch[lane] = C;
+      }
+    }
+    if (MODE == GF_TR_CLOSED_FORM) return;
+    const int incl = warp_incl_sum(n, lane);
+    const int total = __shfl_sync(kFull, incl, 31);
+    Q.end[lane + 1] = incl;
+    if (lane == 0) Q.end[0] = 0;
+    __syncwarp();
+    for (int f = (int)lane; f < total; f += 32) {
+      int c = 0;  // the chord of node f: the largest c with end[c] <= f
+#pragma unroll
+      for (int wd = 16; wd > 0; wd >>= 1)
+        if (Q.end[c + wd] <= f) c += wd;
+      const CoopChord& C = Q.ch[c];
+      const int k = C.off + (f - Q.end[c]);
+      const float dt = fmaf(C.hl, glx[k], C.mid);
+      const float y = fmaf(fmaf(C.y2, dt, C.y1), dt, C.y0);
+      neumaier_add(s_acc, c_acc, C.scale * glw[k] * ex2f(y) * cosf(fmaf(C.B, dt, C.delta)));
+      ++cnt.evals;
+    }
+  });
 }
 
 template <int MODE>
@@ -307,6 +327,141 @@ __global__ void __launch_bounds__(kBlock, 3)
       P.out_T[r] = expf(-tau);
       if (P.out_tau) P.out_tau[r] = tau;
     }
+  }
+  flush_counters(F, cnt, lane);
+}
+
+// ---------------------------------------------------------------------------
+// Ratio tracking of small batches, one ray per warp.  The warp traverses the
+// ray's tree together; each round's chords (one per lane) store their
+// evaluation records in shared memory and draw all their tentative points in
+// [t0, t1] (chord_points: the per-chord streams of the per-thread tracker, so
+// the same points), written in lane order after a counting pass.  Then each
+// lane takes points i = lane, lane + 32, ..., sums kappa and kappa_bar at them
+// over all stored chords in order, and multiplies its factors 1 - kappa /
+// kappa_bar; the lanes' products are combined in a fixed butterfly order.  A
+// ray with more chords or points than the buffers hold is tracked by the
+// per-thread tracker instead (lane 0).
+// ---------------------------------------------------------------------------
+constexpr int kRtChords = 256;  // chords of one ray held in shared memory
+constexpr int kRtPts = 128;     // tentative points of one ray
+struct RtQ {
+  CoopTrav t;
+  float4 rec[kRtChords][2];  // centred on the envelope peak t*: (t*, t_in, t_out, B),
+                             // (-a log2(e) / 2, log2 h, phase at t*, sqrt(a))
+  float pt[kRtPts], pu[kRtPts];
+};
+
+__device__ float rt_coop(const DevField& F, RtQ& Q, const Mask& M, float3 o, float3 v, float3 inv,
+                         float tmin, float tmax, float t0, float t1, uint64_t seed, uint32_t ray,
+                         uint32_t word, const float* env, uint32_t lane, Counters& cnt) {
+  const unsigned lt = (1u << lane) - 1u;
+  int nch = 0, npts = 0;  // warp-uniform
+  coop_traverse(F, Q.t, M, o, inv, t0, t1, lane, cnt, [&](int j) {
+    Chord ch;
+    float w, h = 0.f;
+    bool ok = false;
+    if (j >= 0 &&
+        prim_chord(F, j, o, v, tmin, tmax, [&](uint32_t cl) { return mask_weight(M, cl); }, w, ch) &&
+        ch.tc + ch.dtin <= t1 && ch.tc + ch.dtout >= t0) {
+      ok = true;
+      h = w * ch.absA * expf(-0.5f * ch.qmin);
+    }
+    const unsigned bc = __ballot_sync(kFull, ok);
+    if (ok) {
+      ++cnt.chords;
+      const int k = nch + __popc(bc & lt);
+      if (k < kRtChords) {
+        Q.rec[k][0] = make_float4(ch.tc + ch.dts, ch.tc + ch.dtin, ch.tc + ch.dtout, ch.B);
+        Q.rec[k][1] = make_float4(-0.5f * kLog2e * ch.a, __log2f(h),
+                                  reduce_2pi(fmaf(ch.B, ch.dts, ch.delta)), sqrtf(ch.a));
+      }
+    }
+    nch += __popc(bc);
+    // the round's points in lane order: count, then write at the prefix offsets
+    int m = 0;
+    if (ok)
+      chord_points(F, ch, h, seed, ray, word, env, [&](float t, float) {
+        if (t > t1) return false;
+        if (t >= t0) ++m;
+        return true;
+      });
+    const int incl = warp_incl_sum(m, lane);
+    if (ok && m > 0) {
+      int q = npts + incl - m;
+      chord_points(F, ch, h, seed, ray, word, env, [&](float t, float u) {
+        if (t > t1) return false;
+        if (t >= t0) {
+          if (q < kRtPts) {
+            Q.pt[q] = t;
+            Q.pu[q] = u;
+          }
+          ++q;
+        }
+        return true;
+      });
+    }
+    npts += __shfl_sync(kFull, incl, 31);
+  });
+  if (lane == 0) cnt.points += (unsigned long long)npts;
+  __syncwarp();
+  if (nch > kRtChords || npts > kRtPts) {  // too many for the buffers: per-thread tracker
+    float T = 1.f;
+    if (lane == 0) T = track<false>(F, M, o, v, tmin, tmax, false, seed, ray, word, env, cnt, nullptr);
+    return __shfl_sync(kFull, T, 0);
+  }
+  float prod = 1.f;
+  for (int i = (int)lane; i < npts; i += 32) {
+    const float t = Q.pt[i];
+    float kap = 0.f, kb = 0.f;
+    for (int c = 0; c < nch; ++c) {
+      const float4 a = Q.rec[c][0];
+      if (t >= a.y && t <= a.z) {
+        const float4 b = Q.rec[c][1];
+        const float dt = t - a.x;
+        kap = fmaf(ex2f(fmaf(b.x, dt * dt, b.y)), cosf_fast(fmaf(a.w, dt, b.z)), kap);
+        int mm = (int)(fabsf(dt) * b.w);
+        mm = mm > 7 ? 7 : mm;
+        kb = fmaf(ex2f(b.y), env[mm], kb);  // h exp(-m^2/2)
+        ++cnt.evals;
+      }
+    }
+    if (kb > 0.f) prod *= 1.f - kap / kb;
+  }
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) prod *= __shfl_xor_sync(kFull, prod, off);
+  return prod;
+}
+
+__global__ void __launch_bounds__(kBlock, 3)
+    k_transmittance_rt_coop(const __grid_constant__ DevField F, const TrParams P) {
+  __shared__ BlockTables sm;
+  __shared__ RtQ qs[kBlock / 32];
+  init_tables(sm, F);
+  const uint32_t lane = threadIdx.x & 31u;
+  RtQ& Q = qs[threadIdx.x >> 5];
+  Counters cnt;
+  for (;;) {
+    const int64_t r = next_tile(P.counter, lane);  // one ray per warp
+    if (r >= P.n) break;
+    const float3 o = make_float3(P.o[3 * r], P.o[3 * r + 1], P.o[3 * r + 2]);
+    const float3 v = unit_dir(make_float3(P.d[3 * r], P.d[3 * r + 1], P.d[3 * r + 2]));
+    const float tmin = P.trange ? P.trange[2 * r] : 0.f;
+    const float tmax = P.trange ? P.trange[2 * r + 1] : INFINITY;
+    const float3 inv = safe_inv(v);
+    float acc = 0.f;
+    for (int s = 0; s < P.spp; ++s) {
+      const Mask m = sample_mask(F, P.lod, v, P.seed, (uint32_t)r, (uint32_t)s, 0, TAG_MASK);
+      if (lane == 0) cnt.rays += 1;
+      float t0, t1, T = 1.f;
+      if (m.bits != 0ull && scene_span(F, o, inv, tmin, tmax, t0, t1)) {
+        if (lane == 0) cnt.windows += 1;
+        T = rt_coop(F, Q, m, o, v, inv, tmin, tmax, t0, t1, P.seed, (uint32_t)r,
+                    stream_word((uint32_t)s, 0, TAG_TRACK), sm.env, lane, cnt);
+      }
+      acc += T;
+    }
+    if (lane == 0) P.out_T[r] = acc / (float)P.spp;
   }
   flush_counters(F, cnt, lane);
 }
@@ -479,6 +634,10 @@ cudaError_t launch_transmittance(const Field& F, const TrParams& P, cudaStream_t
       auto k = k_transmittance<GF_TR_CLOSED_FORM>;
       k<<<persistent_grid(F, k, tiles_g), kBlock, 0, s>>>(F.dev, Q);
     }
+  } else if (P.n * 8 <= (int64_t)F.ctx.sm_count * 16 * 32) {
+    // few rays: the whole warp on each ray (k_transmittance_rt_coop)
+    auto k = k_transmittance_rt_coop;
+    k<<<persistent_grid(F, k, P.n), kBlock, 0, s>>>(F.dev, P);
   } else {
     const int64_t tiles = (P.n + 31) / 32;
     auto k = k_transmittance<GF_TR_RATIO_TRACKING>;

@@ -654,6 +654,51 @@ struct PointBuf {
   float t[kPts], u[kPts];
 };
 
+// The tentative points of one chord under the per-segment majorant (Sec. 3;
+// R2/R3): rate h exp(-n^2/2) on the chord's whitened-distance pieces n, drawn
+// from the chord's own Philox stream from its entry on.  emit(t, u) receives
+// each point, in order along the chord, with its acceptance uniform, and
+// returns false to end the walk.
+template <class Emit>
+__device__ __forceinline__ void chord_points(const DevField& F, const Chord& ch, float h,
+                                             uint64_t seed, uint32_t ray, uint32_t word,
+                                             const float* env, Emit emit) {
+  const float sa = sqrtf(ch.a), invs = 1.0f / sa, dts = ch.dts, dtout = ch.dtout;
+  int J = (int)ceilf(sa * ch.hw) - 1;
+  J = J < 0 ? 0 : (J > 6 ? 6 : J);
+  float dt = ch.dtin;
+  int p = 0;
+  while (p < 2 * J) {
+    const float bp = p < J ? dts - (float)(J - p) * invs : dts + (float)(p - J + 1) * invs;
+    if (bp <= dt) ++p;
+    else break;
+  }
+  for (uint32_t draw = 0; draw < (1u << 16); ++draw) {
+    const uint4 x = rng4(seed, draw, ch.orig, ray, word);
+    float z = -__logf(1.0f - u01(x.x));
+    bool more = false;
+    for (int q = 0; q < 2 * J + 2; ++q) {
+      const float bp = p < J ? dts - (float)(J - p) * invs : dts + (float)(p - J + 1) * invs;
+      const float end = p < 2 * J ? fminf(bp, dtout) : dtout;
+      const int nn = p < J ? J - p : p - J;
+      const float lam = h * env[nn];
+      const float capz = lam * (end - dt);
+      if (z < capz) {
+        dt += z / lam;
+        more = true;
+        break;
+      }
+      z -= capz;
+      dt = end;
+      if (dt >= dtout) return;
+      ++p;
+    }
+    if (!more) return;
+    if (!emit(ch.tc + dt, u01(x.y))) return;
+  }
+  set_err(F, ERR_GUARD);
+}
+
 struct CollectLeaf {
   const DevField* F;
   const Mask* M;
@@ -687,44 +732,12 @@ struct CollectLeaf {
       return;
     if (!(ch.tc + ch.dtin <= bound && ch.tc + ch.dtout >= ta)) return;
     ++nch;
-    // piecewise rate h exp(-n^2/2) on whitened-distance pieces of the chord
     const float h = w * ch.absA * expf(-0.5f * ch.qmin);
-    const float sa = sqrtf(ch.a), invs = 1.0f / sa, dts = ch.dts, dtout = ch.dtout;
-    int J = (int)ceilf(sa * ch.hw) - 1;
-    J = J < 0 ? 0 : (J > 6 ? 6 : J);
-    float dt = ch.dtin;
-    int p = 0;
-    while (p < 2 * J) {
-      const float bp = p < J ? dts - (float)(J - p) * invs : dts + (float)(p - J + 1) * invs;
-      if (bp <= dt) ++p;
-      else break;
-    }
-    for (uint32_t draw = 0; draw < (1u << 16); ++draw) {
-      const uint4 x = rng4(seed, draw, ch.orig, ray, word);
-      float z = -__logf(1.0f - u01(x.x));
-      bool emit = false;
-      for (int q = 0; q < 2 * J + 2; ++q) {
-        const float bp = p < J ? dts - (float)(J - p) * invs : dts + (float)(p - J + 1) * invs;
-        const float end = p < 2 * J ? fminf(bp, dtout) : dtout;
-        const int nn = p < J ? J - p : p - J;
-        const float lam = h * env[nn];
-        const float capz = lam * (end - dt);
-        if (z < capz) {
-          dt += z / lam;
-          emit = true;
-          break;
-        }
-        z -= capz;
-        dt = end;
-        if (dt >= dtout) return;
-        ++p;
-      }
-      if (!emit) return;
-      const float t = ch.tc + dt;
-      if (t > bound) return;
-      if (first ? t >= ta : t > ta) insert(t, u01(x.y));
-    }
-    set_err(*F, ERR_GUARD);
+    chord_points(*F, ch, h, seed, ray, word, env, [&](float t, float u) {
+      if (t > bound) return false;
+      if (first ? t >= ta : t > ta) insert(t, u);
+      return true;
+    });
   }
 };
 
