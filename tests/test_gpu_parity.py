@@ -157,6 +157,59 @@ def test_deterministic_transmittance_lane_groups_agree(api, ctx):
     _T_abs(np.exp(-b[:64].astype(np.float64)), np.exp(-tau_ref), "lane groups")
 
 
+def test_transmittance_small_batches_deep_trees(api, ctx):
+    """A 200k-kernel field: rays whose frontiers are wide enough to push the
+    warp's shared stack past its breadth-first limit (it then steps depth first)
+    give the same optical depth in a small batch (one warp per ray) and in a
+    large one (one lane per ray), in both deterministic modes."""
+    p = synth.octave_field(200_000, 4, seed=3)
+    f = api.Field(ctx, p)
+    o, d, tr = synth.random_rays(100_000, seed=13)
+    for mode in ("det", "closed"):
+        _, tau_all = f.transmittance(_t(o), _t(d), _t(tr), mode=mode)
+        _, tau_few = f.transmittance(_t(o[:300]), _t(d[:300]), _t(tr[:300]), mode=mode)
+        f.sync()
+        a, b = tau_all.cpu().numpy()[:300], tau_few.cpu().numpy()
+        assert np.all(np.abs(a - b) <= 2e-6 * np.maximum(1.0, np.abs(a))), mode
+        assert np.abs(a).max() > 1.0
+
+
+def test_ratio_tracking_small_batches_and_overflow(api, ctx):
+    """Ratio tracking in a small batch (one warp per ray: every tentative point
+    of the ray at once) and in a large one (one lane per ray, windows of
+    points) samples the same points and gives the same estimate up to FP32
+    rounding (kappa at a point summed in another order and parametrisation).
+    On a dense positive field (the Gaussians of the same kernels at nine times
+    the weight: tau ~ 70, and on the rays crossing it most densely more
+    tentative points than the warp's buffers hold) the small batch falls back
+    to the per-lane tracker for those rays, bit for bit."""
+    p = synth.octave_field(6000, 4, seed=5)
+    o, d, tr = synth.random_rays(100_000, seed=17)
+    for scale, dense in ((1.0, False), (9.0, True)):
+        q = dict(p, weight=(p["weight"] * scale).astype(np.float32))
+        if dense:
+            q["omega"] = np.zeros_like(p["omega"])
+            q["phase"] = np.zeros_like(p["phase"])
+        f = api.Field(ctx, q, omega_frame="local")
+        T_all, _ = f.transmittance(_t(o), _t(d), _t(tr), mode="rt", spp=2, seed=3)
+        T_few, _ = f.transmittance(_t(o[:400]), _t(d[:400]), _t(tr[:400]), mode="rt", spp=2, seed=3)
+        f.sync()
+        a, b = T_all.cpu().numpy()[:400], T_few.cpu().numpy()
+        assert np.isfinite(a).all() and np.isfinite(b).all()
+        err = np.abs(a - b) / np.maximum(1.0, np.abs(a))
+        assert np.mean(err > 1e-4) <= 0.005, np.sort(err)[-5:]
+        assert np.median(err) <= 1e-6
+        if dense:
+            crossing = (a > 0.0) & (a < 1.0)
+            assert crossing.sum() > 100
+            # the per-lane tracker, for the rays it took over (the others agree to
+            # rounding, which two different summations practically never make exact)
+            assert np.sum(a[crossing] == b[crossing]) >= 5
+        else:
+            assert np.mean(a < 0.999) > 0.3  # the rays cross the field
+        f.free()
+
+
 def test_faddeeva_matches_library(api):
     """The Faddeeva function behind the closed-form chord integrals (Sec. 4.4
     complex error function) against scipy's FP64 wofz over the arguments the
