@@ -38,7 +38,6 @@ constexpr int kChordQ = 64;     // queued chords per warp (<= 31 left + 32 new)
 constexpr int kPK = 8;          // tentative points per lane and window
 constexpr int kSlotCh = 256;    // stored chords per lane and window (global scratch)
 constexpr int kRecF4 = 2;       // float4s per stored chord record
-constexpr int kLongList = 32;   // chords per slot (average) from which evaluation goes by slot
 
 // One slot per lane, 47 words: an odd stride keeps same-field accesses of the
 // 32 slots in distinct shared-memory banks.
@@ -424,8 +423,6 @@ __device__ __forceinline__ bool start_ray(const DevField& F, LaneRay& R, PathSta
 // stored.  The lanes share out the (slot, chord) pairs of all slots evenly, so
 // no lane waits on one slot's short list; each pair tests the chord against
 // the slot's points and adds its terms to the slot's sums in shared memory.
-// Windows with long lists go slot by slot instead (lanes over the slot's
-// chords, sums reduced over the warp); both give the same exact sums.
 // The sums are exact in 64-bit fixed point: a term is at most the peak h of
 // its chord, so with H the largest peak of the slot's window and at most
 // kSlotCh = 2^8 chords, scaling by 2^(54 - e) (H < 2^e) keeps every partial
@@ -458,54 +455,6 @@ __device__ void eval_stored(WarpQ& Q, const float4* wch, const float* env, uint3
     E.kb[i * 32 + lane] = 0ull;
   }
   __syncwarp();
-  if (total >= 32 * kLongList) {
-    // long lists (an average of kLongList chords or more per slot): the lanes
-    // go over one slot's chords at a time, coalesced, each summing all the
-    // slot's points in registers, and one reduction per point writes the sum
-    for (int s = 0; s < 32; ++s) {
-      const LaneRay& R = Q.r[s];
-      const int ns = R.npts;
-      if (ns <= 0) continue;  // the same slot for every lane
-      const int ex = slot_exp(R);
-      const float S = __int_as_float((127 + 54 - ex) << 23);  // 2^(54 - ex)
-      const float4* base = wch + (size_t)s * kSlotCh * kRecF4;
-      float pt[kPK];
-      long long kap[kPK], kb[kPK];
-#pragma unroll
-      for (int i = 0; i < kPK; ++i) {
-        pt[i] = i < ns ? R.pt[i] : INFINITY;
-        kap[i] = 0;
-        kb[i] = 0;
-      }
-      for (int c = (int)lane; c < R.nch; c += 32) {
-        const float4 a = base[kRecF4 * c], b = base[kRecF4 * c + 1];
-#pragma unroll
-        for (int i = 0; i < kPK; ++i) {
-          const float t = pt[i];
-          if (t >= a.y && t <= a.z) {
-            const float dt = t - a.x;
-            kap[i] += __float2ll_rn(ex2f(fmaf(b.x, dt * dt, b.y)) * cosf_fast(fmaf(a.w, dt, b.z)) * S);
-            int mm = (int)(fabsf(dt) * b.w);
-            mm = mm > 7 ? 7 : mm;
-            kb[i] += __float2ll_rn(ex2f(b.y + env[8 + mm]) * S);  // h exp(-m^2/2)
-            ++cnt.evals;
-          }
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < kPK; ++i) {
-        if (i < ns) {
-          const long long k1 = warp_sum_ll(kap[i]), k2 = warp_sum_ll(kb[i]);
-          if (lane == 0) {
-            E.kap[i * 32 + s] = (unsigned long long)k1;
-            E.kb[i * 32 + s] = (unsigned long long)k2;
-          }
-        }
-      }
-    }
-    __syncwarp();
-    return;
-  }
   // lane l takes the pairs [l per, (l + 1) per): a lane stays within one slot
   // for most of its pairs, and lanes of a long list sit in different slots at
   // any moment, so the atomics below rarely meet on one address.  Each pair's
