@@ -1,7 +1,8 @@
 // gf_kernels.cu -- render, transmittance and test kernels of the Gabor-field
 // renderer.  Persistent warps pull work tiles from a global counter: 32 rays,
-// or an 8x4 block of pixels, per warp; each lane owns one ray or pixel
-// (gf_trace.cuh).
+// or an 8x4 block of pixels, per warp, each lane owning one ray or pixel
+// (gf_trace.cuh); small transmittance batches take one ray per warp instead,
+// the whole warp traversing and integrating it together.
 #include <cuda_runtime.h>
 
 #include "gf_host.h"
